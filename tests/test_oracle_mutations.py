@@ -1,0 +1,68 @@
+"""The pins are not vacuous: plant a mistake in a copy of the oracle (on the
+CPU) and check that the pin aimed at it fails.
+
+Each entry replaces one line of the oracle's C source by a plausible slip
+(a flipped sign, a dropped term, a transposed index, a wrong constant) and
+names the pin tests that must catch it.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+T = "tests/test_oracle_pins.py::"
+
+MUTATIONS = {
+    "dissipation_sign": ("double dq = lam * (eps2 * D1 - eps4 * D3);",
+                         "double dq = lam * (eps2 * D1 + eps4 * D3);",
+                         ["test_fourth_difference_mode_decays"]),
+    "heat_flux_sign": ("double qx = -kap * gr[3][0]", "double qx = kap * gr[3][0]",
+                       ["test_heat_conduction_sign_and_rate"]),
+    "eta_metric_row": ("M[3 * N + nn] = J * (y_zeta * z_xi - y_xi * z_zeta);",
+                       "M[3 * N + nn] = J * (y_eta * z_xi - y_xi * z_eta);",
+                       ["test_metric_identity"]),
+    "stokes_two_thirds": ("double txx = mu * (2.0 * gr[0][0] - (2.0 / 3.0) * div);",
+                          "double txx = mu * (2.0 * gr[0][0] - (1.0 / 3.0) * div);",
+                          ["test_manufactured_solution_second_order"]),
+    "beta_transposed": ("double bx = txx * uf + txy * vf + txz * wf - qx;",
+                        "double bx = txx * uf + txy * wf + txz * vf - qx;",
+                        ["test_manufactured_solution_second_order"]),
+    "rk_alpha3": ("3.0 / 8.0, 1.0 / 2.0", "3.0 / 7.0, 1.0 / 2.0",
+                  ["test_rk5_amplification_polynomial"]),
+    "closure_sign": ("double Dm = (am >= 0) ? W_of(S, a, q) - W_of(S, am, q) : -D1;",
+                     "double Dm = (am >= 0) ? W_of(S, a, q) - W_of(S, am, q) : D1;",
+                     ["test_fourth_difference_boundary_closure"]),
+    "lbar_ratio": ("S->lbar[1][n] = l[1] * (1.0 + sqrt(l[0] / l[1]) + sqrt(l[2] / l[1]));",
+                   "S->lbar[1][n] = l[1] * (1.0 + sqrt(l[0] / l[1]) + sqrt(l[1] / l[2]));",
+                   ["test_fourth_difference_mode_decays"]),
+    "tangential_sum": ("dphi[q][t] = 0.25 * ((phi[q][ap] - phi[q][amt]) +",
+                       "dphi[q][t] = 0.25 * ((phi[q][ap] - phi[q][amt]) -",
+                       ["test_manufactured_solution_second_order"]),
+    "riemann_plus": ("double Rp = qne + 2.0 * a_e / gm1;", "double Rp = qne - 2.0 * a_e / gm1;",
+                     ["test_far_field_keeps_free_stream"]),
+    "energy_flux_p": ("F[4] = Jinv * ((S->Q[4 * N + n] + p) * Th);",
+                      "F[4] = Jinv * ((S->Q[4 * N + n]) * Th);",
+                      ["test_one_dimensional_jst_reduction"]),
+    "face_sensor": ("return fabs(pp - 2.0 * p0 + pm) / (pp + 2.0 * p0 + pm);\n  }",
+                    "return fabs(pp - 2.0 * p0 + pm) / (pp + p0 + pm);\n  }",
+                    ["test_one_dimensional_jst_reduction"]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new, targets = MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "les_oracle.c")).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} vanished"
+    for d in ("oracle", "tests", "paper_2301_00817_gb300"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("*.so", "__pycache__", "csrc"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
+    (tmp_path / "oracle" / "les_oracle.c").write_text(src.replace(old, new, 1))
+    ids = [T + t for t in targets]
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", *ids],
+                       cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and "failed" in r.stdout, r.stdout[-2000:]

@@ -1,0 +1,648 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms of linearised/1-D special cases, discrete
+invariants (metric identity, free-stream preservation, telescoping
+conservation), the RK amplification polynomial, locality of the stencil, and
+the boundary-condition invariants.  A dropped term, a wrong sign or a
+transposed index anywhere in the residual breaks at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2301_00817_gb300 import synth
+
+GAMMA = 1.4
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ------------------------------------------------------------------ Philox
+
+def test_philox_known_answers(orc):
+    """Philox4x32-10 against the published known-answer vectors."""
+    path = os.path.join(HERE, "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        vals = [int(x, 16) for x in r]
+        assert orc.philox4x32_10(vals[0:4], vals[4:6]) == tuple(vals[6:10])
+
+
+def test_box_muller_normals_are_standard(orc):
+    """Box-Muller over Philox gives N(0,1): moments and a KS test."""
+    stats = pytest.importorskip("scipy.stats")
+    z = np.array([orc.normals3(7, n) for n in range(40000)]).reshape(-1)
+    assert abs(z.mean()) < 0.02 and abs(z.var() - 1.0) < 0.03
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # distinct nodes and distinct seeds decorrelate
+    a = np.array([orc.normals3(1, n) for n in range(4000)])
+    b = np.array([orc.normals3(2, n) for n in range(4000)])
+    assert abs(np.corrcoef(a[:, 0], b[:, 0])[0, 1]) < 0.06
+    assert abs(np.corrcoef(a[:, 0], a[:, 2])[0, 1]) < 0.06
+
+
+# ----------------------------------------------------------------- metrics
+
+def _coord_jacobian(xyz, periodic, shift):
+    """X[c, d] = d x_c / d xi_d by numpy finite differences (central; one-sided
+    second order at non-periodic faces; periodic wrap with the period shift)."""
+    X = np.empty((3, 3) + xyz.shape[1:])
+    sh = np.asarray(shift).reshape(3, 3)
+    for c in range(3):
+        for d in range(3):
+            f = xyz[c]
+            if periodic[d]:
+                fp = np.roll(f, -1, axis=d)
+                fm = np.roll(f, 1, axis=d)
+                idx_last = [slice(None)] * 3
+                idx_last[d] = -1
+                idx_first = [slice(None)] * 3
+                idx_first[d] = 0
+                fp[tuple(idx_last)] += sh[d, c]
+                fm[tuple(idx_first)] -= sh[d, c]
+                X[c, d] = 0.5 * (fp - fm)
+            else:
+                X[c, d] = np.gradient(f, axis=d, edge_order=2)
+    return X
+
+
+@pytest.mark.parametrize("case", ["jet", "wavy_box"])
+def test_metric_identity(orc, case):
+    """Reading A1: the nine metrics are the inverse of d(x,y,z)/d(xi,eta,zeta)
+    at every node and J^-1 is its determinant (a wrong eta row fails)."""
+    if case == "jet":
+        xyz, per, shift = synth.jet_grid(20, 12, 16), (0, 0, 1), np.zeros(9)
+    else:
+        xyz, shift = synth.box_grid((10, 9, 8), (1.0, 1.3, 0.7), wave=0.3)
+        per = (1, 1, 1)
+    M = orc.metrics(xyz, per, shift)
+    X = _coord_jacobian(xyz, per, shift)
+    Mm = M[:9].reshape((3, 3) + xyz.shape[1:])  # Mm[d, c] = d xi_d / d x_c
+    ident = np.einsum("dc...,ce...->de...", Mm, X)
+    assert np.abs(ident - np.eye(3)[:, :, None, None, None]).max() < 1e-12
+    det = np.linalg.det(np.moveaxis(X, (0, 1), (-2, -1)))
+    assert np.allclose(det, M[9], rtol=1e-13, atol=0)
+    assert (M[9] > 0).all()
+
+
+# --------------------------------------------------------- jet grid and IC
+
+def test_jet_grid_recipe():
+    x, r, th = synth.jet_lines(48, 24, 32)
+    assert x[0] == 0.0 and abs(x[-1] - 20.0) < 1e-12
+    assert np.allclose(np.diff(x)[1:] / np.diff(x)[:-1], 1.01, rtol=1e-12)
+    assert abs(r[0] - 0.02) < 1e-14 and abs(r[-1] - 10.0) < 1e-12
+    dr = np.diff(r)
+    assert (dr > 0).all()
+    rmid = 0.5 * (r[1:] + r[:-1])
+    assert abs(rmid[np.argmin(dr)] - 0.5) < 0.1
+    assert np.allclose(np.diff(th), 2 * math.pi / 32)
+
+
+def test_jet_initial_condition_profile(orc):
+    """Noise-free IC is the tanh profile with rho = 1, p = 1/gamma; the noise
+    is noise*U_j times the node's three normals."""
+    P = orc.params()
+    xyz = synth.jet_grid(8, 10, 8)
+    Q = orc.init_jet(P, xyz, seed=3, noise=0.0)
+    r = np.sqrt(xyz[1] ** 2 + xyz[2] ** 2)
+    u = 0.7 * (1.0 + np.tanh((0.5 - r) / 0.1))
+    assert np.allclose(Q[0], 1.0, rtol=0, atol=0)
+    assert np.allclose(Q[1], u, rtol=1e-15, atol=1e-15)
+    assert np.abs(Q[2:4]).max() == 0.0
+    assert np.allclose(Q[4], 1.0 / (GAMMA * 0.4) + 0.5 * u * u, rtol=1e-15)
+    Qn = orc.init_jet(P, xyz, seed=3, noise=1e-3)
+    z = np.array([orc.normals3(3, n) for n in range(xyz[0].size)]).T.reshape((3,) + xyz.shape[1:])
+    assert np.allclose(Qn[2], 1e-3 * 1.4 * z[1], rtol=1e-14, atol=1e-15)
+    assert np.allclose(Qn[1], u + 1e-3 * 1.4 * z[0], rtol=1e-14, atol=1e-15)
+
+
+# ------------------------------------------------- free stream / conservation
+
+@pytest.mark.parametrize("sgs", [0, 1, 2])
+def test_free_stream_preservation_jet_grid(orc, sgs):
+    """A uniform state on the curvilinear jet grid has zero residual to
+    round-off (Reading A9 makes the dissipation vanish exactly)."""
+    P = orc.params(sgs_model=sgs)
+    xyz = synth.jet_grid(24, 16, 16)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Q = orc.prim_to_cons(P, synth.uniform_prim(xyz.shape[1:], u=0.9, v=-0.3, w=0.2))
+    R = orc.rhs(P, Q, M)
+    # flux scale: J^-1 |grad xi| (rho|u|^2 + p)
+    scale = np.abs(M[9]).max() * 10.0
+    assert np.abs(R).max() / scale < 1e-13
+
+
+@pytest.mark.parametrize("wave", [0.0, 0.25])
+@pytest.mark.parametrize("sgs", [1, 2])
+def test_discrete_conservation_periodic_box(orc, wave, sgs):
+    """Interface fluxes telescope: sum J^-1 Q is constant in a periodic box."""
+    P = orc.params(periodic=(1, 1, 1), bc=0, sgs_model=sgs, Re=200.0, cfl=0.8)
+    L = (1.0, 1.2, 0.9)
+    xyz, shift = synth.box_grid((12, 10, 9), L, wave=wave)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    Q = orc.prim_to_cons(P, synth.smooth_periodic_prim(xyz, L, amp=0.2, seed=4))
+    tot0 = orc.totals(Q, M)
+    Qn, t = orc.run(P, Q, M, xyz, 20)
+    tot1 = orc.totals(Qn, M)
+    assert t > 0 and np.isfinite(Qn).all()
+    assert np.abs(Qn - Q).max() > 1e-3  # the state really evolved
+    scale = np.abs(orc.totals(np.abs(Q), M)).max()
+    assert np.abs(tot1 - tot0).max() / scale < 1e-13
+
+
+# ------------------------------------------------- manufactured solution
+
+def _mms_exact_divergence(Re, Mj=1.4, Pr=0.72, Tref=288.15):
+    """Exact d/dx_j (F_inviscid_j - F_viscous_j) of the continuous System I
+    equations (Eq. modified_system_I with sigma = 0) for analytic periodic
+    fields, by symbolic differentiation."""
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z", real=True)
+    tp = 2 * sp.pi
+    rho = 1 + sp.Rational(1, 10) * sp.sin(tp * x) * sp.cos(tp * y) + sp.Rational(1, 20) * sp.sin(tp * z)
+    u = sp.Rational(3, 10) + sp.Rational(1, 10) * sp.cos(tp * (x + z))
+    v = -sp.Rational(1, 5) + sp.Rational(1, 10) * sp.sin(tp * y) * sp.cos(tp * z)
+    w = sp.Rational(1, 10) + sp.Rational(1, 10) * sp.sin(tp * (x - y))
+    p = sp.Rational(5, 7) * (1 + sp.Rational(1, 10) * sp.cos(tp * x) * sp.sin(tp * y + tp * z))
+    g = sp.Rational(7, 5)
+    X = (x, y, z)
+    U = (u, v, w)
+    e = p / (g - 1) + rho * (u * u + v * v + w * w) / 2
+    T = g * p / rho
+    S = sp.Float(110.4) / sp.Float(Tref)
+    mu = (sp.Float(Mj) / sp.Float(Re)) * T ** sp.Rational(3, 2) * (1 + S) / (T + S)
+    kap = mu / ((g - 1) * sp.Float(Pr))
+    grad = [[sp.diff(U[i], X[j]) for j in range(3)] for i in range(3)]
+    div = grad[0][0] + grad[1][1] + grad[2][2]
+    tau = [[mu * (grad[i][j] + grad[j][i]) - (2 * mu / 3) * div * (1 if i == j else 0)
+            for j in range(3)] for i in range(3)]
+    q = [-kap * sp.diff(T, X[j]) for j in range(3)]
+    res = []
+    res.append(sum(sp.diff(rho * U[j], X[j]) for j in range(3)))
+    for i in range(3):
+        res.append(sum(sp.diff(rho * U[i] * U[j] + (p if i == j else 0) - tau[i][j], X[j])
+                       for j in range(3)))
+    res.append(sum(sp.diff((e + p) * U[j] - sum(tau[i][j] * U[i] for i in range(3)) + q[j], X[j])
+                   for j in range(3)))
+    visc = []
+    for i in range(3):
+        visc.append(sum(sp.diff(-tau[i][j], X[j]) for j in range(3)))
+    visc.append(sum(sp.diff(-sum(tau[i][j] * U[i] for i in range(3)) + q[j], X[j]) for j in range(3)))
+    f_prim = sp.lambdify((x, y, z), [rho, u, v, w, p], "numpy")
+    f_res = sp.lambdify((x, y, z), res, "numpy")
+    f_visc = sp.lambdify((x, y, z), visc, "numpy")
+    return f_prim, f_res, f_visc
+
+
+def test_manufactured_solution_second_order(orc):
+    """J * RHS converges at second order to the exact flux divergence of the
+    paper's continuous equations on a non-separable periodic curvilinear grid
+    (viscous terms made O(1) with a low Reynolds number)."""
+    Re = 20.0
+    f_prim, f_res, f_visc = _mms_exact_divergence(Re)
+    P = orc.params(periodic=(1, 1, 1), bc=0, Re=Re, sgs_model=0)
+    errs, vmag = [], None
+    for n in (12, 24, 48):
+        xyz, shift = synth.box_grid((n, n, n), (1.0, 1.0, 1.0), wave=0.2)
+        M = orc.metrics(xyz, (1, 1, 1), shift)
+        prim = np.array([np.broadcast_to(f, xyz.shape[1:]) for f in f_prim(*xyz)])
+        Q = orc.prim_to_cons(P, prim)
+        R = orc.rhs(P, Q, M)
+        JR = R / M[9]
+        exact = np.array([np.broadcast_to(f, xyz.shape[1:]) for f in f_res(*xyz)])
+        errs.append(np.abs(JR - exact).max())
+        vmag = np.abs(np.array([np.broadcast_to(f, xyz.shape[1:]) for f in f_visc(*xyz)])).max()
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.4 < r1 < 4.8 and 3.6 < r2 < 4.5, errs
+    # the finest error is far below the viscous contribution itself, so a sign
+    # or factor error in the viscous fluxes could not hide in the tolerance
+    assert errs[2] < 0.05 * vmag, (errs, vmag)
+
+
+# ------------------------------------------------------- 1-D special cases
+
+def _cartesian_box(n, h):
+    L = tuple(m * h for m in n)
+    return synth.box_grid(n, L, wave=0.0)
+
+
+@pytest.mark.parametrize("periodic_x", [1, 0])
+def test_one_dimensional_jst_reduction(orc, periodic_x):
+    """Uniform Cartesian grid, inviscid, variation along x only: the residual
+    equals the textbook 1-D central flux plus JST/Turkel-Vatsa dissipation
+    with the sensor normalised by the pressure sum.  On a non-periodic line
+    the faces use the paper's closure (DW)_{1/2} = -(DW)_{1+1/2} and the face
+    sensor copies its neighbour."""
+    n, h = (10, 5, 5), 0.1
+    xyz, shift = _cartesian_box(n, h)
+    per = (periodic_x, 1, 1)
+    P = orc.params(periodic=per, bc=0, Re=0.0, sgs_model=0, k2=0.25, k4=0.016)
+    M = orc.metrics(xyz, per, shift)
+    xs = xyz[0][:, 0, 0]
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * xs / 0.8)
+    u = 0.5 + 0.3 * np.cos(2 * np.pi * xs / 0.8)
+    p = (1.0 / GAMMA) * (1.0 + 0.4 * (xs > 0.35) + 0.3 * (xs < 0.15))
+    prim = np.zeros((5,) + n)
+    prim[0] = rho[:, None, None]
+    prim[1] = u[:, None, None]
+    prim[4] = p[:, None, None]
+    Q = orc.prim_to_cons(P, prim)
+    R = orc.rhs(P, Q, M)
+    # textbook 1-D JST on the line, fluxes per unit area h^2
+    E = p / (GAMMA - 1) + 0.5 * rho * u * u
+    f = np.array([rho * u, rho * u * u + p, 0 * u, 0 * u, (E + p) * u])
+    Wv = np.array([rho, rho * u, 0 * u, 0 * u, E + p])
+    a = np.sqrt(GAMMA * p / rho)
+    lx, ly = (np.abs(u) + a) / h, a / h
+    lbar = lx * (1 + 2 * np.sqrt(ly / lx))
+    m = n[0]
+    nu = np.empty(m)
+    for i in range(m):
+        c = i
+        if not periodic_x:
+            c = min(max(i, 1), m - 2)  # face sensor = neighbour's sensor
+        pp, p0, pm = p[(c + 1) % m], p[c], p[(c - 1) % m]
+        nu[i] = abs(pp - 2 * p0 + pm) / (pp + 2 * p0 + pm)
+    nint = m if periodic_x else m - 1
+    Fh = np.zeros((5, nint))
+    for i in range(nint):
+        b = (i + 1) % m
+        D1 = Wv[:, b] - Wv[:, i]
+        if periodic_x or i > 0:
+            Dm = Wv[:, i] - Wv[:, (i - 1) % m]
+        else:
+            Dm = -D1
+        if periodic_x or i < m - 2:
+            Dp = Wv[:, (i + 2) % m] - Wv[:, b]
+        else:
+            Dp = -D1
+        e2 = 0.25 * max(nu[i], nu[b])
+        e4 = max(0.0, 0.016 - e2)
+        lam = 0.5 * (lbar[i] + lbar[b])
+        Fh[:, i] = h * h * 0.5 * (f[:, i] + f[:, b]) - h ** 3 * lam * (e2 * D1 - e4 * (Dp - 2 * D1 + Dm))
+    expect = np.zeros((5, m))
+    for i in range(m):
+        if periodic_x:
+            expect[:, i] = Fh[:, i] - Fh[:, (i - 1) % m]
+        elif 0 < i < m - 1:
+            expect[:, i] = Fh[:, i] - Fh[:, i - 1]
+    for c in range(5):
+        assert np.allclose(R[c], expect[c][:, None, None], rtol=0, atol=1e-14 * np.abs(Fh).max())
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_fourth_difference_mode_decays(orc, d):
+    """Reading A8/A10: at rest with uniform p (eps2 = 0) a density wave along
+    direction d on anisotropic cells is damped by the fourth difference:
+    J RHS_rho = 16 lbar_d k4 sin^4(k h_d/2) rho', with
+    lbar_d = (a/h_d)[1 + sum over the other two e of (h_d/h_e)^0.5]."""
+    n = [5, 5, 5]
+    n[d] = 16
+    n = tuple(n)
+    hs = (0.05, 0.08, 0.03)
+    eps = 1e-8
+    xyz, shift = synth.box_grid(n, tuple(m * h for m, h in zip(n, hs)))
+    P = orc.params(periodic=(1, 1, 1), bc=0, Re=0.0, sgs_model=0)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    xs = xyz[d]
+    kw = 2 * np.pi * 3 / (n[d] * hs[d])
+    prim = synth.uniform_prim(n)
+    prim[0] = 1.0 + eps * np.sin(kw * xs)
+    Q = orc.prim_to_cons(P, prim)
+    JR = orc.rhs(P, Q, M)[0] / M[9]
+    h = hs[d]
+    lbar = (1.0 / h) * (1.0 + sum(math.sqrt(h / hs[e]) for e in range(3) if e != d))
+    expect = 16 * lbar * 0.016 * np.sin(kw * h / 2) ** 4 * (eps * np.sin(kw * xs))
+    assert np.allclose(JR, expect, rtol=0, atol=1e-5 * np.abs(expect).max())
+    assert np.sum(JR * (prim[0] - 1.0)) > 0  # d rho/dt = -J RHS opposes the mode
+
+
+def test_fourth_difference_boundary_closure(orc):
+    """Sec. "Centerline Boundary Condition": with (DW)_{1/2} = -(DW)_{1+1/2}
+    the first interface's fourth difference is DW_{3/2} - 3 DW_{1/2}.  A
+    linear density ramp (slope c per node) at rest is annihilated by the
+    interior fourth difference; the closure leaves J RHS_rho = +2 lbar k4 c
+    at the node next to the low face and -2 lbar k4 c next to the high face."""
+    n, h, c = (10, 5, 5), 0.05, 1e-9
+    L = (n[0] * h, n[1] * h, n[2] * h)
+    xyz, shift = synth.box_grid(n, L)
+    P = orc.params(periodic=(0, 1, 1), bc=0, Re=0.0, sgs_model=0)
+    M = orc.metrics(xyz, (0, 1, 1), shift)
+    prim = synth.uniform_prim(n)
+    prim[0] = 1.0 + c * np.arange(n[0])[:, None, None]
+    Q = orc.prim_to_cons(P, prim)
+    JR = orc.rhs(P, Q, M)[0] / M[9]
+    lbar = 3.0 / h
+    expect = np.zeros(n)
+    expect[1] = 2 * lbar * 0.016 * c
+    expect[-2] = -2 * lbar * 0.016 * c
+    expect[0] = expect[-1] = 0.0
+    assert np.allclose(JR, expect, rtol=0, atol=1e-6 * 2 * lbar * 0.016 * c)
+
+
+def test_viscous_shear_wave_rate(orc):
+    """Reading A4/A11: a shear wave u(y) at uniform rho, p decays by the
+    compact viscous second difference with mu = M_j/Re (T = 1)."""
+    n, h, eps = (5, 16, 5), 0.05, 1e-6
+    xyz, shift = _cartesian_box(n, h)
+    Re = 100.0
+    P = orc.params(periodic=(1, 1, 1), bc=0, Re=Re, sgs_model=0, k2=0.0, k4=0.0)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    ys = xyz[1]
+    kw = 2 * np.pi * 2 / (n[1] * h)
+    prim = synth.uniform_prim(n)
+    prim[1] = eps * np.sin(kw * ys)
+    Q = orc.prim_to_cons(P, prim)
+    JR = orc.rhs(P, Q, M) / M[9]
+    mu = 1.4 / Re
+    expect = mu * 4 * np.sin(kw * h / 2) ** 2 / h ** 2 * eps * np.sin(kw * ys)
+    assert np.allclose(JR[1], expect, rtol=0, atol=1e-8 * np.abs(expect).max())
+    assert np.abs(JR[0]).max() < 1e-14 and np.abs(JR[2:4]).max() < 1e-14
+
+
+def test_heat_conduction_sign_and_rate(orc):
+    """Reading A2: at rest with uniform p, a temperature wave in the energy
+    equation obeys J RHS_e = kappa 4 sin^2(kh/2)/h^2 T' (heat flows from hot
+    to cold), kappa = (M_j/Re)/((gamma-1) Pr)."""
+    n, h, eps = (16, 5, 5), 0.05, 1e-7
+    xyz, shift = _cartesian_box(n, h)
+    Re = 100.0
+    P = orc.params(periodic=(1, 1, 1), bc=0, Re=Re, sgs_model=0, k2=0.0, k4=0.0)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    xs = xyz[0]
+    kw = 2 * np.pi * 3 / (n[0] * h)
+    Tp = eps * np.cos(kw * xs)
+    prim = synth.uniform_prim(n)
+    prim[0] = 1.0 / (1.0 + Tp)  # T = gamma p / rho = 1 + T'
+    Q = orc.prim_to_cons(P, prim)
+    JR = orc.rhs(P, Q, M) / M[9]
+    kap = (1.4 / Re) / (0.4 * 0.72)
+    expect = kap * 4 * np.sin(kw * h / 2) ** 2 / h ** 2 * Tp
+    assert np.allclose(JR[4], expect, rtol=0, atol=1e-5 * np.abs(expect).max())
+
+
+# -------------------------------------------------------------- SGS / mu
+
+def _linear_velocity_box(orc, grad, sgs, n=(7, 7, 7), h=0.1):
+    xyz = _cartesian_box(n, h)[0]
+    P = orc.params(periodic=(0, 0, 0), bc=0, sgs_model=sgs, Re=1e4)
+    M = orc.metrics(xyz, (0, 0, 0), np.zeros(9))
+    prim = synth.uniform_prim(n)
+    for i in range(3):
+        prim[1 + i] = sum(grad[i][j] * xyz[j] for j in range(3))
+    Q = orc.prim_to_cons(P, prim)
+    MK = orc.mu_eff(P, Q, M)
+    mu_l = (1.4 / 1e4) * 1.0
+    return MK, mu_l, h
+
+
+def test_sgs_closed_forms(orc):
+    """Smagorinsky and Vreman on linear velocity fields (exact gradients)."""
+    Cs = 0.148
+    s = 0.7
+    shear = [[0, s, 0], [0, 0, 0], [0, 0, 0]]  # u = s y
+    MK, mu_l, h = _linear_velocity_box(orc, shear, 1)
+    T = np.ones_like(MK[0])
+    assert np.allclose(MK[0], mu_l * T + (Cs * h) ** 2 * s, rtol=1e-12)
+    MK, mu_l, h = _linear_velocity_box(orc, shear, 2)
+    assert np.allclose(MK[0], mu_l, rtol=1e-12)  # Vreman vanishes for pure shear
+    rot = [[0, -0.5, 0], [0.5, 0, 0], [0, 0, 0]]
+    MK, mu_l, h = _linear_velocity_box(orc, rot, 1)
+    assert np.allclose(MK[0], mu_l, rtol=1e-12)  # no strain in solid rotation
+    rng = np.random.default_rng(5)
+    G = rng.normal(size=(3, 3))
+    MK, mu_l, h = _linear_velocity_box(orc, G, 2)
+    alpha = G.T  # alpha_ij = d u_j / d x_i
+    beta = h * h * alpha.T @ alpha
+    Bb = 0.5 * (np.trace(beta) ** 2 - np.trace(beta @ beta))  # 2nd invariant
+    mu_v = 2.5 * Cs * Cs * np.sqrt(Bb / np.sum(alpha * alpha))
+    assert np.allclose(MK[0], mu_l + mu_v, rtol=1e-12)
+    # kappa split with the two Prandtl numbers
+    assert np.allclose(MK[1], mu_l / (0.4 * 0.72) + mu_v / (0.4 * 0.9), rtol=1e-12)
+
+
+def test_sutherland_law(orc):
+    n = (5, 5, 5)
+    xyz = _cartesian_box(n, 0.1)[0]
+    P = orc.params(periodic=(1, 1, 1), bc=0, Re=1e5, sgs_model=0)
+    xyz, shift = _cartesian_box(n, 0.1)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    prim = synth.uniform_prim(n, rho=0.5)  # T = gamma p / rho = 2
+    MK = orc.mu_eff(P, orc.prim_to_cons(P, prim), M)
+    S = 110.4 / 288.15
+    assert np.allclose(MK[0], 1.4e-5 * 2 ** 1.5 * (1 + S) / (2 + S), rtol=1e-14)
+
+
+# --------------------------------------------------------------- locality
+
+def test_stencil_locality(orc):
+    """Perturbing one node changes the residual exactly on the stencil:
+    +-1, +-2 along each axis, +-1 in two axes (cross derivatives), itself."""
+    n = (9, 9, 9)
+    xyz, shift = synth.box_grid(n, (1.0, 1.0, 1.0), wave=0.2)
+    P = orc.params(periodic=(1, 1, 1), bc=0, Re=50.0, sgs_model=2)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    Q = orc.prim_to_cons(P, synth.smooth_periodic_prim(xyz, amp=0.2, seed=1))
+    MK = orc.mu_eff(P, Q, M)
+    R0 = orc.rhs(P, Q, M, MK)
+    Qp = Q.copy()
+    Qp[1, 4, 4, 4] += 1e-3  # changes u, T (viscous) and W, p (inviscid)
+    Qp[4, 4, 4, 4] += 1e-3
+    R1 = orc.rhs(P, Qp, M, MK)  # viscosity frozen, as within the stages
+    changed = set(map(tuple, np.argwhere(np.abs(R1 - R0).max(axis=0) > 0)))
+    expect = set()
+    for di in range(-2, 3):
+        for dj in range(-2, 3):
+            for dk in range(-2, 3):
+                nz = [abs(x) for x in (di, dj, dk) if x != 0]
+                if len(nz) <= 1 or (len(nz) == 2 and max(nz) == 1):
+                    expect.add((4 + di, 4 + dj, 4 + dk))
+    assert changed == expect
+
+
+# ----------------------------------------------------------------- RK5
+
+def test_rk5_amplification_polynomial(orc):
+    """Eq. localdt with alpha = 1/4,1/6,3/8,1/2,1 on y' = z y gives
+    G(z) = 1 + z + z^2/2 + 3 z^3/16 + z^4/32 + z^5/128 (second order)."""
+    zs = np.array([-0.3, -1.7, 0.5, -2.5])
+    y0 = np.ones((1, zs.size))
+
+    def rhs_fn(q):
+        return -zs[None, :] * q  # RHS = -dQ/dt
+
+    y1 = orc.rk5(y0, rhs_fn, 1.0)[0]
+    G = 1 + zs + zs ** 2 / 2 + 3 * zs ** 3 / 16 + zs ** 4 / 32 + zs ** 5 / 128
+    assert np.allclose(y1, G, rtol=1e-15, atol=1e-15)
+    # temporal order two: error of y' = -y ratio ~ 4 when dt halves
+    errs = []
+    for nstep in (10, 20, 40):
+        y = np.ones((1, 1))
+        for _ in range(nstep):
+            y = orc.rk5(y, lambda q: q, 1.0 / nstep)
+        errs.append(abs(y[0, 0] - math.exp(-1.0)))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_rk5_linear_stability_bound():
+    """The paper states linear stability up to CFL 2 sqrt(2): |G(iy)| <= 1 on
+    the imaginary axis for |y| <= 2 sqrt(2) (and up to ~4)."""
+    y = np.linspace(0.0, 2.0 * math.sqrt(2.0), 400)
+    z = 1j * y
+    G = 1 + z + z ** 2 / 2 + 3 * z ** 3 / 16 + z ** 4 / 32 + z ** 5 / 128
+    assert (np.abs(G) <= 1.0 + 1e-12).all()
+    z = 1j * 4.2
+    assert abs(1 + z + z ** 2 / 2 + 3 * z ** 3 / 16 + z ** 4 / 32 + z ** 5 / 128) > 1.0
+
+
+def test_rk_step_boundary_nodes_and_masks(orc):
+    """Stages never touch boundary nodes (bc = 0 keeps them frozen)."""
+    P = orc.params(bc=0)
+    xyz = synth.jet_grid(12, 10, 8)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Q = orc.init_jet(P, xyz, 1)
+    Q1, dt = orc.rk_step(P, Q, M, xyz, 0.0)
+    for sl in [(slice(None), 0), (slice(None), -1), (slice(None), slice(None), 0),
+               (slice(None), slice(None), -1)]:
+        assert np.array_equal(Q1[sl], Q[sl])
+    assert np.abs(Q1[:, 1:-1, 1:-1] - Q[:, 1:-1, 1:-1]).max() > 0
+
+
+# --------------------------------------------------------------- time step
+
+def test_time_step_closed_form(orc):
+    """Uniform state on a Cartesian grid with spacings (hx, hy, hz):
+    dt = CFL / sum_d (|u_d| + a)/h_d."""
+    n = (6, 6, 6)
+    hs = (0.1, 0.2, 0.05)
+    xyz, shift = synth.box_grid(n, tuple(m * h for m, h in zip(n, hs)))
+    P = orc.params(periodic=(1, 1, 1), bc=0, cfl=0.7)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    vel = (0.3, -0.8, 0.1)
+    Q = orc.prim_to_cons(P, synth.uniform_prim(n, u=vel[0], v=vel[1], w=vel[2]))
+    expect = 0.7 / sum((abs(vel[d]) + 1.0) / hs[d] for d in range(3))
+    assert abs(orc.dt(P, Q, M) - expect) < 1e-15 * expect * 10
+
+
+# --------------------------------------------------------- boundaries
+
+def _jet_setup(orc, n=(10, 12, 8), **kw):
+    P = orc.params(**kw)
+    xyz = synth.jet_grid(*n)
+    M = orc.metrics(xyz, (0, 0, 1))
+    return P, xyz, M
+
+
+def _prim(Q):
+    rho = Q[0]
+    u, v, w = Q[1] / rho, Q[2] / rho, Q[3] / rho
+    p = 0.4 * (Q[4] - 0.5 * rho * (u * u + v * v + w * w))
+    return rho, u, v, w, p
+
+
+def test_far_field_keeps_free_stream(orc):
+    P, xyz, M = _jet_setup(orc)
+    Q = orc.prim_to_cons(P, synth.uniform_prim(xyz.shape[1:]))
+    Qb = orc.bc_jet(P, Q, M, xyz, 0.0)
+    assert np.allclose(Qb[:, 1:-1, -1], Q[:, 1:-1, -1], rtol=0, atol=1e-14)
+
+
+def test_far_field_riemann_invariants(orc):
+    """Subsonic branches: the boundary state carries the interior R+ and the
+    free-stream R-, and the entropy of its source state."""
+    P, xyz, M = _jet_setup(orc)
+    n = xyz.shape[1:]
+    rng = np.random.default_rng(2)
+    prim = synth.uniform_prim(n)
+    prim[0] = 1.0 + 0.05 * rng.standard_normal(n)
+    prim[1:4] = 0.3 * rng.standard_normal((3,) + n)
+    prim[4] = (1 / GAMMA) * (1.0 + 0.05 * rng.standard_normal(n))
+    Q = orc.prim_to_cons(P, prim)
+    Qb = orc.bc_jet(P, Q, M, xyz, 0.0)
+    rho, u, v, w, p = _prim(Q[:, 1:-1, -2])
+    rf, uf, vf, wf, pf = _prim(Qb[:, 1:-1, -1])
+    e = M[3:6, 1:-1, -1]
+    nvec = e / np.sqrt((e ** 2).sum(axis=0))
+    qe = u * nvec[0] + v * nvec[1] + w * nvec[2]
+    ae = np.sqrt(GAMMA * p / rho)
+    qf = uf * nvec[0] + vf * nvec[1] + wf * nvec[2]
+    af = np.sqrt(GAMMA * pf / rf)
+    sub = np.abs(qe / ae) < 1
+    assert sub.sum() > 10
+    assert np.allclose((qf + 5 * af)[sub], (qe + 5 * ae)[sub], atol=1e-12)
+    assert np.allclose((qf - 5 * af)[sub], -5.0, atol=1e-12)
+    out = sub & (qe >= 0)
+    inn = sub & (qe < 0)
+    assert out.sum() > 0 and inn.sum() > 0
+    assert np.allclose((pf / rf ** GAMMA)[out], (p / rho ** GAMMA)[out], rtol=1e-12)
+    assert np.allclose((pf / rf ** GAMMA)[inn], 1 / GAMMA, rtol=1e-12)
+    # tangential velocity of the source state is kept
+    tan = lambda a, b, c, q: np.stack([a - q * nvec[0], b - q * nvec[1], c - q * nvec[2]])
+    assert np.allclose(tan(uf, vf, wf, qf)[:, out], tan(u, v, w, qe)[:, out], atol=1e-12)
+    assert np.allclose(tan(uf, vf, wf, qf)[:, inn], 0.0, atol=1e-12)
+
+
+def test_exit_and_inner_ring(orc):
+    P, xyz, M = _jet_setup(orc)
+    n = xyz.shape[1:]
+    prim = synth.uniform_prim(n)
+    rng = np.random.default_rng(8)
+    prim[0] = 1.0 + 0.1 * rng.random(n)
+    prim[1] = np.where(np.arange(n[1])[None, :, None] < 5, 2.0, 0.3) + 0 * prim[1]
+    prim[4] = (1 / GAMMA) * (1.0 + 0.1 * rng.random(n))
+    Q = orc.prim_to_cons(P, prim)
+    Qb = orc.bc_jet(P, Q, M, xyz, 0.0)
+    # inner ring = azimuthal mean of the first interior ring
+    assert np.allclose(Qb[:, 1:-1, 0, :], Q[:, 1:-1, 1, :].mean(axis=-1, keepdims=True), atol=1e-15)
+    # exit: supersonic rows copy, subsonic rows keep T and u with p = p_inf
+    rho, u, v, w, p = _prim(Qb[:, -2])
+    rf, uf, vf, wf, pf = _prim(Qb[:, -1])
+    sup = (u / np.sqrt(GAMMA * p / rho)) >= 1.0
+    assert sup.any() and (~sup).any()
+    assert np.allclose(Qb[:, -1][:, sup], Qb[:, -2][:, sup], rtol=0, atol=0)
+    assert np.allclose(pf[~sup], 1 / GAMMA, rtol=1e-13)
+    assert np.allclose((pf / rf)[~sup], (p / rho)[~sup], rtol=1e-13)
+    assert np.allclose(uf[~sup], u[~sup], rtol=1e-13)
+
+
+def test_inflow_forcing(orc):
+    """Entrance plane: profile plus the 16-mode forcing at time t."""
+    amp = synth.forcing_amplitudes(3)
+    P, xyz, M = _jet_setup(orc, amp=tuple(amp))
+    Q = orc.prim_to_cons(P, synth.uniform_prim(xyz.shape[1:]))
+    t = 0.37
+    Qb = orc.bc_jet(P, Q, M, xyz, t)
+    y, z = xyz[1, 0], xyz[2, 0]
+    r, th = np.sqrt(y * y + z * z), np.arctan2(z, y)
+    u = 0.7 * (1 + np.tanh((0.5 - r) / 0.1))
+    g = np.exp(-((r - 0.5) / 0.05) ** 2)
+    St = (0.25, 0.5, 0.75, 1.0)
+    for m in range(4):
+        for f in range(4):
+            u = u + amp[m * 4 + f] * g * np.cos(m * th - 2 * np.pi * St[f] * 1.4 * t)
+    assert np.allclose(Qb[1, 0], u, rtol=1e-14, atol=1e-15)
+    assert np.allclose(Qb[0, 0], 1.0) and np.abs(Qb[2:4, 0]).max() == 0
+
+
+def test_azimuthal_rotation_equivariance(orc):
+    """Rotating the initial state by one azimuthal index rotates the result of
+    a full step (periodic wrap, BCs and reductions are index-shift
+    invariant on the rotationally symmetric grid)."""
+    P, xyz, M = _jet_setup(orc, n=(10, 12, 8), sgs_model=2)
+    Q = orc.init_jet(P, xyz, 11)
+    Q1, dt1 = orc.rk_step(P, Q, M, xyz, 0.0)
+    c, s = math.cos(2 * math.pi / 8), math.sin(2 * math.pi / 8)
+
+    def rotate(A):  # shift one azimuthal index and turn (v, w) with it
+        B = np.roll(A, 1, axis=3)
+        v, w = B[2].copy(), B[3].copy()
+        B[2], B[3] = c * v - s * w, s * v + c * w
+        return B
+
+    Q2, dt2 = orc.rk_step(P, rotate(Q), M, xyz, 0.0)
+    assert abs(dt1 - dt2) < 1e-12 * dt1
+    assert np.allclose(rotate(Q1), Q2, rtol=0, atol=1e-12)
