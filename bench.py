@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the LES hot path: grid-point RK-step updates per second.
+
+A step is one full time step of the method (viscosity, time step, five
+Runge-Kutta stages of the residual, boundary conditions) on the jet workload
+288 x 160 x 128 (5.9M points, the size of the paper's Mesh A), Re_D = 1e5,
+Mach 1.4, CFL 0.5, Smagorinsky SGS, synthetic seeded initial state resident
+in HBM.  The headline is the FP32-mixed form; the FP64 form is measured on
+the same GPU and reported beside it with the mixed form's error against it.
+
+Contract: rank 0 prints one JSON line.  ``--impl reference`` times the CPU
+oracle (the only other implementation of the method) on the host cores.
+Multi-GPU runs are independent replicas (the path does not exchange data on
+one node here): value = all ranks' point-steps / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpt·RK-steps/s FP32-mixed vs FP64 at stated error, %HBM peak; adjoint/fwd ratio"
+UNIT = "Gpt*RK-steps/s"
+WORKLOAD = (288, 160, 128)
+WORKLOAD_NAME = "jet 288x160x128 (5.9M pts, Mesh-A size), Re_D 1e5, M_j 1.4, CFL 0.5, Smagorinsky"
+
+# Algorithmic bytes per grid point of one launch of each kernel class (what
+# the kernel must read and write at least once; halos assumed cached), for
+# (FP64, mixed).  Stage-1 kernels of the mixed form read the FP64 state.
+BYTES_PER_POINT = {
+    "node": (5 * 8 + 9 * 8 + 8 * 8, 5 * 4 + 9 * 4 + 8 * 4),
+    "mu_eff": (4 * 8 + 8 + 10 * 8 + 2 * 8, 4 * 4 + 8 + 10 * 4 + 2 * 4),
+    "flux_xi": (5 * 8 + 6 * 8 + 10 * 8 + 2 * 8 + 5 * 8, 5 * 4 + 6 * 4 + 10 * 4 + 2 * 4 + 5 * 4),
+    "update": (15 * 8 + 5 * 8 + 8 + 5 * 8, 15 * 4 + 5 * 8 + 4 + 5 * 4),
+}
+BYTES_PER_POINT["flux_eta"] = BYTES_PER_POINT["flux_xi"]
+BYTES_PER_POINT["flux_zeta"] = BYTES_PER_POINT["flux_xi"]
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(self.dev).uuid)
+        except Exception:
+            uuid = None
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power) if power else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_baseline(shape, steps: int, warmup: int):
+    """CPU oracle on an axial slab of the workload (same grid spacing and
+    flow), all host cores; returns (Gpt*steps/s, seconds per step, points)."""
+    import numpy as np
+
+    import oracle
+    from paper_2301_00817_gb300 import synth
+    x, r, th = synth.jet_lines(*WORKLOAD)
+    ns = shape
+    xyz = np.empty((3,) + ns)
+    xyz[0] = x[:ns[0], None, None]
+    xyz[1] = r[None, :, None] * np.cos(th)[None, None, :]
+    xyz[2] = r[None, :, None] * np.sin(th)[None, None, :]
+    P = oracle.params(sgs_model=1)
+    M = oracle.metrics(xyz, (0, 0, 1))
+    Q = oracle.init_jet(P, xyz, seed=0)
+    t = 0.0
+    for _ in range(warmup):
+        Q, d = oracle.rk_step(P, Q, M, xyz, t)
+        t += d
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        Q, d = oracle.rk_step(P, Q, M, xyz, t)
+        t += d
+    el = time.perf_counter() - t0
+    npts = ns[0] * ns[1] * ns[2]
+    return npts * steps / el / 1e9, el / steps, npts, oracle.num_threads()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    slab = (48, WORKLOAD[1], WORKLOAD[2])
+    val, sec, npts, cores = oracle_baseline(slab, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "sample": f"axial slab {slab} of the workload",
+                   "global_batch": 1, "seq_len": 0, "parallelism": "host cores"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full RK steps on the axial slab {slab} "
+                                   f"({npts} points) of the workload"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(lj, torch, ctx, Q, steps, stream):
+    """Device time of `steps` full steps through les_run_n_steps."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    diag = ctx.les_run_n_steps(steps, Q, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), diag
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2301_00817_gb300 as lj
+    from paper_2301_00817_gb300 import _build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    lj.load_library()
+    shape = WORKLOAD
+    N = shape[0] * shape[1] * shape[2]
+    xyz = torch.from_numpy(lj.synth.jet_grid(*shape)).cuda()
+    stream = torch.cuda.current_stream()
+    hbm_peak, peak_src = load_peaks()
+
+    results = {}
+    for name, prec in (("mixed", lj.PREC_MIXED), ("fp64", lj.PREC_FP64)):
+        params = lj.make_params(sgs_model=lj.SGS_SMAGORINSKY, precision=prec)
+        ctx = lj.Context(params, shape, f"cuda:{local}")
+        ctx.les_set_grid(xyz)
+        Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+        ctx.les_init_jet(xyz, 0, 1e-3, Q)
+        ctx.les_run_n_steps(args.warmup, Q)
+        ctx.les_profile(True)
+        launches0 = ctx.les_launch_count()
+        barrier(world)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if name == "mixed" else None
+        if sampler:
+            sampler.start()
+        ms, diag = time_steps(lj, torch, ctx, Q, args.steps, stream)
+        clocks = sampler.stop() if sampler else None
+        barrier(world)
+        prof = ctx.les_profile_read()
+        ctx.les_profile(False)
+        launches = ctx.les_launch_count() - launches0
+        ms = max_over_ranks(world, ms)
+        results[name] = dict(ms=ms, diag=diag, prof=prof, launches=launches, clocks=clocks,
+                             ctx=ctx, Q=Q)
+
+    # e2e: the same step through the C ABI on a pinned host state
+    ctx = results["mixed"]["ctx"]
+    Qh = results["mixed"]["Q"].cpu().pin_memory()
+    Qstage = torch.empty_like(results["mixed"]["Q"])
+    ctx.les_run_host(1, Qh, Qstage)  # warm the copy path
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.les_run_host(1, Qh, Qstage)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+
+    # error of the mixed form against FP64 (same seed, 100 steps)
+    err = None
+    if not args.no_accuracy:
+        outs = {}
+        for name in ("fp64", "mixed"):
+            c = results[name]["ctx"]
+            Qa = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+            c.les_init_jet(xyz, 0, 1e-3, Qa)
+            c.les_set_time(0.0)
+            c.les_run_n_steps(args.accuracy_steps, Qa)
+            outs[name] = Qa
+        a, b = outs["mixed"], outs["fp64"]
+        err = {f"rel_l2_{nm}": float(torch.linalg.vector_norm(a[c] - b[c]) /
+                                     torch.linalg.vector_norm(b[c]))
+               for c, nm in ((0, "rho"), (1, "rho_u"), (4, "rho_E"))}
+        err["steps"] = args.accuracy_steps
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, sec, npts, cores = oracle_baseline(WORKLOAD, 1, 0)
+        cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "seconds": sec,
+               "sample": f"1 full RK step of the whole workload ({npts} points), "
+                         "all host threads"}
+
+    def roofline(res, prec_idx):
+        prof = res["prof"]
+        top = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+        ms_tot, n_launch = prof[top]
+        per_launch_s = ms_tot / n_launch / 1e3
+        bpp = BYTES_PER_POINT.get(top, (None, None))[prec_idx]
+        if bpp is None:
+            return {"kernel": top, "bound": "hbm", "achieved": None, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": None, "traffic": None}
+        achieved = bpp * N / per_launch_s / 1e9
+        share = ms_tot / sum(v[0] for v in prof.values())
+        return {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_point": bpp, "avg_launch_us": per_launch_s * 1e6,
+                "share_of_step": share}
+
+    mixed, fp64 = results["mixed"], results["fp64"]
+    ms_step = mixed["ms"] / args.steps
+    value = world * N * args.steps / (mixed["ms"] / 1e3) / 1e9
+    fp64_value = world * N * args.steps / (fp64["ms"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "points": N, "global_batch": world,
+                   "seq_len": 0, "parallelism": f"replicas x{world}",
+                   "precision": "FP32 fluxes/dissipation/SGS, FP64 metrics + RK accumulation",
+                   "l2": "state and metrics (~0.9 GB) exceed the 129 MB L2; no flush needed"},
+        "roofline": roofline(mixed, 1),
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * N * args.steps / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8,
+                "api": "les_run_host (pinned host state in and out every step)"},
+        "gpu_launches": mixed["launches"],
+        "clocks": mixed["clocks"],
+        "fp64": {"value": fp64_value, "ms_per_step": fp64["ms"] / args.steps, "dtype": "f64",
+                 "roofline_hbm": roofline(fp64, 0), "gpu_launches": fp64["launches"]},
+        "mixed_error_vs_fp64": err,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in mixed["prof"].items() if v[1]},
+        "kernel_ms_per_step_fp64": {k: v[0] / args.steps for k, v in fp64["prof"].items() if v[1]},
+        "adjoint_fwd_ratio": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--accuracy-steps", type=int, default=100)
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

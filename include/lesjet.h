@@ -1,0 +1,195 @@
+/*
+ * lesjet.h -- C ABI of the GB300 (sm_103a) implementation of the LES hot path
+ * of "Computational Performance of a LES Solver for Supersonic Jet Flow
+ * Applications" (arXiv 2301.00817): the residual of the filtered compressible
+ * Navier-Stokes equations (System I energy) on a structured curvilinear grid,
+ * fused into the paper's five-stage Runge-Kutta update.
+ *
+ * Conventions for every entry point:
+ *  - Return value: LES_OK (0) or a negative LES_ERR_* code; les_last_error()
+ *    gives a message.  No C++ exception crosses this boundary.
+ *  - Memory: the library allocates no device memory.  The caller owns every
+ *    device buffer (PyTorch tensors in the Python binding) and passes raw
+ *    device pointers; one caller-owned workspace of les_workspace_bytes()
+ *    holds the metrics, viscosity, stage states and scratch.  Every device
+ *    pointer must be 16-byte aligned (LES_ERR_ALIGN otherwise).
+ *  - Layout: structure of arrays, k (azimuthal, zeta) fastest, then j (radial,
+ *    eta), then i (axial, xi): node n = (i*nj + j)*nk + k.  A field with C
+ *    components is C contiguous arrays of N = ni*nj*nk values ([C][N]).
+ *    Q is [5][N] FP64 holding the UNSCALED conserved variables
+ *    rho, rho u, rho v, rho w, e (the paper's Q-hat is J^-1 Q).
+ *  - Streams: work is queued on the given stream (NULL = legacy default
+ *    stream).  Calls are asynchronous unless documented as synchronising.
+ *  - Variables are dimensionless as in Sec. "Dimensionless Formulation":
+ *    lengths by D, velocities by a_j, pressure by rho_j a_j^2, rho by rho_j.
+ */
+#ifndef LESJET_H
+#define LESJET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *les_stream_t; /* same type as cudaStream_t */
+
+enum {
+  LES_OK = 0,
+  LES_ERR_INVALID_ARG = -1, /* null pointer, bad enum or bad value */
+  LES_ERR_SHAPE = -2,       /* grid too small or too large */
+  LES_ERR_ALIGN = -3,       /* a device pointer is not 16-byte aligned */
+  LES_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+  LES_ERR_NONFINITE = -5,   /* non-finite or non-positive rho/p/dt seen */
+  LES_ERR_UNSUPPORTED = -6, /* option not available in this build */
+  LES_ERR_STATE = -7        /* call order violated (e.g. no grid set) */
+};
+
+enum { LES_SGS_NONE = 0, LES_SGS_SMAGORINSKY = 1, LES_SGS_VREMAN = 2 };
+enum { LES_PREC_FP64 = 0, LES_PREC_MIXED = 1 };
+enum { LES_BC_FROZEN = 0, LES_BC_JET = 1 };
+enum { LES_DT_CFL = 0, LES_DT_FIXED = 1 };
+
+/* Flow and scheme parameters (Sec. "Large Eddy Simulation Filtering" to
+ * Sec. "Boundary Conditions").  Defaults used by the jet workloads:
+ * gamma 1.4, Pr 0.72, Pr_sgs 0.9, Mj 1.4, T_ref 288.15 K, k2 0.25,
+ * k4 0.016, Cs 0.148, cfl 0.5, r_jet 0.5, theta_m 0.05, force_width 0.05,
+ * St = {0.25, 0.5, 0.75, 1.0}. */
+typedef struct les_params {
+  double gamma;       /* ratio of specific heats */
+  double Pr;          /* laminar Prandtl number */
+  double Pr_sgs;      /* subgrid-scale Prandtl number */
+  double Mj;          /* jet Mach number U_j / a_j (also U_j in a_j units) */
+  double Re;          /* Reynolds number rho_j U_j D / mu_j; <= 0: inviscid */
+  double T_ref;       /* Sutherland reference temperature, K */
+  double k2, k4;      /* Turkel-Vatsa constants k^(2), k^(4) */
+  double Cs;          /* Smagorinsky constant (Vreman uses 2.5 Cs^2) */
+  double cfl;         /* CFL number of the global time step */
+  double dt_fixed;    /* time step when dt_mode == LES_DT_FIXED */
+  double r_jet;       /* jet radius of the inflow profile */
+  double theta_m;     /* momentum thickness of the inflow shear layer */
+  double force_width; /* radial width of the inflow forcing */
+  double St[4];       /* forcing Strouhal numbers */
+  double amp[16];     /* forcing amplitudes a_{m f}, index m*4 + f */
+  int sgs_model;      /* LES_SGS_* */
+  int periodic[3];    /* per direction xi, eta, zeta: 1 = periodic */
+  int bc;             /* LES_BC_FROZEN (non-periodic faces never change)
+                         or LES_BC_JET (needs periodic = {0,0,1}) */
+  int dt_mode;        /* LES_DT_CFL or LES_DT_FIXED */
+  int freeze_visc;    /* 1: mu_eff, kappa_eff from Q^n held for 5 stages */
+  int precision;      /* LES_PREC_FP64 or LES_PREC_MIXED */
+} les_params;
+
+/* Diagnostics returned by the synchronising run calls. */
+typedef struct les_diag {
+  double t;          /* simulation time after the last step */
+  double dt;         /* time step of the last step */
+  double totals[5];  /* sum_n J^-1_n Q_c(n), fixed-order reduction */
+  int status;        /* LES_OK or LES_ERR_NONFINITE */
+  int steps;         /* steps taken by the call */
+} les_diag;
+
+typedef struct les_ctx les_ctx;
+
+/* Create a context for an ni x nj x nk grid (each >= 5, N < 2^40).  Host
+ * memory only; *out is owned by the caller and released by les_destroy. */
+int les_create(const les_params *p, int ni, int nj, int nk, les_ctx **out);
+int les_destroy(les_ctx *ctx);
+/* Last error message of this context (never NULL; "" when none). */
+const char *les_last_error(const les_ctx *ctx);
+/* Replace the parameters (same grid and precision), e.g. new forcing. */
+int les_set_params(les_ctx *ctx, const les_params *p);
+
+/* Bytes of the caller-owned device workspace this context needs. */
+size_t les_workspace_bytes(const les_ctx *ctx);
+
+/* Bind the workspace and compute the Jacobian and the nine metric terms on
+ * the device (Sec. "Transformation of Coordinates"; the eta row is the
+ * cofactor form, the printed eta row being garbled).  xyz: device [3][N]
+ * FP64 Cartesian coordinates.  shift: host [3][3] coordinate jump over one
+ * period of each periodic direction (shift[3*d + c]; zeros for the jet grid).
+ * Derivatives are second-order central, one-sided second order at
+ * non-periodic faces.  The workspace must stay allocated while the context
+ * is used.  Asynchronous. */
+int les_set_grid(les_ctx *ctx, const double *xyz, const double shift[9],
+                 void *workspace, les_stream_t stream);
+
+/* Device pointer to the FP64 metrics [10][N] inside the workspace:
+ * xi_x xi_y xi_z eta_x eta_y eta_z zeta_x zeta_y zeta_z J^-1. */
+const double *les_metrics(const les_ctx *ctx);
+
+/* Jet initial condition into Q (device [5][N]): rho = 1, p = 1/gamma,
+ * u = Mj/2 [1 + tanh((r_jet - r)/(2 theta_m))], plus noise*Mj*N(0,1) on
+ * u, v, w from Philox4x32-10 (counter = node, block; key = seed) and
+ * Box-Muller.  xyz as in les_set_grid.  Asynchronous. */
+int les_init_jet(les_ctx *ctx, const double *xyz, uint64_t seed,
+                 double noise, double *Q, les_stream_t stream);
+
+/* Effective viscosity/conductivity of state Q into MK (device [2][N] FP64):
+ * Sutherland laminar part times Mj/Re plus the SGS model (Sec. "Subgrid
+ * Scale Modeling").  Asynchronous. */
+int les_mu_eff(les_ctx *ctx, const double *Q, double *MK, les_stream_t stream);
+
+/* Residual RHS of Eq. spatial_discret for state Q into R (device [5][N]
+ * FP64): interior nodes get sum_d (F_{+1/2} - F_{-1/2}) with F = centred
+ * inviscid flux minus J^-1 times the Turkel-Vatsa dissipation minus the
+ * viscous+SGS flux; boundary nodes of non-periodic directions get 0.  The
+ * viscosity is evaluated from the same Q.  Computed in the context's
+ * precision.  Asynchronous. */
+int les_rhs(les_ctx *ctx, const double *Q, double *R, les_stream_t stream);
+
+/* Global time step dt = cfl * min_n 1/(lambda_xi + lambda_eta + lambda_zeta)
+ * of state Q (or dt_fixed).  SYNCHRONISES the stream; returns
+ * LES_ERR_NONFINITE if rho, p or dt is not finite and positive. */
+int les_time_step(les_ctx *ctx, const double *Q, double *dt_out,
+                  les_stream_t stream);
+
+/* Jet boundary conditions on Q at time t (entrance, far field, inner ring,
+ * then exit).  Requires bc == LES_BC_JET.  Asynchronous. */
+int les_apply_bc(les_ctx *ctx, double *Q, double t, les_stream_t stream);
+
+/* Set the device-resident simulation time used by the stepping calls. */
+int les_set_time(les_ctx *ctx, double t, les_stream_t stream);
+
+/* One time step of Eq. localdt on Q in place: viscosity from Q^n, dt, five
+ * stages Q^(l) = Q^(0) - alpha_l dt J RHS(Q^(l-1)) with alpha = 1/4, 1/6,
+ * 3/8, 1/2, 1 (boundary nodes keep Q^(0)), then the boundary conditions at
+ * t + dt.  t and dt stay on the device.  Asynchronous. */
+int les_rk_step(les_ctx *ctx, double *Q, les_stream_t stream);
+
+/* n time steps on Q in place, then SYNCHRONISES and fills *diag (may be
+ * NULL).  Returns LES_ERR_NONFINITE if any step saw a non-finite state. */
+int les_run_n_steps(les_ctx *ctx, int n, double *Q, les_diag *diag,
+                    les_stream_t stream);
+
+/* Same as les_run_n_steps for a HOST state: copies Q_host (pinned or
+ * pageable host [5][N]) into the device buffer Q_dev, runs n steps and
+ * copies the result back into Q_host.  SYNCHRONISES. */
+int les_run_host(les_ctx *ctx, int n, double *Q_host, double *Q_dev,
+                 les_diag *diag, les_stream_t stream);
+
+/* sum_n J^-1_n Q_c(n) for c = 0..4 (fixed-order, deterministic).
+ * SYNCHRONISES. */
+int les_totals(les_ctx *ctx, const double *Q, double out[5],
+               les_stream_t stream);
+
+/* Number of kernel launches the library issued on this context so far. */
+uint64_t les_launch_count(const les_ctx *ctx);
+
+/* Measurement support (no counterpart in the paper, which reports whole-
+ * iteration CPU time only).  les_profile(ctx, 1) clears and enables an event
+ * profiler: every later launch group records a CUDA event pair on its own
+ * stream.  les_profile_read SYNCHRONISES the stream and returns, per kernel
+ * class k < 16, the summed device milliseconds ms[k] and launch groups
+ * counts[k]; les_profile_name(k) names class k ("" past the last). */
+int les_profile(les_ctx *ctx, int enable);
+int les_profile_read(les_ctx *ctx, double ms[16], uint64_t counts[16],
+                     les_stream_t stream);
+const char *les_profile_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LESJET_H */

@@ -1,0 +1,507 @@
+// api.cu -- the extern "C" boundary of liblesjet: argument validation,
+// workspace layout and the order of kernel launches of one time step
+// (Table tab:JAZzY: viscosity, time step, five Runge-Kutta stages, boundary
+// conditions).  The library allocates no device memory.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lesjet.h"
+#include "lesjet_dev.cuh"
+#include "lesjet_host.h"
+
+using lesjet::DevScalars;
+using lesjet::Grid;
+
+// Kernel classes timed by the optional event profiler.
+enum ProfKind {
+  PK_NODE = 0, PK_DT, PK_MU, PK_FLUX_XI, PK_FLUX_ETA, PK_FLUX_ZETA, PK_UPDATE, PK_BC, PK_TOTALS,
+  PK_COUNT
+};
+static const char* kProfNames[PK_COUNT] = {"node", "dt_finalize", "mu_eff", "flux_xi",
+                                           "flux_eta", "flux_zeta", "update", "bc_jet",
+                                           "totals"};
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct les_ctx {
+  les_params p;
+  Grid g;
+  // workspace layout (byte offsets, 256-byte aligned)
+  size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_node, off_flux, off_rth, off_sc, off_part;
+  size_t total;
+  char* ws;
+  bool grid_set;
+  std::string err;
+  unsigned long long launches;
+  // event profiler (off unless les_profile(ctx, 1))
+  bool prof_on;
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[PK_COUNT];
+  unsigned long long prof_n[PK_COUNT];
+};
+
+namespace {
+
+constexpr double kAlpha[5] = {1.0 / 4.0, 1.0 / 6.0, 3.0 / 8.0, 1.0 / 2.0, 1.0};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int fail(les_ctx* c, int code, const char* msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_check(les_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return LES_ERR_CUDA;
+  }
+  return LES_OK;
+}
+
+cudaEvent_t prof_event(les_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records an event pair around one launch group on its own stream.
+struct ProfScope {
+  les_ctx* c;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a;
+  ProfScope(les_ctx* c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_), a(nullptr) {
+    if (c->prof_on) {
+      a = prof_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (c->prof_on && a) {
+      cudaEvent_t b = prof_event(c);
+      cudaEventRecord(b, s);
+      c->prof_pending.push_back(ProfRec{kind, a, b});
+    }
+  }
+};
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int validate_params(const les_params* p, std::string& why) {
+  if (!(p->gamma > 1.0) || !(p->Pr > 0.0) || !(p->Pr_sgs > 0.0) || !(p->Mj > 0.0) ||
+      !(p->T_ref > 0.0) || !(p->k2 >= 0.0) || !(p->k4 >= 0.0) || !(p->Cs >= 0.0)) {
+    why = "gamma > 1, Pr, Pr_sgs, Mj, T_ref > 0 and k2, k4, Cs >= 0 are required";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (p->sgs_model < 0 || p->sgs_model > 2) {
+    why = "sgs_model must be LES_SGS_NONE, LES_SGS_SMAGORINSKY or LES_SGS_VREMAN";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (p->precision != LES_PREC_FP64 && p->precision != LES_PREC_MIXED) {
+    why = "precision must be LES_PREC_FP64 or LES_PREC_MIXED";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (p->dt_mode == LES_DT_CFL ? !(p->cfl > 0.0) : (p->dt_mode != LES_DT_FIXED || !(p->dt_fixed > 0.0))) {
+    why = "dt_mode CFL needs cfl > 0; dt_mode FIXED needs dt_fixed > 0";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (p->bc != LES_BC_FROZEN && p->bc != LES_BC_JET) {
+    why = "bc must be LES_BC_FROZEN or LES_BC_JET";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (p->bc == LES_BC_JET && !(p->periodic[0] == 0 && p->periodic[1] == 0 && p->periodic[2] == 1)) {
+    why = "jet boundary conditions need periodic = {0, 0, 1}";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (p->bc == LES_BC_JET && !(p->theta_m > 0.0 && p->force_width > 0.0)) {
+    why = "jet boundary conditions need theta_m > 0 and force_width > 0";
+    return LES_ERR_INVALID_ARG;
+  }
+  return LES_OK;
+}
+
+void layout(les_ctx* c) {
+  const size_t N = (size_t)c->g.N;
+  const bool mixed = c->p.precision == LES_PREC_MIXED;
+  const size_t rs = mixed ? sizeof(float) : sizeof(double);
+  size_t o = 0;
+  c->off_m64 = o; o = align256(o + 10 * N * sizeof(double));
+  c->off_m32 = o; o = align256(o + (mixed ? 10 * N * sizeof(float) : 0));
+  c->off_mk = o; o = align256(o + 2 * N * rs);
+  c->off_sa = o; o = align256(o + 5 * N * rs);
+  c->off_sb = o; o = align256(o + 5 * N * rs);
+  c->off_node = o; o = align256(o + 8 * N * rs);
+  c->off_flux = o; o = align256(o + 15 * N * rs);
+  c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
+  c->off_sc = o; o = align256(o + sizeof(DevScalars));
+  c->off_part = o; o = align256(o + 5 * (size_t)lesjet::kMaxPartials * sizeof(double));
+  c->total = o;
+}
+
+template <typename T>
+T* at(les_ctx* c, size_t off) {
+  return reinterpret_cast<T*>(c->ws + off);
+}
+
+lesjet::StageIO stage_io(les_ctx* c) {
+  lesjet::StageIO io;
+  const bool mixed = c->p.precision == LES_PREC_MIXED;
+  io.Qin = nullptr;
+  io.qin_is_double = 1;
+  io.M = mixed ? (const void*)at<float>(c, c->off_m32) : (const void*)at<double>(c, c->off_m64);
+  io.node = c->ws + c->off_node;
+  io.mk = c->ws + c->off_mk;
+  io.flux = c->ws + c->off_flux;
+  io.partials = at<double>(c, c->off_part);
+  io.sc = at<DevScalars>(c, c->off_sc);
+  return io;
+}
+
+int ready(les_ctx* c) {
+  if (!c) return LES_ERR_INVALID_ARG;
+  if (!c->grid_set || !c->ws) return fail(c, LES_ERR_STATE, "les_set_grid has not been called");
+  return LES_OK;
+}
+
+// One residual evaluation of state Qin into the interface-flux buffer.
+void residual(les_ctx* c, lesjet::StageIO& io, bool with_mu, bool with_dt, int advance,
+              const lesjet::Launch& L) {
+  const int prec = c->p.precision;
+  {
+    ProfScope ps(c, PK_NODE, L.s);
+    lesjet::launch_node(prec, c->g, c->p, io, with_dt, L);
+  }
+  if (with_dt) {
+    ProfScope ps(c, PK_DT, L.s);
+    lesjet::launch_dt_finalize(c->p, io, advance, L);
+  }
+  if (with_mu) {
+    ProfScope ps(c, PK_MU, L.s);
+    lesjet::launch_mu(prec, c->g, c->p, io, L);
+  }
+  for (int d = 0; d < 3; ++d) {
+    ProfScope ps(c, PK_FLUX_XI + d, L.s);
+    lesjet::launch_flux(prec, c->g, c->p, io, d, L);
+  }
+}
+
+void rk_step(les_ctx* c, double* Q, cudaStream_t s) {
+  lesjet::Launch L{s, &c->launches};
+  const int prec = c->p.precision;
+  const bool mixed = prec == LES_PREC_MIXED;
+  lesjet::StageIO io = stage_io(c);
+  void* SA = c->ws + c->off_sa;
+  void* SB = c->ws + c->off_sb;
+  for (int l = 1; l <= 5; ++l) {
+    const void* in = (l == 1) ? (const void*)Q : ((l % 2 == 0) ? SA : SB);
+    void* out = (l == 5) ? (void*)Q : ((l % 2 == 1) ? SA : SB);
+    io.Qin = in;
+    io.qin_is_double = (l == 1 || !mixed) ? 1 : 0;
+    residual(c, io, l == 1 || !c->p.freeze_visc, l == 1, 1, L);
+    ProfScope ps(c, PK_UPDATE, s);
+    lesjet::launch_update(prec, c->g, io, Q, kAlpha[l - 1], l == 5 ? 2 : 1, out, L);
+  }
+  if (c->p.bc == LES_BC_JET) {
+    ProfScope ps(c, PK_BC, s);
+    lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth),
+                          io.sc, 0, 0.0, L);
+  }
+}
+
+int read_scalars(les_ctx* c, DevScalars* h, cudaStream_t s) {
+  cudaMemcpyAsync(h, c->ws + c->off_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "stream synchronize");
+  return cuda_check(c, "read scalars");
+}
+
+}  // namespace
+
+extern "C" {
+
+int les_create(const les_params* p, int ni, int nj, int nk, les_ctx** out) {
+  if (!p || !out) return LES_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  int rc = validate_params(p, why);
+  if (rc != LES_OK) return rc;
+  if (ni < 5 || nj < 5 || nk < 5) return LES_ERR_SHAPE;
+  const long long N = (long long)ni * nj * nk;
+  if (N >= (1LL << 40)) return LES_ERR_SHAPE;
+  les_ctx* c = new (std::nothrow) les_ctx();
+  if (!c) return LES_ERR_INVALID_ARG;
+  c->p = *p;
+  c->g.n[0] = ni;
+  c->g.n[1] = nj;
+  c->g.n[2] = nk;
+  for (int d = 0; d < 3; ++d) c->g.per[d] = p->periodic[d] ? 1 : 0;
+  c->g.N = N;
+  c->g.stride[0] = (long long)nj * nk;
+  c->g.stride[1] = nk;
+  c->g.stride[2] = 1;
+  c->ws = nullptr;
+  c->grid_set = false;
+  c->launches = 0;
+  c->prof_on = false;
+  for (int k = 0; k < PK_COUNT; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_n[k] = 0;
+  }
+  layout(c);
+  *out = c;
+  return LES_OK;
+}
+
+int les_destroy(les_ctx* c) {
+  if (!c) return LES_OK;
+  for (auto& r : c->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
+  delete c;
+  return LES_OK;
+}
+
+const char* les_last_error(const les_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int les_set_params(les_ctx* c, const les_params* p) {
+  if (!c || !p) return LES_ERR_INVALID_ARG;
+  std::string why;
+  int rc = validate_params(p, why);
+  if (rc != LES_OK) return fail(c, rc, why.c_str());
+  if (p->precision != c->p.precision) return fail(c, LES_ERR_INVALID_ARG, "precision is fixed at creation");
+  for (int d = 0; d < 3; ++d)
+    if ((p->periodic[d] ? 1 : 0) != c->g.per[d])
+      return fail(c, LES_ERR_INVALID_ARG, "periodicity is fixed at creation");
+  c->p = *p;
+  return LES_OK;
+}
+
+size_t les_workspace_bytes(const les_ctx* c) { return c ? c->total : 0; }
+
+int les_set_grid(les_ctx* c, const double* xyz, const double shift[9], void* workspace,
+                 les_stream_t stream) {
+  if (!c || !xyz || !workspace) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(xyz) || !aligned16(workspace))
+    return fail(c, LES_ERR_ALIGN, "device pointers must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  c->ws = (char*)workspace;
+  double* M64 = at<double>(c, c->off_m64);
+  lesjet::launch_metrics(c->g, xyz, shift, M64, L);
+  if (c->p.precision == LES_PREC_MIXED)
+    lesjet::launch_to_float(10 * c->g.N, M64, at<float>(c, c->off_m32), L);
+  lesjet::launch_inflow_geometry(c->g, xyz, at<double>(c, c->off_rth), L);
+  lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), 0.0, L);
+  int rc = cuda_check(c, "les_set_grid");
+  if (rc == LES_OK) c->grid_set = true;
+  return rc;
+}
+
+const double* les_metrics(const les_ctx* c) {
+  if (!c || !c->ws) return nullptr;
+  return reinterpret_cast<const double*>(c->ws + c->off_m64);
+}
+
+int les_init_jet(les_ctx* c, const double* xyz, uint64_t seed, double noise, double* Q,
+                 les_stream_t stream) {
+  if (!c || !xyz || !Q) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(xyz) || !aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  lesjet::launch_init_jet(c->g, xyz, seed, noise, c->p, Q, L);
+  return cuda_check(c, "les_init_jet");
+}
+
+int les_mu_eff(les_ctx* c, const double* Q, double* MK, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || !MK) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q) || !aligned16(MK)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  lesjet::StageIO io = stage_io(c);
+  io.Qin = Q;
+  io.qin_is_double = 1;
+  lesjet::launch_node(c->p.precision, c->g, c->p, io, false, L);
+  lesjet::launch_mu(c->p.precision, c->g, c->p, io, L);
+  lesjet::launch_mk_to_double(c->p.precision, c->g, io.mk, MK, L);
+  return cuda_check(c, "les_mu_eff");
+}
+
+int les_rhs(les_ctx* c, const double* Q, double* R, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || !R) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q) || !aligned16(R)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  if (Q == R) return fail(c, LES_ERR_INVALID_ARG, "Q and R must not alias");
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  lesjet::StageIO io = stage_io(c);
+  io.Qin = Q;
+  io.qin_is_double = 1;
+  residual(c, io, true, false, 0, L);
+  lesjet::launch_update(c->p.precision, c->g, io, Q, 0.0, 0, R, L);
+  return cuda_check(c, "les_rhs");
+}
+
+int les_time_step(les_ctx* c, const double* Q, double* dt_out, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || !dt_out) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  lesjet::StageIO io = stage_io(c);
+  io.Qin = Q;
+  io.qin_is_double = 1;
+  lesjet::launch_node(c->p.precision, c->g, c->p, io, true, L);
+  lesjet::launch_dt_finalize(c->p, io, 0, L);
+  if ((rc = cuda_check(c, "les_time_step")) != LES_OK) return rc;
+  DevScalars h;
+  if ((rc = read_scalars(c, &h, s)) != LES_OK) return rc;
+  *dt_out = h.dt;
+  if (h.status != 0) return fail(c, LES_ERR_NONFINITE, "non-finite or non-positive state");
+  return LES_OK;
+}
+
+int les_apply_bc(les_ctx* c, double* Q, double t, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  if (c->p.bc != LES_BC_JET) return fail(c, LES_ERR_STATE, "bc is not LES_BC_JET");
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth),
+                        at<DevScalars>(c, c->off_sc), 1, t, L);
+  return cuda_check(c, "les_apply_bc");
+}
+
+int les_set_time(les_ctx* c, double t, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), t, L);
+  return cuda_check(c, "les_set_time");
+}
+
+int les_rk_step(les_ctx* c, double* Q, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  rk_step(c, Q, (cudaStream_t)stream);
+  return cuda_check(c, "les_rk_step");
+}
+
+int les_run_n_steps(les_ctx* c, int n, double* Q, les_diag* diag, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || n < 0) return fail(c, LES_ERR_INVALID_ARG, "null pointer or negative n");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  for (int i = 0; i < n; ++i) rk_step(c, Q, s);
+  lesjet::launch_totals(c->g, Q, at<double>(c, c->off_m64), at<double>(c, c->off_part),
+                        at<DevScalars>(c, c->off_sc), L);
+  if ((rc = cuda_check(c, "les_run_n_steps")) != LES_OK) return rc;
+  DevScalars h;
+  if ((rc = read_scalars(c, &h, s)) != LES_OK) return rc;
+  if (diag) {
+    diag->t = h.t;
+    diag->dt = h.dt;
+    for (int q = 0; q < 5; ++q) diag->totals[q] = h.totals[q];
+    diag->status = h.status ? LES_ERR_NONFINITE : LES_OK;
+    diag->steps = n;
+  }
+  if (h.status != 0) return fail(c, LES_ERR_NONFINITE, "non-finite or non-positive state");
+  return LES_OK;
+}
+
+int les_run_host(les_ctx* c, int n, double* Q_host, double* Q_dev, les_diag* diag,
+                 les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q_host || !Q_dev) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q_dev)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = 5 * (size_t)c->g.N * sizeof(double);
+  if (cudaMemcpyAsync(Q_dev, Q_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return cuda_check(c, "les_run_host upload");
+  rc = les_run_n_steps(c, n, Q_dev, diag, stream);
+  if (rc != LES_OK && rc != LES_ERR_NONFINITE) return rc;
+  if (cudaMemcpyAsync(Q_host, Q_dev, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return cuda_check(c, "les_run_host download");
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "les_run_host sync");
+  return rc;
+}
+
+int les_totals(les_ctx* c, const double* Q, double out[5], les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || !out) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  lesjet::launch_totals(c->g, Q, at<double>(c, c->off_m64), at<double>(c, c->off_part),
+                        at<DevScalars>(c, c->off_sc), L);
+  if ((rc = cuda_check(c, "les_totals")) != LES_OK) return rc;
+  DevScalars h;
+  if ((rc = read_scalars(c, &h, s)) != LES_OK) return rc;
+  for (int q = 0; q < 5; ++q) out[q] = h.totals[q];
+  return LES_OK;
+}
+
+uint64_t les_launch_count(const les_ctx* c) { return c ? c->launches : 0; }
+
+int les_profile(les_ctx* c, int enable) {
+  if (!c) return LES_ERR_INVALID_ARG;
+  c->prof_on = enable != 0;
+  if (enable) {
+    for (int k = 0; k < PK_COUNT; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_n[k] = 0;
+    }
+  }
+  return LES_OK;
+}
+
+int les_profile_read(les_ctx* c, double ms[16], uint64_t counts[16], les_stream_t stream) {
+  if (!c || !ms || !counts) return LES_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    return cuda_check(c, "les_profile_read");
+  for (auto& r : c->prof_pending) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.kind] += t;
+      c->prof_n[r.kind] += 1;
+    }
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+  for (int k = 0; k < 16; ++k) {
+    ms[k] = k < PK_COUNT ? c->prof_ms[k] : 0.0;
+    counts[k] = k < PK_COUNT ? c->prof_n[k] : 0;
+  }
+  return cuda_check(c, "les_profile_read");
+}
+
+const char* les_profile_name(int kind) {
+  return (kind >= 0 && kind < PK_COUNT) ? kProfNames[kind] : "";
+}
+
+}  // extern "C"

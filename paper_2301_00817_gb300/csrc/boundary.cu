@@ -1,0 +1,246 @@
+// boundary.cu -- jet boundary conditions (Sec. "Boundary Conditions"),
+// conserved totals and time bookkeeping.  All FP64.
+#include "lesjet_dev.cuh"
+#include "lesjet_host.h"
+
+namespace lesjet {
+
+struct JetBC {
+  double gamma, Mj, r_jet, theta_m, force_width;
+  double St[4];
+  double amp[16];
+};
+
+__device__ __forceinline__ void store_prim(double* __restrict__ Q, long long N, long long n,
+                                           double gamma, double rho, double u, double v, double w,
+                                           double p) {
+  Q[n] = rho;
+  Q[N + n] = rho * u;
+  Q[2 * N + n] = rho * v;
+  Q[3 * N + n] = rho * w;
+  Q[4 * N + n] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
+}
+
+__device__ __forceinline__ void load_prim(const double* __restrict__ Q, long long N, long long n,
+                                          double gamma, double& rho, double& u, double& v,
+                                          double& w, double& p) {
+  rho = Q[n];
+  u = Q[N + n] / rho;
+  v = Q[2 * N + n] / rho;
+  w = Q[3 * N + n] / rho;
+  p = (gamma - 1.0) * (Q[4 * N + n] - 0.5 * rho * (u * u + v * v + w * w));
+}
+
+// Entrance i = 0: rho = 1, p = 1/gamma, v = w = 0, u = jet profile plus the
+// 16-mode forcing sum a_{mf} g(r) cos(m theta - 2 pi St_f Mj t).
+__global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
+                            const DevScalars* __restrict__ sc, int use_host_t, double t_host,
+                            double* __restrict__ Q) {
+  const long long plane = (long long)g.n[1] * g.n[2];
+  const double t = use_host_t ? t_host : sc->t;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < plane;
+       n += (long long)gridDim.x * blockDim.x) {
+    const double r = rth[n], th = rth[plane + n];
+    double u = 0.5 * b.Mj * (1.0 + tanh((b.r_jet - r) / (2.0 * b.theta_m)));
+    const double x = (r - b.r_jet) / b.force_width;
+    const double gr = exp(-(x * x));
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        u += b.amp[m * 4 + f] * gr * cos(m * th - two_pi * b.St[f] * b.Mj * t);
+    store_prim(Q, g.N, n, b.gamma, 1.0, u, 0.0, 0.0, 1.0 / b.gamma);
+  }
+}
+
+// Far field j = nj-1 (0 < i < ni-1): Riemann invariants along the unit
+// eta-normal with R+ from the adjacent interior node and R- from the free
+// stream at rest (rho = 1, p = 1/gamma, a = 1); four branches by q_n/a.
+__global__ void k_bc_farfield(Grid g, double gamma, const double* __restrict__ M,
+                              double* __restrict__ Q) {
+  const int ni = g.n[0], nj = g.n[1], nk = g.n[2];
+  const long long count = (long long)(ni - 2) * nk;
+  const long long N = g.N;
+  const double gm1 = gamma - 1.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = 1 + (int)(e / nk), k = (int)(e % nk);
+    const long long nf = idx3(g, i, nj - 1, k), ne = idx3(g, i, nj - 2, k);
+    const double ex = M[3 * N + nf], ey = M[4 * N + nf], ez = M[5 * N + nf];
+    const double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
+    const double nx = ex * inv, ny = ey * inv, nz = ez * inv;
+    double rho, u, v, w, p;
+    load_prim(Q, N, ne, gamma, rho, u, v, w, p);
+    const double ae = sqrt(gamma * p / rho);
+    const double qne = u * nx + v * ny + w * nz;
+    const double Rp = qne + 2.0 * ae / gm1;
+    const double Rm = 0.0 - 2.0 * 1.0 / gm1;
+    const double qnf = 0.5 * (Rp + Rm);
+    const double af = 0.25 * gm1 * (Rp - Rm);
+    const double Mn = qne / ae;
+    if (Mn >= 1.0) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Q[q * N + nf] = Q[q * N + ne];
+    } else if (Mn >= 0.0) {
+      const double dq = qnf - qne;
+      const double rf = pow(pow(rho, gamma) * af * af / (gamma * p), 1.0 / gm1);
+      store_prim(Q, N, nf, gamma, rf, u + dq * nx, v + dq * ny, w + dq * nz, rf * af * af / gamma);
+    } else if (Mn > -1.0) {
+      const double rf = pow(af * af / (gamma * (1.0 / gamma)), 1.0 / gm1);
+      store_prim(Q, N, nf, gamma, rf, qnf * nx, qnf * ny, qnf * nz, rf * af * af / gamma);
+    } else {
+      store_prim(Q, N, nf, gamma, 1.0, 0.0, 0.0, 0.0, 1.0 / gamma);
+    }
+  }
+}
+
+// Inner ring j = 0 (0 < i < ni-1): azimuthal mean of the first interior
+// ring, one block per axial station, fixed-order tree (deterministic).
+__global__ void k_bc_ring(Grid g, double* __restrict__ Q) {
+  const int i = 1 + blockIdx.x;
+  const int nk = g.n[2];
+  const long long N = g.N;
+  __shared__ double red[5][32];
+  double s[5] = {0, 0, 0, 0, 0};
+  const long long base1 = idx3(g, i, 1, 0), base0 = idx3(g, i, 0, 0);
+  for (int k = threadIdx.x; k < nk; k += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) s[q] += Q[q * N + base1 + k];
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) red[q][threadIdx.x >> 5] = s[q];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[q][threadIdx.x] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (threadIdx.x == 0) red[q][0] = v / (double)nk;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nk; k += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Q[q * N + base0 + k] = red[q][0];
+}
+
+// Exit i = ni-1 from the updated column i = ni-2: supersonic (q/a >= 1 along
+// the unit xi-normal) copies; subsonic takes p = 1/gamma and extrapolates the
+// velocity and the internal energy p/((gamma-1) rho).
+__global__ void k_bc_exit(Grid g, double gamma, const double* __restrict__ M,
+                          double* __restrict__ Q) {
+  const int ni = g.n[0];
+  const long long plane = (long long)g.n[1] * g.n[2];
+  const long long N = g.N;
+  const double gm1 = gamma - 1.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long nx_ = (long long)(ni - 1) * plane + e, ne = nx_ - plane;
+    const double ex = M[nx_], ey = M[N + nx_], ez = M[2 * N + nx_];
+    const double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
+    double rho, u, v, w, p;
+    load_prim(Q, N, ne, gamma, rho, u, v, w, p);
+    const double ae = sqrt(gamma * p / rho);
+    const double qn = (u * ex + v * ey + w * ez) * inv;
+    if (qn / ae >= 1.0) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Q[q * N + nx_] = Q[q * N + ne];
+    } else {
+      const double eint = p / (gm1 * rho);
+      const double rf = (1.0 / gamma) / (gm1 * eint);
+      Q[nx_] = rf;
+      Q[N + nx_] = rf * u;
+      Q[2 * N + nx_] = rf * v;
+      Q[3 * N + nx_] = rf * w;
+      Q[4 * N + nx_] = rf * (eint + 0.5 * (u * u + v * v + w * w));
+    }
+  }
+}
+
+// Block partials of sum_n J^-1 Q_c (grid-stride order fixed by the launch).
+__global__ void k_totals_partial(Grid g, const double* __restrict__ Q, const double* __restrict__ M,
+                                 double* __restrict__ partials) {
+  const long long N = g.N;
+  double s[5] = {0, 0, 0, 0, 0};
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const double jv = M[9 * N + n];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) s[q] += jv * Q[q * N + n];
+  }
+  __shared__ double red[5][32];
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) red[q][threadIdx.x >> 5] = s[q];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[q][threadIdx.x] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (threadIdx.x == 0) partials[q * kRedBlocks + blockIdx.x] = v;
+    }
+  }
+}
+
+__global__ void k_totals_final(const double* __restrict__ partials, DevScalars* sc) {
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (q >= 5) return;
+  double v = 0.0;
+  for (int b = lane; b < kRedBlocks; b += 32) v += partials[q * kRedBlocks + b];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (lane == 0) sc->totals[q] = v;
+}
+
+__global__ void k_set_time(DevScalars* sc, double t) {
+  sc->t = t;
+  sc->dt = 0.0;
+  sc->status = 0;
+  sc->steps = 0;
+}
+
+static int nblocks(long long count) {
+  long long b = (count + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* M64,
+                   const double* rth, const DevScalars* sc, int use_host_t, double t_host,
+                   const Launch& L) {
+  JetBC b;
+  b.gamma = p.gamma;
+  b.Mj = p.Mj;
+  b.r_jet = p.r_jet;
+  b.theta_m = p.theta_m;
+  b.force_width = p.force_width;
+  for (int i = 0; i < 4; ++i) b.St[i] = p.St[i];
+  for (int i = 0; i < 16; ++i) b.amp[i] = p.amp[i];
+  const long long plane = (long long)g.n[1] * g.n[2];
+  k_bc_inflow<<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, sc, use_host_t, t_host, Q);
+  k_bc_farfield<<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M64, Q);
+  k_bc_ring<<<g.n[0] - 2, 256, 0, L.s>>>(g, Q);
+  k_bc_exit<<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M64, Q);
+  *L.counter += 4;
+}
+
+void launch_totals(const Grid& g, const double* Q, const double* M64, double* partials,
+                   DevScalars* sc, const Launch& L) {
+  k_totals_partial<<<kRedBlocks, kRedThreads, 0, L.s>>>(g, Q, M64, partials);
+  k_totals_final<<<1, 160, 0, L.s>>>(partials, sc);
+  *L.counter += 2;
+}
+
+void launch_set_time(DevScalars* sc, double t, const Launch& L) {
+  k_set_time<<<1, 1, 0, L.s>>>(sc, t);
+  ++*L.counter;
+}
+
+}  // namespace lesjet

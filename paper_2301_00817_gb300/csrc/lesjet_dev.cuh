@@ -1,0 +1,124 @@
+// lesjet_dev.cuh -- device-side types and helpers shared by the CUDA
+// translation units of liblesjet (sm_103a).  Nothing here is shared with the
+// CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lesjet.h"
+
+namespace lesjet {
+
+// Structured grid, k fastest: node n = (i*nj + j)*nk + k.
+struct Grid {
+  int n[3];
+  int per[3];
+  long long N;
+  long long stride[3];  // {nj*nk, nk, 1}
+};
+
+// Scheme constants in the compute precision R.
+template <typename R>
+struct Consts {
+  R gamma, gm1;      // gamma, gamma - 1
+  R k2, k4;          // dissipation constants
+  R mu_scale;        // M_j / Re (0 when inviscid)
+  R S_suth;          // 110.4 K / T_ref
+  R cs2;             // Cs^2 (Smagorinsky) or 2.5 Cs^2 (Vreman)
+  R inv_gm1_pr;      // 1/((gamma-1) Pr)
+  R inv_gm1_prs;     // 1/((gamma-1) Pr_sgs)
+  int sgs;           // LES_SGS_*
+};
+
+// Device-resident scalars of a context (inside the workspace).
+struct DevScalars {
+  double t;          // simulation time (t^{n+1} once a step's dt is known)
+  double dt;         // current step
+  int status;        // LES_OK or LES_ERR_NONFINITE (sticky)
+  int steps;
+  double totals[5];
+};
+
+constexpr int kRedBlocks = 1216;   // 152 SMs x 8: fixed, so reductions are
+constexpr int kRedThreads = 256;   // deterministic run to run
+constexpr int kMaxPartials = kRedBlocks;
+
+__host__ __device__ inline long long idx3(const Grid& g, int i, int j, int k) {
+  return ((long long)i * g.n[1] + j) * g.n[2] + k;
+}
+
+__device__ __forceinline__ void decompose(const Grid& g, long long n, int c[3]) {
+  long long r = n / g.n[2];
+  c[2] = (int)(n - r * g.n[2]);
+  c[0] = (int)(r / g.n[1]);
+  c[1] = (int)(r - (long long)c[0] * g.n[1]);
+}
+
+// Node 'off' steps from node n (coordinates c) along direction d; -1 when it
+// falls outside a non-periodic direction.  Periodic directions wrap.
+__device__ __forceinline__ long long step(const Grid& g, long long n, const int c[3],
+                                          int d, int off) {
+  int nd = g.n[d];
+  int v = c[d] + off;
+  if (g.per[d]) {
+    if (v >= nd) v -= nd;
+    else if (v < 0) v += nd;
+  } else if (v < 0 || v >= nd) {
+    return -1;
+  }
+  return n + (long long)(v - c[d]) * g.stride[d];
+}
+
+__device__ __forceinline__ bool is_interior(const Grid& g, const int c[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (!g.per[d] && (c[d] == 0 || c[d] == g.n[d] - 1)) return false;
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T dev_sqrt(T x);
+template <>
+__device__ __forceinline__ double dev_sqrt<double>(double x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float dev_sqrt<float>(float x) { return sqrtf(x); }
+
+template <typename T>
+__device__ __forceinline__ T dev_abs(T x) { return x < T(0) ? -x : x; }
+
+template <typename T>
+__device__ __forceinline__ T dev_max(T a, T b) { return a > b ? a : b; }
+
+// ----------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with the round multipliers, word swap, xor with the
+// key; the key advances by the two Weyl increments between rounds.
+__device__ inline void philox4x32_10(uint32_t x[4], uint32_t k0, uint32_t k1) {
+  const uint32_t A = 0xD2511F53u, B = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hiA = __umulhi(A, x[0]), loA = A * x[0];
+    uint32_t hiB = __umulhi(B, x[2]), loB = B * x[2];
+    uint32_t y0 = hiB ^ x[1] ^ k0;
+    uint32_t y2 = hiA ^ x[3] ^ k1;
+    x[0] = y0;
+    x[1] = loB;
+    x[2] = y2;
+    x[3] = loA;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+}  // namespace lesjet
+
+// Host-side launch helpers implemented in the .cu files.
+namespace lesjet {
+
+struct Launch {
+  cudaStream_t s;
+  unsigned long long* counter;
+};
+
+}  // namespace lesjet

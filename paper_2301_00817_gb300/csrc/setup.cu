@@ -1,0 +1,163 @@
+// setup.cu -- one-off kernels: grid metrics, jet initial condition, inflow
+// geometry, FP32 metric copy.
+#include "lesjet_dev.cuh"
+#include "lesjet_host.h"
+
+namespace lesjet {
+
+// d(coordinate)/d(direction d) at node n: second-order central difference;
+// a periodic wrap adds/subtracts the period's coordinate jump sh; faces of a
+// non-periodic direction use the one-sided second-order formulas.
+__device__ double coord_deriv(const Grid& g, const double* __restrict__ f, long long n,
+                              const int c[3], int d, double sh) {
+  const int nd = g.n[d];
+  const long long s = g.stride[d];
+  if (g.per[d]) {
+    double fp = (c[d] == nd - 1) ? f[n - (long long)(nd - 1) * s] + sh : f[n + s];
+    double fm = (c[d] == 0) ? f[n + (long long)(nd - 1) * s] - sh : f[n - s];
+    return 0.5 * (fp - fm);
+  }
+  if (c[d] == 0) return 0.5 * (-3.0 * f[n] + 4.0 * f[n + s] - f[n + 2 * s]);
+  if (c[d] == nd - 1) return 0.5 * (3.0 * f[n] - 4.0 * f[n - s] + f[n - 2 * s]);
+  return 0.5 * (f[n + s] - f[n - s]);
+}
+
+struct Shift {
+  double v[9];
+};
+
+// Jacobian determinant J^-1 of d(x,y,z)/d(xi,eta,zeta) and the metric terms
+// as its cofactors times J (Sec. "Transformation of Coordinates"; the eta
+// row uses the zeta/xi cofactors).
+__global__ void k_metrics(Grid g, const double* __restrict__ xyz, Shift sh,
+                          double* __restrict__ M) {
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    double d[3][3];  // d[comp][dir]
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir)
+        d[comp][dir] = coord_deriv(g, xyz + comp * N, n, c, dir, sh.v[3 * dir + comp]);
+    const double xa = d[0][0], xb = d[0][1], xc = d[0][2];
+    const double ya = d[1][0], yb = d[1][1], yc = d[1][2];
+    const double za = d[2][0], zb = d[2][1], zc = d[2][2];
+    const double c00 = yb * zc - yc * zb, c01 = zb * xc - zc * xb, c02 = xb * yc - xc * yb;
+    const double c10 = yc * za - ya * zc, c11 = zc * xa - za * xc, c12 = xc * ya - xa * yc;
+    const double c20 = ya * zb - yb * za, c21 = za * xb - zb * xa, c22 = xa * yb - xb * ya;
+    const double Jinv = xa * yb * zc + xb * yc * za + xc * ya * zb - xa * yc * zb -
+                        xb * ya * zc - xc * yb * za;
+    const double J = 1.0 / Jinv;
+    M[0 * N + n] = J * c00;
+    M[1 * N + n] = J * c01;
+    M[2 * N + n] = J * c02;
+    M[3 * N + n] = J * c10;
+    M[4 * N + n] = J * c11;
+    M[5 * N + n] = J * c12;
+    M[6 * N + n] = J * c20;
+    M[7 * N + n] = J * c21;
+    M[8 * N + n] = J * c22;
+    M[9 * N + n] = Jinv;
+  }
+}
+
+__global__ void k_to_float(long long count, const double* __restrict__ a, float* __restrict__ b) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < count;
+       n += (long long)gridDim.x * blockDim.x)
+    b[n] = (float)a[n];
+}
+
+// Radius and azimuth of the entrance-plane nodes (i = 0), used by the inflow
+// profile and forcing.
+__global__ void k_inflow_geometry(Grid g, const double* __restrict__ xyz, double* __restrict__ rth) {
+  const long long plane = (long long)g.n[1] * g.n[2];
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < plane;
+       n += (long long)gridDim.x * blockDim.x) {
+    double y = xyz[g.N + n], z = xyz[2 * g.N + n];
+    rth[n] = sqrt(y * y + z * z);
+    rth[plane + n] = atan2(z, y);
+  }
+}
+
+__device__ __forceinline__ double u01_53(uint32_t lo, uint32_t hi) {
+  uint64_t b = ((((uint64_t)hi) << 32) | lo) >> 11;
+  return ((double)b + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+// Jet initial condition: rho = 1, p = 1/gamma, tanh axial profile, and
+// noise*Mj*N(0,1) on u, v, w from Philox4x32-10 + Box-Muller (counter =
+// (node lo, node hi, block, 0), key = seed; block 0 -> u', v'; block 1 -> w').
+__global__ void k_init_jet(Grid g, const double* __restrict__ xyz, uint64_t seed, double noise,
+                           double gamma, double Mj, double r_jet, double theta_m,
+                           double* __restrict__ Q) {
+  const long long N = g.N;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    double z[3];
+#pragma unroll
+    for (uint32_t blk = 0; blk < 2; ++blk) {
+      uint32_t x[4] = {(uint32_t)n, (uint32_t)((unsigned long long)n >> 32), blk, 0u};
+      philox4x32_10(x, (uint32_t)seed, (uint32_t)(seed >> 32));
+      double u1 = u01_53(x[0], x[1]);
+      double u2 = u01_53(x[2], x[3]);
+      double rad = sqrt(-2.0 * log(u1));
+      double s, co;
+      sincos(two_pi * u2, &s, &co);
+      if (blk == 0) {
+        z[0] = rad * co;
+        z[1] = rad * s;
+      } else {
+        z[2] = rad * co;
+      }
+    }
+    double y = xyz[N + n], zc = xyz[2 * N + n];
+    double r = sqrt(y * y + zc * zc);
+    double u = 0.5 * Mj * (1.0 + tanh((r_jet - r) / (2.0 * theta_m))) + noise * Mj * z[0];
+    double v = noise * Mj * z[1];
+    double w = noise * Mj * z[2];
+    double rho = 1.0, p = 1.0 / gamma;
+    Q[n] = rho;
+    Q[N + n] = rho * u;
+    Q[2 * N + n] = rho * v;
+    Q[3 * N + n] = rho * w;
+    Q[4 * N + n] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
+  }
+}
+
+static int grid_blocks(long long count, int threads) {
+  long long b = (count + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+void launch_metrics(const Grid& g, const double* xyz, const double shift[9], double* M,
+                    const Launch& L) {
+  Shift sh;
+  for (int i = 0; i < 9; ++i) sh.v[i] = shift ? shift[i] : 0.0;
+  k_metrics<<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, sh, M);
+  ++*L.counter;
+}
+
+void launch_to_float(long long count, const double* a, float* b, const Launch& L) {
+  k_to_float<<<grid_blocks(count, 256), 256, 0, L.s>>>(count, a, b);
+  ++*L.counter;
+}
+
+void launch_inflow_geometry(const Grid& g, const double* xyz, double* rth, const Launch& L) {
+  k_inflow_geometry<<<grid_blocks((long long)g.n[1] * g.n[2], 256), 256, 0, L.s>>>(g, xyz, rth);
+  ++*L.counter;
+}
+
+void launch_init_jet(const Grid& g, const double* xyz, uint64_t seed, double noise,
+                     const les_params& p, double* Q, const Launch& L) {
+  k_init_jet<<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, seed, noise, p.gamma, p.Mj, p.r_jet,
+                                                      p.theta_m, Q);
+  ++*L.counter;
+}
+
+}  // namespace lesjet

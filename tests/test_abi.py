@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every symbol include/lesjet.h
+declares; host-only entry points validate their arguments.  No compute call
+is made (these run without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lesjet.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2301_00817_gb300 import _build
+    _build.build()
+    import paper_2301_00817_gb300 as lj
+    return lj.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(les_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("les_create", "les_set_grid", "les_init_jet", "les_rhs", "les_rk_step",
+                     "les_run_n_steps", "les_time_step", "les_apply_bc", "les_mu_eff"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_create_validates_and_sizes_workspace(lib):
+    import paper_2301_00817_gb300 as lj
+    h = C.c_void_p()
+    p = lj.make_params()
+    assert lib.les_create(C.byref(p), 48, 24, 32, C.byref(h)) == lj.LES_OK
+    ws = lib.les_workspace_bytes(h)
+    N = 48 * 24 * 32
+    assert ws >= N * 8 * (10 + 2 + 10)  # metrics, viscosity, two stage states
+    assert lib.les_destroy(h) == lj.LES_OK
+    assert lib.les_create(C.byref(p), 4, 24, 32, C.byref(h)) == lj.LES_ERR_SHAPE
+    bad = lj.make_params(sgs_model=7)
+    assert lib.les_create(C.byref(bad), 8, 8, 8, C.byref(h)) == lj.LES_ERR_INVALID_ARG
+    bad = lj.make_params(periodic=(1, 1, 1), bc=lj.BC_JET)
+    assert lib.les_create(C.byref(bad), 8, 8, 8, C.byref(h)) == lj.LES_ERR_INVALID_ARG
+    bad = lj.make_params(dt_mode=lj.DT_FIXED, dt_fixed=0.0)
+    assert lib.les_create(C.byref(bad), 8, 8, 8, C.byref(h)) == lj.LES_ERR_INVALID_ARG
+    mixed = lj.make_params(precision=lj.PREC_MIXED)
+    assert lib.les_create(C.byref(mixed), 48, 24, 32, C.byref(h)) == lj.LES_OK
+    assert lib.les_workspace_bytes(h) > 0
+    lib.les_destroy(h)
+
+
+def test_calls_before_grid_are_rejected_without_touching_the_device(lib):
+    import paper_2301_00817_gb300 as lj
+    h = C.c_void_p()
+    p = lj.make_params()
+    assert lib.les_create(C.byref(p), 8, 8, 8, C.byref(h)) == lj.LES_OK
+    assert lib.les_rk_step(h, C.c_void_p(16), None) == lj.LES_ERR_STATE
+    assert b"les_set_grid" in lib.les_last_error(h)
+    assert lib.les_set_grid(h, C.c_void_p(3), None, C.c_void_p(16), None) == lj.LES_ERR_ALIGN
+    lib.les_destroy(h)

@@ -1,0 +1,296 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same grid and the same initial bits.
+
+Tolerances.  FP64: the paper's quantities are O(1) and every kernel performs
+the oracle's arithmetic in a different order (and with fused multiply-add),
+so single evaluations agree to a few ulps of the largest term; the stated
+bars are relative L-inf <= 1e-12 after one step and <= 1e-10 after 20 steps
+(chaotic flow, short windows).  The residual is compared against the flux
+scale because it is a difference of O(J^-1 |grad xi|) interface fluxes.
+Mixed: FP32 flux arithmetic with FP64 accumulation, <= 1e-5 relative L2 on
+rho, rho u, rho E against the FP64 path.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import device_ctx, oracle_params, rel_l2, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+C1 = (48, 24, 32)
+
+
+@pytest.fixture(scope="module")
+def lj():
+    from paper_2301_00817_gb300 import _build
+    _build.build()
+    import paper_2301_00817_gb300 as lj
+    lj.load_library()
+    return lj
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _grid(lj, case):
+    if case == "jet_c1":
+        return C1, lj.synth.jet_grid(*C1), None, dict(periodic=(0, 0, 1), bc=1)
+    if case == "jet_ragged":
+        s = (13, 9, 7)
+        return s, lj.synth.jet_grid(*s), None, dict(periodic=(0, 0, 1), bc=1)
+    if case == "jet_min":
+        s = (5, 5, 5)
+        return s, lj.synth.jet_grid(*s), None, dict(periodic=(0, 0, 1), bc=1)
+    if case == "wavy_box":
+        s = (17, 11, 9)
+        xyz, shift = lj.synth.box_grid(s, (1.0, 1.3, 0.8), wave=0.25)
+        return s, xyz, shift, dict(periodic=(1, 1, 1), bc=0)
+    raise ValueError(case)
+
+
+def _state(orc, lj, case, shape, xyz, P):
+    if case.startswith("jet"):
+        return orc.init_jet(P, xyz, seed=5, noise=2e-2)
+    prim = lj.synth.smooth_periodic_prim(xyz, (1.0, 1.3, 0.8), amp=0.2, seed=2)
+    return orc.prim_to_cons(P, prim)
+
+
+# ------------------------------------------------------------------ setup
+
+@pytest.mark.parametrize("case", ["jet_c1", "wavy_box", "jet_ragged"])
+def test_metrics(orc, lj, torch, case):
+    shape, xyz, shift, kw = _grid(lj, case)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, **kw)
+    Mg = ctx.les_metrics().cpu().numpy()
+    Mo = orc.metrics(xyz, kw["periodic"], shift)
+    # a metric row that vanishes analytically (xi_y on the separable jet grid)
+    # is rounding noise on both sides: scale each row by its direction's
+    # largest metric magnitude
+    for r in range(10):
+        scale = np.abs(Mo[9]).max() if r == 9 else np.abs(Mo[3 * (r // 3):3 * (r // 3) + 3]).max()
+        assert np.abs(Mg[r] - Mo[r]).max() <= 1e-14 * scale, r
+
+
+def test_init_jet(orc, lj, torch):
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    ctx, xyz_d = device_ctx(lj, torch, shape, xyz)
+    Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_init_jet(xyz_d, 1234, 1e-3, Q)
+    Qo = orc.init_jet(orc.params(), xyz, seed=1234, noise=1e-3)
+    assert rel_linf(Q.cpu().numpy(), Qo) <= 1e-14
+
+
+# -------------------------------------------------------------- residual
+
+@pytest.mark.parametrize("sgs", [0, 1, 2])
+@pytest.mark.parametrize("case", ["jet_c1", "wavy_box", "jet_ragged", "jet_min"])
+def test_mu_eff(orc, lj, torch, case, sgs):
+    shape, xyz, shift, kw = _grid(lj, case)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=sgs, Re=2000.0, **kw)
+    P = oracle_params(orc, sgs_model=sgs, Re=2000.0, **kw)
+    M = orc.metrics(xyz, kw["periodic"], shift)
+    Q = _state(orc, lj, case, shape, xyz, P)
+    MK = torch.empty((2,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_mu_eff(torch.from_numpy(Q).cuda(), MK)
+    MKo = orc.mu_eff(P, Q, M)
+    for r in range(2):
+        assert np.abs(MK[r].cpu().numpy() - MKo[r]).max() <= 1e-13 * np.abs(MKo[r]).max()
+
+
+@pytest.mark.parametrize("sgs", [0, 1, 2])
+@pytest.mark.parametrize("case", ["jet_c1", "wavy_box", "jet_ragged", "jet_min"])
+def test_rhs(orc, lj, torch, case, sgs):
+    shape, xyz, shift, kw = _grid(lj, case)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=sgs, Re=2000.0, **kw)
+    P = oracle_params(orc, sgs_model=sgs, Re=2000.0, **kw)
+    M = orc.metrics(xyz, kw["periodic"], shift)
+    Q = _state(orc, lj, case, shape, xyz, P)
+    R = torch.empty_like(torch.from_numpy(Q)).cuda()
+    ctx.les_rhs(torch.from_numpy(Q).cuda(), R)
+    Ro = orc.rhs(P, Q, M)
+    Rg = R.cpu().numpy()
+    # flux scale of each component: J^-1 |grad xi|-weighted state magnitude
+    fscale = (np.abs(M[9]) * np.sqrt(M[0] ** 2 + M[1] ** 2 + M[2] ** 2)).max()
+    for c in range(5):
+        qs = np.abs(Q[c]).max() + (np.abs(Q[4]).max() if c in (1, 2, 3, 4) else 0.0)
+        assert np.abs(Rg[c] - Ro[c]).max() <= 1e-13 * fscale * qs, c
+    if not case.startswith("wavy"):
+        assert np.abs(Rg[:, 0]).max() == 0.0 and np.abs(Rg[:, :, -1]).max() == 0.0
+
+
+def test_time_step(orc, lj, torch):
+    shape, xyz, shift, kw = _grid(lj, "jet_c1")
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, **kw)
+    P = oracle_params(orc, **kw)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Q = orc.init_jet(P, xyz, seed=3)
+    dt = ctx.les_time_step(torch.from_numpy(Q).cuda())
+    assert abs(dt - orc.dt(P, Q, M)) <= 1e-14 * dt
+
+
+def test_boundary_conditions(orc, lj, torch):
+    shape, xyz, shift, kw = _grid(lj, "jet_c1")
+    amp = lj.synth.forcing_amplitudes(9, scale=0.05)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, amp=tuple(amp), **kw)
+    P = oracle_params(orc, amp=tuple(amp), **kw)
+    M = orc.metrics(xyz, (0, 0, 1))
+    rng = np.random.default_rng(4)
+    prim = lj.synth.uniform_prim(shape)
+    prim[0] = 1.0 + 0.05 * rng.standard_normal(shape)
+    prim[1] = 1.3 * rng.random(shape) + 0.3 * rng.standard_normal(shape)
+    prim[2:4] = 0.3 * rng.standard_normal((2,) + shape)
+    prim[4] = (1 / 1.4) * (1.0 + 0.05 * rng.standard_normal(shape))
+    Q = orc.prim_to_cons(P, prim)
+    Qd = torch.from_numpy(Q).cuda()
+    ctx.les_apply_bc(Qd, 0.731)
+    Qo = orc.bc_jet(P, Q, M, xyz, 0.731)
+    assert rel_linf(Qd.cpu().numpy(), Qo) <= 1e-14
+
+
+# ------------------------------------------------------------- time steps
+
+@pytest.mark.parametrize("sgs", [0, 1, 2])
+def test_steps_c1(orc, lj, torch, sgs):
+    """The small jet configuration: 1 step <= 1e-12, 20 steps <= 1e-10."""
+    shape, xyz, shift, kw = _grid(lj, "jet_c1")
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=sgs, **kw)
+    P = oracle_params(orc, sgs_model=sgs, **kw)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Q0 = orc.init_jet(P, xyz, seed=0)
+    Qd = torch.from_numpy(Q0).cuda()
+    d1 = ctx.les_run_n_steps(1, Qd)
+    Q1, dt1 = orc.rk_step(P, Q0, M, xyz, 0.0)
+    assert abs(d1.dt - dt1) <= 1e-13 * dt1
+    assert rel_linf(Qd.cpu().numpy(), Q1) <= 1e-12
+    d20 = ctx.les_run_n_steps(19, Qd)
+    Q20, t20 = orc.run(P, Q1, M, xyz, 19, t=dt1)
+    assert abs(d20.t - t20) <= 1e-12 * t20
+    assert rel_linf(Qd.cpu().numpy(), Q20) <= 1e-10
+
+
+def test_steps_frozen_faces_and_unfrozen_viscosity(orc, lj, torch):
+    shape, xyz, shift, kw = _grid(lj, "jet_ragged")
+    kw = dict(kw, bc=0, freeze_visc=0, sgs_model=2, Re=500.0)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, **kw)
+    P = oracle_params(orc, **kw)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Q0 = orc.init_jet(P, xyz, seed=8, noise=1e-2)
+    Qd = torch.from_numpy(Q0).cuda()
+    ctx.les_run_n_steps(5, Qd)
+    Qo, _ = orc.run(P, Q0, M, xyz, 5)
+    assert rel_linf(Qd.cpu().numpy(), Qo) <= 1e-12
+
+
+def test_periodic_box_conservation_and_parity(orc, lj, torch):
+    shape, xyz, shift, kw = _grid(lj, "wavy_box")
+    kw = dict(kw, sgs_model=1, Re=300.0, cfl=0.8)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, **kw)
+    P = oracle_params(orc, **kw)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    Q0 = _state(orc, lj, "wavy_box", shape, xyz, P)
+    Qd = torch.from_numpy(Q0).cuda()
+    tot0 = np.array(ctx.les_totals(Qd))
+    diag = ctx.les_run_n_steps(20, Qd)
+    tot1 = np.array(diag.totals)
+    scale = np.abs(orc.totals(np.abs(Q0), M)).max()
+    assert np.abs(tot1 - tot0).max() / scale <= 1e-13
+    Qo, _ = orc.run(P, Q0, M, xyz, 20)
+    assert rel_linf(Qd.cpu().numpy(), Qo) <= 1e-10
+
+
+def test_full_size_step_c2(orc, lj, torch):
+    """Jet workload of the benchmark (288 x 160 x 128, 5.9M points) in the
+    benchmark's launch configuration: one full step against the oracle."""
+    shape = (288, 160, 128)
+    xyz = lj.synth.jet_grid(*shape)
+    ctx, _ = device_ctx(lj, torch, shape, xyz)
+    P = orc.params()
+    M = orc.metrics(xyz, (0, 0, 1))
+    Q0 = orc.init_jet(P, xyz, seed=0)
+    Qd = torch.from_numpy(Q0).cuda()
+    d = ctx.les_run_n_steps(1, Qd)
+    Q1, dt1 = orc.rk_step(P, Q0, M, xyz, 0.0)
+    assert abs(d.dt - dt1) <= 1e-13 * dt1
+    assert rel_linf(Qd.cpu().numpy(), Q1) <= 1e-12
+
+
+# ------------------------------------------------------------- robustness
+
+def test_deterministic_bitwise(lj, torch):
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    outs = []
+    for _ in range(2):
+        ctx, xyz_d = device_ctx(lj, torch, shape, xyz, sgs_model=2)
+        Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+        ctx.les_init_jet(xyz_d, 77, 1e-3, Q)
+        d = ctx.les_run_n_steps(10, Q)
+        outs.append((Q.cpu().numpy().copy(), d.t, list(d.totals)))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2]
+
+
+def test_nonfinite_state_is_reported(orc, lj, torch):
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    ctx, _ = device_ctx(lj, torch, shape, xyz)
+    Q = orc.init_jet(orc.params(), xyz, seed=1)
+    Q[0, 20, 10, 5] = np.nan
+    with pytest.raises(lj.LesError) as e:
+        ctx.les_run_n_steps(2, torch.from_numpy(Q).cuda())
+    assert e.value.code == lj.LES_ERR_NONFINITE
+    Q = orc.init_jet(orc.params(), xyz, seed=1)
+    Q[4, 20, 10, 5] = -1.0  # negative pressure
+    ctx.les_set_time(0.0)
+    with pytest.raises(lj.LesError) as e:
+        ctx.les_time_step(torch.from_numpy(Q).cuda())
+    assert e.value.code == lj.LES_ERR_NONFINITE
+
+
+def test_argument_errors(lj, torch):
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    ctx, _ = device_ctx(lj, torch, shape, xyz)
+    buf = torch.zeros(5 * 48 * 24 * 32 + 1, dtype=torch.float64, device="cuda")
+    import ctypes as C
+    rc = ctx.lib.les_rk_step(ctx.h, C.c_void_p(buf.data_ptr() + 8), None)
+    assert rc == lj.LES_ERR_ALIGN
+    rc = ctx.lib.les_run_n_steps(ctx.h, -1, C.c_void_p(buf.data_ptr()), None, None)
+    assert rc == lj.LES_ERR_INVALID_ARG
+
+
+def test_run_host_matches_device(orc, lj, torch):
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    ctx, _ = device_ctx(lj, torch, shape, xyz)
+    Q0 = orc.init_jet(orc.params(), xyz, seed=2)
+    Qd = torch.from_numpy(Q0).cuda()
+    ctx.les_run_n_steps(3, Qd)
+    ctx.les_set_time(0.0)
+    Qh = torch.from_numpy(Q0.copy()).pin_memory()
+    stage = torch.empty_like(Qd)
+    ctx.les_run_host(3, Qh, stage)
+    assert np.array_equal(Qh.numpy(), Qd.cpu().numpy())
+
+
+# ------------------------------------------------------------ mixed form
+
+def test_mixed_against_fp64(orc, lj, torch):
+    """FP32 fluxes/dissipation/SGS with FP64 metrics construction and RK
+    accumulation: <= 1e-5 relative L2 on rho, rho u, rho E after 100 steps."""
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    Q0 = orc.init_jet(orc.params(), xyz, seed=0)
+    res = {}
+    for prec in (lj.PREC_FP64, lj.PREC_MIXED):
+        ctx, _ = device_ctx(lj, torch, shape, xyz, sgs_model=1, precision=prec)
+        Qd = torch.from_numpy(Q0).cuda()
+        d = ctx.les_run_n_steps(100, Qd)
+        res[prec] = (Qd.cpu().numpy(), d.t)
+    assert rel_l2(res[lj.PREC_MIXED][0], res[lj.PREC_FP64][0]) <= 1e-5
+    assert abs(res[lj.PREC_MIXED][1] - res[lj.PREC_FP64][1]) <= 1e-5 * res[lj.PREC_FP64][1]
