@@ -333,6 +333,26 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_profile_case(which: str):
+    """Small case for ncu captures: 96 x 160 x 128 jet (1.97M points, state
+    and metrics above the 129 MB L2), two full steps, one precision."""
+    import torch
+
+    import paper_2301_00817_gb300 as lj
+    from paper_2301_00817_gb300 import _build
+    _build.build()
+    prec = lj.PREC_MIXED if which == "mixed" else lj.PREC_FP64
+    shape = (96, 160, 128)
+    ctx = lj.Context(lj.make_params(sgs_model=lj.SGS_SMAGORINSKY, precision=prec), shape)
+    xyz = torch.from_numpy(lj.synth.jet_grid(*shape)).cuda()
+    ctx.les_set_grid(xyz)
+    Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_init_jet(xyz, 0, 1e-3, Q)
+    d = ctx.les_run_n_steps(2, Q)
+    print(f"profile case {which}: t={d.t:.6e} dt={d.dt:.6e} launches={ctx.les_launch_count()}")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,7 +362,11 @@ def main():
     ap.add_argument("--accuracy-steps", type=int, default=100)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", choices=("fp64", "mixed"), default=None,
+                    help="run the small ncu case (two steps) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)

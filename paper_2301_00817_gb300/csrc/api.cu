@@ -505,3 +505,4 @@ const char* les_profile_name(int kind) {
 }
 
 }  // extern "C"
+
