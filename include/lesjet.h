@@ -188,6 +188,25 @@ int les_profile_read(les_ctx *ctx, double ms[16], uint64_t counts[16],
                      les_stream_t stream);
 const char *les_profile_name(int kind);
 
+/* Global time step of state Q, like les_time_step, for callers that cannot
+ * allocate device memory (the paper has no counterpart): for example a
+ * monitoring or steering hook that runs between solver steps in an
+ * application that has committed all device memory to its own fixed pool, or
+ * a plain-C tool that is handed only raw device pointers.  It needs no
+ * workspace and no les_set_grid: only a context from les_create (host memory)
+ * and the caller's Q (device [5][N] FP64) and FP64 metrics M (device [10][N],
+ * e.g. les_metrics() of another context).  It allocates nothing: its scratch
+ * is one static device array inside the library, sized for ni <=
+ * LES_STATIC_MAX_NI axial planes (256 KiB, held on every GPU that loads the
+ * library until the process exits); larger grids are rejected with
+ * LES_ERR_SHAPE.  The first call on each device looks up that array's device
+ * address with the device current; make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race.
+ * Always FP64.  SYNCHRONISES the stream; LES_ERR_NONFINITE as les_time_step. */
+#define LES_STATIC_MAX_NI 16384
+int les_time_step_static(les_ctx *ctx, const double *Q, const double *M,
+                         double *dt_out, les_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

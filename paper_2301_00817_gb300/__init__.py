@@ -118,6 +118,8 @@ def load_library(path: str = LIB_PATH):
     lib.les_profile_read.restype = C.c_int
     lib.les_profile_name.argtypes = [i]
     lib.les_profile_name.restype = C.c_char_p
+    lib.les_time_step_static.argtypes = [vp, vp, vp, C.POINTER(d), vp]
+    lib.les_time_step_static.restype = C.c_int
     for name in ("les_create", "les_destroy", "les_set_params", "les_set_grid", "les_init_jet",
                  "les_mu_eff", "les_rhs", "les_time_step", "les_apply_bc", "les_set_time",
                  "les_rk_step", "les_run_n_steps", "les_run_host", "les_totals"):
@@ -200,6 +202,13 @@ class Context:
     def les_time_step(self, Q, stream=None) -> float:
         out = C.c_double()
         self._check(self.lib.les_time_step(self.h, _ptr(Q), C.byref(out), _stream(stream)))
+        return out.value
+
+    def les_time_step_static(self, Q, M, stream=None) -> float:
+        """Time step without workspace or allocation (static library scratch)."""
+        out = C.c_double()
+        self._check(self.lib.les_time_step_static(self.h, _ptr(Q), _ptr(M), C.byref(out),
+                                                  _stream(stream)))
         return out.value
 
     def les_apply_bc(self, Q, t: float, stream=None):

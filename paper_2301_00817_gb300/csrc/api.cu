@@ -506,3 +506,18 @@ const char* les_profile_name(int kind) {
 
 }  // extern "C"
 
+// Read-only views of a context for other translation units of the library
+// (not exported from the shared object).
+namespace lesjet {
+__attribute__((visibility("hidden"))) const les_params* ctx_params(const les_ctx* c) {
+  return &c->p;
+}
+__attribute__((visibility("hidden"))) void ctx_shape(const les_ctx* c, int shape[3]) {
+  shape[0] = c->g.n[0];
+  shape[1] = c->g.n[1];
+  shape[2] = c->g.n[2];
+}
+__attribute__((visibility("hidden"))) void ctx_set_error(les_ctx* c, const char* msg) {
+  c->err = msg;
+}
+}  // namespace lesjet
