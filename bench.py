@@ -34,16 +34,15 @@ WORKLOAD = (288, 160, 128)
 WORKLOAD_NAME = "jet 288x160x128 (5.9M pts, Mesh-A size), Re_D 1e5, M_j 1.4, CFL 0.5, Smagorinsky"
 
 # Algorithmic bytes per grid point of one launch of each kernel class (what
-# the kernel must read and write at least once; halos assumed cached), for
-# (FP64, mixed).  Stage-1 kernels of the mixed form read the FP64 state.
+# the kernel must read and write at least once, halos assumed cached), as
+# (FP64, mixed).  stage_fused: mean over the five stages of state in (Q or
+# stage buffer), Q^(0) for the update, metrics (10), mu/kappa (2) and the
+# stage state out; mixed: float stage states and metrics, Q^(0) as float hi
+# (+ lo in the last stage).  prestep: Q^n + metrics in, mu/kappa out.
 BYTES_PER_POINT = {
-    "node": (5 * 8 + 9 * 8 + 8 * 8, 5 * 4 + 9 * 4 + 8 * 4),
-    "mu_eff": (4 * 8 + 8 + 10 * 8 + 2 * 8, 4 * 4 + 8 + 10 * 4 + 2 * 4),
-    "flux_xi": (5 * 8 + 6 * 8 + 10 * 8 + 2 * 8 + 5 * 8, 5 * 4 + 6 * 4 + 10 * 4 + 2 * 4 + 5 * 4),
-    "update": (15 * 8 + 5 * 8 + 8 + 5 * 8, 15 * 4 + 5 * 8 + 4 + 5 * 4),
+    "stage_fused": ((176 + 4 * 216) / 5, (88 + 3 * 108 + 148) / 5),
+    "prestep": (40 + 80 + 16, 20 + 40 + 8),
 }
-BYTES_PER_POINT["flux_eta"] = BYTES_PER_POINT["flux_xi"]
-BYTES_PER_POINT["flux_zeta"] = BYTES_PER_POINT["flux_xi"]
 
 
 def load_peaks():

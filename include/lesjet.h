@@ -92,7 +92,7 @@ typedef struct les_diag {
 
 typedef struct les_ctx les_ctx;
 
-/* Create a context for an ni x nj x nk grid (each >= 5, N < 2^40).  Host
+/* Create a context for an ni x nj x nk grid (each >= 5; N < 2^40, N < 2^31 in the mixed form).  Host
  * memory only; *out is owned by the caller and released by les_destroy. */
 int les_create(const les_params *p, int ni, int nj, int nk, les_ctx **out);
 int les_destroy(les_ctx *ctx);

@@ -20,6 +20,9 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",
               "--expt-relaxed-constexpr"]
+# Per-file flags: the FP32-mixed kernels use approximate FP32 division and
+# square root (FP64 code is unaffected by these flags).
+FILE_FLAGS = {"fused.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def _nvcc() -> str:
@@ -36,6 +39,7 @@ def sources() -> list[str]:
 def _deps() -> list[str]:
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(INCLUDE, "lesjet.h"))
+    files.append(os.path.abspath(__file__))
     return files
 
 
@@ -55,7 +59,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *flags, "-I", INCLUDE, "-c", src, "-o", obj]
+        extra = FILE_FLAGS.get(os.path.basename(src), [])
+        cmd = [nvcc, *ARCH, *flags, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -20,12 +20,12 @@ using lesjet::Grid;
 
 // Kernel classes timed by the optional event profiler.
 enum ProfKind {
-  PK_NODE = 0, PK_DT, PK_MU, PK_FLUX_XI, PK_FLUX_ETA, PK_FLUX_ZETA, PK_UPDATE, PK_BC, PK_TOTALS,
-  PK_COUNT
+  PK_PRESTEP = 0, PK_DT, PK_STAGE, PK_NODE, PK_MU, PK_FLUX, PK_UPDATE, PK_BC, PK_TOTALS,
+  PK_CONVERT, PK_COUNT
 };
-static const char* kProfNames[PK_COUNT] = {"node", "dt_finalize", "mu_eff", "flux_xi",
-                                           "flux_eta", "flux_zeta", "update", "bc_jet",
-                                           "totals"};
+static const char* kProfNames[PK_COUNT] = {"prestep", "dt_finalize", "stage_fused", "node",
+                                           "mu_eff",  "flux",        "update",      "bc_jet",
+                                           "totals",  "convert"};
 
 struct ProfRec {
   int kind;
@@ -36,7 +36,8 @@ struct les_ctx {
   les_params p;
   Grid g;
   // workspace layout (byte offsets, 256-byte aligned)
-  size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_node, off_flux, off_rth, off_sc, off_part;
+  size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_hi, off_lo, off_node, off_flux, off_rth,
+      off_sc, off_part;
   size_t total;
   char* ws;
   bool grid_set;
@@ -147,8 +148,10 @@ void layout(les_ctx* c) {
   c->off_mk = o; o = align256(o + 2 * N * rs);
   c->off_sa = o; o = align256(o + 5 * N * rs);
   c->off_sb = o; o = align256(o + 5 * N * rs);
-  c->off_node = o; o = align256(o + 8 * N * rs);
-  c->off_flux = o; o = align256(o + 15 * N * rs);
+  c->off_hi = o; o = align256(o + (mixed ? 5 * N * sizeof(float) : 0));
+  c->off_lo = o; o = align256(o + (mixed ? 5 * N * sizeof(float) : 0));
+  c->off_node = o; o = align256(o + (mixed ? 0 : 8 * N * sizeof(double)));
+  c->off_flux = o; o = align256(o + (mixed ? 0 : 15 * N * sizeof(double)));
   c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
   c->off_sc = o; o = align256(o + sizeof(DevScalars));
   c->off_part = o; o = align256(o + 5 * (size_t)lesjet::kMaxPartials * sizeof(double));
@@ -160,68 +163,118 @@ T* at(les_ctx* c, size_t off) {
   return reinterpret_cast<T*>(c->ws + off);
 }
 
-lesjet::StageIO stage_io(les_ctx* c) {
-  lesjet::StageIO io;
-  const bool mixed = c->p.precision == LES_PREC_MIXED;
-  io.Qin = nullptr;
-  io.qin_is_double = 1;
-  io.M = mixed ? (const void*)at<float>(c, c->off_m32) : (const void*)at<double>(c, c->off_m64);
-  io.node = c->ws + c->off_node;
-  io.mk = c->ws + c->off_mk;
-  io.flux = c->ws + c->off_flux;
-  io.partials = at<double>(c, c->off_part);
-  io.sc = at<DevScalars>(c, c->off_sc);
-  return io;
-}
-
 int ready(les_ctx* c) {
   if (!c) return LES_ERR_INVALID_ARG;
   if (!c->grid_set || !c->ws) return fail(c, LES_ERR_STATE, "les_set_grid has not been called");
   return LES_OK;
 }
 
-// One residual evaluation of state Qin into the interface-flux buffer.
-void residual(les_ctx* c, lesjet::StageIO& io, bool with_mu, bool with_dt, int advance,
-              const lesjet::Launch& L) {
-  const int prec = c->p.precision;
+bool is_mixed(const les_ctx* c) { return c->p.precision == LES_PREC_MIXED; }
+
+// ---- FP64 form: node, viscosity, per-direction flux and update passes
+lesjet::StageIO64 io64(les_ctx* c, const double* Qin) {
+  lesjet::StageIO64 io;
+  io.Qin = Qin;
+  io.M = at<double>(c, c->off_m64);
+  io.node = at<double>(c, c->off_node);
+  io.mk = at<double>(c, c->off_mk);
+  io.flux = at<double>(c, c->off_flux);
+  io.partials = at<double>(c, c->off_part);
+  io.sc = at<DevScalars>(c, c->off_sc);
+  return io;
+}
+
+void residual64(les_ctx* c, const lesjet::StageIO64& io, bool with_mu, bool with_dt,
+                int advance, const lesjet::Launch& L) {
   {
     ProfScope ps(c, PK_NODE, L.s);
-    lesjet::launch_node(prec, c->g, c->p, io, with_dt, L);
+    lesjet::launch_node64(c->g, c->p, io, with_dt, L);
   }
   if (with_dt) {
     ProfScope ps(c, PK_DT, L.s);
-    lesjet::launch_dt_finalize(c->p, io, advance, L);
+    lesjet::launch_dt_finalize(c->p, io.partials, io.sc, advance, L);
   }
   if (with_mu) {
     ProfScope ps(c, PK_MU, L.s);
-    lesjet::launch_mu(prec, c->g, c->p, io, L);
+    lesjet::launch_mu64(c->g, c->p, io, L);
   }
-  for (int d = 0; d < 3; ++d) {
-    ProfScope ps(c, PK_FLUX_XI + d, L.s);
-    lesjet::launch_flux(prec, c->g, c->p, io, d, L);
-  }
+  ProfScope ps(c, PK_FLUX, L.s);
+  for (int d = 0; d < 3; ++d) lesjet::launch_flux64(c->g, c->p, io, d, L);
 }
 
+// ---- mixed form: float pair (hi, lo) state in the workspace
+void split_state(les_ctx* c, const double* Q, const lesjet::Launch& L) {
+  ProfScope ps(c, PK_CONVERT, L.s);
+  lesjet::launch_split(5 * c->g.N, Q, at<float>(c, c->off_hi), at<float>(c, c->off_lo), L);
+}
+void join_state(les_ctx* c, double* Q, const lesjet::Launch& L) {
+  ProfScope ps(c, PK_CONVERT, L.s);
+  lesjet::launch_join(5 * c->g.N, at<float>(c, c->off_hi), at<float>(c, c->off_lo), Q, L);
+}
+
+// mu_eff/kappa_eff of the float state (frozen for the step) and the block
+// minima of the CFL step; sc == nullptr leaves the status word alone.
+void prestep32(les_ctx* c, const float* Qs, DevScalars* sc, const lesjet::Launch& L) {
+  ProfScope ps(c, PK_PRESTEP, L.s);
+  lesjet::launch_prestep(c->g, c->p, Qs, at<float>(c, c->off_m32), at<float>(c, c->off_mk),
+                         at<double>(c, c->off_part), sc, L);
+}
+
+lesjet::FusedIO fused_io(les_ctx* c, const void* Qin, void* out) {
+  lesjet::FusedIO io;
+  io.Qin = Qin;
+  io.Q0 = at<float>(c, c->off_hi);
+  io.Q0lo = at<float>(c, c->off_lo);
+  io.M = at<float>(c, c->off_m32);
+  io.mk = at<float>(c, c->off_mk);
+  io.sc = at<DevScalars>(c, c->off_sc);
+  io.out = out;
+  return io;
+}
+
+// One time step (Table tab:JAZzY): viscosity + CFL step from Q^n, five
+// stages Q^(l) = Q^(0) - alpha_l dt J RHS(Q^(l-1)), boundary conditions at
+// t^{n+1}.  In the mixed form the state must already be split into (hi, lo).
 void rk_step(les_ctx* c, double* Q, cudaStream_t s) {
   lesjet::Launch L{s, &c->launches};
-  const int prec = c->p.precision;
-  const bool mixed = prec == LES_PREC_MIXED;
-  lesjet::StageIO io = stage_io(c);
-  void* SA = c->ws + c->off_sa;
-  void* SB = c->ws + c->off_sb;
+  DevScalars* sc = at<DevScalars>(c, c->off_sc);
+  if (!is_mixed(c)) {
+    double* SA = at<double>(c, c->off_sa);
+    double* SB = at<double>(c, c->off_sb);
+    for (int l = 1; l <= 5; ++l) {
+      const double* in = (l == 1) ? Q : ((l % 2 == 0) ? SA : SB);
+      double* out = (l == 5) ? Q : ((l % 2 == 1) ? SA : SB);
+      lesjet::StageIO64 io = io64(c, in);
+      residual64(c, io, l == 1 || !c->p.freeze_visc, l == 1, 1, L);
+      ProfScope ps(c, PK_UPDATE, s);
+      lesjet::launch_update64(c->g, io, Q, kAlpha[l - 1], l == 5 ? 2 : 1, out, L);
+    }
+    if (c->p.bc == LES_BC_JET) {
+      ProfScope ps(c, PK_BC, s);
+      lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth),
+                            sc, 0, 0.0, L);
+    }
+    return;
+  }
+  float* hi = at<float>(c, c->off_hi);
+  float* SA = at<float>(c, c->off_sa);
+  float* SB = at<float>(c, c->off_sb);
+  prestep32(c, hi, sc, L);
+  {
+    ProfScope ps(c, PK_DT, s);
+    lesjet::launch_dt_finalize(c->p, at<double>(c, c->off_part), sc, 1, L);
+  }
   for (int l = 1; l <= 5; ++l) {
-    const void* in = (l == 1) ? (const void*)Q : ((l % 2 == 0) ? SA : SB);
-    void* out = (l == 5) ? (void*)Q : ((l % 2 == 1) ? SA : SB);
-    io.Qin = in;
-    io.qin_is_double = (l == 1 || !mixed) ? 1 : 0;
-    residual(c, io, l == 1 || !c->p.freeze_visc, l == 1, 1, L);
-    ProfScope ps(c, PK_UPDATE, s);
-    lesjet::launch_update(prec, c->g, io, Q, kAlpha[l - 1], l == 5 ? 2 : 1, out, L);
+    const float* in = (l == 1) ? hi : ((l % 2 == 0) ? SA : SB);
+    float* out = (l == 5) ? nullptr : ((l % 2 == 1) ? SA : SB);
+    if (l > 1 && !c->p.freeze_visc) prestep32(c, in, nullptr, L);  // Reading A17, unfrozen
+    ProfScope ps(c, PK_STAGE, s);
+    lesjet::launch_stage_fused(l == 5 ? 2 : 1, c->g, c->p, fused_io(c, in, out), kAlpha[l - 1], L);
   }
   if (c->p.bc == LES_BC_JET) {
     ProfScope ps(c, PK_BC, s);
-    lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth),
-                          io.sc, 0, 0.0, L);
+    lesjet::launch_bc_jet_hl(c->g, c->p, hi, at<float>(c, c->off_lo), at<double>(c, c->off_m64),
+                             at<double>(c, c->off_rth), sc, L);
   }
 }
 
@@ -244,6 +297,8 @@ int les_create(const les_params* p, int ni, int nj, int nk, les_ctx** out) {
   if (ni < 5 || nj < 5 || nk < 5) return LES_ERR_SHAPE;
   const long long N = (long long)ni * nj * nk;
   if (N >= (1LL << 40)) return LES_ERR_SHAPE;
+  // the mixed form indexes each field with 32 bits
+  if (p->precision == LES_PREC_MIXED && N >= (1LL << 31)) return LES_ERR_SHAPE;
   les_ctx* c = new (std::nothrow) les_ctx();
   if (!c) return LES_ERR_INVALID_ARG;
   c->p = *p;
@@ -335,12 +390,15 @@ int les_mu_eff(les_ctx* c, const double* Q, double* MK, les_stream_t stream) {
   if (!Q || !MK) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
   if (!aligned16(Q) || !aligned16(MK)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
   lesjet::Launch L{(cudaStream_t)stream, &c->launches};
-  lesjet::StageIO io = stage_io(c);
-  io.Qin = Q;
-  io.qin_is_double = 1;
-  lesjet::launch_node(c->p.precision, c->g, c->p, io, false, L);
-  lesjet::launch_mu(c->p.precision, c->g, c->p, io, L);
-  lesjet::launch_mk_to_double(c->p.precision, c->g, io.mk, MK, L);
+  if (is_mixed(c)) {
+    split_state(c, Q, L);
+    prestep32(c, at<float>(c, c->off_hi), nullptr, L);
+  } else {
+    lesjet::StageIO64 io = io64(c, Q);
+    lesjet::launch_node64(c->g, c->p, io, false, L);
+    lesjet::launch_mu64(c->g, c->p, io, L);
+  }
+  lesjet::launch_mk_to_double(c->p.precision, c->g, c->ws + c->off_mk, MK, L);
   return cuda_check(c, "les_mu_eff");
 }
 
@@ -351,11 +409,16 @@ int les_rhs(les_ctx* c, const double* Q, double* R, les_stream_t stream) {
   if (!aligned16(Q) || !aligned16(R)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
   if (Q == R) return fail(c, LES_ERR_INVALID_ARG, "Q and R must not alias");
   lesjet::Launch L{(cudaStream_t)stream, &c->launches};
-  lesjet::StageIO io = stage_io(c);
-  io.Qin = Q;
-  io.qin_is_double = 1;
-  residual(c, io, true, false, 0, L);
-  lesjet::launch_update(c->p.precision, c->g, io, Q, 0.0, 0, R, L);
+  if (is_mixed(c)) {
+    split_state(c, Q, L);
+    float* hi = at<float>(c, c->off_hi);
+    prestep32(c, hi, nullptr, L);
+    lesjet::launch_stage_fused(0, c->g, c->p, fused_io(c, hi, R), 0.0, L);
+  } else {
+    lesjet::StageIO64 io = io64(c, Q);
+    residual64(c, io, true, false, 0, L);
+    lesjet::launch_update64(c->g, io, Q, 0.0, 0, R, L);
+  }
   return cuda_check(c, "les_rhs");
 }
 
@@ -366,11 +429,14 @@ int les_time_step(les_ctx* c, const double* Q, double* dt_out, les_stream_t stre
   if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
   cudaStream_t s = (cudaStream_t)stream;
   lesjet::Launch L{s, &c->launches};
-  lesjet::StageIO io = stage_io(c);
-  io.Qin = Q;
-  io.qin_is_double = 1;
-  lesjet::launch_node(c->p.precision, c->g, c->p, io, true, L);
-  lesjet::launch_dt_finalize(c->p, io, 0, L);
+  DevScalars* sc = at<DevScalars>(c, c->off_sc);
+  if (is_mixed(c)) {
+    split_state(c, Q, L);
+    prestep32(c, at<float>(c, c->off_hi), sc, L);
+  } else {
+    lesjet::launch_node64(c->g, c->p, io64(c, Q), true, L);
+  }
+  lesjet::launch_dt_finalize(c->p, at<double>(c, c->off_part), sc, 0, L);
   if ((rc = cuda_check(c, "les_time_step")) != LES_OK) return rc;
   DevScalars h;
   if ((rc = read_scalars(c, &h, s)) != LES_OK) return rc;
@@ -404,7 +470,11 @@ int les_rk_step(les_ctx* c, double* Q, les_stream_t stream) {
   if (rc != LES_OK) return rc;
   if (!Q) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
   if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
-  rk_step(c, Q, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  if (is_mixed(c)) split_state(c, Q, L);
+  rk_step(c, Q, s);
+  if (is_mixed(c)) join_state(c, Q, L);
   return cuda_check(c, "les_rk_step");
 }
 
@@ -415,9 +485,14 @@ int les_run_n_steps(les_ctx* c, int n, double* Q, les_diag* diag, les_stream_t s
   if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
   cudaStream_t s = (cudaStream_t)stream;
   lesjet::Launch L{s, &c->launches};
+  if (is_mixed(c)) split_state(c, Q, L);
   for (int i = 0; i < n; ++i) rk_step(c, Q, s);
-  lesjet::launch_totals(c->g, Q, at<double>(c, c->off_m64), at<double>(c, c->off_part),
-                        at<DevScalars>(c, c->off_sc), L);
+  if (is_mixed(c)) join_state(c, Q, L);
+  {
+    ProfScope ps(c, PK_TOTALS, s);
+    lesjet::launch_totals(c->g, Q, at<double>(c, c->off_m64), at<double>(c, c->off_part),
+                          at<DevScalars>(c, c->off_sc), L);
+  }
   if ((rc = cuda_check(c, "les_run_n_steps")) != LES_OK) return rc;
   DevScalars h;
   if ((rc = read_scalars(c, &h, s)) != LES_OK) return rc;

@@ -5,37 +5,57 @@
 
 namespace lesjet {
 
+// State accessors: plain FP64 state, or the mixed form's unevaluated float
+// pair hi + lo (read and written in FP64 here, surface nodes only).
+struct AccD {
+  double* q;
+  __device__ __forceinline__ double ld(long long i) const { return q[i]; }
+  __device__ __forceinline__ void st(long long i, double v) const { q[i] = v; }
+};
+struct AccHL {
+  float* hi;
+  float* lo;
+  __device__ __forceinline__ double ld(long long i) const { return (double)hi[i] + (double)lo[i]; }
+  __device__ __forceinline__ void st(long long i, double v) const {
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
+};
+
 struct JetBC {
   double gamma, Mj, r_jet, theta_m, force_width;
   double St[4];
   double amp[16];
 };
 
-__device__ __forceinline__ void store_prim(double* __restrict__ Q, long long N, long long n,
-                                           double gamma, double rho, double u, double v, double w,
-                                           double p) {
-  Q[n] = rho;
-  Q[N + n] = rho * u;
-  Q[2 * N + n] = rho * v;
-  Q[3 * N + n] = rho * w;
-  Q[4 * N + n] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
+template <class Acc>
+__device__ __forceinline__ void store_prim(const Acc& Q, long long N, long long n, double gamma,
+                                           double rho, double u, double v, double w, double p) {
+  Q.st(n, rho);
+  Q.st(N + n, rho * u);
+  Q.st(2 * N + n, rho * v);
+  Q.st(3 * N + n, rho * w);
+  Q.st(4 * N + n, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w));
 }
 
-__device__ __forceinline__ void load_prim(const double* __restrict__ Q, long long N, long long n,
-                                          double gamma, double& rho, double& u, double& v,
-                                          double& w, double& p) {
-  rho = Q[n];
-  u = Q[N + n] / rho;
-  v = Q[2 * N + n] / rho;
-  w = Q[3 * N + n] / rho;
-  p = (gamma - 1.0) * (Q[4 * N + n] - 0.5 * rho * (u * u + v * v + w * w));
+template <class Acc>
+__device__ __forceinline__ void load_prim(const Acc& Q, long long N, long long n, double gamma,
+                                          double& rho, double& u, double& v, double& w,
+                                          double& p) {
+  rho = Q.ld(n);
+  u = Q.ld(N + n) / rho;
+  v = Q.ld(2 * N + n) / rho;
+  w = Q.ld(3 * N + n) / rho;
+  p = (gamma - 1.0) * (Q.ld(4 * N + n) - 0.5 * rho * (u * u + v * v + w * w));
 }
 
 // Entrance i = 0: rho = 1, p = 1/gamma, v = w = 0, u = jet profile plus the
 // 16-mode forcing sum a_{mf} g(r) cos(m theta - 2 pi St_f Mj t).
+template <class Acc>
 __global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
                             const DevScalars* __restrict__ sc, int use_host_t, double t_host,
-                            double* __restrict__ Q) {
+                            Acc Q) {
   const long long plane = (long long)g.n[1] * g.n[2];
   const double t = use_host_t ? t_host : sc->t;
   const double two_pi = 6.283185307179586476925286766559;
@@ -57,8 +77,8 @@ __global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
 // Far field j = nj-1 (0 < i < ni-1): Riemann invariants along the unit
 // eta-normal with R+ from the adjacent interior node and R- from the free
 // stream at rest (rho = 1, p = 1/gamma, a = 1); four branches by q_n/a.
-__global__ void k_bc_farfield(Grid g, double gamma, const double* __restrict__ M,
-                              double* __restrict__ Q) {
+template <class Acc>
+__global__ void k_bc_farfield(Grid g, double gamma, const double* __restrict__ M, Acc Q) {
   const int ni = g.n[0], nj = g.n[1], nk = g.n[2];
   const long long count = (long long)(ni - 2) * nk;
   const long long N = g.N;
@@ -81,7 +101,7 @@ __global__ void k_bc_farfield(Grid g, double gamma, const double* __restrict__ M
     const double Mn = qne / ae;
     if (Mn >= 1.0) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) Q[q * N + nf] = Q[q * N + ne];
+      for (int q = 0; q < 5; ++q) Q.st(q * N + nf, Q.ld(q * N + ne));
     } else if (Mn >= 0.0) {
       const double dq = qnf - qne;
       const double rf = pow(pow(rho, gamma) * af * af / (gamma * p), 1.0 / gm1);
@@ -97,7 +117,8 @@ __global__ void k_bc_farfield(Grid g, double gamma, const double* __restrict__ M
 
 // Inner ring j = 0 (0 < i < ni-1): azimuthal mean of the first interior
 // ring, one block per axial station, fixed-order tree (deterministic).
-__global__ void k_bc_ring(Grid g, double* __restrict__ Q) {
+template <class Acc>
+__global__ void k_bc_ring(Grid g, Acc Q) {
   const int i = 1 + blockIdx.x;
   const int nk = g.n[2];
   const long long N = g.N;
@@ -106,7 +127,7 @@ __global__ void k_bc_ring(Grid g, double* __restrict__ Q) {
   const long long base1 = idx3(g, i, 1, 0), base0 = idx3(g, i, 0, 0);
   for (int k = threadIdx.x; k < nk; k += blockDim.x)
 #pragma unroll
-    for (int q = 0; q < 5; ++q) s[q] += Q[q * N + base1 + k];
+    for (int q = 0; q < 5; ++q) s[q] += Q.ld(q * N + base1 + k);
 #pragma unroll
   for (int q = 0; q < 5; ++q)
     for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
@@ -125,14 +146,14 @@ __global__ void k_bc_ring(Grid g, double* __restrict__ Q) {
   __syncthreads();
   for (int k = threadIdx.x; k < nk; k += blockDim.x)
 #pragma unroll
-    for (int q = 0; q < 5; ++q) Q[q * N + base0 + k] = red[q][0];
+    for (int q = 0; q < 5; ++q) Q.st(q * N + base0 + k, red[q][0]);
 }
 
 // Exit i = ni-1 from the updated column i = ni-2: supersonic (q/a >= 1 along
 // the unit xi-normal) copies; subsonic takes p = 1/gamma and extrapolates the
 // velocity and the internal energy p/((gamma-1) rho).
-__global__ void k_bc_exit(Grid g, double gamma, const double* __restrict__ M,
-                          double* __restrict__ Q) {
+template <class Acc>
+__global__ void k_bc_exit(Grid g, double gamma, const double* __restrict__ M, Acc Q) {
   const int ni = g.n[0];
   const long long plane = (long long)g.n[1] * g.n[2];
   const long long N = g.N;
@@ -148,15 +169,15 @@ __global__ void k_bc_exit(Grid g, double gamma, const double* __restrict__ M,
     const double qn = (u * ex + v * ey + w * ez) * inv;
     if (qn / ae >= 1.0) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) Q[q * N + nx_] = Q[q * N + ne];
+      for (int q = 0; q < 5; ++q) Q.st(q * N + nx_, Q.ld(q * N + ne));
     } else {
       const double eint = p / (gm1 * rho);
       const double rf = (1.0 / gamma) / (gm1 * eint);
-      Q[nx_] = rf;
-      Q[N + nx_] = rf * u;
-      Q[2 * N + nx_] = rf * v;
-      Q[3 * N + nx_] = rf * w;
-      Q[4 * N + nx_] = rf * (eint + 0.5 * (u * u + v * v + w * w));
+      Q.st(nx_, rf);
+      Q.st(N + nx_, rf * u);
+      Q.st(2 * N + nx_, rf * v);
+      Q.st(3 * N + nx_, rf * w);
+      Q.st(4 * N + nx_, rf * (eint + 0.5 * (u * u + v * v + w * w)));
     }
   }
 }
@@ -212,7 +233,8 @@ static int nblocks(long long count) {
   return (int)(b < 1 ? 1 : b);
 }
 
-void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* M64,
+template <class Acc>
+static void bc_jet(const Grid& g, const les_params& p, Acc Q, const double* M64,
                    const double* rth, const DevScalars* sc, int use_host_t, double t_host,
                    const Launch& L) {
   JetBC b;
@@ -224,11 +246,22 @@ void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* 
   for (int i = 0; i < 4; ++i) b.St[i] = p.St[i];
   for (int i = 0; i < 16; ++i) b.amp[i] = p.amp[i];
   const long long plane = (long long)g.n[1] * g.n[2];
-  k_bc_inflow<<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, sc, use_host_t, t_host, Q);
-  k_bc_farfield<<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M64, Q);
-  k_bc_ring<<<g.n[0] - 2, 256, 0, L.s>>>(g, Q);
-  k_bc_exit<<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M64, Q);
+  k_bc_inflow<Acc><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, sc, use_host_t, t_host, Q);
+  k_bc_farfield<Acc><<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M64, Q);
+  k_bc_ring<Acc><<<g.n[0] - 2, 256, 0, L.s>>>(g, Q);
+  k_bc_exit<Acc><<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M64, Q);
   *L.counter += 4;
+}
+
+void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* M64,
+                   const double* rth, const DevScalars* sc, int use_host_t, double t_host,
+                   const Launch& L) {
+  bc_jet(g, p, AccD{Q}, M64, rth, sc, use_host_t, t_host, L);
+}
+
+void launch_bc_jet_hl(const Grid& g, const les_params& p, float* hi, float* lo, const double* M64,
+                      const double* rth, const DevScalars* sc, const Launch& L) {
+  bc_jet(g, p, AccHL{hi, lo}, M64, rth, sc, 0, 0.0, L);
 }
 
 void launch_totals(const Grid& g, const double* Q, const double* M64, double* partials,

@@ -1,0 +1,912 @@
+// fused.cu -- one kernel per Runge-Kutta stage (residual + update fused).
+//
+// A CTA owns a TJ x TK = 16 x 32 tile of (eta, zeta) columns and marches along
+// xi over a chunk of axial planes.  Per plane it stages the conserved state
+// of the tile plus a two-node halo in shared memory with cp.async (one plane
+// ahead), derives the primitives and the anisotropic spectral radii once per
+// node, and keeps the own column's data of the neighbouring planes in
+// registers.  Every interface flux (centred inviscid flux minus J^-1 times
+// the Turkel-Vatsa dissipation minus the viscous flux) is computed once: the
+// xi interface i+1/2 is carried in registers to the next plane, the eta and
+// zeta interfaces are exchanged through shared memory.  The stage update
+// Q^(l) = Q^(0) - alpha_l dt J RHS is applied in the epilogue, so the residual
+// never touches HBM.
+//
+// This is the FP32-mixed form: it computes in float, stores the stage states
+// and metrics in float, and keeps Q^(0) as an unevaluated float pair (hi +
+// lo) updated with compensated (TwoSum) arithmetic in the last stage, so the
+// steady state issues no FP64 instruction on GB300's narrow FP64 pipe.  The
+// translation unit is built with approximate FP32 division and square root
+// (their error is inside the form's measured error budget).
+#include "lesjet_dev.cuh"
+#include "lesjet_host.h"
+
+namespace lesjet {
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  if (sizeof(T) == 8)
+    cp_async8(smem, gmem);
+  else
+    cp_async4(smem, gmem);
+}
+
+// Wrapped index along direction d, or -1 outside a non-periodic direction.
+__device__ __forceinline__ int wrap_idx(const Grid& g, int d, int v) {
+  const int n = g.n[d];
+  if (g.per[d]) {
+    v %= n;
+    return v < 0 ? v + n : v;
+  }
+  return (v >= 0 && v < n) ? v : -1;
+}
+
+// ----------------------------------------------------------- interface flux
+// Flux through the interface between nodes a and b (b = a + e_D): centred
+// inviscid flux (Eqs. hat-flux-G, inv_flux_vec) minus J^-1 d (Eqs.
+// dissip_term, eps_2/4_dissip with the boundary closure of the centerline
+// section) minus the viscous + SGS flux (Eqs. hat-flux-Ev/Fv/Gv, tau_mod,
+// q_mod with Fourier's sign) from compact interface gradients.
+// m*[0..8] = xi_x .. zeta_z, m*[9] = J^-1; W* = (rho, rho u, rho v, rho w,
+// e + p); dphi[q][t] = computational derivative of u, v, w, T along t.
+template <int D, typename R>
+__device__ __forceinline__ void iface_flux(const Consts<R>& K, const R* Wm, const R* Wa,
+                                           const R* Wb, const R* Wp, bool has_m, bool has_p,
+                                           R nua, R nub, R lba, R lbb, const R* ma, const R* mb,
+                                           R pa, R pb, R ua, R va, R wa, R ub, R vb, R wb,
+                                           const R (&dphi)[4][3], R mua, R mub, R kaa, R kab,
+                                           R F[5]) {
+  const R tha = ma[3 * D] * ua + ma[3 * D + 1] * va + ma[3 * D + 2] * wa;
+  const R thb = mb[3 * D] * ub + mb[3 * D + 1] * vb + mb[3 * D + 2] * wb;
+  const R Ja = ma[9], Jb = mb[9];
+  R Fc[5];
+  // W[0..3] = Q[0..3]; W[4] = e + p, so (e + p) Th = W[4] Th
+  Fc[0] = Ja * (Wa[0] * tha) + Jb * (Wb[0] * thb);
+  Fc[1] = Ja * (Wa[1] * tha + pa * ma[3 * D]) + Jb * (Wb[1] * thb + pb * mb[3 * D]);
+  Fc[2] = Ja * (Wa[2] * tha + pa * ma[3 * D + 1]) + Jb * (Wb[2] * thb + pb * mb[3 * D + 1]);
+  Fc[3] = Ja * (Wa[3] * tha + pa * ma[3 * D + 2]) + Jb * (Wb[3] * thb + pb * mb[3 * D + 2]);
+  Fc[4] = Ja * (Wa[4] * tha) + Jb * (Wb[4] * thb);
+  const R eps2 = K.k2 * dev_max(nua, nub);
+  const R eps4 = dev_max(R(0), K.k4 - eps2);
+  const R Jh = R(0.5) * (Ja + Jb);
+  const R lJ = R(0.5) * (lba + lbb) * Jh;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const R D1 = Wb[q] - Wa[q];
+    const R Dm = has_m ? Wa[q] - Wm[q] : -D1;
+    const R Dp = has_p ? Wp[q] - Wb[q] : -D1;
+    const R D3 = Dp - R(2) * D1 + Dm;
+    F[q] = R(0.5) * Fc[q] - lJ * (eps2 * D1 - eps4 * D3);
+  }
+  R mh[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) mh[t] = R(0.5) * (ma[t] + mb[t]);
+  R gr[4][3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+      gr[q][x] = mh[x] * dphi[q][0] + mh[3 + x] * dphi[q][1] + mh[6 + x] * dphi[q][2];
+  const R mu = R(0.5) * (mua + mub);
+  const R kap = R(0.5) * (kaa + kab);
+  const R div = gr[0][0] + gr[1][1] + gr[2][2];
+  const R two3 = R(2.0 / 3.0);
+  const R txx = mu * (R(2) * gr[0][0] - two3 * div);
+  const R tyy = mu * (R(2) * gr[1][1] - two3 * div);
+  const R tzz = mu * (R(2) * gr[2][2] - two3 * div);
+  const R txy = mu * (gr[0][1] + gr[1][0]);
+  const R txz = mu * (gr[0][2] + gr[2][0]);
+  const R tyz = mu * (gr[1][2] + gr[2][1]);
+  const R uf = R(0.5) * (ua + ub), vf = R(0.5) * (va + vb), wf = R(0.5) * (wa + wb);
+  const R bx = txx * uf + txy * vf + txz * wf + kap * gr[3][0];
+  const R by = txy * uf + tyy * vf + tyz * wf + kap * gr[3][1];
+  const R bz = txz * uf + tyz * vf + tzz * wf + kap * gr[3][2];
+  const R mx = mh[3 * D], my = mh[3 * D + 1], mz = mh[3 * D + 2];
+  F[1] -= Jh * (mx * txx + my * txy + mz * txz);
+  F[2] -= Jh * (mx * txy + my * tyy + mz * tyz);
+  F[3] -= Jh * (mx * txz + my * tyz + mz * tzz);
+  F[4] -= Jh * (mx * bx + my * by + mz * bz);
+}
+
+// Pressure sensor from the three pressures around a (possibly shifted) node.
+template <typename R>
+__device__ __forceinline__ R sensor3(R pm, R p0, R pp) {
+  return dev_abs(pp - R(2) * p0 + pm) / (pp + R(2) * p0 + pm);
+}
+
+// Radii lambda_d = |U_d| + a |grad d| and the scaled lbar_d of one node.
+template <typename R>
+__device__ __forceinline__ void node_lbar(const R* m, R u, R v, R w, R T, R lb[3]) {
+  const R a = dev_sqrt(T);
+  R l[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const R mx = m[3 * d], my = m[3 * d + 1], mz = m[3 * d + 2];
+    l[d] = dev_abs(mx * u + my * v + mz * w) + a * dev_sqrt(mx * mx + my * my + mz * mz);
+  }
+  const R s01 = dev_sqrt(l[0] * l[1]), s02 = dev_sqrt(l[0] * l[2]), s12 = dev_sqrt(l[1] * l[2]);
+  lb[0] = l[0] + s01 + s02;
+  lb[1] = l[1] + s01 + s12;
+  lb[2] = l[2] + s02 + s12;
+}
+
+template <typename TM, typename R>
+__device__ __forceinline__ void load_metrics(const TM* __restrict__ M, long long N, long long n,
+                                             R m[10]) {
+#pragma unroll
+  for (int t = 0; t < 10; ++t) m[t] = (R)__ldg(M + t * N + n);
+}
+
+// --------------------------------------------------------------- prestep
+// Once per time step, from Q^n: block minima of 1/(sum of radii) for the CFL
+// step, the non-finite flag, and mu_eff / kappa_eff (frozen over the five
+// stages).  Q^n is read as TQ (double, or the float hi part of the mixed
+// state); gradients for the SGS model use the node-centred central
+// differences (one-sided at non-periodic faces).
+template <typename R, typename TQ, typename TM>
+__device__ __forceinline__ void prim_uvw(const TQ* __restrict__ Q, long long N, long long n, R& u,
+                                         R& v, R& w) {
+  const R rho = (R)Q[n];
+  const R ir = R(1) / rho;
+  u = (R)Q[N + n] * ir;
+  v = (R)Q[2 * N + n] * ir;
+  w = (R)Q[3 * N + n] * ir;
+}
+
+template <typename R, typename TQ, typename TM>
+__global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* __restrict__ Q,
+                                                 const TM* __restrict__ M, R* __restrict__ mk,
+                                                 double* __restrict__ partials,
+                                                 DevScalars* __restrict__ sc) {
+  const long long N = g.N;
+  R local_min = R(1e30);
+  int bad = 0;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const R rho = (R)Q[n];
+    const R ir = R(1) / rho;
+    const R u = (R)Q[N + n] * ir, v = (R)Q[2 * N + n] * ir, w = (R)Q[3 * N + n] * ir;
+    const R p = K.gm1 * ((R)Q[4 * N + n] - R(0.5) * rho * (u * u + v * v + w * w));
+    const R T = K.gamma * p * ir;
+    const R a = dev_sqrt(T);
+    R m[10];
+    load_metrics(M, N, n, m);
+    R lsum = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const R mx = m[3 * d], my = m[3 * d + 1], mz = m[3 * d + 2];
+      lsum += dev_abs(mx * u + my * v + mz * w) + a * dev_sqrt(mx * mx + my * my + mz * mz);
+    }
+    const R inv = R(1) / lsum;
+    if (!(rho > R(0)) || !(p > R(0)) || !(inv > R(0)) || !(inv < R(1e30))) bad = 1;
+    local_min = inv < local_min ? inv : local_min;
+
+    const R mu_l = K.mu_scale * T * dev_sqrt(T) * (R(1) + K.S_suth) / (T + K.S_suth);
+    R mu_s = R(0);
+    if (K.sgs != LES_SGS_NONE) {
+      int c[3];
+      decompose(g, n, c);
+      R dd[3][3];  // dd[q][d] = computational derivative of u_q along d
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const long long s = g.stride[d];
+        const int nd = g.n[d];
+        R fm[3], f0[3], fp[3];
+        long long np_, nm_;
+        int mode;  // 0 central, 1 one-sided low face, 2 one-sided high face
+        if (g.per[d]) {
+          np_ = (c[d] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
+          nm_ = (c[d] == 0) ? n + (long long)(nd - 1) * s : n - s;
+          mode = 0;
+        } else if (c[d] == 0) {
+          np_ = n + s;
+          nm_ = n + 2 * s;
+          mode = 1;
+        } else if (c[d] == nd - 1) {
+          np_ = n - 2 * s;
+          nm_ = n - s;
+          mode = 2;
+        } else {
+          np_ = n + s;
+          nm_ = n - s;
+          mode = 0;
+        }
+        prim_uvw<R, TQ, TM>(Q, N, np_, fp[0], fp[1], fp[2]);
+        prim_uvw<R, TQ, TM>(Q, N, nm_, fm[0], fm[1], fm[2]);
+        f0[0] = u;
+        f0[1] = v;
+        f0[2] = w;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (mode == 0)
+            dd[q][d] = R(0.5) * (fp[q] - fm[q]);
+          else if (mode == 1)  // (-3 f0 + 4 f1 - f2)/2 with f1 = fp, f2 = fm
+            dd[q][d] = R(0.5) * (R(-3) * f0[q] + R(4) * fp[q] - fm[q]);
+          else  // (3 f0 - 4 f_{-1} + f_{-2})/2 with f_{-1} = fm, f_{-2} = fp
+            dd[q][d] = R(0.5) * (R(3) * f0[q] - R(4) * fm[q] + fp[q]);
+        }
+      }
+      R gr[3][3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int x = 0; x < 3; ++x) gr[q][x] = m[x] * dd[q][0] + m[3 + x] * dd[q][1] + m[6 + x] * dd[q][2];
+      const R delta = cbrt(m[9]);
+      if (K.sgs == LES_SGS_SMAGORINSKY) {
+        R ss = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const R sij = R(0.5) * (gr[i][j] + gr[j][i]);
+            ss += sij * sij;
+          }
+        mu_s = rho * (delta * delta) * K.cs2 * dev_sqrt(R(2) * ss);
+      } else {
+        R aa = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) aa += gr[i][j] * gr[i][j];
+        R be[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            be[i][j] = delta * delta * (gr[i][0] * gr[j][0] + gr[i][1] * gr[j][1] + gr[i][2] * gr[j][2]);
+        R B = be[0][0] * be[1][1] - be[0][1] * be[0][1] + be[0][0] * be[2][2] -
+              be[0][2] * be[0][2] + be[1][1] * be[2][2] - be[1][2] * be[1][2];
+        B = B > R(0) ? B : R(0);
+        mu_s = (aa == R(0)) ? R(0) : rho * K.cs2 * dev_sqrt(B / aa);
+      }
+    }
+    mk[n] = mu_l + mu_s;
+    mk[N + n] = mu_l * K.inv_gm1_pr + mu_s * K.inv_gm1_prs;
+  }
+  __shared__ R smin[32];
+  __shared__ int sbad[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    // every lane executes each shuffle unconditionally (full mask)
+    const R o = __shfl_xor_sync(0xffffffffu, local_min, off);
+    local_min = local_min < o ? local_min : o;
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    smin[threadIdx.x >> 5] = local_min;
+    sbad[threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool live = threadIdx.x < (blockDim.x >> 5);
+    R mm = live ? smin[threadIdx.x] : R(1e30);
+    int bb = live ? sbad[threadIdx.x] : 0;
+    for (int off = 16; off > 0; off >>= 1) {
+      const R o = __shfl_xor_sync(0xffffffffu, mm, off);
+      mm = mm < o ? mm : o;
+      bb |= __shfl_xor_sync(0xffffffffu, bb, off);
+    }
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = (double)mm;
+      if (bb && sc) atomicOr(&sc->status, 1);
+    }
+  }
+}
+
+// ------------------------------------------------------------ fused stage
+enum { FMODE_RHS = 0, FMODE_STAGE = 1, FMODE_LAST = 2 };
+
+// Tile of FTJ x FTK (eta, zeta) columns, one thread per column.
+constexpr int FTJ = 16, FTK = 32, FNT = FTJ * FTK;
+// Shared-memory rows are circular in zeta with period SK: tile column kk in
+// [-2, FTK+1] lives at column kk (kk >= 0) or SK + kk (kk < 0), so the 32
+// tile columns start 16-byte aligned and the halo wraps around the row end.
+constexpr int SK = 36;
+constexpr int R2 = FTJ + 4, R1 = FTJ + 2;  // rows with a 2-node / 1-node halo
+constexpr int PL2 = R2 * SK, PL1 = R1 * SK;
+__host__ __device__ constexpr int colk(int kk) { return kk < 0 ? kk + SK : kk; }
+
+// Shared-memory plan (floats):
+//   sQ[3][5][PL2]  conserved state of planes i, i+1, i+2 (2-node halo)
+//   sP[3][5][PL2]  u v w T p of planes i-1, i, i+1
+//   sM[3][10][PL1] metrics of planes i, i+1, i+2 (1-node halo)
+//   sK[3][2][PL1]  mu_eff kappa_eff of planes i, i+1, i+2
+//   sL[2][3][PL1]  lbar of planes i, i+1
+//   sFe[5][FTJ+1][FTK], sFz[5][FTJ][FTK+1]  eta / zeta interface fluxes
+constexpr int OFF_P = 3 * 5 * PL2, OFF_M = OFF_P + 3 * 5 * PL2, OFF_K = OFF_M + 3 * 10 * PL1,
+              OFF_L = OFF_K + 3 * 2 * PL1, OFF_FE = OFF_L + 2 * 3 * PL1,
+              OFF_FZ = OFF_FE + 5 * (FTJ + 1) * FTK, SMEM_FLOATS = OFF_FZ + 5 * FTJ * (FTK + 1);
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Per-field base pointers (32-bit indexing inside a field, N < 2^31).
+struct FusedPtrs {
+  const float* qin[5];  // stage input state
+  const float* hi[5];   // Q^(0) hi part
+  float* lo[5];         // Q^(0) lo part (last stage)
+  float* hiw[5];        // Q^(0) hi part, written in the last stage
+  const float* m[10];   // metrics
+  const float* mk[2];   // mu_eff, kappa_eff
+  float* out[5];        // stage output
+  double* outd[5];      // residual output (RHS mode)
+};
+
+struct FusedGeom {
+  int ni, nj, nk;
+  int per[3];
+  int chunk;
+  int vec16;  // rows of every field start 16-byte aligned (nk % 4 == 0)
+};
+
+__device__ __forceinline__ int wrap_fast(int v, int n, int per) {
+  if (per) {
+    if (v < 0) v += n;
+    if (v >= n) v -= n;
+    if (v < 0 || v >= n) {  // tiles wider than a small periodic extent
+      v %= n;
+      if (v < 0) v += n;
+    }
+    return v;
+  }
+  return (v >= 0 && v < n) ? v : -1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(FNT, 1)
+    k_stage_fused(const FusedGeom G, const Consts<float> K, const FusedPtrs P,
+                  const DevScalars* __restrict__ sc, double alpha) {
+  extern __shared__ __align__(16) float smem[];
+  float* sQ = smem;
+  float* sP = smem + OFF_P;
+  float* sM = smem + OFF_M;
+  float* sK = smem + OFF_K;
+  float* sL = smem + OFF_L;
+  float* sFe = smem + OFF_FE;
+  float* sFz = smem + OFF_FZ;
+  const int ni = G.ni, nj = G.nj, nk = G.nk;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int k0 = blockIdx.x * FTK, j0 = blockIdx.y * FTJ;
+  const int ib = blockIdx.z * G.chunk;
+  const int ie = min(ib + G.chunk, ni);
+  const int jown = j0 + ty, kown = k0 + tx;
+  const bool own = jown < nj && kown < nk;
+  const bool jint = G.per[1] || (jown > 0 && jown < nj - 1);
+  const bool kint = G.per[2] || (kown > 0 && kown < nk - 1);
+  const bool per_i = G.per[0] != 0;
+  const int cm1 = colk(tx - 1), cm2 = colk(tx - 2);
+  const int o2 = (ty + 2) * SK + tx;  // own node, 2-node-halo planes
+  const int o1 = (ty + 1) * SK + tx;  // own node, 1-node-halo planes
+  const bool vec_ok = G.vec16 && (k0 + FTK <= nk);
+
+  // ---- stage plane x (state: 2-node halo; metrics, mu/kappa: 1-node halo)
+  auto stage_plane = [&](int slot, int x) {
+    const int ig = wrap_fast(x, ni, G.per[0]);
+    constexpr int JQ = 5 * R2, JM = 10 * R1, JK = 2 * R1;
+    if (tid >= JQ + JM + JK) return;
+    const float* src;
+    float* dst;
+    int jj, halo;
+    float benign;
+    if (tid < JQ) {
+      const int f = tid / R2;
+      jj = tid - f * R2 - 2;
+      src = P.qin[f];
+      dst = sQ + (slot * 5 + f) * PL2 + (jj + 2) * SK;
+      halo = 2;
+      benign = (f == 0 || f == 4) ? 1.f : 0.f;
+    } else if (tid < JQ + JM) {
+      const int u = tid - JQ, f = u / R1;
+      jj = u - f * R1 - 1;
+      src = P.m[f];
+      dst = sM + (slot * 10 + f) * PL1 + (jj + 1) * SK;
+      halo = 1;
+      benign = 1.f;
+    } else {
+      const int u = tid - JQ - JM, f = u / R1;
+      jj = u - f * R1 - 1;
+      src = P.mk[f];
+      dst = sK + (slot * 2 + f) * PL1 + (jj + 1) * SK;
+      halo = 1;
+      benign = 0.f;
+    }
+    const int jg = wrap_fast(j0 + jj, nj, G.per[1]);
+    if (ig < 0 || jg < 0) {
+      for (int c = 0; c < SK; ++c) dst[c] = benign;
+      return;
+    }
+    const float* row = src + (ig * nj + jg) * nk;
+    if (vec_ok) {
+#pragma unroll
+      for (int v = 0; v < FTK / 4; ++v) cp_async16(dst + 4 * v, row + k0 + 4 * v);
+    } else {
+      for (int kk = 0; kk < FTK; ++kk) {
+        const int kg = wrap_fast(k0 + kk, nk, G.per[2]);
+        if (kg >= 0)
+          cp_async4(dst + kk, row + kg);
+        else
+          dst[kk] = benign;
+      }
+    }
+    for (int h = 1; h <= halo; ++h) {
+      const int kl = wrap_fast(k0 - h, nk, G.per[2]);
+      const int kr = wrap_fast(k0 + FTK - 1 + h, nk, G.per[2]);
+      if (kl >= 0)
+        cp_async4(dst + colk(-h), row + kl);
+      else
+        dst[colk(-h)] = benign;
+      if (kr >= 0)
+        cp_async4(dst + FTK - 1 + h, row + kr);
+      else
+        dst[FTK - 1 + h] = benign;
+    }
+  };
+
+  // ---- primitives (2-node halo) and lbar (1-node halo) of a staged plane
+  auto derive_plane = [&](int qs, int ps, int ms, int ls) {
+    const float* q = sQ + qs * 5 * PL2;
+    float* pp = sP + ps * 5 * PL2;
+    const float* mm = sM + ms * 10 * PL1;
+    float* ll = sL + ls * 3 * PL1;
+    for (int r = tid; r < PL2; r += FNT) {
+      const float rho = q[r];
+      const float ir = __frcp_rn(rho);
+      const float u = q[PL2 + r] * ir, v = q[2 * PL2 + r] * ir, w = q[3 * PL2 + r] * ir;
+      const float p = K.gm1 * (q[4 * PL2 + r] - 0.5f * rho * (u * u + v * v + w * w));
+      const float T = K.gamma * p * ir;
+      pp[r] = u;
+      pp[PL2 + r] = v;
+      pp[2 * PL2 + r] = w;
+      pp[3 * PL2 + r] = T;
+      pp[4 * PL2 + r] = p;
+      const int row = r / SK, col = r - row * SK;
+      // 1-node halo: rows 1 .. R2-2 of the 2-node layout, columns kk in [-1, FTK]
+      if (row >= 1 && row <= R2 - 2 && (col <= FTK || col == SK - 1)) {
+        const int r1 = r - SK;
+        float m[10];
+#pragma unroll
+        for (int t = 0; t < 10; ++t) m[t] = mm[t * PL1 + r1];
+        float lb[3];
+        node_lbar(m, u, v, w, T, lb);
+        ll[r1] = lb[0];
+        ll[PL1 + r1] = lb[1];
+        ll[2 * PL1 + r1] = lb[2];
+      }
+    }
+  };
+
+  // ---- own-column state along xi: planes i-1, i, i+1, i+2 (registers)
+  float Wq[4][5] = {}, pq[4] = {};
+  bool vq[4] = {false, false, false, false};
+  auto load_W = [&](int x, float W[5], float& p, bool& valid) {
+    const int ig = wrap_fast(x, ni, G.per[0]);
+    valid = own && ig >= 0;
+    if (!valid) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) W[c] = 0.f;
+      p = 1.f;
+      return;
+    }
+    const int n = (ig * nj + jown) * nk + kown;
+    float q[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) q[c] = __ldg(P.qin[c] + n);
+    const float ir = __frcp_rn(q[0]);
+    const float u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
+    p = K.gm1 * (q[4] - 0.5f * q[0] * (u * u + v * v + w * w));
+#pragma unroll
+    for (int c = 0; c < 4; ++c) W[c] = q[c];
+    W[4] = q[4] + p;
+  };
+
+  // xi interface (x, x+1) of the own column: sP/sM/sK/sL slots of both planes
+  auto xi_flux = [&](int x, int p0, int p1, int m0, int m1, int l0, int l1, float F[5]) {
+    const float* A0 = sP + p0 * 5 * PL2;
+    const float* A1 = sP + p1 * 5 * PL2;
+    float nua, nub;
+    if (!per_i && x == 0)
+      nua = sensor3(pq[1], pq[2], pq[3]);
+    else
+      nua = sensor3(pq[0], pq[1], pq[2]);
+    if (!per_i && x + 1 == ni - 1)
+      nub = sensor3(pq[0], pq[1], pq[2]);
+    else
+      nub = sensor3(pq[1], pq[2], pq[3]);
+    float dphi[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float* a = A0 + q * PL2;
+      const float* b = A1 + q * PL2;
+      dphi[q][0] = b[o2] - a[o2];
+      dphi[q][1] = 0.25f * ((a[o2 + SK] - a[o2 - SK]) + (b[o2 + SK] - b[o2 - SK]));
+      dphi[q][2] = 0.25f * ((a[o2 + 1] - a[o2 - tx + cm1]) + (b[o2 + 1] - b[o2 - tx + cm1]));
+    }
+    float ma[10], mb[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+      ma[t] = sM[(m0 * 10 + t) * PL1 + o1];
+      mb[t] = sM[(m1 * 10 + t) * PL1 + o1];
+    }
+    const float* Ka = sK + m0 * 2 * PL1;
+    const float* Kb = sK + m1 * 2 * PL1;
+    iface_flux<0, float>(K, Wq[0], Wq[1], Wq[2], Wq[3], vq[0], vq[3], nua, nub,
+                         sL[l0 * 3 * PL1 + o1], sL[l1 * 3 * PL1 + o1], ma, mb, A0[4 * PL2 + o2],
+                         A1[4 * PL2 + o2], A0[o2], A0[PL2 + o2], A0[2 * PL2 + o2], A1[o2],
+                         A1[PL2 + o2], A1[2 * PL2 + o2], dphi, Ka[o1], Kb[o1], Ka[PL1 + o1],
+                         Kb[PL1 + o1], F);
+  };
+
+  // eta interface between tile rows ra and ra+1 (ra in [-1, FTJ-1]), own
+  // column; plane i in slots qs (sQ), ps (sP, with pm/pp for i-1/i+1), ms, ls
+  auto eta_flux = [&](int ra, int qs, int pm, int ps, int pp, int ms, int ls, float F[5]) {
+    const float* Qs = sQ + qs * 5 * PL2;
+    const float* Pc = sP + ps * 5 * PL2;
+    const float* Pm = sP + pm * 5 * PL2;
+    const float* Pp = sP + pp * 5 * PL2;
+    const int a2 = (ra + 2) * SK + tx, b2 = a2 + SK;
+    const int a1 = (ra + 1) * SK + tx, b1 = a1 + SK;
+    const int jga = j0 + ra;
+    const bool has_m = G.per[1] || jga - 1 >= 0;
+    const bool has_p = G.per[1] || jga + 2 <= nj - 1;
+    const float* p4 = Pc + 4 * PL2;
+    float Wm[5], Wa[5], Wb[5], Wp[5];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      Wa[c] = Qs[c * PL2 + a2];
+      Wb[c] = Qs[c * PL2 + b2];
+      Wm[c] = Qs[c * PL2 + a2 - SK];
+      Wp[c] = Qs[c * PL2 + b2 + SK];
+    }
+    Wa[4] = Qs[4 * PL2 + a2] + p4[a2];
+    Wb[4] = Qs[4 * PL2 + b2] + p4[b2];
+    Wm[4] = Qs[4 * PL2 + a2 - SK] + p4[a2 - SK];
+    Wp[4] = Qs[4 * PL2 + b2 + SK] + p4[b2 + SK];
+    float nua, nub;
+    if (!G.per[1] && jga == 0)
+      nua = sensor3(p4[a2], p4[a2 + SK], p4[a2 + 2 * SK]);
+    else
+      nua = sensor3(p4[a2 - SK], p4[a2], p4[a2 + SK]);
+    if (!G.per[1] && jga + 1 == nj - 1)
+      nub = sensor3(p4[b2 - 2 * SK], p4[b2 - SK], p4[b2]);
+    else
+      nub = sensor3(p4[b2 - SK], p4[b2], p4[b2 + SK]);
+    const int am1 = a2 - tx + cm1, bm1 = b2 - tx + cm1;
+    float dphi[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float* c0 = Pc + q * PL2;
+      dphi[q][1] = c0[b2] - c0[a2];
+      dphi[q][0] = 0.25f * ((Pp[q * PL2 + a2] - Pm[q * PL2 + a2]) + (Pp[q * PL2 + b2] - Pm[q * PL2 + b2]));
+      dphi[q][2] = 0.25f * ((c0[a2 + 1] - c0[am1]) + (c0[b2 + 1] - c0[bm1]));
+    }
+    float ma[10], mb[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+      ma[t] = sM[(ms * 10 + t) * PL1 + a1];
+      mb[t] = sM[(ms * 10 + t) * PL1 + b1];
+    }
+    const float* Kc = sK + ms * 2 * PL1;
+    const float* L = sL + ls * 3 * PL1 + PL1;
+    iface_flux<1, float>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, p4[a2],
+                         p4[b2], Pc[a2], Pc[PL2 + a2], Pc[2 * PL2 + a2], Pc[b2], Pc[PL2 + b2],
+                         Pc[2 * PL2 + b2], dphi, Kc[a1], Kc[b1], Kc[PL1 + a1], Kc[PL1 + b1], F);
+  };
+
+  // zeta interface between tile columns ca and ca+1 (ca in [-1, FTK-1]), own row
+  auto zeta_flux = [&](int ca, int qs, int pm, int ps, int pp, int ms, int ls, float F[5]) {
+    const float* Qs = sQ + qs * 5 * PL2;
+    const float* Pc = sP + ps * 5 * PL2;
+    const float* Pm = sP + pm * 5 * PL2;
+    const float* Pp = sP + pp * 5 * PL2;
+    const int rb2 = (ty + 2) * SK, rb1 = (ty + 1) * SK;
+    const int ca_c = colk(ca), cb_c = colk(ca + 1), cm_c = colk(ca - 1), cp_c = colk(ca + 2);
+    const int a2 = rb2 + ca_c, b2 = rb2 + cb_c, m2 = rb2 + cm_c, q2 = rb2 + cp_c;
+    const int a1 = rb1 + ca_c, b1 = rb1 + cb_c;
+    const int kga = k0 + ca;
+    const bool has_m = G.per[2] || kga - 1 >= 0;
+    const bool has_p = G.per[2] || kga + 2 <= nk - 1;
+    const float* p4 = Pc + 4 * PL2;
+    float Wm[5], Wa[5], Wb[5], Wp[5];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      Wa[c] = Qs[c * PL2 + a2];
+      Wb[c] = Qs[c * PL2 + b2];
+      Wm[c] = Qs[c * PL2 + m2];
+      Wp[c] = Qs[c * PL2 + q2];
+    }
+    Wa[4] = Qs[4 * PL2 + a2] + p4[a2];
+    Wb[4] = Qs[4 * PL2 + b2] + p4[b2];
+    Wm[4] = Qs[4 * PL2 + m2] + p4[m2];
+    Wp[4] = Qs[4 * PL2 + q2] + p4[q2];
+    float nua, nub;
+    if (!G.per[2] && kga == 0)
+      nua = sensor3(p4[a2], p4[b2], p4[q2]);
+    else
+      nua = sensor3(p4[m2], p4[a2], p4[b2]);
+    if (!G.per[2] && kga + 1 == nk - 1)
+      nub = sensor3(p4[m2], p4[a2], p4[b2]);
+    else
+      nub = sensor3(p4[a2], p4[b2], p4[q2]);
+    float dphi[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float* c0 = Pc + q * PL2;
+      dphi[q][2] = c0[b2] - c0[a2];
+      dphi[q][0] = 0.25f * ((Pp[q * PL2 + a2] - Pm[q * PL2 + a2]) + (Pp[q * PL2 + b2] - Pm[q * PL2 + b2]));
+      dphi[q][1] = 0.25f * ((c0[a2 + SK] - c0[a2 - SK]) + (c0[b2 + SK] - c0[b2 - SK]));
+    }
+    float ma[10], mb[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+      ma[t] = sM[(ms * 10 + t) * PL1 + a1];
+      mb[t] = sM[(ms * 10 + t) * PL1 + b1];
+    }
+    const float* Kc = sK + ms * 2 * PL1;
+    const float* L = sL + ls * 3 * PL1 + 2 * PL1;
+    iface_flux<2, float>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, p4[a2],
+                         p4[b2], Pc[a2], Pc[PL2 + a2], Pc[2 * PL2 + a2], Pc[b2], Pc[PL2 + b2],
+                         Pc[2 * PL2 + b2], dphi, Kc[a1], Kc[b1], Kc[PL1 + a1], Kc[PL1 + b1], F);
+  };
+
+  auto m3 = [](int x) { return ((x % 3) + 3) % 3; };
+  auto m2 = [](int x) { return ((x % 2) + 2) % 2; };
+  // ---------------------------------------------------------- prologue
+  // sQ/sM/sK slot of plane x: x mod 3 (planes i, i+1, i+2 live); sP slot:
+  // x mod 3 (planes i-1, i, i+1); sL slot: x mod 2 (planes i, i+1).
+  stage_plane(m3(ib - 1), ib - 1);
+  stage_plane(m3(ib), ib);
+  cp_async_commit();
+  stage_plane(m3(ib + 1), ib + 1);
+  cp_async_commit();
+  load_W(ib - 2, Wq[0], pq[0], vq[0]);
+  load_W(ib - 1, Wq[1], pq[1], vq[1]);
+  load_W(ib, Wq[2], pq[2], vq[2]);
+  load_W(ib + 1, Wq[3], pq[3], vq[3]);
+  cp_async_wait<1>();
+  __syncthreads();
+  derive_plane(m3(ib - 1), m3(ib - 1), m3(ib - 1), m2(ib - 1));
+  derive_plane(m3(ib), m3(ib), m3(ib), m2(ib));
+  __syncthreads();
+  float Fx_prev[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  if (own && jint && kint && (per_i || ib - 1 >= 0))
+    xi_flux(ib - 1, m3(ib - 1), m3(ib), m3(ib - 1), m3(ib), m2(ib - 1), m2(ib), Fx_prev);
+  const float adt = (MODE == FMODE_RHS) ? 0.f : (float)(alpha * sc->dt);
+
+  for (int i = ib; i < ie; ++i) {
+    // own-column queue: planes i-1 .. i+2
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Wq[s][c] = Wq[s + 1][c];
+      pq[s] = pq[s + 1];
+      vq[s] = vq[s + 1];
+    }
+    load_W(i + 2, Wq[3], pq[3], vq[3]);
+    // plane i+1 has landed; reuse the slots of plane i-1 for plane i+2
+    cp_async_wait<0>();
+    __syncthreads();
+    stage_plane(m3(i + 2), i + 2);
+    cp_async_commit();
+    derive_plane(m3(i + 1), m3(i + 1), m3(i + 1), m2(i + 1));
+    __syncthreads();
+
+    const int ig = wrap_fast(i, ni, G.per[0]);
+    const bool iint = per_i || (i > 0 && i < ni - 1);
+    float Fx[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (own && jint && kint && (per_i || i + 1 <= ni - 1))
+      xi_flux(i, m3(i), m3(i + 1), m3(i), m3(i + 1), m2(i), m2(i + 1), Fx);
+    if (own && iint && kint) {
+      float F[5];
+      if (G.per[1] || jown + 1 <= nj - 1) {
+        eta_flux(ty, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1) + ty + 1) * FTK + tx] = F[c];
+      }
+      if (ty == 0 && (G.per[1] || j0 - 1 >= 0)) {
+        eta_flux(-1, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1)) * FTK + tx] = F[c];
+      }
+    }
+    if (own && iint && jint) {
+      float F[5];
+      if (G.per[2] || kown + 1 <= nk - 1) {
+        zeta_flux(tx, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] = F[c];
+      }
+      if (tx == 0 && (G.per[2] || k0 - 1 >= 0)) {
+        zeta_flux(-1, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1)] = F[c];
+      }
+    }
+    __syncthreads();
+    if (own && ig >= 0) {
+      const int n = (ig * nj + jown) * nk + kown;
+      if (iint && jint && kint) {
+        const float Jn = __frcp_rn(sM[(m3(i) * 10 + 9) * PL1 + o1]);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          float r = 0.f;
+          r += Fx[c] - Fx_prev[c];
+          r += sFe[(c * (FTJ + 1) + ty + 1) * FTK + tx] - sFe[(c * (FTJ + 1) + ty) * FTK + tx];
+          r += sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] - sFz[(c * FTJ + ty) * (FTK + 1) + tx];
+          if (MODE == FMODE_RHS) {
+            P.outd[c][n] = (double)r;
+          } else if (MODE == FMODE_STAGE) {
+            P.out[c][n] = P.hi[c][n] - adt * (Jn * r);
+          } else {
+            // compensated update of the pair (hi, lo) by d (TwoSum, then
+            // renormalisation), all in FP32
+            const float d = -adt * (Jn * r);
+            const float hi = P.hi[c][n], lo = P.lo[c][n];
+            const float s = hi + d;
+            const float bb = s - hi;
+            const float e = (hi - (s - bb)) + (d - bb);
+            const float lo2 = lo + e;
+            const float h2 = s + lo2;
+            P.hiw[c][n] = h2;
+            P.lo[c][n] = lo2 - (h2 - s);
+          }
+        }
+      } else if (MODE == FMODE_RHS) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) P.outd[c][n] = 0.0;
+      } else if (MODE == FMODE_STAGE) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) P.out[c][n] = P.hi[c][n];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Fx_prev[c] = Fx[c];
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+// ------------------------------------------------------- mixed-state helpers
+// Q (double) -> (hi, lo) floats with hi + lo == Q to ~2^-48 relative.
+__global__ void k_split(long long count, const double* __restrict__ q, float* __restrict__ hi,
+                        float* __restrict__ lo) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < count;
+       n += (long long)gridDim.x * blockDim.x) {
+    const double v = q[n];
+    const float h = (float)v;
+    hi[n] = h;
+    lo[n] = (float)(v - (double)h);
+  }
+}
+
+__global__ void k_join(long long count, const float* __restrict__ hi, const float* __restrict__ lo,
+                       double* __restrict__ q) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < count;
+       n += (long long)gridDim.x * blockDim.x)
+    q[n] = (double)hi[n] + (double)lo[n];
+}
+
+// ------------------------------------------------------------- launchers
+
+static int fblocks(long long count) {
+  long long b = (count + 255) / 256;
+  if (b > 152LL * 32) b = 152LL * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename R>
+static Consts<R> fused_consts(const les_params& p) {
+  Consts<R> K;
+  K.gamma = (R)p.gamma;
+  K.gm1 = (R)(p.gamma - 1.0);
+  K.k2 = (R)p.k2;
+  K.k4 = (R)p.k4;
+  K.mu_scale = (R)(p.Re > 0.0 ? p.Mj / p.Re : 0.0);
+  K.S_suth = (R)(110.4 / p.T_ref);
+  K.cs2 = (R)(p.sgs_model == LES_SGS_VREMAN ? 2.5 * p.Cs * p.Cs : p.Cs * p.Cs);
+  K.inv_gm1_pr = (R)(1.0 / ((p.gamma - 1.0) * p.Pr));
+  K.inv_gm1_prs = (R)(1.0 / ((p.gamma - 1.0) * p.Pr_sgs));
+  K.sgs = p.sgs_model;
+  return K;
+}
+
+void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
+                    float* mk, double* partials, DevScalars* sc, const Launch& L) {
+  k_prestep<float, float, float><<<kRedBlocks, kRedThreads, 0, L.s>>>(
+      g, fused_consts<float>(p), Q0, M, mk, partials, sc);
+  ++*L.counter;
+}
+
+// Axial chunk so that the grid is about a whole number of waves.
+static int choose_chunk(int ni, int tiles, int ctas_per_sm) {
+  const int wave = 152 * ctas_per_sm;
+  int best_chunk = ni;
+  double best_cost = 1e300;
+  for (int chunks = 1; chunks <= ni; ++chunks) {
+    const int chunk = (ni + chunks - 1) / chunks;
+    const int nch = (ni + chunk - 1) / chunk;
+    const long long ctas = (long long)tiles * nch;
+    const long long waves = (ctas + wave - 1) / wave;
+    // cost: waves x (chunk + 3 prologue planes)
+    const double cost = (double)waves * (chunk + 3);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best_chunk = chunk;
+    }
+    if (chunk <= 8) break;
+  }
+  return best_chunk;
+}
+
+template <int MODE>
+static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const FusedPtrs& P,
+                           const DevScalars* sc, double alpha, const Launch& L) {
+  FusedGeom G = G0;
+  const size_t smem = (size_t)SMEM_FLOATS * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_stage_fused<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
+  G.chunk = choose_chunk(G.ni, tk * tj, 1);
+  dim3 grid(tk, tj, (G.ni + G.chunk - 1) / G.chunk);
+  k_stage_fused<MODE><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
+  ++*L.counter;
+}
+
+void launch_stage_fused(int mode, const Grid& g, const les_params& p, const FusedIO& io,
+                        double alpha, const Launch& L) {
+  FusedGeom G;
+  G.ni = g.n[0];
+  G.nj = g.n[1];
+  G.nk = g.n[2];
+  for (int d = 0; d < 3; ++d) G.per[d] = g.per[d];
+  G.chunk = 0;
+  G.vec16 = (g.n[2] % 4 == 0) ? 1 : 0;
+  const long long N = g.N;
+  FusedPtrs P;
+  for (int c = 0; c < 5; ++c) {
+    P.qin[c] = (const float*)io.Qin + c * N;
+    P.hi[c] = (const float*)io.Q0 + c * N;
+    P.hiw[c] = (float*)io.Q0 + c * N;
+    P.lo[c] = io.Q0lo ? (float*)io.Q0lo + c * N : nullptr;
+    P.out[c] = (mode == FMODE_STAGE) ? (float*)io.out + c * N : nullptr;
+    P.outd[c] = (mode == FMODE_RHS) ? (double*)io.out + c * N : nullptr;
+  }
+  for (int t = 0; t < 10; ++t) P.m[t] = (const float*)io.M + t * N;
+  for (int t = 0; t < 2; ++t) P.mk[t] = (const float*)io.mk + t * N;
+  const Consts<float> K = fused_consts<float>(p);
+  if (mode == FMODE_RHS)
+    launch_stage_t<FMODE_RHS>(G, K, P, io.sc, alpha, L);
+  else if (mode == FMODE_STAGE)
+    launch_stage_t<FMODE_STAGE>(G, K, P, io.sc, alpha, L);
+  else
+    launch_stage_t<FMODE_LAST>(G, K, P, io.sc, alpha, L);
+}
+
+void launch_split(long long count, const double* q, float* hi, float* lo, const Launch& L) {
+  k_split<<<fblocks(count), 256, 0, L.s>>>(count, q, hi, lo);
+  ++*L.counter;
+}
+
+void launch_join(long long count, const float* hi, const float* lo, double* q, const Launch& L) {
+  k_join<<<fblocks(count), 256, 0, L.s>>>(count, hi, lo, q);
+  ++*L.counter;
+}
+
+}  // namespace lesjet

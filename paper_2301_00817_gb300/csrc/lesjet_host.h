@@ -18,40 +18,58 @@ void launch_inflow_geometry(const Grid& g, const double* xyz, double* rth, const
 void launch_init_jet(const Grid& g, const double* xyz, uint64_t seed, double noise,
                      const les_params& p, double* Q, const Launch& L);
 
-// Pointers of one residual evaluation (v1 multi-kernel path).  R is the
-// compute precision; Q_in is double (first stage) or the stage type.
-struct StageIO {
-  const void* Qin;      // [5][N] stage input state
-  int qin_is_double;    // 1: double, 0: float
-  const void* M;        // [10][N] metrics (double for FP64, float for mixed)
-  void* node;           // [8][N] R: u v w p T lbar_xi lbar_eta lbar_zeta
-  void* mk;             // [2][N] R: mu_eff kappa_eff
-  void* flux;           // [3][5][N] R: interface fluxes per direction
-  double* partials;     // [kRedBlocks] block minima (dt)
-  DevScalars* sc;       // device scalars
-};
-
 // stage.cu
-// precision: LES_PREC_FP64 or LES_PREC_MIXED
-void launch_node(int precision, const Grid& g, const les_params& p, const StageIO& io,
-                 bool with_dt, const Launch& L);
-void launch_dt_finalize(const les_params& p, const StageIO& io, int advance, const Launch& L);
-void launch_mu(int precision, const Grid& g, const les_params& p, const StageIO& io,
-               const Launch& L);
-void launch_flux(int precision, const Grid& g, const les_params& p, const StageIO& io, int dir,
-                 const Launch& L);
-// mode 0: write RHS to out (double [5][N]); 1: stage update into out
-// (stage type: double for FP64, float for mixed); 2: final stage in place
-// into out == Q0 (double).
-void launch_update(int precision, const Grid& g, const StageIO& io, const double* Q0,
-                   double alpha, int mode, void* out, const Launch& L);
+void launch_dt_finalize(const les_params& p, double* partials, DevScalars* sc, int advance,
+                        const Launch& L);
 void launch_mk_to_double(int precision, const Grid& g, const void* mk, double* out,
                          const Launch& L);
+
+// stage64.cu (FP64 form): node, viscosity, per-direction flux and update
+// passes; each node quantity and interface flux is computed once.
+struct StageIO64 {
+  const double* Qin;   // [5][N] stage input state
+  const double* M;     // [10][N] metrics
+  double* node;        // [8][N] u v w p T lbar_xi lbar_eta lbar_zeta
+  double* mk;          // [2][N] mu_eff kappa_eff
+  double* flux;        // [3][5][N] interface fluxes
+  double* partials;    // [kRedBlocks] block minima (dt)
+  DevScalars* sc;
+};
+void launch_node64(const Grid& g, const les_params& p, const StageIO64& io, bool with_dt,
+                   const Launch& L);
+void launch_mu64(const Grid& g, const les_params& p, const StageIO64& io, const Launch& L);
+void launch_flux64(const Grid& g, const les_params& p, const StageIO64& io, int dir,
+                   const Launch& L);
+// mode 0: RHS into out; 1: stage update into out; 2: last stage in place
+void launch_update64(const Grid& g, const StageIO64& io, const double* Q0, double alpha, int mode,
+                     double* out, const Launch& L);
+
+// fused.cu
+struct FusedIO {
+  const void* Qin;      // stage input state [5][N] (stage type)
+  const void* Q0;       // Q^(0): double (FP64) or float hi part (mixed) [5][N]
+  void* Q0lo;           // mixed: float lo part of Q^(0) [5][N]
+  const void* M;        // metrics [10][N] (double or float)
+  const void* mk;       // mu_eff, kappa_eff [2][N] (compute type)
+  const DevScalars* sc; // device scalars (dt)
+  void* out;            // RHS mode: double [5][N]; stage mode: stage type [5][N]
+};
+// mixed form: mu_eff/kappa_eff and CFL block minima of the float state
+void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
+                    float* mk, double* partials, DevScalars* sc, const Launch& L);
+// mode 0: residual into io.out (double); 1: stage update into io.out;
+// 2: last stage, Q^(0) (hi, lo) updated in place with compensated sums
+void launch_stage_fused(int mode, const Grid& g, const les_params& p, const FusedIO& io,
+                        double alpha, const Launch& L);
+void launch_split(long long count, const double* q, float* hi, float* lo, const Launch& L);
+void launch_join(long long count, const float* hi, const float* lo, double* q, const Launch& L);
 
 // boundary.cu
 void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* M64,
                    const double* rth, const DevScalars* sc, int use_host_t, double t_host,
                    const Launch& L);
+void launch_bc_jet_hl(const Grid& g, const les_params& p, float* hi, float* lo, const double* M64,
+                      const double* rth, const DevScalars* sc, const Launch& L);
 void launch_totals(const Grid& g, const double* Q, const double* M64, double* partials,
                    DevScalars* sc, const Launch& L);
 void launch_set_time(DevScalars* sc, double t, const Launch& L);
