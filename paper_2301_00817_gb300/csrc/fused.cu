@@ -490,28 +490,50 @@ __global__ void __launch_bounds__(FNT, 1)
     }
   };
 
-  // ---- own-column state along xi: planes i-1, i, i+1, i+2 (registers)
+  // ---- own-column state along xi: planes i-1, i, i+1, i+2 (registers); the
+  // raw state of the next plane to enter the queue is fetched one iteration
+  // early so its latency hides behind a whole plane of work
   float Wq[4][5] = {}, pq[4] = {};
   bool vq[4] = {false, false, false, false};
-  auto load_W = [&](int x, float W[5], float& p, bool& valid) {
+  float qn[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  bool vn = false;
+  auto fetch_q = [&](int x) {
     const int ig = wrap_fast(x, ni, G.per[0]);
-    valid = own && ig >= 0;
+    vn = own && ig >= 0;
+    if (vn) {
+      const int n = (ig * nj + jown) * nk + kown;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) qn[c] = __ldg(P.qin[c] + n);
+    }
+  };
+  // Q^(0) hi part of the own node, fetched one plane ahead of its update
+  float h0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  auto fetch_h = [&](int x) {
+    const int ig = wrap_fast(x, ni, G.per[0]);
+    if (MODE != FMODE_RHS && own && ig >= 0) {
+      const int n = (ig * nj + jown) * nk + kown;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) h0[c] = P.hi[c][n];
+    }
+  };
+  auto finish_W = [&](float W[5], float& p, bool& valid) {
+    valid = vn;
     if (!valid) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) W[c] = 0.f;
       p = 1.f;
       return;
     }
-    const int n = (ig * nj + jown) * nk + kown;
-    float q[5];
+    const float ir = __frcp_rn(qn[0]);
+    const float u = qn[1] * ir, v = qn[2] * ir, w = qn[3] * ir;
+    p = K.gm1 * (qn[4] - 0.5f * qn[0] * (u * u + v * v + w * w));
 #pragma unroll
-    for (int c = 0; c < 5; ++c) q[c] = __ldg(P.qin[c] + n);
-    const float ir = __frcp_rn(q[0]);
-    const float u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
-    p = K.gm1 * (q[4] - 0.5f * q[0] * (u * u + v * v + w * w));
-#pragma unroll
-    for (int c = 0; c < 4; ++c) W[c] = q[c];
-    W[4] = q[4] + p;
+    for (int c = 0; c < 4; ++c) W[c] = qn[c];
+    W[4] = qn[4] + p;
+  };
+  auto load_W = [&](int x, float W[5], float& p, bool& valid) {
+    fetch_q(x);
+    finish_W(W, p, valid);
   };
 
   // xi interface (x, x+1) of the own column: sP/sM/sK/sL slots of both planes
@@ -607,13 +629,14 @@ __global__ void __launch_bounds__(FNT, 1)
                          Pc[2 * PL2 + b2], dphi, Kc[a1], Kc[b1], Kc[PL1 + a1], Kc[PL1 + b1], F);
   };
 
-  // zeta interface between tile columns ca and ca+1 (ca in [-1, FTK-1]), own row
-  auto zeta_flux = [&](int ca, int qs, int pm, int ps, int pp, int ms, int ls, float F[5]) {
+  // zeta interface between tile columns ca and ca+1 (ca in [-1, FTK-1]) in
+  // tile row rr
+  auto zeta_flux = [&](int rr, int ca, int qs, int pm, int ps, int pp, int ms, int ls, float F[5]) {
     const float* Qs = sQ + qs * 5 * PL2;
     const float* Pc = sP + ps * 5 * PL2;
     const float* Pm = sP + pm * 5 * PL2;
     const float* Pp = sP + pp * 5 * PL2;
-    const int rb2 = (ty + 2) * SK, rb1 = (ty + 1) * SK;
+    const int rb2 = (rr + 2) * SK, rb1 = (rr + 1) * SK;
     const int ca_c = colk(ca), cb_c = colk(ca + 1), cm_c = colk(ca - 1), cp_c = colk(ca + 2);
     const int a2 = rb2 + ca_c, b2 = rb2 + cb_c, m2 = rb2 + cm_c, q2 = rb2 + cp_c;
     const int a1 = rb1 + ca_c, b1 = rb1 + cb_c;
@@ -677,6 +700,8 @@ __global__ void __launch_bounds__(FNT, 1)
   load_W(ib - 1, Wq[1], pq[1], vq[1]);
   load_W(ib, Wq[2], pq[2], vq[2]);
   load_W(ib + 1, Wq[3], pq[3], vq[3]);
+  fetch_q(ib + 2);  // enters the queue in the first iteration
+  fetch_h(ib);
   cp_async_wait<1>();
   __syncthreads();
   derive_plane(m3(ib - 1), m3(ib - 1), m3(ib - 1), m2(ib - 1));
@@ -696,7 +721,8 @@ __global__ void __launch_bounds__(FNT, 1)
       pq[s] = pq[s + 1];
       vq[s] = vq[s + 1];
     }
-    load_W(i + 2, Wq[3], pq[3], vq[3]);
+    finish_W(Wq[3], pq[3], vq[3]);  // plane i+2, fetched one iteration ago
+    fetch_q(i + 3);
     // plane i+1 has landed; reuse the slots of plane i-1 for plane i+2
     cp_async_wait<0>();
     __syncthreads();
@@ -723,20 +749,28 @@ __global__ void __launch_bounds__(FNT, 1)
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1)) * FTK + tx] = F[c];
       }
     }
-    if (own && iint && jint) {
+    if (own && iint && jint && (G.per[2] || kown + 1 <= nk - 1)) {
       float F[5];
-      if (G.per[2] || kown + 1 <= nk - 1) {
-        zeta_flux(tx, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+      zeta_flux(ty, tx, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] = F[c];
-      }
-      if (tx == 0 && (G.per[2] || k0 - 1 >= 0)) {
-        zeta_flux(-1, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+      for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] = F[c];
+    }
+    // left-edge zeta interfaces (k0-1, k0) of the FTJ rows: lanes of warp 1
+    if (ty == 1 && tx < FTJ && iint && (G.per[2] || k0 - 1 >= 0)) {
+      const int rr = tx, jr = j0 + rr;
+      const bool rint = G.per[1] || (jr > 0 && jr < nj - 1);
+      if (jr < nj && rint) {
+        float F[5];
+        zeta_flux(rr, -1, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1)] = F[c];
+        for (int c = 0; c < 5; ++c) sFz[(c * FTJ + rr) * (FTK + 1)] = F[c];
       }
     }
     __syncthreads();
+    float hc[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) hc[c] = h0[c];
+    fetch_h(i + 1);
     if (own && ig >= 0) {
       const int n = (ig * nj + jown) * nk + kown;
       if (iint && jint && kint) {
@@ -750,12 +784,12 @@ __global__ void __launch_bounds__(FNT, 1)
           if (MODE == FMODE_RHS) {
             P.outd[c][n] = (double)r;
           } else if (MODE == FMODE_STAGE) {
-            P.out[c][n] = P.hi[c][n] - adt * (Jn * r);
+            P.out[c][n] = hc[c] - adt * (Jn * r);
           } else {
             // compensated update of the pair (hi, lo) by d (TwoSum, then
             // renormalisation), all in FP32
             const float d = -adt * (Jn * r);
-            const float hi = P.hi[c][n], lo = P.lo[c][n];
+            const float hi = hc[c], lo = P.lo[c][n];
             const float s = hi + d;
             const float bb = s - hi;
             const float e = (hi - (s - bb)) + (d - bb);
@@ -770,7 +804,7 @@ __global__ void __launch_bounds__(FNT, 1)
         for (int c = 0; c < 5; ++c) P.outd[c][n] = 0.0;
       } else if (MODE == FMODE_STAGE) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) P.out[c][n] = P.hi[c][n];
+        for (int c = 0; c < 5; ++c) P.out[c][n] = hc[c];
       }
     }
 #pragma unroll
