@@ -188,6 +188,50 @@ int les_profile_read(les_ctx *ctx, double ms[16], uint64_t counts[16],
                      les_stream_t stream);
 const char *les_profile_name(int kind);
 
+/* ------------------------------------------------------------------------
+ * Discrete adjoint of the FP64 time step (the paper has no adjoint; this is
+ * the gradient form of the same scheme).  Requirements: precision FP64,
+ * dt_mode LES_DT_FIXED (the step does not depend on the CFL minimum),
+ * sgs_model LES_SGS_NONE, freeze_visc 1; LES_ERR_UNSUPPORTED otherwise.
+ * Scratch lives in a caller-owned adjoint workspace of
+ * les_adjoint_workspace_bytes(ctx, nsteps, ckpt_every) bytes (its size grows
+ * with the number of checkpoints of les_adjoint_window).  At non-smooth
+ * points the derivative follows the forward branch: |x| has slope -1 for
+ * x < 0 and +1 otherwise; a max passes to the operand it selected.
+ * ------------------------------------------------------------------------ */
+size_t les_adjoint_workspace_bytes(const les_ctx *ctx, int nsteps, int ckpt_every);
+
+/* Tangent of the residual (Eq. spatial_discret): R = RHS(Q, MK) and
+ * dR = dRHS/dQ dQ + dRHS/dMK dMK at MK = mu_eff/kappa_eff of Q.  dMK may be
+ * NULL (zero); R may be NULL.  Device [5][N] / [2][N] FP64.  Asynchronous. */
+int les_rhs_jvp(les_ctx *ctx, const double *Q, const double *dQ,
+                const double *dMK, double *R, double *dR, void *adj_ws,
+                les_stream_t stream);
+
+/* Adjoint of the residual: lamQ = (dRHS/dQ)^T lamR and lamMK =
+ * (dRHS/dMK)^T lamR at MK of Q.  Entries of lamR on boundary nodes (where
+ * the residual is defined as 0) are ignored.  Asynchronous. */
+int les_rhs_vjp(les_ctx *ctx, const double *Q, const double *lamR,
+                double *lamQ, double *lamMK, void *adj_ws, les_stream_t stream);
+
+/* Adjoint of one time step Q^{n+1} = BC(RK5(Q^n)) taken at time t_n:
+ * lam_out = (dQ^{n+1}/dQ^n)^T lam_next (lam_out may alias lam_next) and
+ * grad[16] += (dQ^{n+1}/da)^T lam_next for the 16 inflow forcing amplitudes
+ * a_{mf}.  Recomputes the five stage states from Q^n.  SYNCHRONISES. */
+int les_adjoint_step(les_ctx *ctx, const double *Qn, double t_n,
+                     const double *lam_next, double *lam_out, double grad[16],
+                     void *adj_ws, les_stream_t stream);
+
+/* Forward window of nsteps steps from Q_start at t0 and its adjoint: returns
+ * J = sum_{n=1..nsteps} dt sum_{i,k} (p(i, j_surface, k) - 1/gamma)^2 dA with
+ * dA = J^-1 |grad eta| (the eta-face area) and grad[16] = dJ/da.  Stores a
+ * checkpoint every ckpt_every steps and recomputes each segment's states in
+ * the reverse sweep.  Q_start is not modified.  SYNCHRONISES. */
+int les_adjoint_window(les_ctx *ctx, const double *Q_start, double t0,
+                       int nsteps, int ckpt_every, int j_surface,
+                       void *adj_ws, double *J_out, double grad[16],
+                       les_stream_t stream);
+
 /* Global time step of state Q, like les_time_step, for callers that cannot
  * allocate device memory (the paper has no counterpart): for example a
  * monitoring or steering hook that runs between solver steps in an

@@ -120,6 +120,14 @@ def load_library(path: str = LIB_PATH):
     lib.les_profile_name.restype = C.c_char_p
     lib.les_time_step_static.argtypes = [vp, vp, vp, C.POINTER(d), vp]
     lib.les_time_step_static.restype = C.c_int
+    lib.les_adjoint_workspace_bytes.argtypes = [vp, i, i]
+    lib.les_adjoint_workspace_bytes.restype = C.c_size_t
+    lib.les_rhs_jvp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.les_rhs_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.les_adjoint_step.argtypes = [vp, vp, d, vp, vp, C.POINTER(d), vp, vp]
+    lib.les_adjoint_window.argtypes = [vp, vp, d, i, i, i, vp, C.POINTER(d), C.POINTER(d), vp]
+    for name in ("les_rhs_jvp", "les_rhs_vjp", "les_adjoint_step", "les_adjoint_window"):
+        getattr(lib, name).restype = C.c_int
     for name in ("les_create", "les_destroy", "les_set_params", "les_set_grid", "les_init_jet",
                  "les_mu_eff", "les_rhs", "les_time_step", "les_apply_bc", "les_set_time",
                  "les_rk_step", "les_run_n_steps", "les_run_host", "les_totals"):
@@ -211,6 +219,36 @@ class Context:
                                                   _stream(stream)))
         return out.value
 
+    # --- discrete adjoint (FP64) -------------------------------------------
+    def adjoint_workspace(self, nsteps: int = 1, ckpt_every: int = 1):
+        torch = _torch()
+        nbytes = int(self.lib.les_adjoint_workspace_bytes(self.h, nsteps, ckpt_every))
+        return torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def les_rhs_jvp(self, Q, dQ, dMK, R, dR, aw, stream=None):
+        opt = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(self.lib.les_rhs_jvp(self.h, _ptr(Q), _ptr(dQ), opt(dMK), opt(R), _ptr(dR),
+                                         _ptr(aw), _stream(stream)))
+
+    def les_rhs_vjp(self, Q, lamR, lamQ, lamMK, aw, stream=None):
+        self._check(self.lib.les_rhs_vjp(self.h, _ptr(Q), _ptr(lamR), _ptr(lamQ), _ptr(lamMK),
+                                         _ptr(aw), _stream(stream)))
+
+    def les_adjoint_step(self, Qn, t_n: float, lam_next, lam_out, aw, stream=None):
+        g = (C.c_double * 16)()
+        self._check(self.lib.les_adjoint_step(self.h, _ptr(Qn), t_n, _ptr(lam_next), _ptr(lam_out),
+                                              g, _ptr(aw), _stream(stream)))
+        return list(g)
+
+    def les_adjoint_window(self, Q_start, t0: float, nsteps: int, ckpt_every: int,
+                           j_surface: int, aw, stream=None):
+        J = C.c_double()
+        g = (C.c_double * 16)()
+        self._check(self.lib.les_adjoint_window(self.h, _ptr(Q_start), t0, nsteps, ckpt_every,
+                                                j_surface, _ptr(aw), C.byref(J), g,
+                                                _stream(stream)))
+        return J.value, list(g)
+
     def les_apply_bc(self, Q, t: float, stream=None):
         self._check(self.lib.les_apply_bc(self.h, _ptr(Q), t, _stream(stream)))
 
@@ -289,3 +327,31 @@ class Solver:
 
     def run(self, Q, n: int) -> LesDiag:
         return self.ctx.les_run_n_steps(n, Q)
+
+
+def window_functional(ctx: "Context", amplitudes, Q_start, t0: float, nsteps: int,
+                      ckpt_every: int, j_surface: int, aw=None):
+    """Differentiable far-field functional of the 16 inflow forcing amplitudes.
+
+    Returns J (0-d float64 tensor) whose backward gives dJ/da from the
+    hand-written discrete adjoint (les_adjoint_window)."""
+    torch = _torch()
+
+    class _Window(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, amps):
+            p = LesParams.from_buffer_copy(ctx.params)
+            for k in range(16):
+                p.amp[k] = float(amps[k])
+            ctx.les_set_params(p)
+            ws = aw if aw is not None else ctx.adjoint_workspace(nsteps, ckpt_every)
+            J, g = ctx.les_adjoint_window(Q_start, t0, nsteps, ckpt_every, j_surface, ws)
+            fctx.save_for_backward(torch.tensor(g, dtype=torch.float64))
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(fctx, gJ):
+            (g,) = fctx.saved_tensors
+            return gJ * g
+
+    return _Window.apply(torch.as_tensor(amplitudes, dtype=torch.float64))

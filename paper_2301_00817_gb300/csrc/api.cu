@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/lesjet.h"
+#include "dual.cuh"
 #include "lesjet_dev.cuh"
 #include "lesjet_host.h"
 
@@ -577,6 +578,274 @@ int les_profile_read(les_ctx* c, double ms[16], uint64_t counts[16], les_stream_
 
 const char* les_profile_name(int kind) {
   return (kind >= 0 && kind < PK_COUNT) ? kProfNames[kind] : "";
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ adjoint
+namespace {
+
+struct AdjLayout {
+  size_t acc, node, mk, lamMK, S, lamS, lamR, lamQ0, work, lam, Qnext, E, partials, scal;
+  size_t qd, mkd, noded, fluxd, rd, ckpt, seg, total;
+  int nckpt, K;
+};
+
+AdjLayout adj_layout(const les_ctx* c, int nsteps, int K) {
+  const size_t N = (size_t)c->g.N, d = sizeof(double), dd = sizeof(lesjet::Dual);
+  AdjLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at_ = o;
+    o = align256(o + bytes);
+    return at_;
+  };
+  L.acc = take(18 * N * d);
+  L.node = take(8 * N * d);
+  L.mk = take(2 * N * d);
+  L.lamMK = take(2 * N * d);
+  L.S = take(6 * 5 * N * d);
+  L.lamS = take(5 * N * d);
+  L.lamR = take(5 * N * d);
+  L.lamQ0 = take(5 * N * d);
+  L.work = take(5 * N * d);
+  L.lam = take(5 * N * d);
+  L.Qnext = take(5 * N * d);
+  L.E = take(5 * (size_t)c->g.n[1] * c->g.n[2] * d);
+  L.partials = take(((size_t)152 * 8 * 16 + 64) * d);
+  L.scal = take(64 * d);
+  L.qd = take(5 * N * dd);
+  L.mkd = take(2 * N * dd);
+  L.noded = take(8 * N * dd);
+  L.fluxd = take(15 * N * dd);
+  L.rd = take(5 * N * dd);
+  L.K = K > 0 ? K : 1;
+  L.nckpt = nsteps > 0 ? (nsteps + L.K - 1) / L.K + 1 : 1;
+  L.ckpt = take((size_t)L.nckpt * 5 * N * d);
+  L.seg = take((size_t)(L.K + 1) * 5 * N * d);
+  L.total = o;
+  return L;
+}
+
+int adj_check(les_ctx* c) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (c->p.precision != LES_PREC_FP64)
+    return fail(c, LES_ERR_UNSUPPORTED, "the adjoint is provided for the FP64 form");
+  if (c->p.sgs_model != LES_SGS_NONE)
+    return fail(c, LES_ERR_UNSUPPORTED, "the adjoint supports sgs_model = LES_SGS_NONE");
+  if (c->p.dt_mode != LES_DT_FIXED)
+    return fail(c, LES_ERR_UNSUPPORTED, "the adjoint needs dt_mode = LES_DT_FIXED");
+  if (!c->p.freeze_visc)
+    return fail(c, LES_ERR_UNSUPPORTED, "the adjoint needs freeze_visc = 1");
+  return LES_OK;
+}
+
+template <typename T>
+T* aw_at(void* aw, size_t off) {
+  return reinterpret_cast<T*>(reinterpret_cast<char*>(aw) + off);
+}
+
+lesjet::StageIO64 adj_io(les_ctx* c, void* aw, const AdjLayout& Ly, const double* Qin) {
+  lesjet::StageIO64 io;
+  io.Qin = Qin;
+  io.M = at<double>(c, c->off_m64);
+  io.node = aw_at<double>(aw, Ly.node);
+  io.mk = aw_at<double>(aw, Ly.mk);
+  io.flux = at<double>(c, c->off_flux);
+  io.partials = at<double>(c, c->off_part);
+  io.sc = at<DevScalars>(c, c->off_sc);
+  return io;
+}
+
+// lam_out = (dQ^{n+1}/dQ^n)^T lam_next; grad_dev[16] += (dQ^{n+1}/da)^T lam_next.
+// lam_out may alias lam_next.
+void adj_step(les_ctx* c, void* aw, const AdjLayout& Ly, const double* Qn, double t_n,
+              const double* lam_next, double* lam_out, double* grad_dev, cudaStream_t s) {
+  lesjet::Launch L{s, &c->launches};
+  const Grid& g = c->g;
+  const size_t bytes = 5 * (size_t)g.N * sizeof(double);
+  const double dt = c->p.dt_fixed;
+  const double* M = at<double>(c, c->off_m64);
+  DevScalars* sc = at<DevScalars>(c, c->off_sc);
+  double* S[6];
+  for (int l = 0; l < 6; ++l) S[l] = aw_at<double>(aw, Ly.S) + (size_t)l * 5 * g.N;
+  double* lamS = aw_at<double>(aw, Ly.lamS);
+  double* lamR = aw_at<double>(aw, Ly.lamR);
+  double* lamQ0 = aw_at<double>(aw, Ly.lamQ0);
+  double* lamMK = aw_at<double>(aw, Ly.lamMK);
+  double* Qnext = aw_at<double>(aw, Ly.Qnext);
+  // forward recompute: viscosity of Q^n, the five stage states, Q^{n+1}
+  cudaMemcpyAsync(S[0], Qn, bytes, cudaMemcpyDeviceToDevice, s);
+  lesjet::launch_dt_finalize(c->p, at<double>(c, c->off_part), sc, 0, L);
+  lesjet::StageIO64 io = adj_io(c, aw, Ly, S[0]);
+  lesjet::launch_node64(g, c->p, io, false, L);
+  lesjet::launch_mu64(g, c->p, io, L);
+  for (int l = 1; l <= 5; ++l) {
+    io.Qin = S[l - 1];
+    lesjet::launch_node64(g, c->p, io, false, L);
+    for (int d = 0; d < 3; ++d) lesjet::launch_flux64(g, c->p, io, d, L);
+    lesjet::launch_update64(g, io, S[0], kAlpha[l - 1], 1, S[l], L);
+  }
+  // reverse: boundary conditions at t^{n+1}
+  if (c->p.bc == LES_BC_JET) {
+    cudaMemcpyAsync(Qnext, S[5], bytes, cudaMemcpyDeviceToDevice, s);
+    lesjet::launch_bc_jet(g, c->p, Qnext, M, at<double>(c, c->off_rth), sc, 1, t_n + dt, L);
+    lesjet::launch_bc_vjp(g, c->p, M, at<double>(c, c->off_rth), S[5], Qnext, lam_next, t_n + dt,
+                          lamS, aw_at<double>(aw, Ly.E), aw_at<double>(aw, Ly.partials), grad_dev, L);
+  } else {
+    cudaMemcpyAsync(lamS, lam_next, bytes, cudaMemcpyDeviceToDevice, s);
+  }
+  // reverse: stages 5 .. 1
+  cudaMemsetAsync(lamQ0, 0, bytes, s);
+  cudaMemsetAsync(lamMK, 0, 2 * (size_t)g.N * sizeof(double), s);
+  for (int l = 5; l >= 1; --l) {
+    lesjet::launch_stage_prep(g, M, kAlpha[l - 1] * dt, lamS, lamR, lamQ0, L);
+    io.Qin = S[l - 1];
+    lesjet::launch_node64(g, c->p, io, false, L);
+    lesjet::launch_rhs_vjp(g, c->p, S[l - 1], M, io.node, io.mk, lamR, aw_at<double>(aw, Ly.acc),
+                           lamS, lamMK, L);
+  }
+  lesjet::launch_axpy(5 * g.N, 1.0, lamS, lamQ0, L);
+  lesjet::launch_mu_vjp(g, c->p, S[0], lamMK, lamQ0, L);
+  cudaMemcpyAsync(lam_out, lamQ0, bytes, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t les_adjoint_workspace_bytes(const les_ctx* c, int nsteps, int ckpt_every) {
+  return c ? adj_layout(c, nsteps, ckpt_every).total : 0;
+}
+
+int les_rhs_jvp(les_ctx* c, const double* Q, const double* dQ, const double* dMK, double* R,
+                double* dR, void* aw, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (c->p.precision != LES_PREC_FP64) return fail(c, LES_ERR_UNSUPPORTED, "FP64 contexts only");
+  if (!Q || !dQ || !dR || !aw) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q) || !aligned16(dQ) || !aligned16(dR) || !aligned16(aw) || (R && !aligned16(R)) ||
+      (dMK && !aligned16(dMK)))
+    return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  const AdjLayout Ly = adj_layout(c, 0, 1);
+  const long long N = c->g.N;
+  lesjet::StageIO64 io = adj_io(c, aw, Ly, Q);
+  lesjet::launch_node64(c->g, c->p, io, false, L);
+  lesjet::launch_mu64(c->g, c->p, io, L);
+  lesjet::Dual* qd = aw_at<lesjet::Dual>(aw, Ly.qd);
+  lesjet::Dual* mkd = aw_at<lesjet::Dual>(aw, Ly.mkd);
+  lesjet::Dual* rd = aw_at<lesjet::Dual>(aw, Ly.rd);
+  lesjet::launch_pack_dual(5 * N, Q, dQ, qd, L);
+  lesjet::launch_pack_dual(2 * N, io.mk, dMK, mkd, L);
+  lesjet::launch_rhs_jvp(c->g, c->p, qd, io.M, mkd, aw_at<lesjet::Dual>(aw, Ly.noded),
+                         aw_at<lesjet::Dual>(aw, Ly.fluxd), rd, L);
+  lesjet::launch_unpack_dual(5 * N, rd, R, dR, L);
+  return cuda_check(c, "les_rhs_jvp");
+}
+
+int les_rhs_vjp(les_ctx* c, const double* Q, const double* lamR, double* lamQ, double* lamMK,
+                void* aw, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (c->p.precision != LES_PREC_FP64) return fail(c, LES_ERR_UNSUPPORTED, "FP64 contexts only");
+  if (!Q || !lamR || !lamQ || !lamMK || !aw) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q) || !aligned16(lamR) || !aligned16(lamQ) || !aligned16(lamMK) || !aligned16(aw))
+    return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  const AdjLayout Ly = adj_layout(c, 0, 1);
+  lesjet::StageIO64 io = adj_io(c, aw, Ly, Q);
+  lesjet::launch_node64(c->g, c->p, io, false, L);
+  lesjet::launch_mu64(c->g, c->p, io, L);
+  cudaMemsetAsync(lamMK, 0, 2 * (size_t)c->g.N * sizeof(double), s);
+  lesjet::launch_rhs_vjp(c->g, c->p, Q, io.M, io.node, io.mk, lamR, aw_at<double>(aw, Ly.acc), lamQ,
+                         lamMK, L);
+  return cuda_check(c, "les_rhs_vjp");
+}
+
+int les_adjoint_step(les_ctx* c, const double* Qn, double t_n, const double* lam_next,
+                     double* lam_out, double grad[16], void* aw, les_stream_t stream) {
+  int rc = adj_check(c);
+  if (rc != LES_OK) return rc;
+  if (!Qn || !lam_next || !lam_out || !aw) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Qn) || !aligned16(lam_next) || !aligned16(lam_out) || !aligned16(aw))
+    return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const AdjLayout Ly = adj_layout(c, 0, 1);
+  double* gdev = aw_at<double>(aw, Ly.scal) + 1;
+  cudaMemsetAsync(gdev, 0, 16 * sizeof(double), s);
+  adj_step(c, aw, Ly, Qn, t_n, lam_next, lam_out, gdev, s);
+  if ((rc = cuda_check(c, "les_adjoint_step")) != LES_OK) return rc;
+  double h[16];
+  cudaMemcpyAsync(h, gdev, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "les_adjoint_step sync");
+  if (grad)
+    for (int m = 0; m < 16; ++m) grad[m] += h[m];
+  return cuda_check(c, "les_adjoint_step");
+}
+
+int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps, int ckpt_every,
+                       int j_surface, void* aw, double* J_out, double grad[16],
+                       les_stream_t stream) {
+  int rc = adj_check(c);
+  if (rc != LES_OK) return rc;
+  if (!Q_start || !aw || nsteps < 1 || ckpt_every < 1)
+    return fail(c, LES_ERR_INVALID_ARG, "null pointer, nsteps < 1 or ckpt_every < 1");
+  if (j_surface < 0 || j_surface >= c->g.n[1]) return fail(c, LES_ERR_INVALID_ARG, "j_surface out of range");
+  if (!aligned16(Q_start) || !aligned16(aw)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  const AdjLayout Ly = adj_layout(c, nsteps, ckpt_every);
+  const int K = Ly.K;
+  const Grid& g = c->g;
+  const size_t bytes = 5 * (size_t)g.N * sizeof(double);
+  const double dt = c->p.dt_fixed;
+  const double* M = at<double>(c, c->off_m64);
+  double* scal = aw_at<double>(aw, Ly.scal);
+  double* Jdev = scal;            // J
+  double* gdev = scal + 1;        // gradient [16]
+  double* Jscratch = scal + 17;   // discarded J of the reverse pass
+  double* part = aw_at<double>(aw, Ly.partials);
+  double* work = aw_at<double>(aw, Ly.work);
+  double* lam = aw_at<double>(aw, Ly.lam);
+  auto ckpt = [&](int k) { return aw_at<double>(aw, Ly.ckpt) + (size_t)k * 5 * g.N; };
+  auto seg = [&](int k) { return aw_at<double>(aw, Ly.seg) + (size_t)k * 5 * g.N; };
+  cudaMemsetAsync(scal, 0, 64 * sizeof(double), s);
+  // forward window, checkpoints every K steps
+  cudaMemcpyAsync(ckpt(0), Q_start, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(work, Q_start, bytes, cudaMemcpyDeviceToDevice, s);
+  lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), t0, L);
+  for (int n = 1; n <= nsteps; ++n) {
+    rk_step(c, work, s);
+    lesjet::launch_functional(g, c->p, j_surface, dt, M, work, nullptr, part, Jdev, L);
+    if (n % K == 0 && n < nsteps) cudaMemcpyAsync(ckpt(n / K), work, bytes, cudaMemcpyDeviceToDevice, s);
+  }
+  // reverse sweep, segment by segment, recomputing the segment's states
+  cudaMemsetAsync(lam, 0, bytes, s);
+  for (int sg = (nsteps - 1) / K; sg >= 0; --sg) {
+    const int n0 = sg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
+    cudaMemcpyAsync(seg(0), ckpt(sg), bytes, cudaMemcpyDeviceToDevice, s);
+    lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), t0 + n0 * dt, L);
+    for (int m = 1; m <= n1 - 1 - n0; ++m) {
+      cudaMemcpyAsync(seg(m), seg(m - 1), bytes, cudaMemcpyDeviceToDevice, s);
+      rk_step(c, seg(m), s);
+    }
+    for (int n = n1; n >= n0 + 1; --n) {
+      const double* Qn = (n == nsteps) ? work : ((n == n1) ? ckpt(sg + 1) : seg(n - n0));
+      lesjet::launch_functional(g, c->p, j_surface, dt, M, Qn, lam, part, Jscratch, L);
+      adj_step(c, aw, Ly, seg(n - 1 - n0), t0 + (n - 1) * dt, lam, lam, gdev, s);
+    }
+  }
+  if ((rc = cuda_check(c, "les_adjoint_window")) != LES_OK) return rc;
+  double h[17];
+  cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "les_adjoint_window sync");
+  if (J_out) *J_out = h[0];
+  if (grad)
+    for (int m = 0; m < 16; ++m) grad[m] = h[1 + m];
+  return cuda_check(c, "les_adjoint_window");
 }
 
 }  // extern "C"

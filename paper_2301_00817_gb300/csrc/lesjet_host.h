@@ -64,6 +64,28 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
 void launch_split(long long count, const double* q, float* hi, float* lo, const Launch& L);
 void launch_join(long long count, const float* hi, const float* lo, double* q, const Launch& L);
 
+// adjoint.cu (FP64): residual tangent / adjoint, viscosity adjoint, stage
+// bookkeeping, boundary-condition adjoint and the surface functional
+struct Dual;
+void launch_rhs_vjp(const Grid& g, const les_params& p, const double* Q, const double* M,
+                    const double* node, const double* mk, const double* lamR, double* acc,
+                    double* lamQ, double* lamMK, const Launch& L);
+void launch_rhs_jvp(const Grid& g, const les_params& p, const Dual* Q, const double* M,
+                    const Dual* mk, Dual* node, Dual* flux, Dual* R, const Launch& L);
+void launch_mu_vjp(const Grid& g, const les_params& p, const double* Q, const double* lamMK,
+                   double* lamQ, const Launch& L);
+void launch_stage_prep(const Grid& g, const double* M, double coef, const double* lamS,
+                       double* lamR, double* lamQ0, const Launch& L);
+void launch_axpy(long long count, double a, const double* x, double* y, const Launch& L);
+void launch_bc_vjp(const Grid& g, const les_params& p, const double* M, const double* rth,
+                   const double* S5, const double* Qnext, const double* lamNext, double t_next,
+                   double* lamS, double* E, double* partials, double* grad, const Launch& L);
+void launch_functional(const Grid& g, const les_params& p, int j5, double dt, const double* M,
+                       const double* Q, double* lam, double* partials, double* Jout,
+                       const Launch& L);
+void launch_pack_dual(long long count, const double* v, const double* d, Dual* out, const Launch& L);
+void launch_unpack_dual(long long count, const Dual* in, double* v, double* d, const Launch& L);
+
 // boundary.cu
 void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* M64,
                    const double* rth, const DevScalars* sc, int use_host_t, double t_host,

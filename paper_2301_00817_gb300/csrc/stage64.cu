@@ -13,390 +13,9 @@
 // Each interface is computed once and read by its two nodes, so the scheme
 // telescopes exactly.  The kernels are written for a compute type R and are
 // instantiated for double only (the mixed form uses fused.cu).
-#include "lesjet_dev.cuh"
-#include "lesjet_host.h"
+#include "stage64_kernels.cuh"
 
 namespace lesjet {
-
-template <typename R>
-static Consts<R> make_consts(const les_params& p) {
-  Consts<R> K;
-  K.gamma = (R)p.gamma;
-  K.gm1 = (R)(p.gamma - 1.0);
-  K.k2 = (R)p.k2;
-  K.k4 = (R)p.k4;
-  K.mu_scale = (R)(p.Re > 0.0 ? p.Mj / p.Re : 0.0);
-  K.S_suth = (R)(110.4 / p.T_ref);
-  K.cs2 = (R)(p.sgs_model == LES_SGS_VREMAN ? 2.5 * p.Cs * p.Cs : p.Cs * p.Cs);
-  K.inv_gm1_pr = (R)(1.0 / ((p.gamma - 1.0) * p.Pr));
-  K.inv_gm1_prs = (R)(1.0 / ((p.gamma - 1.0) * p.Pr_sgs));
-  K.sgs = p.sgs_model;
-  return K;
-}
-
-static int blocks_for(long long count, int threads, long long cap = 152LL * 64) {
-  long long b = (count + threads - 1) / threads;
-  if (b > cap) b = cap;
-  if (b < 1) b = 1;
-  return (int)b;
-}
-
-// ------------------------------------------------------------------ k_node
-// Primitive recovery (System I energy), spectral radii lambda_d = |U_d| +
-// a |grad d| and lbar_xi = lambda_xi + sqrt(lambda_xi lambda_eta) +
-// sqrt(lambda_xi lambda_zeta) (= lambda_xi [1 + (lambda_eta/lambda_xi)^0.5 +
-// (lambda_zeta/lambda_xi)^0.5]), cyclic for eta and zeta.
-template <typename R, typename TQ, typename TM, bool WITH_DT>
-__global__ void __launch_bounds__(256) k_node(Grid g, Consts<R> K, const TQ* __restrict__ Q,
-                                              const TM* __restrict__ M, R* __restrict__ node,
-                                              double* __restrict__ partials,
-                                              DevScalars* __restrict__ sc) {
-  const long long N = g.N;
-  double local_min = 1.0e300;
-  int bad = 0;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    const R rho = (R)Q[n];
-    const R inv_rho = R(1) / rho;
-    const R u = (R)Q[N + n] * inv_rho;
-    const R v = (R)Q[2 * N + n] * inv_rho;
-    const R w = (R)Q[3 * N + n] * inv_rho;
-    const R p = K.gm1 * ((R)Q[4 * N + n] - R(0.5) * rho * (u * u + v * v + w * w));
-    const R T = K.gamma * p * inv_rho;
-    const R a = dev_sqrt(T);
-    R lam[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const R mx = (R)M[(3 * d) * N + n], my = (R)M[(3 * d + 1) * N + n],
-              mz = (R)M[(3 * d + 2) * N + n];
-      lam[d] = dev_abs(mx * u + my * v + mz * w) + a * dev_sqrt(mx * mx + my * my + mz * mz);
-    }
-    const R s01 = dev_sqrt(lam[0] * lam[1]);
-    const R s02 = dev_sqrt(lam[0] * lam[2]);
-    const R s12 = dev_sqrt(lam[1] * lam[2]);
-    node[n] = u;
-    node[N + n] = v;
-    node[2 * N + n] = w;
-    node[3 * N + n] = p;
-    node[4 * N + n] = T;
-    node[5 * N + n] = lam[0] + s01 + s02;
-    node[6 * N + n] = lam[1] + s01 + s12;
-    node[7 * N + n] = lam[2] + s02 + s12;
-    if (WITH_DT) {
-      const double inv = 1.0 / ((double)lam[0] + (double)lam[1] + (double)lam[2]);
-      if (!(rho > R(0)) || !(p > R(0)) || !(inv > 0.0) || !(inv < 1.0e300)) bad = 1;
-      local_min = inv < local_min ? inv : local_min;
-    }
-  }
-  if (WITH_DT) {
-    __shared__ double smin[32];
-    __shared__ int sbad;
-    if (threadIdx.x == 0) sbad = 0;
-    for (int off = 16; off > 0; off >>= 1)
-      local_min = fmin(local_min, __shfl_xor_sync(0xffffffffu, local_min, off));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = local_min;
-    if (bad) atomicOr(&sbad, 1);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double m = threadIdx.x < (blockDim.x >> 5) ? smin[threadIdx.x] : 1.0e300;
-      for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
-      if (threadIdx.x == 0) {
-        partials[blockIdx.x] = m;
-        if (sbad) atomicOr(&sc->status, 1);
-      }
-    }
-  }
-}
-
-// -------------------------------------------------------------------- k_mu
-// Node-centred computational derivative (central; one-sided second order at
-// non-periodic faces).
-template <typename R>
-__device__ __forceinline__ R node_deriv(const Grid& g, const R* __restrict__ f, long long n,
-                                        const int c[3], int d) {
-  const long long s = g.stride[d];
-  const int nd = g.n[d];
-  if (g.per[d]) {
-    const long long np = (c[d] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
-    const long long nm = (c[d] == 0) ? n + (long long)(nd - 1) * s : n - s;
-    return R(0.5) * (f[np] - f[nm]);
-  }
-  if (c[d] == 0) return R(0.5) * (R(-3) * f[n] + R(4) * f[n + s] - f[n + 2 * s]);
-  if (c[d] == nd - 1) return R(0.5) * (R(3) * f[n] - R(4) * f[n - s] + f[n - 2 * s]);
-  return R(0.5) * (f[n + s] - f[n - s]);
-}
-
-// mu_eff = (Mj/Re) T^1.5 (1+S)/(T+S) + mu_sgs; kappa_eff = mu_lam/((g-1)Pr)
-// + mu_sgs/((g-1)Pr_sgs).  Smagorinsky: rho (Cs Delta)^2 |S|; Vreman:
-// rho c sqrt(B_beta/alpha:alpha) (0 when alpha:alpha = 0, B_beta >= 0);
-// Delta = (J^-1)^(1/3).
-template <typename R, typename TQ, typename TM>
-__global__ void __launch_bounds__(256) k_mu(Grid g, Consts<R> K, const TQ* __restrict__ Q,
-                                            const TM* __restrict__ M,
-                                            const R* __restrict__ node, R* __restrict__ mk) {
-  const long long N = g.N;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    const R T = node[4 * N + n];
-    const R mu_l = K.mu_scale * T * dev_sqrt(T) * (R(1) + K.S_suth) / (T + K.S_suth);
-    R mu_s = R(0);
-    if (K.sgs != LES_SGS_NONE) {
-      int c[3];
-      decompose(g, n, c);
-      R gr[3][3];  // gr[i][x] = d u_i / d x_x
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        R dd[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) dd[d] = node_deriv(g, node + q * N, n, c, d);
-#pragma unroll
-        for (int x = 0; x < 3; ++x)
-          gr[q][x] = (R)M[x * N + n] * dd[0] + (R)M[(3 + x) * N + n] * dd[1] +
-                     (R)M[(6 + x) * N + n] * dd[2];
-      }
-      const R Jinv = (R)M[9 * N + n];
-      const R delta = cbrt(Jinv);
-      const R rho = (R)Q[n];
-      if (K.sgs == LES_SGS_SMAGORINSKY) {
-        R ss = R(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            const R sij = R(0.5) * (gr[i][j] + gr[j][i]);
-            ss += sij * sij;
-          }
-        mu_s = rho * (delta * delta) * K.cs2 * dev_sqrt(R(2) * ss);
-      } else {
-        // alpha_ij = d u_j / d x_i = gr[j][i]; beta_ij = Delta^2 alpha_mi alpha_mj
-        R aa = R(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) aa += gr[i][j] * gr[i][j];
-        R be[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j)
-            be[i][j] = delta * delta *
-                       (gr[i][0] * gr[j][0] + gr[i][1] * gr[j][1] + gr[i][2] * gr[j][2]);
-        R B = be[0][0] * be[1][1] - be[0][1] * be[0][1] + be[0][0] * be[2][2] -
-              be[0][2] * be[0][2] + be[1][1] * be[2][2] - be[1][2] * be[1][2];
-        B = B > R(0) ? B : R(0);
-        mu_s = (aa == R(0)) ? R(0) : rho * K.cs2 * dev_sqrt(B / aa);
-      }
-    }
-    mk[n] = mu_l + mu_s;
-    mk[N + n] = mu_l * K.inv_gm1_pr + mu_s * K.inv_gm1_prs;
-  }
-}
-
-// ------------------------------------------------------------------ k_flux
-// Pressure sensor |p+ - 2p + p-| / (p+ + 2p + p-) of node x along D; a face
-// node of a non-periodic direction takes its inward neighbour's value.
-template <int D, typename R>
-__device__ __forceinline__ R sensor(const Grid& g, const R* __restrict__ P, long long x, int cx) {
-  const long long s = g.stride[D];
-  const int nd = g.n[D];
-  long long xc = x;
-  int cc = cx;
-  if (!g.per[D]) {
-    if (cx == 0) { xc = x + s; cc = 1; }
-    else if (cx == nd - 1) { xc = x - s; cc = nd - 2; }
-  }
-  const long long xp = (cc == nd - 1) ? xc - (long long)(nd - 1) * s : xc + s;
-  const long long xm = (cc == 0) ? xc + (long long)(nd - 1) * s : xc - s;
-  const R pp = P[xp], p0 = P[xc], pm = P[xm];
-  return dev_abs(pp - R(2) * p0 + pm) / (pp + R(2) * p0 + pm);
-}
-
-template <int D, typename R, typename TQ, typename TM>
-__global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __restrict__ Q,
-                                              const TM* __restrict__ M,
-                                              const R* __restrict__ node,
-                                              const R* __restrict__ mk, R* __restrict__ F) {
-  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-  const long long N = g.N;
-  const R* __restrict__ U = node;
-  const R* __restrict__ V = node + N;
-  const R* __restrict__ Wv = node + 2 * N;
-  const R* __restrict__ P = node + 3 * N;
-  const R* __restrict__ Tt = node + 4 * N;
-  const R* __restrict__ LB = node + (5 + D) * N;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    decompose(g, n, c);
-    if (!g.per[D] && c[D] == g.n[D] - 1) continue;
-    if (!g.per[T1] && (c[T1] == 0 || c[T1] == g.n[T1] - 1)) continue;
-    if (!g.per[T2] && (c[T2] == 0 || c[T2] == g.n[T2] - 1)) continue;
-    const long long a = n;
-    const long long b = step(g, n, c, D, 1);
-    const long long am = step(g, n, c, D, -1);
-    const long long bp = step(g, n, c, D, 2);
-    int cb[3] = {c[0], c[1], c[2]};
-    cb[D] = (c[D] + 1 == g.n[D]) ? 0 : c[D] + 1;
-
-    // centred inviscid flux (Eq. hat-flux-G, xi_t = 0)
-    const R Ja = (R)M[9 * N + a], Jb = (R)M[9 * N + b];
-    const R ma0 = (R)M[(3 * D) * N + a], ma1 = (R)M[(3 * D + 1) * N + a],
-            ma2 = (R)M[(3 * D + 2) * N + a];
-    const R mb0 = (R)M[(3 * D) * N + b], mb1 = (R)M[(3 * D + 1) * N + b],
-            mb2 = (R)M[(3 * D + 2) * N + b];
-    const R pa = P[a], pb = P[b];
-    const R tha = ma0 * U[a] + ma1 * V[a] + ma2 * Wv[a];
-    const R thb = mb0 * U[b] + mb1 * V[b] + mb2 * Wv[b];
-    R Qa[5], Qb[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      Qa[q] = (R)Q[q * N + a];
-      Qb[q] = (R)Q[q * N + b];
-    }
-    R Fa[5], Fb[5];
-    Fa[0] = Ja * (Qa[0] * tha);
-    Fa[1] = Ja * (Qa[1] * tha + pa * ma0);
-    Fa[2] = Ja * (Qa[2] * tha + pa * ma1);
-    Fa[3] = Ja * (Qa[3] * tha + pa * ma2);
-    Fa[4] = Ja * ((Qa[4] + pa) * tha);
-    Fb[0] = Jb * (Qb[0] * thb);
-    Fb[1] = Jb * (Qb[1] * thb + pb * mb0);
-    Fb[2] = Jb * (Qb[2] * thb + pb * mb1);
-    Fb[3] = Jb * (Qb[3] * thb + pb * mb2);
-    Fb[4] = Jb * ((Qb[4] + pb) * thb);
-
-    // Turkel-Vatsa dissipation (Eqs. dissip_term, eps_2/4_dissip, W_dissip)
-    const R nua = sensor<D>(g, P, a, c[D]);
-    const R nub = sensor<D>(g, P, b, cb[D]);
-    const R eps2 = K.k2 * dev_max(nua, nub);
-    const R eps4 = dev_max(R(0), K.k4 - eps2);
-    const R lam = R(0.5) * (LB[a] + LB[b]);
-    const R Jh = R(0.5) * (Ja + Jb);
-    R Fq[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const R wa = (q == 4) ? Qa[4] + pa : Qa[q];
-      const R wb = (q == 4) ? Qb[4] + pb : Qb[q];
-      const R D1 = wb - wa;
-      R Dm, Dp;
-      if (am >= 0) {
-        const R wm = (q == 4) ? (R)Q[4 * N + am] + P[am] : (R)Q[q * N + am];
-        Dm = wa - wm;
-      } else {
-        Dm = -D1;
-      }
-      if (bp >= 0) {
-        const R wp = (q == 4) ? (R)Q[4 * N + bp] + P[bp] : (R)Q[q * N + bp];
-        Dp = wp - wb;
-      } else {
-        Dp = -D1;
-      }
-      const R D3 = Dp - R(2) * D1 + Dm;
-      Fq[q] = R(0.5) * (Fa[q] + Fb[q]) - Jh * (lam * (eps2 * D1 - eps4 * D3));
-    }
-
-    // viscous + SGS flux with compact interface gradients (Eqs.
-    // hat-flux-Ev/Fv/Gv, tau_mod, q_mod with Fourier's sign)
-    const R* phi[4] = {U, V, Wv, Tt};
-    R dphi[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dphi[q][D] = phi[q][b] - phi[q][a];
-    {
-      const long long ap = step(g, a, c, T1, 1), amm = step(g, a, c, T1, -1);
-      const long long bpp = step(g, b, cb, T1, 1), bm = step(g, b, cb, T1, -1);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        dphi[q][T1] = R(0.25) * ((phi[q][ap] - phi[q][amm]) + (phi[q][bpp] - phi[q][bm]));
-    }
-    {
-      const long long ap = step(g, a, c, T2, 1), amm = step(g, a, c, T2, -1);
-      const long long bpp = step(g, b, cb, T2, 1), bm = step(g, b, cb, T2, -1);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        dphi[q][T2] = R(0.25) * ((phi[q][ap] - phi[q][amm]) + (phi[q][bpp] - phi[q][bm]));
-    }
-    R mh[3][3];
-#pragma unroll
-    for (int t = 0; t < 3; ++t)
-#pragma unroll
-      for (int x = 0; x < 3; ++x)
-        mh[t][x] = R(0.5) * ((R)M[(3 * t + x) * N + a] + (R)M[(3 * t + x) * N + b]);
-    R gr[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int x = 0; x < 3; ++x)
-        gr[q][x] = mh[0][x] * dphi[q][0] + mh[1][x] * dphi[q][1] + mh[2][x] * dphi[q][2];
-    const R mu = R(0.5) * (mk[a] + mk[b]);
-    const R kap = R(0.5) * (mk[N + a] + mk[N + b]);
-    const R div = gr[0][0] + gr[1][1] + gr[2][2];
-    const R two3 = R(2.0 / 3.0);
-    const R txx = mu * (R(2) * gr[0][0] - two3 * div);
-    const R tyy = mu * (R(2) * gr[1][1] - two3 * div);
-    const R tzz = mu * (R(2) * gr[2][2] - two3 * div);
-    const R txy = mu * (gr[0][1] + gr[1][0]);
-    const R txz = mu * (gr[0][2] + gr[2][0]);
-    const R tyz = mu * (gr[1][2] + gr[2][1]);
-    const R uf = R(0.5) * (U[a] + U[b]);
-    const R vf = R(0.5) * (V[a] + V[b]);
-    const R wf = R(0.5) * (Wv[a] + Wv[b]);
-    const R bx = txx * uf + txy * vf + txz * wf + kap * gr[3][0];
-    const R by = txy * uf + tyy * vf + tyz * wf + kap * gr[3][1];
-    const R bz = txz * uf + tyz * vf + tzz * wf + kap * gr[3][2];
-    const R mx = mh[D][0], my = mh[D][1], mz = mh[D][2];
-    F[n] = Fq[0];
-    F[N + n] = Fq[1] - Jh * (mx * txx + my * txy + mz * txz);
-    F[2 * N + n] = Fq[2] - Jh * (mx * txy + my * tyy + mz * tyz);
-    F[3 * N + n] = Fq[3] - Jh * (mx * txz + my * tyz + mz * tzz);
-    F[4 * N + n] = Fq[4] - Jh * (mx * bx + my * by + mz * bz);
-  }
-}
-
-// ---------------------------------------------------------------- k_update
-template <typename R, typename TM, typename TO, int MODE>
-__global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
-                                                const double* __restrict__ Q0,
-                                                const TM* __restrict__ M,
-                                                const DevScalars* __restrict__ sc, double alpha,
-                                                TO* __restrict__ out) {
-  const long long N = g.N;
-  const R* F0 = F;
-  const R* F1 = F + 5 * N;
-  const R* F2 = F + 10 * N;
-  const double adt = (MODE == 0) ? 0.0 : alpha * sc->dt;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    decompose(g, n, c);
-    if (!is_interior(g, c)) {
-      if (MODE == 0) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) out[q * N + n] = (TO)0;
-      } else if (MODE == 1) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) out[q * N + n] = (TO)Q0[q * N + n];
-      }
-      continue;
-    }
-    const long long m0 = step(g, n, c, 0, -1);
-    const long long m1 = step(g, n, c, 1, -1);
-    const long long m2 = step(g, n, c, 2, -1);
-    const double Jinv = (double)M[9 * N + n];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      R r = R(0);
-      r += F0[q * N + n] - F0[q * N + m0];
-      r += F1[q * N + n] - F1[q * N + m1];
-      r += F2[q * N + n] - F2[q * N + m2];
-      if (MODE == 0) {
-        out[q * N + n] = (TO)r;
-      } else {
-        out[q * N + n] = (TO)(Q0[q * N + n] - adt * ((double)r / Jinv));
-      }
-    }
-  }
-}
 
 // ------------------------------------------------------------- launchers
 

@@ -1,0 +1,189 @@
+"""Discrete adjoint of the FP64 step (vector-Jacobian products) on the GPU.
+
+* Residual: the hand-written adjoint against the exact tangent obtained by
+  running the FP64 residual kernels on dual numbers: <lamR, J dQ> must equal
+  <J^T lamR, dQ> to round-off (dot-product test).
+* One time step (stages + boundary conditions + frozen viscosity): adjoint
+  against central finite differences of the GPU step, in a random state
+  direction and in every forcing-amplitude direction.
+* Window: the checkpointed adjoint gradient of the surface functional against
+  central finite differences (step 1e-6) of the whole window, and the
+  torch.autograd wrapper against the direct call.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lj():
+    from paper_2301_00817_gb300 import _build
+    _build.build()
+    import paper_2301_00817_gb300 as lj
+    lj.load_library()
+    return lj
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _jet(lj, torch, shape, **kw):
+    ctx = lj.Context(lj.make_params(**kw), shape, "cuda:0")
+    xyz = torch.from_numpy(lj.synth.jet_grid(*shape)).cuda()
+    ctx.les_set_grid(xyz)
+    return ctx, xyz
+
+
+def _vdot(a, b):
+    return float((a * b).sum())
+
+
+@pytest.mark.parametrize("case", ["jet", "box"])
+def test_residual_adjoint_dot_product(lj, torch, case):
+    if case == "jet":
+        shape = (13, 11, 8)
+        ctx, xyz = _jet(lj, torch, shape, Re=300.0)
+        Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+        ctx.les_init_jet(xyz, 3, 3e-2, Q)
+    else:
+        shape = (9, 11, 10)
+        xyz_np, shift = lj.synth.box_grid(shape, (1.0, 1.3, 0.8), wave=0.25)
+        ctx = lj.Context(lj.make_params(periodic=(1, 1, 1), bc=0, Re=300.0), shape, "cuda:0")
+        ctx.les_set_grid(torch.from_numpy(xyz_np).cuda(), shift)
+        import oracle
+        P = oracle.params(periodic=(1, 1, 1), bc=0)
+        prim = lj.synth.smooth_periodic_prim(xyz_np, (1.0, 1.3, 0.8), amp=0.2, seed=4)
+        Q = torch.from_numpy(oracle.prim_to_cons(P, prim)).cuda()
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    dQ = 1e-2 * torch.randn(Q.shape, dtype=torch.float64, device="cuda", generator=gen)
+    dMK = 1e-4 * torch.randn((2,) + shape, dtype=torch.float64, device="cuda", generator=gen)
+    lamR = torch.randn(Q.shape, dtype=torch.float64, device="cuda", generator=gen)
+    aw = ctx.adjoint_workspace()
+    R = torch.empty_like(Q)
+    dR = torch.empty_like(Q)
+    ctx.les_rhs_jvp(Q, dQ, dMK, R, dR, aw)
+    R_ref = torch.empty_like(Q)
+    ctx.les_rhs(Q, R_ref)
+    assert torch.equal(R, R_ref)  # the dual-number run reproduces the residual
+    lamQ = torch.empty_like(Q)
+    lamMK = torch.empty_like(dMK)
+    ctx.les_rhs_vjp(Q, lamR, lamQ, lamMK, aw)
+    lhs = _vdot(lamR, dR)
+    rhs = _vdot(lamQ, dQ) + _vdot(lamMK, dMK)
+    scale = _vdot(lamR.abs(), dR.abs())
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs)
+    # the viscosity direction alone, too
+    ctx.les_rhs_jvp(Q, torch.zeros_like(Q), dMK, None, dR, aw)
+    assert abs(_vdot(lamR, dR) - _vdot(lamMK, dMK)) <= 1e-12 * _vdot(lamR.abs(), dR.abs())
+
+
+def _step_ctx(lj, torch, shape, amps):
+    ctx, xyz = _jet(lj, torch, shape, Re=500.0, dt_mode=lj.DT_FIXED, dt_fixed=1.0e-3,
+                    amp=tuple(amps))
+    return ctx, xyz
+
+
+def test_step_adjoint_against_finite_differences(lj, torch):
+    shape = (14, 12, 8)
+    amps = lj.synth.forcing_amplitudes(5, scale=2e-2)
+    ctx, xyz = _step_ctx(lj, torch, shape, amps)
+    Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_init_jet(xyz, 7, 1e-2, Q)
+    t_n = 0.0137
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    # The initial pressure is uniform, so every pressure sensor |d2p| sits on
+    # its kink and a central difference straddles it.  Pressure fluctuations of
+    # 1e-2 (energy only) move the state to a generic point, far from the kinks
+    # at the finite-difference step used below.
+    Q[4] += 1e-2 / (lj.make_params().gamma - 1.0) * torch.randn(
+        shape, dtype=torch.float64, device="cuda", generator=gen)
+    lam = torch.randn(Q.shape, dtype=torch.float64, device="cuda", generator=gen)
+    u = torch.randn(Q.shape, dtype=torch.float64, device="cuda", generator=gen) * Q.abs().amax(
+        dim=(1, 2, 3), keepdim=True)
+    aw = ctx.adjoint_workspace()
+    lam_out = torch.empty_like(Q)
+    grad = ctx.les_adjoint_step(Q, t_n, lam, lam_out, aw)
+
+    def step(Qs, p=None):
+        if p is not None:
+            ctx.les_set_params(p)
+        Qw = Qs.clone()
+        ctx.les_set_time(t_n)
+        ctx.les_rk_step(Qw)
+        return Qw
+
+    eps = 1e-6
+    dq = (step(Q + eps * u) - step(Q - eps * u)) / (2 * eps)
+    lhs, rhs = _vdot(lam, dq), _vdot(lam_out, u)
+    assert abs(lhs - rhs) <= 1e-6 * abs(rhs), (lhs, rhs)
+    base = lj.LesParams.from_buffer_copy(ctx.params)
+    for m in range(16):
+        pp = lj.LesParams.from_buffer_copy(base)
+        pm = lj.LesParams.from_buffer_copy(base)
+        pp.amp[m] += eps
+        pm.amp[m] -= eps
+        fd = _vdot(lam, (step(Q, pp) - step(Q, pm)) / (2 * eps))
+        assert abs(fd - grad[m]) <= 1e-6 * max(abs(g) for g in grad), (m, fd, grad[m])
+    ctx.les_set_params(base)
+
+
+def _j_surface(lj, shape, radius):
+    r = lj.synth.jet_radial(shape[1])
+    return int(np.argmin(np.abs(r - radius)))
+
+
+def test_window_gradient_against_finite_differences(lj, torch):
+    """Well-conditioned companion of the far-field functional (pressure
+    fluctuation on the shear-layer surface r = 0.5 D), 6 steps with a
+    checkpoint every 2 steps."""
+    shape = (16, 14, 16)
+    amps = lj.synth.forcing_amplitudes(9, scale=2e-2)
+    ctx, xyz = _step_ctx(lj, torch, shape, amps)
+    Q0 = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_init_jet(xyz, 1, 1e-3, Q0)
+    j5 = _j_surface(lj, shape, 0.5)
+    nsteps, K = 6, 2
+    aw = ctx.adjoint_workspace(nsteps, K)
+    J, grad = ctx.les_adjoint_window(Q0, 0.0, nsteps, K, j5, aw)
+    assert J > 0 and max(abs(g) for g in grad) > 0
+    base = lj.LesParams.from_buffer_copy(ctx.params)
+    h = 1e-6
+    fd = []
+    for m in range(16):
+        pp = lj.LesParams.from_buffer_copy(base)
+        pm = lj.LesParams.from_buffer_copy(base)
+        pp.amp[m] += h
+        pm.amp[m] -= h
+        ctx.les_set_params(pp)
+        Jp, _ = ctx.les_adjoint_window(Q0, 0.0, nsteps, K, j5, aw)
+        ctx.les_set_params(pm)
+        Jm, _ = ctx.les_adjoint_window(Q0, 0.0, nsteps, K, j5, aw)
+        fd.append((Jp - Jm) / (2 * h))
+    ctx.les_set_params(base)
+    gmax = max(abs(g) for g in grad)
+    for m in range(16):
+        assert abs(fd[m] - grad[m]) <= 1e-6 * gmax, (m, fd[m], grad[m])
+    # same J and gradient through torch.autograd
+    a = torch.tensor(list(base.amp), dtype=torch.float64, requires_grad=True)
+    Jt = lj.window_functional(ctx, a, Q0, 0.0, nsteps, K, j5, aw)
+    Jt.backward()
+    assert math.isclose(float(Jt.detach()), J, rel_tol=1e-12)
+    assert np.allclose(a.grad.numpy(), np.array(grad), rtol=1e-12, atol=0)
+
+
+def test_adjoint_rejects_unsupported_settings(lj, torch):
+    shape = (8, 8, 8)
+    ctx, xyz = _jet(lj, torch, shape)  # CFL time step: not supported
+    Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_init_jet(xyz, 1, 1e-3, Q)
+    aw = ctx.adjoint_workspace(2, 1)
+    with pytest.raises(lj.LesError) as e:
+        ctx.les_adjoint_window(Q, 0.0, 2, 1, 3, aw)
+    assert e.value.code == lj.LES_ERR_UNSUPPORTED
