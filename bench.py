@@ -56,9 +56,10 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms; only the
+    samples stamped inside the timed region (mark_begin .. mark_end) count."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -66,6 +67,7 @@ class ClockSampler:
         self.proc = None
         self.path = None
         self.dev = device_index
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -76,7 +78,7 @@ class ClockSampler:
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "100"]
         if uuid:
             cmd += ["-i", uuid]
         try:
@@ -84,36 +86,59 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait for the first sample so that the timed region is covered
+        deadline = time.time() + 10.0
+        while time.time() < deadline and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
+
+    def mark_begin(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)  # let the sample after the timed region land
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons, power = [], [], set(), []
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-                power.append(float(parts[3]))
+                rows.append((self._stamp(parts[0]), float(parts[2]), float(parts[3]),
+                             float(parts[4]),
+                             {nm for nm, v in zip(names, parts[6:10]) if v.lower().startswith("active")}))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
         os.unlink(self.path)
-        if not sm:
+        inside = [r for r in rows if r[0] is not None and self.t0 is not None and
+                  self.t0 - 0.05 <= r[0] <= self.t1 + 0.1]
+        window = "timed region"
+        if not inside:
+            inside, window = rows, "whole sampler run (no sample stamped inside the timed region)"
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "power_w_max": max(power) if power else None, "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside),
+                "power_w_max": max(r[3] for r in inside), "samples": len(inside),
+                "window": window, "reasons": sorted(set().union(*(r[4] for r in inside)))}
 
 
 def dist_setup():
@@ -200,6 +225,83 @@ def time_steps(lj, torch, ctx, Q, steps, stream):
     return e0.elapsed_time(e1), diag
 
 
+ADJ_WORKLOAD = (192, 96, 128)
+ADJ_STEPS, ADJ_CKPT = 50, 10
+
+
+def adjoint_leg(lj, torch, local):
+    """Adjoint/forward cost on the jet 192 x 96 x 128 window: 50 FP64 steps,
+    checkpoint every 10, 16 seeded forcing amplitudes, functional on the
+    eta-surface nearest r = 5 D, no SGS model, fixed time step (the CFL step
+    of the initial state).  Forward = les_run_n_steps over the window;
+    adjoint = les_adjoint_window (forward sweep with checkpoints, segment
+    recompute, reverse sweep)."""
+    import numpy as np
+    shape = ADJ_WORKLOAD
+    xyz = torch.from_numpy(lj.synth.jet_grid(*shape)).cuda()
+    amps = tuple(lj.synth.forcing_amplitudes(0))
+    ctx = lj.Context(lj.make_params(precision=lj.PREC_FP64, sgs_model=lj.SGS_NONE, amp=amps),
+                     shape, f"cuda:{local}")
+    ctx.les_set_grid(xyz)
+    Q0 = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_init_jet(xyz, 0, 1e-3, Q0)
+    dt = ctx.les_time_step(Q0)
+    ctx.les_set_params(lj.make_params(precision=lj.PREC_FP64, sgs_model=lj.SGS_NONE, amp=amps,
+                                      dt_mode=lj.DT_FIXED, dt_fixed=dt))
+    j5 = int(np.argmin(np.abs(lj.synth.jet_radial(shape[1]) - 5.0)))
+    aw = ctx.adjoint_workspace(ADJ_STEPS, ADJ_CKPT)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        Q = Q0.clone()
+        ctx.les_set_time(0.0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.les_run_n_steps(ADJ_STEPS, Q)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def adj():
+        torch.cuda.synchronize()
+        e0.record(stream)
+        J, g = ctx.les_adjoint_window(Q0, 0.0, ADJ_STEPS, ADJ_CKPT, j5, aw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), J, g
+
+    fwd(), adj()  # warm-up
+    t_f = min(fwd() for _ in range(3))
+    runs = [adj() for _ in range(3)]
+    t_a, J, g = min(runs, key=lambda r: r[0])
+    gnorm = float(np.linalg.norm(g))
+    ws = aw.numel()
+    # the same window with every stage state kept by the forward sweep (one
+    # segment, no recompute): the memory-for-time end of the trade
+    del aw
+    aw = ctx.adjoint_workspace(ADJ_STEPS, ADJ_STEPS)
+    K = ADJ_STEPS
+
+    def adj_all():
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.les_adjoint_window(Q0, 0.0, ADJ_STEPS, K, j5, aw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    adj_all()
+    t_all = min(adj_all() for _ in range(3))
+    return {"workload": f"jet {shape[0]}x{shape[1]}x{shape[2]}, FP64, SGS none, "
+                        f"{ADJ_STEPS}-step window, checkpoint every {ADJ_CKPT}",
+            "functional": "sum_n dt sum_(i,k) (p - 1/gamma)^2 dA on the eta surface nearest r = 5",
+            "dt": dt, "j_surface": j5, "forward_ms": t_f, "adjoint_window_ms": t_a,
+            "ratio": t_a / t_f, "J": J, "grad_norm": gnorm, "workspace_gb": ws / 1e9,
+            "store_all": {"adjoint_window_ms": t_all, "ratio": t_all / t_f,
+                          "workspace_gb": aw.numel() / 1e9}}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -234,7 +336,10 @@ def run_ours(args, world, rank, local):
         sampler = ClockSampler(local) if name == "mixed" else None
         if sampler:
             sampler.start()
+            sampler.mark_begin()
         ms, diag = time_steps(lj, torch, ctx, Q, args.steps, stream)
+        if sampler:
+            sampler.mark_end()
         clocks = sampler.stop() if sampler else None
         barrier(world)
         prof = ctx.les_profile_read()
@@ -271,6 +376,10 @@ def run_ours(args, world, rank, local):
                                      torch.linalg.vector_norm(b[c]))
                for c, nm in ((0, "rho"), (1, "rho_u"), (4, "rho_E"))}
         err["steps"] = args.accuracy_steps
+
+    adj = None
+    if not args.no_adjoint:
+        adj = adjoint_leg(lj, torch, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -322,7 +431,8 @@ def run_ours(args, world, rank, local):
         "mixed_error_vs_fp64": err,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in mixed["prof"].items() if v[1]},
         "kernel_ms_per_step_fp64": {k: v[0] / args.steps for k, v in fp64["prof"].items() if v[1]},
-        "adjoint_fwd_ratio": None,
+        "adjoint_fwd_ratio": adj["ratio"] if adj else None,
+        "adjoint": adj,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -334,12 +444,31 @@ def run_ours(args, world, rank, local):
 
 def run_profile_case(which: str):
     """Small case for ncu captures: 96 x 160 x 128 jet (1.97M points, state
-    and metrics above the 129 MB L2), two full steps, one precision."""
+    and metrics above the 129 MB L2), two full steps, one precision; or the
+    adjoint window on 96 x 96 x 128 (10 steps, checkpoint every 5)."""
+    import numpy as np
     import torch
 
     import paper_2301_00817_gb300 as lj
     from paper_2301_00817_gb300 import _build
     _build.build()
+    if which == "adjoint":
+        shape = (96, 96, 128)
+        amps = tuple(lj.synth.forcing_amplitudes(0))
+        kw = dict(precision=lj.PREC_FP64, sgs_model=lj.SGS_NONE, amp=amps)
+        ctx = lj.Context(lj.make_params(**kw), shape)
+        xyz = torch.from_numpy(lj.synth.jet_grid(*shape)).cuda()
+        ctx.les_set_grid(xyz)
+        Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+        ctx.les_init_jet(xyz, 0, 1e-3, Q)
+        dt = ctx.les_time_step(Q)
+        ctx.les_set_params(lj.make_params(dt_mode=lj.DT_FIXED, dt_fixed=dt, **kw))
+        j5 = int(np.argmin(np.abs(lj.synth.jet_radial(shape[1]) - 5.0)))
+        aw = ctx.adjoint_workspace(10, 5)
+        J, g = ctx.les_adjoint_window(Q, 0.0, 10, 5, j5, aw)
+        print(f"profile case adjoint: J={J:.6e} |grad|={float(np.linalg.norm(g)):.3e} "
+              f"launches={ctx.les_launch_count()}")
+        return 0
     prec = lj.PREC_MIXED if which == "mixed" else lj.PREC_FP64
     shape = (96, 160, 128)
     ctx = lj.Context(lj.make_params(sgs_model=lj.SGS_SMAGORINSKY, precision=prec), shape)
@@ -355,13 +484,14 @@ def run_profile_case(which: str):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--accuracy-steps", type=int, default=100)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=("fp64", "mixed"), default=None,
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--profile-case", choices=("fp64", "mixed", "adjoint"), default=None,
                     help="run the small ncu case (two steps) and exit")
     args = ap.parse_args()
     if args.profile_case:

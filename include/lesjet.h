@@ -194,8 +194,10 @@ const char *les_profile_name(int kind);
  * dt_mode LES_DT_FIXED (the step does not depend on the CFL minimum),
  * sgs_model LES_SGS_NONE, freeze_visc 1; LES_ERR_UNSUPPORTED otherwise.
  * Scratch lives in a caller-owned adjoint workspace of
- * les_adjoint_workspace_bytes(ctx, nsteps, ckpt_every) bytes (its size grows
- * with the number of checkpoints of les_adjoint_window).  At non-smooth
+ * les_adjoint_workspace_bytes(ctx, nsteps, ckpt_every) bytes: about
+ * (165 + 5 ceil(nsteps/ckpt_every) + 32 ckpt_every) N doubles for a window
+ * (checkpoints, plus every stage state of one segment), 165 N for
+ * nsteps = 0 (residual and single-step calls only).  At non-smooth
  * points the derivative follows the forward branch: |x| has slope -1 for
  * x < 0 and +1 otherwise; a max passes to the operand it selected.
  * ------------------------------------------------------------------------ */
@@ -225,8 +227,9 @@ int les_adjoint_step(les_ctx *ctx, const double *Qn, double t_n,
 /* Forward window of nsteps steps from Q_start at t0 and its adjoint: returns
  * J = sum_{n=1..nsteps} dt sum_{i,k} (p(i, j_surface, k) - 1/gamma)^2 dA with
  * dA = J^-1 |grad eta| (the eta-face area) and grad[16] = dJ/da.  Stores a
- * checkpoint every ckpt_every steps and recomputes each segment's states in
- * the reverse sweep.  Q_start is not modified.  SYNCHRONISES. */
+ * checkpoint every ckpt_every steps; the reverse sweep recomputes one
+ * segment at a time, keeping its stage states, then runs its adjoint steps.
+ * Q_start is not modified.  SYNCHRONISES. */
 int les_adjoint_window(les_ctx *ctx, const double *Q_start, double t0,
                        int nsteps, int ckpt_every, int j_surface,
                        void *adj_ws, double *J_out, double grad[16],

@@ -587,7 +587,7 @@ namespace {
 
 struct AdjLayout {
   size_t acc, node, mk, lamMK, S, lamS, lamR, lamQ0, work, lam, Qnext, E, partials, scal;
-  size_t qd, mkd, noded, fluxd, rd, ckpt, seg, total;
+  size_t qd, mkd, noded, fluxd, rd, ckpt, segS, segMK, total;
   int nckpt, K;
 };
 
@@ -622,7 +622,11 @@ AdjLayout adj_layout(const les_ctx* c, int nsteps, int K) {
   L.K = K > 0 ? K : 1;
   L.nckpt = nsteps > 0 ? (nsteps + L.K - 1) / L.K + 1 : 1;
   L.ckpt = take((size_t)L.nckpt * 5 * N * d);
-  L.seg = take((size_t)(L.K + 1) * 5 * N * d);
+  // one segment of the window: the six stage states and the frozen viscosity
+  // of each of its K steps, kept from the recompute for the reverse sweep
+  const int ks = nsteps > 0 ? L.K : 0;
+  L.segS = take((size_t)ks * 6 * 5 * N * d);
+  L.segMK = take((size_t)ks * 2 * N * d);
   L.total = o;
   return L;
 }
@@ -658,27 +662,15 @@ lesjet::StageIO64 adj_io(les_ctx* c, void* aw, const AdjLayout& Ly, const double
   return io;
 }
 
-// lam_out = (dQ^{n+1}/dQ^n)^T lam_next; grad_dev[16] += (dQ^{n+1}/da)^T lam_next.
-// lam_out may alias lam_next.
-void adj_step(les_ctx* c, void* aw, const AdjLayout& Ly, const double* Qn, double t_n,
-              const double* lam_next, double* lam_out, double* grad_dev, cudaStream_t s) {
+// Forward recompute of one step from S[0] = Q^n: frozen viscosity mk of Q^n
+// and the stage states S[1..5] (S[5] before the boundary conditions).
+void adj_forward(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], double* mk,
+                 cudaStream_t s) {
   lesjet::Launch L{s, &c->launches};
   const Grid& g = c->g;
-  const size_t bytes = 5 * (size_t)g.N * sizeof(double);
-  const double dt = c->p.dt_fixed;
-  const double* M = at<double>(c, c->off_m64);
-  DevScalars* sc = at<DevScalars>(c, c->off_sc);
-  double* S[6];
-  for (int l = 0; l < 6; ++l) S[l] = aw_at<double>(aw, Ly.S) + (size_t)l * 5 * g.N;
-  double* lamS = aw_at<double>(aw, Ly.lamS);
-  double* lamR = aw_at<double>(aw, Ly.lamR);
-  double* lamQ0 = aw_at<double>(aw, Ly.lamQ0);
-  double* lamMK = aw_at<double>(aw, Ly.lamMK);
-  double* Qnext = aw_at<double>(aw, Ly.Qnext);
-  // forward recompute: viscosity of Q^n, the five stage states, Q^{n+1}
-  cudaMemcpyAsync(S[0], Qn, bytes, cudaMemcpyDeviceToDevice, s);
-  lesjet::launch_dt_finalize(c->p, at<double>(c, c->off_part), sc, 0, L);
   lesjet::StageIO64 io = adj_io(c, aw, Ly, S[0]);
+  io.mk = mk;
+  lesjet::launch_dt_finalize(c->p, at<double>(c, c->off_part), at<DevScalars>(c, c->off_sc), 0, L);
   lesjet::launch_node64(g, c->p, io, false, L);
   lesjet::launch_mu64(g, c->p, io, L);
   for (int l = 1; l <= 5; ++l) {
@@ -687,7 +679,28 @@ void adj_step(les_ctx* c, void* aw, const AdjLayout& Ly, const double* Qn, doubl
     for (int d = 0; d < 3; ++d) lesjet::launch_flux64(g, c->p, io, d, L);
     lesjet::launch_update64(g, io, S[0], kAlpha[l - 1], 1, S[l], L);
   }
-  // reverse: boundary conditions at t^{n+1}
+}
+
+// Reverse of one step whose forward states S[0..5] and viscosity mk are
+// stored: lam_out = (dQ^{n+1}/dQ^n)^T lam_next; grad_dev[16] +=
+// (dQ^{n+1}/da)^T lam_next.  lam_out may alias lam_next.
+void adj_reverse(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], const double* mk,
+                 double t_n, const double* lam_next, double* lam_out, double* grad_dev,
+                 cudaStream_t s) {
+  lesjet::Launch L{s, &c->launches};
+  const Grid& g = c->g;
+  const size_t bytes = 5 * (size_t)g.N * sizeof(double);
+  const double dt = c->p.dt_fixed;
+  const double* M = at<double>(c, c->off_m64);
+  DevScalars* sc = at<DevScalars>(c, c->off_sc);
+  double* lamS = aw_at<double>(aw, Ly.lamS);
+  double* lamR = aw_at<double>(aw, Ly.lamR);
+  double* lamQ0 = aw_at<double>(aw, Ly.lamQ0);
+  double* lamMK = aw_at<double>(aw, Ly.lamMK);
+  double* Qnext = aw_at<double>(aw, Ly.Qnext);
+  lesjet::StageIO64 io = adj_io(c, aw, Ly, S[0]);
+  io.mk = const_cast<double*>(mk);
+  // boundary conditions at t^{n+1}
   if (c->p.bc == LES_BC_JET) {
     cudaMemcpyAsync(Qnext, S[5], bytes, cudaMemcpyDeviceToDevice, s);
     lesjet::launch_bc_jet(g, c->p, Qnext, M, at<double>(c, c->off_rth), sc, 1, t_n + dt, L);
@@ -696,7 +709,7 @@ void adj_step(les_ctx* c, void* aw, const AdjLayout& Ly, const double* Qn, doubl
   } else {
     cudaMemcpyAsync(lamS, lam_next, bytes, cudaMemcpyDeviceToDevice, s);
   }
-  // reverse: stages 5 .. 1
+  // stages 5 .. 1
   cudaMemsetAsync(lamQ0, 0, bytes, s);
   cudaMemsetAsync(lamMK, 0, 2 * (size_t)g.N * sizeof(double), s);
   for (int l = 5; l >= 1; --l) {
@@ -776,7 +789,12 @@ int les_adjoint_step(les_ctx* c, const double* Qn, double t_n, const double* lam
   const AdjLayout Ly = adj_layout(c, 0, 1);
   double* gdev = aw_at<double>(aw, Ly.scal) + 1;
   cudaMemsetAsync(gdev, 0, 16 * sizeof(double), s);
-  adj_step(c, aw, Ly, Qn, t_n, lam_next, lam_out, gdev, s);
+  double* S[6];
+  for (int l = 0; l < 6; ++l) S[l] = aw_at<double>(aw, Ly.S) + (size_t)l * 5 * c->g.N;
+  cudaMemcpyAsync(S[0], Qn, 5 * (size_t)c->g.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  double* mk = aw_at<double>(aw, Ly.mk);
+  adj_forward(c, aw, Ly, S, mk, s);
+  adj_reverse(c, aw, Ly, S, mk, t_n, lam_next, lam_out, gdev, s);
   if ((rc = cuda_check(c, "les_adjoint_step")) != LES_OK) return rc;
   double h[16];
   cudaMemcpyAsync(h, gdev, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -811,31 +829,65 @@ int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps,
   double* work = aw_at<double>(aw, Ly.work);
   double* lam = aw_at<double>(aw, Ly.lam);
   auto ckpt = [&](int k) { return aw_at<double>(aw, Ly.ckpt) + (size_t)k * 5 * g.N; };
-  auto seg = [&](int k) { return aw_at<double>(aw, Ly.seg) + (size_t)k * 5 * g.N; };
+  auto segS = [&](int m, int l) {
+    return aw_at<double>(aw, Ly.segS) + ((size_t)m * 6 + l) * 5 * g.N;
+  };
+  auto segMK = [&](int m) { return aw_at<double>(aw, Ly.segMK) + (size_t)m * 2 * g.N; };
   cudaMemsetAsync(scal, 0, 64 * sizeof(double), s);
+  DevScalars* sc = at<DevScalars>(c, c->off_sc);
+  const int last = (nsteps - 1) / K;  // the last segment is kept by the forward sweep
+  // one step from segS(m, 0), keeping its stage states; Q^{n+1} goes to dst
+  auto kept_step = [&](int m, int n, double* dst) {
+    double* S[6];
+    for (int l = 0; l < 6; ++l) S[l] = segS(m, l);
+    adj_forward(c, aw, Ly, S, segMK(m), s);
+    cudaMemcpyAsync(dst, S[5], bytes, cudaMemcpyDeviceToDevice, s);
+    if (c->p.bc == LES_BC_JET)
+      lesjet::launch_bc_jet(g, c->p, dst, M, at<double>(c, c->off_rth), sc, 1, t0 + (n + 1) * dt, L);
+  };
   // forward window, checkpoints every K steps
   cudaMemcpyAsync(ckpt(0), Q_start, bytes, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(work, Q_start, bytes, cudaMemcpyDeviceToDevice, s);
-  lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), t0, L);
+  lesjet::launch_set_time(sc, t0, L);
   for (int n = 1; n <= nsteps; ++n) {
-    rk_step(c, work, s);
-    lesjet::launch_functional(g, c->p, j_surface, dt, M, work, nullptr, part, Jdev, L);
+    const int m = n - 1 - last * K;
+    const double* Qn = work;
+    if (m < 0) {
+      rk_step(c, work, s);
+    } else {
+      if (m == 0) cudaMemcpyAsync(segS(0, 0), work, bytes, cudaMemcpyDeviceToDevice, s);
+      double* dst = (n == nsteps) ? work : segS(m + 1, 0);
+      kept_step(m, n - 1, dst);
+      Qn = dst;
+    }
+    lesjet::launch_functional(g, c->p, j_surface, dt, M, Qn, nullptr, part, Jdev, L);
     if (n % K == 0 && n < nsteps) cudaMemcpyAsync(ckpt(n / K), work, bytes, cudaMemcpyDeviceToDevice, s);
   }
   // reverse sweep, segment by segment, recomputing the segment's states
   cudaMemsetAsync(lam, 0, bytes, s);
-  for (int sg = (nsteps - 1) / K; sg >= 0; --sg) {
+  for (int sg = last; sg >= 0; --sg) {
     const int n0 = sg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
-    cudaMemcpyAsync(seg(0), ckpt(sg), bytes, cudaMemcpyDeviceToDevice, s);
-    lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), t0 + n0 * dt, L);
-    for (int m = 1; m <= n1 - 1 - n0; ++m) {
-      cudaMemcpyAsync(seg(m), seg(m - 1), bytes, cudaMemcpyDeviceToDevice, s);
-      rk_step(c, seg(m), s);
+    // recompute the segment from its checkpoint, keeping every stage state
+    // and viscosity (Q^{n1} itself is the next checkpoint)
+    if (sg != last) {
+      cudaMemcpyAsync(segS(0, 0), ckpt(sg), bytes, cudaMemcpyDeviceToDevice, s);
+      for (int m = 0; m < n1 - n0; ++m) {
+        if (m + 1 < n1 - n0) {
+          kept_step(m, n0 + m, segS(m + 1, 0));
+        } else {
+          double* S[6];
+          for (int l = 0; l < 6; ++l) S[l] = segS(m, l);
+          adj_forward(c, aw, Ly, S, segMK(m), s);
+        }
+      }
     }
     for (int n = n1; n >= n0 + 1; --n) {
-      const double* Qn = (n == nsteps) ? work : ((n == n1) ? ckpt(sg + 1) : seg(n - n0));
+      const int m = n - 1 - n0;
+      const double* Qn = (n == nsteps) ? work : ((n == n1) ? ckpt(sg + 1) : segS(m + 1, 0));
       lesjet::launch_functional(g, c->p, j_surface, dt, M, Qn, lam, part, Jscratch, L);
-      adj_step(c, aw, Ly, seg(n - 1 - n0), t0 + (n - 1) * dt, lam, lam, gdev, s);
+      double* S[6];
+      for (int l = 0; l < 6; ++l) S[l] = segS(m, l);
+      adj_reverse(c, aw, Ly, S, segMK(m), t0 + (n - 1) * dt, lam, lam, gdev, s);
     }
   }
   if ((rc = cuda_check(c, "les_adjoint_window")) != LES_OK) return rc;

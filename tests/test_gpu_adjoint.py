@@ -7,8 +7,9 @@
   against central finite differences of the GPU step, in a random state
   direction and in every forcing-amplitude direction.
 * Window: the checkpointed adjoint gradient of the surface functional against
-  central finite differences (step 1e-6) of the whole window, and the
-  torch.autograd wrapper against the direct call.
+  central finite differences (step 1e-6) of the whole window, the same result
+  for several checkpoint spacings, and the torch.autograd wrapper against the
+  direct call.
 """
 import math
 
@@ -170,6 +171,13 @@ def test_window_gradient_against_finite_differences(lj, torch):
     gmax = max(abs(g) for g in grad)
     for m in range(16):
         assert abs(fd[m] - grad[m]) <= 1e-6 * gmax, (m, fd[m], grad[m])
+    # other checkpoint spacings (every step, a ragged last segment, the whole
+    # window kept by the forward sweep) give the same functional and gradient
+    for K2 in (1, 4, nsteps):
+        aw2 = ctx.adjoint_workspace(nsteps, K2)
+        J2, g2 = ctx.les_adjoint_window(Q0, 0.0, nsteps, K2, j5, aw2)
+        assert math.isclose(J2, J, rel_tol=1e-12), (K2, J2, J)
+        assert np.allclose(g2, grad, rtol=0, atol=1e-10 * gmax), K2
     # same J and gradient through torch.autograd
     a = torch.tensor(list(base.amp), dtype=torch.float64, requires_grad=True)
     Jt = lj.window_functional(ctx, a, Q0, 0.0, nsteps, K, j5, aw)
