@@ -338,6 +338,77 @@ def adjoint_leg(lj, torch, local):
                           "workspace_gb": aw.numel() / 1e9}}
 
 
+LARGE_WORKLOAD = (2000, 500, 1024)
+LARGE_SUBGRID = (1000, 250, 512)
+LARGE_STEPS = 20
+
+
+def _free_device_bytes(torch):
+    import gc
+    gc.collect()
+    torch.cuda.empty_cache()
+    return torch.cuda.mem_get_info()[0]
+
+
+def large_leg(lj, torch, local, hbm_peak, warmup):
+    """The compact FP32-mixed form on the 2000 x 500 x 1024 jet (1.02e9
+    points): 20 timed steps, the fused stage kernel's HBM fraction, device
+    memory; and its error against FP64 after 20 steps on the 1/8-size
+    1000 x 250 x 512 grid."""
+    shape = LARGE_WORKLOAD
+    N = shape[0] * shape[1] * shape[2]
+    need = N * (40 + 129 + 24) + (4 << 30)
+    free = _free_device_bytes(torch)
+    if free < need:
+        return {"skipped": f"needs {need / 1e9:.0f} GB free device memory, {free / 1e9:.0f} GB free"}
+    stream = torch.cuda.current_stream()
+    ctx = lj.Context(lj.make_params(sgs_model=lj.SGS_SMAGORINSKY,
+                                    precision=lj.PREC_MIXED_COMPACT), shape, f"cuda:{local}")
+    xyz = lj.synth.jet_grid_torch(*shape, f"cuda:{local}")
+    ctx.les_set_grid(xyz)
+    Q = torch.empty((5,) + shape, dtype=torch.float64, device=f"cuda:{local}")
+    ctx.les_init_jet(xyz, 0, 1e-3, Q)
+    del xyz
+    torch.cuda.empty_cache()
+    ctx.les_run_n_steps(warmup, Q)
+    used = torch.cuda.memory_allocated()
+    ctx.les_profile(True)
+    ms, diag = time_steps(lj, torch, ctx, Q, LARGE_STEPS, stream)
+    prof = ctx.les_profile_read()
+    ctx.les_profile(False)
+    ms_f, n_f = prof.get("stage_fused", (0.0, 0))
+    bpp = BYTES_PER_POINT["stage_fused"][1]
+    achieved = bpp * N / (ms_f / n_f / 1e3) / 1e9 if n_f else None
+    out = {"workload": f"jet {shape[0]}x{shape[1]}x{shape[2]} ({N / 1e9:.2f}e9 points), "
+                       "compact FP32-mixed (no FP64 metric copy), Smagorinsky",
+           "value": N * LARGE_STEPS / (ms / 1e3) / 1e9, "unit": UNIT,
+           "ms_per_step": ms / LARGE_STEPS, "status": diag.status,
+           "device_gb_allocated": used / 1e9, "workspace_bytes_per_point": ctx.workspace.numel() / N,
+           "stage_fused_hbm_frac": achieved / hbm_peak if achieved else None}
+    del ctx, Q
+    # error against FP64 on the 1/8-size grid
+    sub = LARGE_SUBGRID
+    xyz = lj.synth.jet_grid_torch(*sub, f"cuda:{local}")
+    res = {}
+    for prec in (lj.PREC_FP64, lj.PREC_MIXED_COMPACT):
+        c = lj.Context(lj.make_params(sgs_model=lj.SGS_SMAGORINSKY, precision=prec), sub,
+                       f"cuda:{local}")
+        c.les_set_grid(xyz)
+        Qs = torch.empty((5,) + sub, dtype=torch.float64, device=f"cuda:{local}")
+        c.les_init_jet(xyz, 0, 1e-3, Qs)
+        c.les_run_n_steps(LARGE_STEPS, Qs)
+        res[prec] = Qs
+        del c
+    a, b = res[lj.PREC_MIXED_COMPACT], res[lj.PREC_FP64]
+    out["error_vs_fp64_subgrid"] = {
+        f"rel_l2_{nm}": float(torch.linalg.vector_norm(a[c] - b[c]) / torch.linalg.vector_norm(b[c]))
+        for c, nm in ((0, "rho"), (1, "rho_u"), (4, "rho_E"))}
+    out["error_vs_fp64_subgrid"]["grid"] = f"{sub[0]}x{sub[1]}x{sub[2]}, {LARGE_STEPS} steps"
+    del res, a, b, xyz
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -416,6 +487,15 @@ def run_ours(args, world, rank, local):
     adj = None
     if not args.no_adjoint:
         adj = adjoint_leg(lj, torch, local)
+    large = None
+    if world > 1:
+        large = {"skipped": "run at n_gpus = 1 only"}
+    elif not args.no_large:
+        for name in ("mixed", "fp64"):
+            results[name].pop("ctx", None)
+            results[name].pop("Q", None)
+        del ctx, Qh, Qstage
+        large = large_leg(lj, torch, local, hbm_peak, args.warmup)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -486,6 +566,7 @@ def run_ours(args, world, rank, local):
         "kernel_ms_per_step_fp64": {k: v[0] / args.steps for k, v in fp64["prof"].items() if v[1]},
         "adjoint_fwd_ratio": adj["ratio"] if adj else None,
         "adjoint": adj,
+        "large": large,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -544,6 +625,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 1.02e9-point compact mixed leg")
     ap.add_argument("--profile-case", choices=("fp64", "mixed", "adjoint"), default=None,
                     help="run the small ncu case (two steps) and exit")
     args = ap.parse_args()

@@ -47,7 +47,11 @@ enum {
 };
 
 enum { LES_SGS_NONE = 0, LES_SGS_SMAGORINSKY = 1, LES_SGS_VREMAN = 2 };
-enum { LES_PREC_FP64 = 0, LES_PREC_MIXED = 1 };
+/* LES_PREC_MIXED_COMPACT is the mixed form without the FP64 copy of the
+ * metrics (80 bytes per point less): metrics are computed in FP64 and stored
+ * once rounded to FP32, which the boundary conditions and the totals then
+ * read; les_metrics() returns NULL.  It is the form for the largest grids. */
+enum { LES_PREC_FP64 = 0, LES_PREC_MIXED = 1, LES_PREC_MIXED_COMPACT = 2 };
 enum { LES_BC_FROZEN = 0, LES_BC_JET = 1 };
 enum { LES_DT_CFL = 0, LES_DT_FIXED = 1 };
 
@@ -78,7 +82,8 @@ typedef struct les_params {
                          or LES_BC_JET (needs periodic = {0,0,1}) */
   int dt_mode;        /* LES_DT_CFL or LES_DT_FIXED */
   int freeze_visc;    /* 1: mu_eff, kappa_eff from Q^n held for 5 stages */
-  int precision;      /* LES_PREC_FP64 or LES_PREC_MIXED */
+  int precision;      /* LES_PREC_FP64, LES_PREC_MIXED or
+                         LES_PREC_MIXED_COMPACT */
 } les_params;
 
 /* Diagnostics returned by the synchronising run calls. */
@@ -92,7 +97,7 @@ typedef struct les_diag {
 
 typedef struct les_ctx les_ctx;
 
-/* Create a context for an ni x nj x nk grid (each >= 5; N < 2^40, N < 2^31 in the mixed form).  Host
+/* Create a context for an ni x nj x nk grid (each >= 5; N < 2^40, N < 2^31 in the mixed forms).  Host
  * memory only; *out is owned by the caller and released by les_destroy. */
 int les_create(const les_params *p, int ni, int nj, int nk, les_ctx **out);
 int les_destroy(les_ctx *ctx);
@@ -116,7 +121,8 @@ int les_set_grid(les_ctx *ctx, const double *xyz, const double shift[9],
                  void *workspace, les_stream_t stream);
 
 /* Device pointer to the FP64 metrics [10][N] inside the workspace:
- * xi_x xi_y xi_z eta_x eta_y eta_z zeta_x zeta_y zeta_z J^-1. */
+ * xi_x xi_y xi_z eta_x eta_y eta_z zeta_x zeta_y zeta_z J^-1.  NULL before
+ * les_set_grid and for LES_PREC_MIXED_COMPACT contexts. */
 const double *les_metrics(const les_ctx *ctx);
 
 /* Jet initial condition into Q (device [5][N]): rho = 1, p = 1/gamma,

@@ -27,7 +27,7 @@ LES_ERR_UNSUPPORTED = -6
 LES_ERR_STATE = -7
 
 SGS_NONE, SGS_SMAGORINSKY, SGS_VREMAN = 0, 1, 2
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_COMPACT = 0, 1, 2
 BC_FROZEN, BC_JET = 0, 1
 DT_CFL, DT_FIXED = 0, 1
 
@@ -193,8 +193,12 @@ class Context:
                                           _stream(stream)))
 
     def les_metrics(self):
+        """FP64 metrics [10, ni, nj, nk] (a view of the workspace), or None for
+        a compact mixed context, which keeps FP32 metrics only."""
         torch = _torch()
         ptr = self.lib.les_metrics(self.h)
+        if not ptr:
+            return None
         off = ptr - self.workspace.data_ptr()
         return self.workspace[off:off + 80 * self.N].view(torch.float64).view(10, *self.shape)
 

@@ -116,8 +116,9 @@ int validate_params(const les_params* p, std::string& why) {
     why = "sgs_model must be LES_SGS_NONE, LES_SGS_SMAGORINSKY or LES_SGS_VREMAN";
     return LES_ERR_INVALID_ARG;
   }
-  if (p->precision != LES_PREC_FP64 && p->precision != LES_PREC_MIXED) {
-    why = "precision must be LES_PREC_FP64 or LES_PREC_MIXED";
+  if (p->precision != LES_PREC_FP64 && p->precision != LES_PREC_MIXED &&
+      p->precision != LES_PREC_MIXED_COMPACT) {
+    why = "precision must be LES_PREC_FP64, LES_PREC_MIXED or LES_PREC_MIXED_COMPACT";
     return LES_ERR_INVALID_ARG;
   }
   if (p->dt_mode == LES_DT_CFL ? !(p->cfl > 0.0) : (p->dt_mode != LES_DT_FIXED || !(p->dt_fixed > 0.0))) {
@@ -141,10 +142,11 @@ int validate_params(const les_params* p, std::string& why) {
 
 void layout(les_ctx* c) {
   const size_t N = (size_t)c->g.N;
-  const bool mixed = c->p.precision == LES_PREC_MIXED;
+  const bool mixed = c->p.precision != LES_PREC_FP64;
+  const bool m64 = c->p.precision != LES_PREC_MIXED_COMPACT;  // FP64 metrics kept
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
   size_t o = 0;
-  c->off_m64 = o; o = align256(o + 10 * N * sizeof(double));
+  c->off_m64 = o; o = align256(o + (m64 ? 10 * N * sizeof(double) : 0));
   c->off_m32 = o; o = align256(o + (mixed ? 10 * N * sizeof(float) : 0));
   c->off_mk = o; o = align256(o + 2 * N * rs);
   c->off_sa = o; o = align256(o + 5 * N * rs);
@@ -170,7 +172,10 @@ int ready(les_ctx* c) {
   return LES_OK;
 }
 
-bool is_mixed(const les_ctx* c) { return c->p.precision == LES_PREC_MIXED; }
+bool is_mixed(const les_ctx* c) { return c->p.precision != LES_PREC_FP64; }
+// The compact mixed form keeps no FP64 copy of the metrics: its boundary
+// conditions and totals read the FP32 metrics.
+bool has_m64(const les_ctx* c) { return c->p.precision != LES_PREC_MIXED_COMPACT; }
 
 // ---- FP64 form: node, viscosity, per-direction flux and update passes
 lesjet::StageIO64 io64(les_ctx* c, const double* Qin) {
@@ -274,9 +279,22 @@ void rk_step(les_ctx* c, double* Q, cudaStream_t s) {
   }
   if (c->p.bc == LES_BC_JET) {
     ProfScope ps(c, PK_BC, s);
-    lesjet::launch_bc_jet_hl(c->g, c->p, hi, at<float>(c, c->off_lo), at<double>(c, c->off_m64),
-                             at<double>(c, c->off_rth), sc, L);
+    if (has_m64(c))
+      lesjet::launch_bc_jet_hl(c->g, c->p, hi, at<float>(c, c->off_lo), at<double>(c, c->off_m64),
+                               at<double>(c, c->off_rth), sc, L);
+    else
+      lesjet::launch_bc_jet_hl(c->g, c->p, hi, at<float>(c, c->off_lo), at<float>(c, c->off_m32),
+                               at<double>(c, c->off_rth), sc, L);
   }
+}
+
+void totals(les_ctx* c, const double* Q, const lesjet::Launch& L) {
+  if (has_m64(c))
+    lesjet::launch_totals(c->g, Q, at<double>(c, c->off_m64), at<double>(c, c->off_part),
+                          at<DevScalars>(c, c->off_sc), L);
+  else
+    lesjet::launch_totals(c->g, Q, at<float>(c, c->off_m32), at<double>(c, c->off_part),
+                          at<DevScalars>(c, c->off_sc), L);
 }
 
 int read_scalars(les_ctx* c, DevScalars* h, cudaStream_t s) {
@@ -299,7 +317,7 @@ int les_create(const les_params* p, int ni, int nj, int nk, les_ctx** out) {
   const long long N = (long long)ni * nj * nk;
   if (N >= (1LL << 40)) return LES_ERR_SHAPE;
   // the mixed form indexes each field with 32 bits
-  if (p->precision == LES_PREC_MIXED && N >= (1LL << 31)) return LES_ERR_SHAPE;
+  if (p->precision != LES_PREC_FP64 && N >= (1LL << 31)) return LES_ERR_SHAPE;
   les_ctx* c = new (std::nothrow) les_ctx();
   if (!c) return LES_ERR_INVALID_ARG;
   c->p = *p;
@@ -360,10 +378,13 @@ int les_set_grid(les_ctx* c, const double* xyz, const double shift[9], void* wor
   cudaStream_t s = (cudaStream_t)stream;
   lesjet::Launch L{s, &c->launches};
   c->ws = (char*)workspace;
-  double* M64 = at<double>(c, c->off_m64);
-  lesjet::launch_metrics(c->g, xyz, shift, M64, L);
-  if (c->p.precision == LES_PREC_MIXED)
-    lesjet::launch_to_float(10 * c->g.N, M64, at<float>(c, c->off_m32), L);
+  if (has_m64(c)) {
+    double* M64 = at<double>(c, c->off_m64);
+    lesjet::launch_metrics(c->g, xyz, shift, M64, L);
+    if (is_mixed(c)) lesjet::launch_to_float(10 * c->g.N, M64, at<float>(c, c->off_m32), L);
+  } else {
+    lesjet::launch_metrics(c->g, xyz, shift, at<float>(c, c->off_m32), L);
+  }
   lesjet::launch_inflow_geometry(c->g, xyz, at<double>(c, c->off_rth), L);
   lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), 0.0, L);
   int rc = cuda_check(c, "les_set_grid");
@@ -372,7 +393,7 @@ int les_set_grid(les_ctx* c, const double* xyz, const double shift[9], void* wor
 }
 
 const double* les_metrics(const les_ctx* c) {
-  if (!c || !c->ws) return nullptr;
+  if (!c || !c->ws || !has_m64(c)) return nullptr;
   return reinterpret_cast<const double*>(c->ws + c->off_m64);
 }
 
@@ -453,8 +474,12 @@ int les_apply_bc(les_ctx* c, double* Q, double t, les_stream_t stream) {
   if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
   if (c->p.bc != LES_BC_JET) return fail(c, LES_ERR_STATE, "bc is not LES_BC_JET");
   lesjet::Launch L{(cudaStream_t)stream, &c->launches};
-  lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth),
-                        at<DevScalars>(c, c->off_sc), 1, t, L);
+  if (has_m64(c))
+    lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth),
+                          at<DevScalars>(c, c->off_sc), 1, t, L);
+  else
+    lesjet::launch_bc_jet(c->g, c->p, Q, at<float>(c, c->off_m32), at<double>(c, c->off_rth),
+                          at<DevScalars>(c, c->off_sc), 1, t, L);
   return cuda_check(c, "les_apply_bc");
 }
 
@@ -491,8 +516,7 @@ int les_run_n_steps(les_ctx* c, int n, double* Q, les_diag* diag, les_stream_t s
   if (is_mixed(c)) join_state(c, Q, L);
   {
     ProfScope ps(c, PK_TOTALS, s);
-    lesjet::launch_totals(c->g, Q, at<double>(c, c->off_m64), at<double>(c, c->off_part),
-                          at<DevScalars>(c, c->off_sc), L);
+    totals(c, Q, L);
   }
   if ((rc = cuda_check(c, "les_run_n_steps")) != LES_OK) return rc;
   DevScalars h;
@@ -532,8 +556,7 @@ int les_totals(les_ctx* c, const double* Q, double out[5], les_stream_t stream) 
   if (!Q || !out) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
   cudaStream_t s = (cudaStream_t)stream;
   lesjet::Launch L{s, &c->launches};
-  lesjet::launch_totals(c->g, Q, at<double>(c, c->off_m64), at<double>(c, c->off_part),
-                        at<DevScalars>(c, c->off_sc), L);
+  totals(c, Q, L);
   if ((rc = cuda_check(c, "les_totals")) != LES_OK) return rc;
   DevScalars h;
   if ((rc = read_scalars(c, &h, s)) != LES_OK) return rc;

@@ -1,5 +1,6 @@
 // boundary.cu -- jet boundary conditions (Sec. "Boundary Conditions"),
-// conserved totals and time bookkeeping.  All FP64.
+// conserved totals and time bookkeeping.  All arithmetic FP64; the metrics
+// are read as FP64, or from the FP32 copy in the compact mixed form.
 #include "lesjet_dev.cuh"
 #include "lesjet_host.h"
 
@@ -77,8 +78,8 @@ __global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
 // Far field j = nj-1 (0 < i < ni-1): Riemann invariants along the unit
 // eta-normal with R+ from the adjacent interior node and R- from the free
 // stream at rest (rho = 1, p = 1/gamma, a = 1); four branches by q_n/a.
-template <class Acc>
-__global__ void k_bc_farfield(Grid g, double gamma, const double* __restrict__ M, Acc Q) {
+template <class Acc, typename TM>
+__global__ void k_bc_farfield(Grid g, double gamma, const TM* __restrict__ M, Acc Q) {
   const int ni = g.n[0], nj = g.n[1], nk = g.n[2];
   const long long count = (long long)(ni - 2) * nk;
   const long long N = g.N;
@@ -87,7 +88,7 @@ __global__ void k_bc_farfield(Grid g, double gamma, const double* __restrict__ M
        e += (long long)gridDim.x * blockDim.x) {
     const int i = 1 + (int)(e / nk), k = (int)(e % nk);
     const long long nf = idx3(g, i, nj - 1, k), ne = idx3(g, i, nj - 2, k);
-    const double ex = M[3 * N + nf], ey = M[4 * N + nf], ez = M[5 * N + nf];
+    const double ex = (double)M[3 * N + nf], ey = (double)M[4 * N + nf], ez = (double)M[5 * N + nf];
     const double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
     const double nx = ex * inv, ny = ey * inv, nz = ez * inv;
     double rho, u, v, w, p;
@@ -152,8 +153,8 @@ __global__ void k_bc_ring(Grid g, Acc Q) {
 // Exit i = ni-1 from the updated column i = ni-2: supersonic (q/a >= 1 along
 // the unit xi-normal) copies; subsonic takes p = 1/gamma and extrapolates the
 // velocity and the internal energy p/((gamma-1) rho).
-template <class Acc>
-__global__ void k_bc_exit(Grid g, double gamma, const double* __restrict__ M, Acc Q) {
+template <class Acc, typename TM>
+__global__ void k_bc_exit(Grid g, double gamma, const TM* __restrict__ M, Acc Q) {
   const int ni = g.n[0];
   const long long plane = (long long)g.n[1] * g.n[2];
   const long long N = g.N;
@@ -161,7 +162,7 @@ __global__ void k_bc_exit(Grid g, double gamma, const double* __restrict__ M, Ac
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane;
        e += (long long)gridDim.x * blockDim.x) {
     const long long nx_ = (long long)(ni - 1) * plane + e, ne = nx_ - plane;
-    const double ex = M[nx_], ey = M[N + nx_], ez = M[2 * N + nx_];
+    const double ex = (double)M[nx_], ey = (double)M[N + nx_], ez = (double)M[2 * N + nx_];
     const double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
     double rho, u, v, w, p;
     load_prim(Q, N, ne, gamma, rho, u, v, w, p);
@@ -183,13 +184,14 @@ __global__ void k_bc_exit(Grid g, double gamma, const double* __restrict__ M, Ac
 }
 
 // Block partials of sum_n J^-1 Q_c (grid-stride order fixed by the launch).
-__global__ void k_totals_partial(Grid g, const double* __restrict__ Q, const double* __restrict__ M,
+template <typename TM>
+__global__ void k_totals_partial(Grid g, const double* __restrict__ Q, const TM* __restrict__ M,
                                  double* __restrict__ partials) {
   const long long N = g.N;
   double s[5] = {0, 0, 0, 0, 0};
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const double jv = M[9 * N + n];
+    const double jv = (double)M[9 * N + n];
 #pragma unroll
     for (int q = 0; q < 5; ++q) s[q] += jv * Q[q * N + n];
   }
@@ -233,8 +235,8 @@ static int nblocks(long long count) {
   return (int)(b < 1 ? 1 : b);
 }
 
-template <class Acc>
-static void bc_jet(const Grid& g, const les_params& p, Acc Q, const double* M64,
+template <class Acc, typename TM>
+static void bc_jet(const Grid& g, const les_params& p, Acc Q, const TM* M,
                    const double* rth, const DevScalars* sc, int use_host_t, double t_host,
                    const Launch& L) {
   JetBC b;
@@ -247,9 +249,9 @@ static void bc_jet(const Grid& g, const les_params& p, Acc Q, const double* M64,
   for (int i = 0; i < 16; ++i) b.amp[i] = p.amp[i];
   const long long plane = (long long)g.n[1] * g.n[2];
   k_bc_inflow<Acc><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, sc, use_host_t, t_host, Q);
-  k_bc_farfield<Acc><<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M64, Q);
+  k_bc_farfield<Acc, TM><<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M, Q);
   k_bc_ring<Acc><<<g.n[0] - 2, 256, 0, L.s>>>(g, Q);
-  k_bc_exit<Acc><<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M64, Q);
+  k_bc_exit<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M, Q);
   *L.counter += 4;
 }
 
@@ -259,16 +261,38 @@ void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* 
   bc_jet(g, p, AccD{Q}, M64, rth, sc, use_host_t, t_host, L);
 }
 
+void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const float* M32,
+                   const double* rth, const DevScalars* sc, int use_host_t, double t_host,
+                   const Launch& L) {
+  bc_jet(g, p, AccD{Q}, M32, rth, sc, use_host_t, t_host, L);
+}
+
 void launch_bc_jet_hl(const Grid& g, const les_params& p, float* hi, float* lo, const double* M64,
                       const double* rth, const DevScalars* sc, const Launch& L) {
   bc_jet(g, p, AccHL{hi, lo}, M64, rth, sc, 0, 0.0, L);
 }
 
-void launch_totals(const Grid& g, const double* Q, const double* M64, double* partials,
-                   DevScalars* sc, const Launch& L) {
-  k_totals_partial<<<kRedBlocks, kRedThreads, 0, L.s>>>(g, Q, M64, partials);
+void launch_bc_jet_hl(const Grid& g, const les_params& p, float* hi, float* lo, const float* M32,
+                      const double* rth, const DevScalars* sc, const Launch& L) {
+  bc_jet(g, p, AccHL{hi, lo}, M32, rth, sc, 0, 0.0, L);
+}
+
+template <typename TM>
+static void totals_t(const Grid& g, const double* Q, const TM* M, double* partials, DevScalars* sc,
+                     const Launch& L) {
+  k_totals_partial<TM><<<kRedBlocks, kRedThreads, 0, L.s>>>(g, Q, M, partials);
   k_totals_final<<<1, 160, 0, L.s>>>(partials, sc);
   *L.counter += 2;
+}
+
+void launch_totals(const Grid& g, const double* Q, const double* M64, double* partials,
+                   DevScalars* sc, const Launch& L) {
+  totals_t(g, Q, M64, partials, sc, L);
+}
+
+void launch_totals(const Grid& g, const double* Q, const float* M32, double* partials,
+                   DevScalars* sc, const Launch& L) {
+  totals_t(g, Q, M32, partials, sc, L);
 }
 
 void launch_set_time(DevScalars* sc, double t, const Launch& L) {

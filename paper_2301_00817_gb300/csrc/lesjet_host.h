@@ -13,6 +13,8 @@ namespace lesjet {
 // setup.cu
 void launch_metrics(const Grid& g, const double* xyz, const double shift[9], double* M,
                     const Launch& L);
+void launch_metrics(const Grid& g, const double* xyz, const double shift[9], float* M,
+                    const Launch& L);
 void launch_to_float(long long count, const double* a, float* b, const Launch& L);
 void launch_inflow_geometry(const Grid& g, const double* xyz, double* rth, const Launch& L);
 void launch_init_jet(const Grid& g, const double* xyz, uint64_t seed, double noise,
@@ -90,9 +92,16 @@ void launch_unpack_dual(long long count, const Dual* in, double* v, double* d, c
 void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* M64,
                    const double* rth, const DevScalars* sc, int use_host_t, double t_host,
                    const Launch& L);
+void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const float* M32,
+                   const double* rth, const DevScalars* sc, int use_host_t, double t_host,
+                   const Launch& L);
 void launch_bc_jet_hl(const Grid& g, const les_params& p, float* hi, float* lo, const double* M64,
                       const double* rth, const DevScalars* sc, const Launch& L);
+void launch_bc_jet_hl(const Grid& g, const les_params& p, float* hi, float* lo, const float* M32,
+                      const double* rth, const DevScalars* sc, const Launch& L);
 void launch_totals(const Grid& g, const double* Q, const double* M64, double* partials,
+                   DevScalars* sc, const Launch& L);
+void launch_totals(const Grid& g, const double* Q, const float* M32, double* partials,
                    DevScalars* sc, const Launch& L);
 void launch_set_time(DevScalars* sc, double t, const Launch& L);
 

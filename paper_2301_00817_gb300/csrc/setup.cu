@@ -28,9 +28,11 @@ struct Shift {
 
 // Jacobian determinant J^-1 of d(x,y,z)/d(xi,eta,zeta) and the metric terms
 // as its cofactors times J (Sec. "Transformation of Coordinates"; the eta
-// row uses the zeta/xi cofactors).
+// row uses the zeta/xi cofactors).  Computed in FP64; stored as TM (FP64, or
+// rounded once to FP32 for the compact mixed form).
+template <typename TM>
 __global__ void k_metrics(Grid g, const double* __restrict__ xyz, Shift sh,
-                          double* __restrict__ M) {
+                          TM* __restrict__ M) {
   const long long N = g.N;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
@@ -51,16 +53,16 @@ __global__ void k_metrics(Grid g, const double* __restrict__ xyz, Shift sh,
     const double Jinv = xa * yb * zc + xb * yc * za + xc * ya * zb - xa * yc * zb -
                         xb * ya * zc - xc * yb * za;
     const double J = 1.0 / Jinv;
-    M[0 * N + n] = J * c00;
-    M[1 * N + n] = J * c01;
-    M[2 * N + n] = J * c02;
-    M[3 * N + n] = J * c10;
-    M[4 * N + n] = J * c11;
-    M[5 * N + n] = J * c12;
-    M[6 * N + n] = J * c20;
-    M[7 * N + n] = J * c21;
-    M[8 * N + n] = J * c22;
-    M[9 * N + n] = Jinv;
+    M[0 * N + n] = (TM)(J * c00);
+    M[1 * N + n] = (TM)(J * c01);
+    M[2 * N + n] = (TM)(J * c02);
+    M[3 * N + n] = (TM)(J * c10);
+    M[4 * N + n] = (TM)(J * c11);
+    M[5 * N + n] = (TM)(J * c12);
+    M[6 * N + n] = (TM)(J * c20);
+    M[7 * N + n] = (TM)(J * c21);
+    M[8 * N + n] = (TM)(J * c22);
+    M[9 * N + n] = (TM)Jinv;
   }
 }
 
@@ -139,7 +141,15 @@ void launch_metrics(const Grid& g, const double* xyz, const double shift[9], dou
                     const Launch& L) {
   Shift sh;
   for (int i = 0; i < 9; ++i) sh.v[i] = shift ? shift[i] : 0.0;
-  k_metrics<<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, sh, M);
+  k_metrics<double><<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, sh, M);
+  ++*L.counter;
+}
+
+void launch_metrics(const Grid& g, const double* xyz, const double shift[9], float* M,
+                    const Launch& L) {
+  Shift sh;
+  for (int i = 0; i < 9; ++i) sh.v[i] = shift ? shift[i] : 0.0;
+  k_metrics<float><<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, sh, M);
   ++*L.counter;
 }
 

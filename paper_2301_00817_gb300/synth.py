@@ -24,8 +24,16 @@ import numpy as np
 # ----------------------------------------------------------------- jet grid
 
 
-def jet_axial(ni: int, length: float = 20.0, ratio: float = 1.01) -> np.ndarray:
-    """Axial stations x_0 = 0 ... x_{ni-1} = length, dx_{i+1} = ratio dx_i."""
+def jet_axial(ni: int, length: float = 20.0, ratio: float | None = None) -> np.ndarray:
+    """Axial stations x_0 = 0 ... x_{ni-1} = length, dx_{i+1} = ratio dx_i.
+
+    The default ratio is 1.01 up to 288 planes (the Mesh-A size); finer grids
+    refine that same geometric mapping, ratio = 1.01^(288/ni), so the spacing
+    still grows 17-fold over the domain.  (Taken literally at 2000 planes, a
+    ratio of 1.01 would make the first cell 4.6e-10 D long, 4.3e8 times
+    shorter than the last, and the convective CFL step viscously unstable.)"""
+    if ratio is None:
+        ratio = 1.01 if ni <= 288 else 1.01 ** (288.0 / ni)
     i = np.arange(ni, dtype=np.float64)
     if ratio == 1.0:
         return length * i / (ni - 1)
@@ -71,6 +79,35 @@ def jet_grid(ni: int, nj: int, nk: int) -> np.ndarray:
     xyz[0] = x[:, None, None]
     xyz[1] = r[None, :, None] * np.cos(th)[None, None, :]
     xyz[2] = r[None, :, None] * np.sin(th)[None, None, :]
+    return xyz
+
+
+def jet_grid_block(ni: int, nj: int, nk: int, ii, jj, kk) -> np.ndarray:
+    """Coordinates [3, len(ii), len(jj), len(kk)] of the nodes (ii x jj x kk)
+    of the ni x nj x nk jet grid (index arrays; kk may wrap)."""
+    x, r, th = jet_lines(ni, nj, nk)
+    x, r, th = x[np.asarray(ii)], r[np.asarray(jj)], th[np.asarray(kk) % nk]
+    xyz = np.empty((3, len(x), len(r), len(th)))
+    xyz[0] = x[:, None, None]
+    xyz[1] = r[None, :, None] * np.cos(th)[None, None, :]
+    xyz[2] = r[None, :, None] * np.sin(th)[None, None, :]
+    return xyz
+
+
+def jet_grid_torch(ni: int, nj: int, nk: int, device):
+    """jet_grid assembled on a torch device from the host's 1-D lines, for
+    grids too large to build on the host: every coordinate is the same single
+    product as in jet_grid, so the two agree bit for bit."""
+    import torch
+    x, r, th = jet_lines(ni, nj, nk)
+    xt = torch.from_numpy(x).to(device)
+    rt = torch.from_numpy(r).to(device)
+    ct = torch.from_numpy(np.cos(th)).to(device)
+    st = torch.from_numpy(np.sin(th)).to(device)
+    xyz = torch.empty((3, ni, nj, nk), dtype=torch.float64, device=device)
+    xyz[0] = xt[:, None, None]
+    xyz[1] = rt[None, :, None] * ct[None, None, :]
+    xyz[2] = rt[None, :, None] * st[None, None, :]
     return xyz
 
 

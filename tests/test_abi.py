@@ -55,8 +55,24 @@ def test_create_validates_and_sizes_workspace(lib):
     assert lib.les_create(C.byref(bad), 8, 8, 8, C.byref(h)) == lj.LES_ERR_INVALID_ARG
     mixed = lj.make_params(precision=lj.PREC_MIXED)
     assert lib.les_create(C.byref(mixed), 48, 24, 32, C.byref(h)) == lj.LES_OK
-    assert lib.les_workspace_bytes(h) > 0
+    ws_mixed = lib.les_workspace_bytes(h)
+    assert ws_mixed > 0
     lib.les_destroy(h)
+    # the compact mixed form drops exactly the FP64 metrics (up to alignment)
+    compact = lj.make_params(precision=lj.PREC_MIXED_COMPACT)
+    assert lib.les_create(C.byref(compact), 48, 24, 32, C.byref(h)) == lj.LES_OK
+    ws_compact = lib.les_workspace_bytes(h)
+    assert abs((ws_mixed - ws_compact) - 80 * N) <= 256
+    lib.les_destroy(h)
+    # 2000 x 500 x 1024 points fit the mixed forms' 32-bit field indexing; the
+    # compact workspace is 128 bytes per point (float metrics 40, mu/kappa 8,
+    # two stage states 40, the state as a float pair 40)
+    assert lib.les_create(C.byref(compact), 2000, 500, 1024, C.byref(h)) == lj.LES_OK
+    assert lib.les_workspace_bytes(h) <= 129 * 2000 * 500 * 1024
+    lib.les_destroy(h)
+    assert lib.les_create(C.byref(compact), 3000, 1000, 1024, C.byref(h)) == lj.LES_ERR_SHAPE
+    bad = lj.make_params(precision=3)
+    assert lib.les_create(C.byref(bad), 8, 8, 8, C.byref(h)) == lj.LES_ERR_INVALID_ARG
 
 
 def test_calls_before_grid_are_rejected_without_touching_the_device(lib):

@@ -287,10 +287,16 @@ def test_mixed_against_fp64(orc, lj, torch):
     xyz = lj.synth.jet_grid(*shape)
     Q0 = orc.init_jet(orc.params(), xyz, seed=0)
     res = {}
-    for prec in (lj.PREC_FP64, lj.PREC_MIXED):
+    for prec in (lj.PREC_FP64, lj.PREC_MIXED, lj.PREC_MIXED_COMPACT):
         ctx, _ = device_ctx(lj, torch, shape, xyz, sgs_model=1, precision=prec)
         Qd = torch.from_numpy(Q0).cuda()
         d = ctx.les_run_n_steps(100, Qd)
-        res[prec] = (Qd.cpu().numpy(), d.t)
-    assert rel_l2(res[lj.PREC_MIXED][0], res[lj.PREC_FP64][0]) <= 1e-5
-    assert abs(res[lj.PREC_MIXED][1] - res[lj.PREC_FP64][1]) <= 1e-5 * res[lj.PREC_FP64][1]
+        res[prec] = (Qd.cpu().numpy(), d.t, np.array(d.totals))
+    for prec in (lj.PREC_MIXED, lj.PREC_MIXED_COMPACT):
+        assert rel_l2(res[prec][0], res[lj.PREC_FP64][0]) <= 1e-5
+        assert abs(res[prec][1] - res[lj.PREC_FP64][1]) <= 1e-5 * res[lj.PREC_FP64][1]
+    # the compact form differs from the default mixed form only in the FP32
+    # metrics its boundary conditions and totals read
+    assert rel_l2(res[lj.PREC_MIXED_COMPACT][0], res[lj.PREC_MIXED][0]) <= 1e-6
+    tot_c, tot_m = res[lj.PREC_MIXED_COMPACT][2], res[lj.PREC_MIXED][2]
+    assert np.all(np.abs(tot_c - tot_m) <= 1e-6 * np.abs(tot_m).max())
