@@ -36,3 +36,38 @@ def oracle_params(orc, **kw):
     kw = dict(kw)
     kw.pop("precision", None)
     return orc.params(**kw)
+
+
+BLOCK_HALF = 13  # one step reaches 12 nodes: 5 stages x 2, viscosity 1, block metrics 1
+
+
+def take_blocks(torch, Q, centres, nk, half=BLOCK_HALF):
+    """Host copies of the (2 half + 1)^3 blocks of device state Q around the
+    given (i, j, k) centres (k wraps)."""
+    out = []
+    for (i, j, k) in centres:
+        kk = torch.arange(k - half, k + half + 1, device=Q.device) % nk
+        blk = Q[:, i - half:i + half + 1, j - half:j + half + 1][:, :, :, kk]
+        out.append(blk.cpu().numpy())
+    return out
+
+
+def check_blocks(orc, synth, shape, Q_after, centres, blocks, dt, tol, half=BLOCK_HALF, **kw):
+    """One oracle step on each block (faces frozen, fixed dt) against the
+    device state after one step at the block centre; tolerance relative to
+    the component scale (rho v, rho w share the momentum scale)."""
+    ni, nj, nk = shape
+    for (i, j, k), Qb in zip(centres, blocks):
+        assert half <= i <= ni - 1 - half and half <= j <= nj - 1 - half
+        ii = np.arange(i - half, i + half + 1)
+        jj = np.arange(j - half, j + half + 1)
+        kk = np.arange(k - half, k + half + 1)
+        xyzb = synth.jet_grid_block(ni, nj, nk, ii, jj, kk)
+        Mb = orc.metrics(xyzb, (0, 0, 0))
+        P = orc.params(dt_mode=1, dt_fixed=dt, bc=0, periodic=(0, 0, 0), **kw)
+        Qb1, _ = orc.rk_step(P, Qb, Mb, xyzb, 0.0)
+        ref = Qb1[:, half, half, half]
+        got = Q_after[:, i, j, k].cpu().numpy()
+        mom = np.abs(Qb[1:4]).max()
+        scale = np.array([np.abs(Qb[0]).max(), mom, mom, mom, np.abs(Qb[4]).max()])
+        assert np.all(np.abs(got - ref) <= tol * scale), ((i, j, k), got, ref)

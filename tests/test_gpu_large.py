@@ -8,15 +8,18 @@
   reaches 12 nodes (five stages of the 2-node stencil, one node for the
   viscosity's derivatives, one for the block metrics' one-sided faces), less
   than the 13 from the centre to the block faces.
+* 576 x 320 x 256 (47M points), Re_D = 1e6: FP64 and mixed side by side, one
+  step at sampled nodes against the oracle (FP64 1e-12, mixed 2e-6), and the
+  mixed form against FP64 after 200 steps.
 * 1000 x 250 x 512 (the 1/8-size subgrid): the compact mixed form against
   plain FP64 after 20 steps, <= 1e-5 relative L2 on rho, rho u, rho E.
 """
 import numpy as np
 import pytest
 
-pytestmark = pytest.mark.gpu
+from gpu_helpers import BLOCK_HALF, check_blocks, take_blocks
 
-HALF = 13  # block half-width of the sampled oracle check
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -65,28 +68,11 @@ def test_c5_compact_mixed_sampled_step_and_run(orc, lj, torch):
     r = lj.synth.jet_radial(nj)
     centres = [(1000, int(np.argmin(np.abs(r - 0.5))), 300),
                (400, int(np.argmin(np.abs(r - 2.0))), 1000),
-               (1700, nj - 1 - HALF - 5, 17)]
-    blocks = []
-    for (i, j, k) in centres:
-        assert HALF <= i <= ni - 1 - HALF and HALF <= j <= nj - 1 - HALF
-        kk = torch.arange(k - HALF, k + HALF + 1, device="cuda") % nk
-        blk = Q[:, i - HALF:i + HALF + 1, j - HALF:j + HALF + 1][:, :, :, kk]
-        blocks.append(blk.cpu().numpy())
+               (1700, nj - 1 - BLOCK_HALF - 5, 17)]
+    blocks = take_blocks(torch, Q, centres, nk)
     d = ctx.les_run_n_steps(1, Q)
     assert d.status == 0 and d.dt > 0
-    for (i, j, k), Qb in zip(centres, blocks):
-        ii = np.arange(i - HALF, i + HALF + 1)
-        jj = np.arange(j - HALF, j + HALF + 1)
-        kk = np.arange(k - HALF, k + HALF + 1)
-        xyzb = lj.synth.jet_grid_block(ni, nj, nk, ii, jj, kk)
-        Mb = orc.metrics(xyzb, (0, 0, 0))
-        P = orc.params(sgs_model=1, dt_mode=1, dt_fixed=d.dt, bc=0, periodic=(0, 0, 0))
-        Qb1, _ = orc.rk_step(P, Qb, Mb, xyzb, 0.0)
-        ref = Qb1[:, HALF, HALF, HALF]
-        got = Q[:, i, j, k].cpu().numpy()
-        mom = np.abs(Qb[1:4]).max()
-        scale = np.array([np.abs(Qb[0]).max(), mom, mom, mom, np.abs(Qb[4]).max()])
-        assert np.all(np.abs(got - ref) <= 2e-6 * scale), ((i, j, k), got, ref)
+    check_blocks(orc, lj.synth, shape, Q, centres, blocks, d.dt, 2e-6, sgs_model=1)
     d = ctx.les_run_n_steps(19, Q)
     assert d.status == 0
     assert bool(torch.isfinite(Q).all())
@@ -114,6 +100,34 @@ def test_subgrid_mixed_error_against_fp64(lj, torch):
         del ctx
         torch.cuda.empty_cache()
     a, b = out[lj.PREC_MIXED_COMPACT], out[lj.PREC_FP64]
+    for c in (0, 1, 4):
+        err = float(torch.linalg.vector_norm(a[c] - b[c]) / torch.linalg.vector_norm(b[c]))
+        assert err <= 1e-5, (c, err)
+
+
+def test_c3_fp64_and_mixed(orc, lj, torch):
+    shape = (576, 320, 256)
+    ni, nj, nk = shape
+    xyz = lj.synth.jet_grid_torch(*shape, "cuda")
+    r = lj.synth.jet_radial(nj)
+    centres = [(300, int(np.argmin(np.abs(r - 0.5))), 40),
+               (100, int(np.argmin(np.abs(r - 3.0))), 255),
+               (ni - 1 - BLOCK_HALF, nj - 1 - BLOCK_HALF, 128)]
+    out = {}
+    for prec, tol in ((lj.PREC_FP64, 1e-12), (lj.PREC_MIXED, 2e-6)):
+        ctx = lj.Context(lj.make_params(Re=1.0e6, sgs_model=lj.SGS_SMAGORINSKY, precision=prec),
+                         shape, "cuda:0")
+        ctx.les_set_grid(xyz)
+        Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+        ctx.les_init_jet(xyz, 0, 1e-3, Q)
+        blocks = take_blocks(torch, Q, centres, nk)
+        d = ctx.les_run_n_steps(1, Q)
+        check_blocks(orc, lj.synth, shape, Q, centres, blocks, d.dt, tol, Re=1.0e6, sgs_model=1)
+        d = ctx.les_run_n_steps(199, Q)
+        assert d.status == 0
+        out[prec] = Q
+        del ctx
+    a, b = out[lj.PREC_MIXED], out[lj.PREC_FP64]
     for c in (0, 1, 4):
         err = float(torch.linalg.vector_norm(a[c] - b[c]) / torch.linalg.vector_norm(b[c]))
         assert err <= 1e-5, (c, err)
