@@ -321,14 +321,36 @@ __host__ __device__ constexpr int colk(int kk) { return kk < 0 ? kk + SK : kk; }
 
 // Shared-memory plan (floats):
 //   sQ[3][5][PL2]  conserved state of planes i, i+1, i+2 (2-node halo)
-//   sP[3][5][PL2]  u v w T p of planes i-1, i, i+1
+//   sPr[3][PL2]    float4 (u, v, w, T) of planes i-1, i, i+1
+//   sPw[3][PL2]    float2 (p, e + p) of the same planes
 //   sM[3][10][PL1] metrics of planes i, i+1, i+2 (1-node halo)
 //   sK[3][2][PL1]  mu_eff kappa_eff of planes i, i+1, i+2
 //   sL[2][3][PL1]  lbar of planes i, i+1
 //   sFe[5][FTJ+1][FTK], sFz[5][FTJ][FTK+1]  eta / zeta interface fluxes
-constexpr int OFF_P = 3 * 5 * PL2, OFF_M = OFF_P + 3 * 5 * PL2, OFF_K = OFF_M + 3 * 10 * PL1,
+constexpr int OFF_PR = 3 * 5 * PL2, OFF_PW = OFF_PR + 3 * 4 * PL2,
+              OFF_M = OFF_PW + 3 * 2 * PL2, OFF_K = OFF_M + 3 * 10 * PL1,
               OFF_L = OFF_K + 3 * 2 * PL1, OFF_FE = OFF_L + 2 * 3 * PL1,
               OFF_FZ = OFF_FE + 5 * (FTJ + 1) * FTK, SMEM_FLOATS = OFF_FZ + 5 * FTJ * (FTK + 1);
+
+// Computational derivatives of (u, v, w, T) at an interface from node
+// records (float4 u, v, w, T): along the interface normal, phi_b - phi_a;
+// along a tangent t, the mean of the two nodes' central differences,
+// 1/4 [(phi_{a+t} - phi_{a-t}) + (phi_{b+t} - phi_{b-t})].
+template <int D>
+__device__ __forceinline__ void dphi_normal(const float4 a, const float4 b, float (&dphi)[4][3]) {
+  dphi[0][D] = b.x - a.x;
+  dphi[1][D] = b.y - a.y;
+  dphi[2][D] = b.z - a.z;
+  dphi[3][D] = b.w - a.w;
+}
+template <int T>
+__device__ __forceinline__ void dphi_tangent(const float4 ap, const float4 am, const float4 bp,
+                                             const float4 bm, float (&dphi)[4][3]) {
+  dphi[0][T] = 0.25f * ((ap.x - am.x) + (bp.x - bm.x));
+  dphi[1][T] = 0.25f * ((ap.y - am.y) + (bp.y - bm.y));
+  dphi[2][T] = 0.25f * ((ap.z - am.z) + (bp.z - bm.z));
+  dphi[3][T] = 0.25f * ((ap.w - am.w) + (bp.w - bm.w));
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -373,7 +395,8 @@ __global__ void __launch_bounds__(FNT, 1)
                   const DevScalars* __restrict__ sc, double alpha) {
   extern __shared__ __align__(16) float smem[];
   float* sQ = smem;
-  float* sP = smem + OFF_P;
+  float4* sPr = reinterpret_cast<float4*>(smem + OFF_PR);
+  float2* sPw = reinterpret_cast<float2*>(smem + OFF_PW);
   float* sM = smem + OFF_M;
   float* sK = smem + OFF_K;
   float* sL = smem + OFF_L;
@@ -460,7 +483,8 @@ __global__ void __launch_bounds__(FNT, 1)
   // ---- primitives (2-node halo) and lbar (1-node halo) of a staged plane
   auto derive_plane = [&](int qs, int ps, int ms, int ls) {
     const float* q = sQ + qs * 5 * PL2;
-    float* pp = sP + ps * 5 * PL2;
+    float4* pr = sPr + ps * PL2;
+    float2* pw = sPw + ps * PL2;
     const float* mm = sM + ms * 10 * PL1;
     float* ll = sL + ls * 3 * PL1;
     for (int r = tid; r < PL2; r += FNT) {
@@ -469,11 +493,8 @@ __global__ void __launch_bounds__(FNT, 1)
       const float u = q[PL2 + r] * ir, v = q[2 * PL2 + r] * ir, w = q[3 * PL2 + r] * ir;
       const float p = K.gm1 * (q[4 * PL2 + r] - 0.5f * rho * (u * u + v * v + w * w));
       const float T = K.gamma * p * ir;
-      pp[r] = u;
-      pp[PL2 + r] = v;
-      pp[2 * PL2 + r] = w;
-      pp[3 * PL2 + r] = T;
-      pp[4 * PL2 + r] = p;
+      pr[r] = make_float4(u, v, w, T);
+      pw[r] = make_float2(p, q[4 * PL2 + r] + p);
       const int row = r / SK, col = r - row * SK;
       // 1-node halo: rows 1 .. R2-2 of the 2-node layout, columns kk in [-1, FTK]
       if (row >= 1 && row <= R2 - 2 && (col <= FTK || col == SK - 1)) {
@@ -536,10 +557,10 @@ __global__ void __launch_bounds__(FNT, 1)
     finish_W(W, p, valid);
   };
 
-  // xi interface (x, x+1) of the own column: sP/sM/sK/sL slots of both planes
+  // xi interface (x, x+1) of the own column: sPr/sPw/sM/sK/sL slots of both planes
   auto xi_flux = [&](int x, int p0, int p1, int m0, int m1, int l0, int l1, float F[5]) {
-    const float* A0 = sP + p0 * 5 * PL2;
-    const float* A1 = sP + p1 * 5 * PL2;
+    const float4* A0 = sPr + p0 * PL2;
+    const float4* A1 = sPr + p1 * PL2;
     float nua, nub;
     if (!per_i && x == 0)
       nua = sensor3(pq[1], pq[2], pq[3]);
@@ -549,15 +570,13 @@ __global__ void __launch_bounds__(FNT, 1)
       nub = sensor3(pq[0], pq[1], pq[2]);
     else
       nub = sensor3(pq[1], pq[2], pq[3]);
+    const float4 a0 = A0[o2], b0 = A1[o2];
+    const float4 an = A0[o2 + SK], as = A0[o2 - SK], bn = A1[o2 + SK], bs = A1[o2 - SK];
+    const float4 ae = A0[o2 + 1], aw = A0[o2 - tx + cm1], be = A1[o2 + 1], bw = A1[o2 - tx + cm1];
     float dphi[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float* a = A0 + q * PL2;
-      const float* b = A1 + q * PL2;
-      dphi[q][0] = b[o2] - a[o2];
-      dphi[q][1] = 0.25f * ((a[o2 + SK] - a[o2 - SK]) + (b[o2 + SK] - b[o2 - SK]));
-      dphi[q][2] = 0.25f * ((a[o2 + 1] - a[o2 - tx + cm1]) + (b[o2 + 1] - b[o2 - tx + cm1]));
-    }
+    dphi_normal<0>(a0, b0, dphi);
+    dphi_tangent<1>(an, as, bn, bs, dphi);
+    dphi_tangent<2>(ae, aw, be, bw, dphi);
     float ma[10], mb[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
@@ -567,25 +586,25 @@ __global__ void __launch_bounds__(FNT, 1)
     const float* Ka = sK + m0 * 2 * PL1;
     const float* Kb = sK + m1 * 2 * PL1;
     iface_flux<0, float>(K, Wq[0], Wq[1], Wq[2], Wq[3], vq[0], vq[3], nua, nub,
-                         sL[l0 * 3 * PL1 + o1], sL[l1 * 3 * PL1 + o1], ma, mb, A0[4 * PL2 + o2],
-                         A1[4 * PL2 + o2], A0[o2], A0[PL2 + o2], A0[2 * PL2 + o2], A1[o2],
-                         A1[PL2 + o2], A1[2 * PL2 + o2], dphi, Ka[o1], Kb[o1], Ka[PL1 + o1],
-                         Kb[PL1 + o1], F);
+                         sL[l0 * 3 * PL1 + o1], sL[l1 * 3 * PL1 + o1], ma, mb, sPw[p0 * PL2 + o2].x,
+                         sPw[p1 * PL2 + o2].x, a0.x, a0.y, a0.z, b0.x, b0.y, b0.z, dphi, Ka[o1],
+                         Kb[o1], Ka[PL1 + o1], Kb[PL1 + o1], F);
   };
 
   // eta interface between tile rows ra and ra+1 (ra in [-1, FTJ-1]), own
   // column; plane i in slots qs (sQ), ps (sP, with pm/pp for i-1/i+1), ms, ls
   auto eta_flux = [&](int ra, int qs, int pm, int ps, int pp, int ms, int ls, float F[5]) {
     const float* Qs = sQ + qs * 5 * PL2;
-    const float* Pc = sP + ps * 5 * PL2;
-    const float* Pm = sP + pm * 5 * PL2;
-    const float* Pp = sP + pp * 5 * PL2;
+    const float4* Pc = sPr + ps * PL2;
+    const float4* Pm = sPr + pm * PL2;
+    const float4* Pp = sPr + pp * PL2;
+    const float2* Pw = sPw + ps * PL2;
     const int a2 = (ra + 2) * SK + tx, b2 = a2 + SK;
     const int a1 = (ra + 1) * SK + tx, b1 = a1 + SK;
     const int jga = j0 + ra;
     const bool has_m = G.per[1] || jga - 1 >= 0;
     const bool has_p = G.per[1] || jga + 2 <= nj - 1;
-    const float* p4 = Pc + 4 * PL2;
+    const float2 wm = Pw[a2 - SK], wa = Pw[a2], wb = Pw[b2], wp = Pw[b2 + SK];
     float Wm[5], Wa[5], Wb[5], Wp[5];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -594,28 +613,25 @@ __global__ void __launch_bounds__(FNT, 1)
       Wm[c] = Qs[c * PL2 + a2 - SK];
       Wp[c] = Qs[c * PL2 + b2 + SK];
     }
-    Wa[4] = Qs[4 * PL2 + a2] + p4[a2];
-    Wb[4] = Qs[4 * PL2 + b2] + p4[b2];
-    Wm[4] = Qs[4 * PL2 + a2 - SK] + p4[a2 - SK];
-    Wp[4] = Qs[4 * PL2 + b2 + SK] + p4[b2 + SK];
+    Wa[4] = wa.y;
+    Wb[4] = wb.y;
+    Wm[4] = wm.y;
+    Wp[4] = wp.y;
     float nua, nub;
     if (!G.per[1] && jga == 0)
-      nua = sensor3(p4[a2], p4[a2 + SK], p4[a2 + 2 * SK]);
+      nua = sensor3(wa.x, wb.x, wp.x);
     else
-      nua = sensor3(p4[a2 - SK], p4[a2], p4[a2 + SK]);
+      nua = sensor3(wm.x, wa.x, wb.x);
     if (!G.per[1] && jga + 1 == nj - 1)
-      nub = sensor3(p4[b2 - 2 * SK], p4[b2 - SK], p4[b2]);
+      nub = sensor3(wm.x, wa.x, wb.x);
     else
-      nub = sensor3(p4[b2 - SK], p4[b2], p4[b2 + SK]);
+      nub = sensor3(wa.x, wb.x, wp.x);
     const int am1 = a2 - tx + cm1, bm1 = b2 - tx + cm1;
+    const float4 ca = Pc[a2], cb = Pc[b2];
     float dphi[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float* c0 = Pc + q * PL2;
-      dphi[q][1] = c0[b2] - c0[a2];
-      dphi[q][0] = 0.25f * ((Pp[q * PL2 + a2] - Pm[q * PL2 + a2]) + (Pp[q * PL2 + b2] - Pm[q * PL2 + b2]));
-      dphi[q][2] = 0.25f * ((c0[a2 + 1] - c0[am1]) + (c0[b2 + 1] - c0[bm1]));
-    }
+    dphi_normal<1>(ca, cb, dphi);
+    dphi_tangent<0>(Pp[a2], Pm[a2], Pp[b2], Pm[b2], dphi);
+    dphi_tangent<2>(Pc[a2 + 1], Pc[am1], Pc[b2 + 1], Pc[bm1], dphi);
     float ma[10], mb[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
@@ -624,18 +640,19 @@ __global__ void __launch_bounds__(FNT, 1)
     }
     const float* Kc = sK + ms * 2 * PL1;
     const float* L = sL + ls * 3 * PL1 + PL1;
-    iface_flux<1, float>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, p4[a2],
-                         p4[b2], Pc[a2], Pc[PL2 + a2], Pc[2 * PL2 + a2], Pc[b2], Pc[PL2 + b2],
-                         Pc[2 * PL2 + b2], dphi, Kc[a1], Kc[b1], Kc[PL1 + a1], Kc[PL1 + b1], F);
+    iface_flux<1, float>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
+                         wb.x, ca.x, ca.y, ca.z, cb.x, cb.y, cb.z, dphi, Kc[a1], Kc[b1],
+                         Kc[PL1 + a1], Kc[PL1 + b1], F);
   };
 
   // zeta interface between tile columns ca and ca+1 (ca in [-1, FTK-1]) in
   // tile row rr
   auto zeta_flux = [&](int rr, int ca, int qs, int pm, int ps, int pp, int ms, int ls, float F[5]) {
     const float* Qs = sQ + qs * 5 * PL2;
-    const float* Pc = sP + ps * 5 * PL2;
-    const float* Pm = sP + pm * 5 * PL2;
-    const float* Pp = sP + pp * 5 * PL2;
+    const float4* Pc = sPr + ps * PL2;
+    const float4* Pm = sPr + pm * PL2;
+    const float4* Pp = sPr + pp * PL2;
+    const float2* Pw = sPw + ps * PL2;
     const int rb2 = (rr + 2) * SK, rb1 = (rr + 1) * SK;
     const int ca_c = colk(ca), cb_c = colk(ca + 1), cm_c = colk(ca - 1), cp_c = colk(ca + 2);
     const int a2 = rb2 + ca_c, b2 = rb2 + cb_c, m2 = rb2 + cm_c, q2 = rb2 + cp_c;
@@ -643,7 +660,7 @@ __global__ void __launch_bounds__(FNT, 1)
     const int kga = k0 + ca;
     const bool has_m = G.per[2] || kga - 1 >= 0;
     const bool has_p = G.per[2] || kga + 2 <= nk - 1;
-    const float* p4 = Pc + 4 * PL2;
+    const float2 wm = Pw[m2], wa = Pw[a2], wb = Pw[b2], wp = Pw[q2];
     float Wm[5], Wa[5], Wb[5], Wp[5];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -652,27 +669,24 @@ __global__ void __launch_bounds__(FNT, 1)
       Wm[c] = Qs[c * PL2 + m2];
       Wp[c] = Qs[c * PL2 + q2];
     }
-    Wa[4] = Qs[4 * PL2 + a2] + p4[a2];
-    Wb[4] = Qs[4 * PL2 + b2] + p4[b2];
-    Wm[4] = Qs[4 * PL2 + m2] + p4[m2];
-    Wp[4] = Qs[4 * PL2 + q2] + p4[q2];
+    Wa[4] = wa.y;
+    Wb[4] = wb.y;
+    Wm[4] = wm.y;
+    Wp[4] = wp.y;
     float nua, nub;
     if (!G.per[2] && kga == 0)
-      nua = sensor3(p4[a2], p4[b2], p4[q2]);
+      nua = sensor3(wa.x, wb.x, wp.x);
     else
-      nua = sensor3(p4[m2], p4[a2], p4[b2]);
+      nua = sensor3(wm.x, wa.x, wb.x);
     if (!G.per[2] && kga + 1 == nk - 1)
-      nub = sensor3(p4[m2], p4[a2], p4[b2]);
+      nub = sensor3(wm.x, wa.x, wb.x);
     else
-      nub = sensor3(p4[a2], p4[b2], p4[q2]);
+      nub = sensor3(wa.x, wb.x, wp.x);
+    const float4 pa = Pc[a2], pb = Pc[b2];
     float dphi[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float* c0 = Pc + q * PL2;
-      dphi[q][2] = c0[b2] - c0[a2];
-      dphi[q][0] = 0.25f * ((Pp[q * PL2 + a2] - Pm[q * PL2 + a2]) + (Pp[q * PL2 + b2] - Pm[q * PL2 + b2]));
-      dphi[q][1] = 0.25f * ((c0[a2 + SK] - c0[a2 - SK]) + (c0[b2 + SK] - c0[b2 - SK]));
-    }
+    dphi_normal<2>(pa, pb, dphi);
+    dphi_tangent<0>(Pp[a2], Pm[a2], Pp[b2], Pm[b2], dphi);
+    dphi_tangent<1>(Pc[a2 + SK], Pc[a2 - SK], Pc[b2 + SK], Pc[b2 - SK], dphi);
     float ma[10], mb[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
@@ -681,9 +695,9 @@ __global__ void __launch_bounds__(FNT, 1)
     }
     const float* Kc = sK + ms * 2 * PL1;
     const float* L = sL + ls * 3 * PL1 + 2 * PL1;
-    iface_flux<2, float>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, p4[a2],
-                         p4[b2], Pc[a2], Pc[PL2 + a2], Pc[2 * PL2 + a2], Pc[b2], Pc[PL2 + b2],
-                         Pc[2 * PL2 + b2], dphi, Kc[a1], Kc[b1], Kc[PL1 + a1], Kc[PL1 + b1], F);
+    iface_flux<2, float>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
+                         wb.x, pa.x, pa.y, pa.z, pb.x, pb.y, pb.z, dphi, Kc[a1], Kc[b1],
+                         Kc[PL1 + a1], Kc[PL1 + b1], F);
   };
 
   auto m3 = [](int x) { return ((x % 3) + 3) % 3; };
@@ -809,9 +823,12 @@ __global__ void __launch_bounds__(FNT, 1)
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) Fx_prev[c] = Fx[c];
-    __syncthreads();
+    // no barrier here: every shared slot read above is next written either by
+    // the staging or derivation after the next iteration's first barrier, or
+    // by the flux phase after its second
   }
   cp_async_wait<0>();
+  __syncthreads();
 }
 
 // ------------------------------------------------------- mixed-state helpers
