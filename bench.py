@@ -333,8 +333,14 @@ def adjoint_leg(lj, torch, local):
                         f"{ADJ_STEPS}-step window, checkpoint every {ADJ_CKPT}",
             "functional": "sum_n dt sum_(i,k) (p - 1/gamma)^2 dA on the eta surface nearest r = 5",
             "dt": dt, "j_surface": j5, "forward_ms": t_f, "adjoint_window_ms": t_a,
-            "ratio": t_a / t_f, "J": J, "grad_norm": gnorm, "workspace_gb": ws / 1e9,
+            "ratio": t_a / t_f,
+            "step_ratio": (t_a - t_f) / t_f,
+            "ratio_note": "ratio: whole window (forward sweep with checkpoints + segment "
+                          "recompute + reverse) over the forward run; step_ratio: the part "
+                          "beyond the forward sweep, per step, over one forward step",
+            "J": J, "grad_norm": gnorm, "workspace_gb": ws / 1e9,
             "store_all": {"adjoint_window_ms": t_all, "ratio": t_all / t_f,
+                          "step_ratio": (t_all - t_f) / t_f,
                           "workspace_gb": aw.numel() / 1e9}}
 
 
