@@ -73,7 +73,7 @@ __device__ __forceinline__ double sgn_abs(double x) { return x < 0.0 ? -1.0 : 1.
 
 // ------------------------------------------------------------- interface
 template <int D>
-__global__ void __launch_bounds__(256) k_adj_iface(Grid g, Consts<double> K,
+__global__ void __launch_bounds__(256, 2) k_adj_iface(Grid g, Consts<double> K,
                                                    const double* __restrict__ Q,
                                                    const double* __restrict__ M,
                                                    const double* __restrict__ node,
@@ -356,7 +356,7 @@ __global__ void k_adj_sensor(Grid g, const double* __restrict__ node, double* __
 // Node quantities back to Q: radii lbar(lambda_d), lambda_d = |m_d.u| +
 // sqrt(T)|grad d|, then u = Q1/rho, p = (g-1)(Q4 - rho|u|^2/2), T = g p/rho.
 // lamQ = direct + chained; mu/kappa cotangents are added to lamMK.
-__global__ void k_adj_node(Grid g, Consts<double> K, const double* __restrict__ Q,
+__global__ void __launch_bounds__(256, 2) k_adj_node(Grid g, Consts<double> K, const double* __restrict__ Q,
                            const double* __restrict__ M, const double* __restrict__ node,
                            const double* __restrict__ A, double* __restrict__ lamQ,
                            double* __restrict__ lamMK) {
