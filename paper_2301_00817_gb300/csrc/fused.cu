@@ -705,10 +705,14 @@ __global__ void __launch_bounds__(FNT, 1)
   // ---------------------------------------------------------- prologue
   // sQ/sM/sK slot of plane x: x mod 3 (planes i, i+1, i+2 live); sP slot:
   // x mod 3 (planes i-1, i, i+1); sL slot: x mod 2 (planes i, i+1).
-  stage_plane(m3(ib - 1), ib - 1);
-  stage_plane(m3(ib), ib);
+  // rotating slots: planes i-1, i, i+1 (plane i+2 is staged into the slot of
+  // plane i-1) and the lbar slots of planes i, i+1
+  int s_m = m3(ib - 1), s_c = m3(ib), s_p = m3(ib + 1);
+  int l_c = m2(ib), l_p = m2(ib + 1);
+  stage_plane(s_m, ib - 1);
+  stage_plane(s_c, ib);
   cp_async_commit();
-  stage_plane(m3(ib + 1), ib + 1);
+  stage_plane(s_p, ib + 1);
   cp_async_commit();
   load_W(ib - 2, Wq[0], pq[0], vq[0]);
   load_W(ib - 1, Wq[1], pq[1], vq[1]);
@@ -718,12 +722,12 @@ __global__ void __launch_bounds__(FNT, 1)
   fetch_h(ib);
   cp_async_wait<1>();
   __syncthreads();
-  derive_plane(m3(ib - 1), m3(ib - 1), m3(ib - 1), m2(ib - 1));
-  derive_plane(m3(ib), m3(ib), m3(ib), m2(ib));
+  derive_plane(s_m, s_m, s_m, l_p);  // m2(ib - 1) == m2(ib + 1)
+  derive_plane(s_c, s_c, s_c, l_c);
   __syncthreads();
   float Fx_prev[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   if (own && jint && kint && (per_i || ib - 1 >= 0))
-    xi_flux(ib - 1, m3(ib - 1), m3(ib), m3(ib - 1), m3(ib), m2(ib - 1), m2(ib), Fx_prev);
+    xi_flux(ib - 1, s_m, s_c, s_m, s_c, l_p, l_c, Fx_prev);
   const float adt = (MODE == FMODE_RHS) ? 0.f : (float)(alpha * sc->dt);
 
   for (int i = ib; i < ie; ++i) {
@@ -740,32 +744,32 @@ __global__ void __launch_bounds__(FNT, 1)
     // plane i+1 has landed; reuse the slots of plane i-1 for plane i+2
     cp_async_wait<0>();
     __syncthreads();
-    stage_plane(m3(i + 2), i + 2);
+    stage_plane(s_m, i + 2);
     cp_async_commit();
-    derive_plane(m3(i + 1), m3(i + 1), m3(i + 1), m2(i + 1));
+    derive_plane(s_p, s_p, s_p, l_p);
     __syncthreads();
 
     const int ig = wrap_fast(i, ni, G.per[0]);
     const bool iint = per_i || (i > 0 && i < ni - 1);
     float Fx[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (own && jint && kint && (per_i || i + 1 <= ni - 1))
-      xi_flux(i, m3(i), m3(i + 1), m3(i), m3(i + 1), m2(i), m2(i + 1), Fx);
+      xi_flux(i, s_c, s_p, s_c, s_p, l_c, l_p, Fx);
     if (own && iint && kint) {
       float F[5];
       if (G.per[1] || jown + 1 <= nj - 1) {
-        eta_flux(ty, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+        eta_flux(ty, s_c, s_m, s_c, s_p, s_c, l_c, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1) + ty + 1) * FTK + tx] = F[c];
       }
       if (ty == 0 && (G.per[1] || j0 - 1 >= 0)) {
-        eta_flux(-1, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+        eta_flux(-1, s_c, s_m, s_c, s_p, s_c, l_c, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1)) * FTK + tx] = F[c];
       }
     }
     if (own && iint && jint && (G.per[2] || kown + 1 <= nk - 1)) {
       float F[5];
-      zeta_flux(ty, tx, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+      zeta_flux(ty, tx, s_c, s_m, s_c, s_p, s_c, l_c, F);
 #pragma unroll
       for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] = F[c];
     }
@@ -775,7 +779,7 @@ __global__ void __launch_bounds__(FNT, 1)
       const bool rint = G.per[1] || (jr > 0 && jr < nj - 1);
       if (jr < nj && rint) {
         float F[5];
-        zeta_flux(rr, -1, m3(i), m3(i - 1), m3(i), m3(i + 1), m3(i), m2(i), F);
+        zeta_flux(rr, -1, s_c, s_m, s_c, s_p, s_c, l_c, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFz[(c * FTJ + rr) * (FTK + 1)] = F[c];
       }
@@ -788,7 +792,7 @@ __global__ void __launch_bounds__(FNT, 1)
     if (own && ig >= 0) {
       const int n = (ig * nj + jown) * nk + kown;
       if (iint && jint && kint) {
-        const float Jn = __frcp_rn(sM[(m3(i) * 10 + 9) * PL1 + o1]);
+        const float Jn = __frcp_rn(sM[(s_c * 10 + 9) * PL1 + o1]);
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           float r = 0.f;
@@ -823,6 +827,15 @@ __global__ void __launch_bounds__(FNT, 1)
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) Fx_prev[c] = Fx[c];
+    {
+      const int t = s_m;
+      s_m = s_c;
+      s_c = s_p;
+      s_p = t;
+      const int u = l_c;
+      l_c = l_p;
+      l_p = u;
+    }
     // no barrier here: every shared slot read above is next written either by
     // the staging or derivation after the next iteration's first barrier, or
     // by the flux phase after its second
