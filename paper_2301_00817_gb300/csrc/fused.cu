@@ -18,6 +18,8 @@
 // steady state issues no FP64 instruction on GB300's narrow FP64 pipe.  The
 // translation unit is built with approximate FP32 division and square root
 // (their error is inside the form's measured error budget).
+#include <atomic>
+
 #include "lesjet_dev.cuh"
 #include "lesjet_host.h"
 
@@ -921,10 +923,15 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
                            const DevScalars* sc, double alpha, const Launch& L) {
   FusedGeom G = G0;
   const size_t smem = (size_t)SMEM_FLOATS * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the shared-memory opt-in is a per-device function attribute: set it once
+  // for each device this process launches on
+  static std::atomic<unsigned long long> attr_set{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_set.load(std::memory_order_acquire) & bit)) {
     cudaFuncSetAttribute(k_stage_fused<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
+    attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
   G.chunk = choose_chunk(G.ni, tk * tj, 1);
