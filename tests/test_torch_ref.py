@@ -89,3 +89,27 @@ def test_autograd_gradient_matches_oracle_differences(orc):
         fd = (_functional_orc(orc, Pp, Q, M, xyz, dt, nsteps, j5) -
               _functional_orc(orc, Pm, Q, M, xyz, dt, nsteps, j5)) / (2 * h)
         assert abs(fd - g[m]) <= 1e-6 * np.abs(g).max(), (m, fd, g[m])
+
+
+@pytest.mark.parametrize("shape", [(16, 8, 8), (6, 5, 4)])
+def test_brute_force_tiny_grids(orc, shape):
+    """Two independent FP64 implementations (C loops, torch array shifts) on
+    tiny jet grids: residual and three forced steps with the CFL time step,
+    <= 1e-14 of each component's scale."""
+    xyz = synth.jet_grid(*shape)
+    M = orc.metrics(xyz, (0, 0, 1))
+    amps = synth.forcing_amplitudes(4, scale=2e-2)
+    P = orc.params(Re=300.0, amp=tuple(amps))
+    Q = orc.init_jet(P, xyz, seed=3, noise=3e-2)
+    Q[4] += 1e-2 / (P.gamma - 1.0) * np.random.default_rng(3).standard_normal(Q[4].shape)
+    MK = orc.mu_eff(P, Q, M)
+    case = torch_ref.Case(M, xyz, Re=300.0)
+    R = orc.rhs(P, Q, M, MK)
+    Rt = case.rhs(torch.from_numpy(Q), tuple(torch.from_numpy(MK))).numpy()
+    assert _rel(Rt, R) <= 1e-14
+    Qo, Qt, t = Q.copy(), torch.from_numpy(Q.copy()), 0.0
+    for _ in range(3):
+        Qo, dt = orc.rk_step(P, Qo, M, xyz, t)
+        Qt = case.step(Qt, torch.from_numpy(amps), t, dt)
+        t += dt
+        assert _rel(Qt.numpy(), Qo) <= 1e-14
