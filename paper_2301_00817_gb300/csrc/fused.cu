@@ -19,6 +19,12 @@
 // translation unit is built with approximate FP32 division and square root
 // (their error is inside the form's measured error budget).
 #include <atomic>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <queue>
+#include <utility>
+#include <vector>
 
 #include "lesjet_dev.cuh"
 #include "lesjet_host.h"
@@ -374,7 +380,7 @@ struct FusedPtrs {
 struct FusedGeom {
   int ni, nj, nk;
   int per[3];
-  int chunk;
+  int nch;  // axial chunks; chunk z holds planes [z ni / nch, (z + 1) ni / nch)
   int vec16;  // rows of every field start 16-byte aligned (nk % 4 == 0)
 };
 
@@ -407,8 +413,8 @@ __global__ void __launch_bounds__(FNT, 1)
   const int ni = G.ni, nj = G.nj, nk = G.nk;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int k0 = blockIdx.x * FTK, j0 = blockIdx.y * FTJ;
-  const int ib = blockIdx.z * G.chunk;
-  const int ie = min(ib + G.chunk, ni);
+  const int ib = (int)((long long)blockIdx.z * ni / G.nch);
+  const int ie = (int)((long long)(blockIdx.z + 1) * ni / G.nch);
   const int jown = j0 + ty, kown = k0 + tx;
   const bool own = jown < nj && kown < nk;
   const bool jint = G.per[1] || (jown > 0 && jown < nj - 1);
@@ -897,25 +903,45 @@ void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const f
   ++*L.counter;
 }
 
-// Axial chunk so that the grid is about a whole number of waves.
-static int choose_chunk(int ni, int tiles, int ctas_per_sm) {
-  const int wave = 152 * ctas_per_sm;
-  int best_chunk = ni;
-  double best_cost = 1e300;
-  for (int chunks = 1; chunks <= ni; ++chunks) {
-    const int chunk = (ni + chunks - 1) / chunks;
-    const int nch = (ni + chunk - 1) / chunk;
-    const long long ctas = (long long)tiles * nch;
-    const long long waves = (ctas + wave - 1) / wave;
-    // cost: waves x (chunk + 3 prologue planes)
-    const double cost = (double)waves * (chunk + 3);
-    if (cost < best_cost - 1e-9) {
-      best_cost = cost;
-      best_chunk = chunk;
-    }
-    if (chunk <= 8) break;
+// Number of axial chunks.  CTAs are dispatched chunk-major (all tiles of a
+// chunk together, which keeps neighbouring tiles' halo rows in L2) and take
+// (chunk planes + one plane of prologue) each; the count minimises the
+// finishing time of a greedy list schedule of the CTAs on the SMs, simulated
+// once per grid shape and cached.
+static int choose_nch(int ni, int tiles, int slots) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({ni, tiles});
+    if (it != cache.end()) return it->second;
   }
-  return best_chunk;
+  int best = 1;
+  double best_t = 1e300;
+  const int max_nch = ni < 64 ? ni : 64;
+  std::vector<double> busy;
+  for (int nch = 1; nch <= max_nch; ++nch) {
+    if ((long long)tiles * nch > 24LL * slots) break;  // beyond 24 waves
+    std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+    for (int s = 0; s < slots; ++s) q.push(0.0);
+    double t_end = 0.0;
+    for (int z = 0; z < nch; ++z) {
+      const double d = (double)((long long)(z + 1) * ni / nch - (long long)z * ni / nch) + 1.0;
+      for (int tile = 0; tile < tiles; ++tile) {
+        const double t = q.top() + d;
+        q.pop();
+        q.push(t);
+        if (t > t_end) t_end = t;
+      }
+    }
+    if (t_end < best_t - 1e-9) {
+      best_t = t_end;
+      best = nch;
+    }
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  cache[{ni, tiles}] = best;
+  return best;
 }
 
 template <int MODE>
@@ -934,8 +960,14 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
-  G.chunk = choose_chunk(G.ni, tk * tj, 1);
-  dim3 grid(tk, tj, (G.ni + G.chunk - 1) / G.chunk);
+  static std::atomic<int> n_sm{0};
+  if (n_sm.load() == 0) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    n_sm.store(sms > 0 ? sms : 152);
+  }
+  G.nch = choose_nch(G.ni, tk * tj, n_sm.load());  // one CTA per SM
+  dim3 grid(tk, tj, G.nch);
   k_stage_fused<MODE><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
   ++*L.counter;
 }
@@ -947,7 +979,7 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   G.nj = g.n[1];
   G.nk = g.n[2];
   for (int d = 0; d < 3; ++d) G.per[d] = g.per[d];
-  G.chunk = 0;
+  G.nch = 1;
   G.vec16 = (g.n[2] % 4 == 0) ? 1 : 0;
   const long long N = g.N;
   FusedPtrs P;
