@@ -191,13 +191,21 @@ def barrier(world):
 
 
 def max_over_ranks(world, value: float) -> float:
+    """Largest value over the ranks (the slowest replica's time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(world: int, points: int, steps: int, ms: float) -> float:
+    """Whole-job Gpt*RK-steps/s: every replica advances `points` for `steps`
+    steps; `ms` is the max-over-ranks time of the timed region."""
+    return world * points * steps / (ms / 1e3) / 1e9
 
 
 def oracle_baseline(shape, steps: int, warmup: int):
@@ -546,8 +554,8 @@ def run_ours(args, world, rank, local):
 
     mixed, fp64 = results["mixed"], results["fp64"]
     ms_step = mixed["ms"] / args.steps
-    value = world * N * args.steps / (mixed["ms"] / 1e3) / 1e9
-    fp64_value = world * N * args.steps / (fp64["ms"] / 1e3) / 1e9
+    value = aggregate_rate(world, N, args.steps, mixed["ms"])
+    fp64_value = aggregate_rate(world, N, args.steps, fp64["ms"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
