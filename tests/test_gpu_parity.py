@@ -300,3 +300,30 @@ def test_mixed_against_fp64(orc, lj, torch):
     assert rel_l2(res[lj.PREC_MIXED_COMPACT][0], res[lj.PREC_MIXED][0]) <= 1e-6
     tot_c, tot_m = res[lj.PREC_MIXED_COMPACT][2], res[lj.PREC_MIXED][2]
     assert np.all(np.abs(tot_c - tot_m) <= 1e-6 * np.abs(tot_m).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_checkpoint_resume_is_bitwise(lj, torch, tmp_path, prec):
+    """Checkpoint/resume: the state is the caller's tensor plus the time, so
+    saving after 4 steps, restoring into a fresh context and running 4 more
+    reproduces 8 uninterrupted steps bit for bit."""
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    precision = lj.PREC_FP64 if prec == "fp64" else lj.PREC_MIXED
+    ctx, xyz_d = device_ctx(lj, torch, shape, xyz, sgs_model=1, precision=precision)
+    Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_init_jet(xyz_d, 5, 1e-3, Q)
+    Qref = Q.clone()
+    d8 = ctx.les_run_n_steps(8, Qref)
+    ctx.les_set_time(0.0)
+    d4 = ctx.les_run_n_steps(4, Q)
+    path = tmp_path / "ckpt.pt"
+    torch.save({"Q": Q.cpu(), "t": d4.t}, path)
+    del ctx
+    ckpt = torch.load(path)
+    ctx2, _ = device_ctx(lj, torch, shape, xyz, sgs_model=1, precision=precision)
+    Q2 = ckpt["Q"].cuda()
+    ctx2.les_set_time(ckpt["t"])
+    d = ctx2.les_run_n_steps(4, Q2)
+    assert torch.equal(Q2, Qref)
+    assert d.t == d8.t
