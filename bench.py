@@ -325,6 +325,7 @@ def adjoint_leg(lj, torch, local):
     # segment, no recompute): the memory-for-time end of the trade
     del aw
     aw = ctx.adjoint_workspace(ADJ_STEPS, ADJ_STEPS)
+    ws_all = aw.numel()
     K = ADJ_STEPS
 
     def adj_all():
@@ -337,6 +338,18 @@ def adjoint_leg(lj, torch, local):
 
     adj_all()
     t_all = min(adj_all() for _ in range(3))
+    del aw
+    # the same functional accumulated along an FP32-mixed forward run
+    cm = lj.Context(lj.make_params(precision=lj.PREC_MIXED, sgs_model=lj.SGS_NONE, amp=amps,
+                                   dt_mode=lj.DT_FIXED, dt_fixed=dt), shape, f"cuda:{local}")
+    cm.les_set_grid(xyz)
+    Qm = Q0.clone()
+    cm.les_set_time(0.0)
+    J_mixed = 0.0
+    for _ in range(ADJ_STEPS):
+        cm.les_run_n_steps(1, Qm)
+        J_mixed += cm.les_surface_functional(Qm, j5, dt)
+    del cm, Qm
     return {"workload": f"jet {shape[0]}x{shape[1]}x{shape[2]}, FP64, SGS none, "
                         f"{ADJ_STEPS}-step window, checkpoint every {ADJ_CKPT}",
             "functional": "sum_n dt sum_(i,k) (p - 1/gamma)^2 dA on the eta surface nearest r = 5",
@@ -347,9 +360,10 @@ def adjoint_leg(lj, torch, local):
                           "recompute + reverse) over the forward run; step_ratio: the part "
                           "beyond the forward sweep, per step, over one forward step",
             "J": J, "grad_norm": gnorm, "workspace_gb": ws / 1e9,
+            "J_mixed_forward": J_mixed, "J_mixed_rel_diff": abs(J_mixed - J) / abs(J),
             "store_all": {"adjoint_window_ms": t_all, "ratio": t_all / t_f,
                           "step_ratio": (t_all - t_f) / t_f,
-                          "workspace_gb": aw.numel() / 1e9}}
+                          "workspace_gb": ws_all / 1e9}}
 
 
 LARGE_WORKLOAD = (2000, 500, 1024)

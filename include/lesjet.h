@@ -241,6 +241,15 @@ int les_adjoint_window(les_ctx *ctx, const double *Q_start, double t0,
                        void *adj_ws, double *J_out, double grad[16],
                        les_stream_t stream);
 
+/* One term of the window functional of les_adjoint_window for state Q
+ * (device [5][N] FP64): J_out = w sum_{i,k} (p(i, j_surface, k) - 1/gamma)^2
+ * J^-1 |grad eta| at (i, j_surface, k).  Works in every precision (the FP64
+ * metrics, or the FP32 copy of a mixed context), so the functional can be
+ * accumulated along a mixed-precision forward run and compared with the FP64
+ * window (the paper has no counterpart).  SYNCHRONISES. */
+int les_surface_functional(les_ctx *ctx, const double *Q, int j_surface, double w,
+                           double *J_out, les_stream_t stream);
+
 /* Global time step of state Q, like les_time_step, for callers that cannot
  * allocate device memory (the paper has no counterpart): for example a
  * monitoring or steering hook that runs between solver steps in an

@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH):
     lib.les_profile_read.restype = C.c_int
     lib.les_profile_name.argtypes = [i]
     lib.les_profile_name.restype = C.c_char_p
+    lib.les_surface_functional.argtypes = [vp, vp, i, d, C.POINTER(d), vp]
     lib.les_time_step_static.argtypes = [vp, vp, vp, C.POINTER(d), vp]
     lib.les_time_step_static.restype = C.c_int
     lib.les_adjoint_workspace_bytes.argtypes = [vp, i, i]
@@ -214,6 +215,13 @@ class Context:
     def les_time_step(self, Q, stream=None) -> float:
         out = C.c_double()
         self._check(self.lib.les_time_step(self.h, _ptr(Q), C.byref(out), _stream(stream)))
+        return out.value
+
+    def les_surface_functional(self, Q, j_surface: int, w: float, stream=None) -> float:
+        """w * sum over the eta surface j_surface of (p - 1/gamma)^2 dA."""
+        out = C.c_double()
+        self._check(self.lib.les_surface_functional(self.h, _ptr(Q), j_surface, w, C.byref(out),
+                                                    _stream(stream)))
         return out.value
 
     def les_time_step_static(self, Q, M, stream=None) -> float:

@@ -709,7 +709,8 @@ __global__ void k_sum_partials16(const double* __restrict__ partials, int nb, do
 // ------------------------------------------------------------ functional
 // J_f contribution of one state: dt sum_{i,k} (p(i, j5, k) - 1/gamma)^2 dA,
 // dA = J^-1 |grad eta| (eta-face area); and its Q cotangent.
-__global__ void k_functional(Grid g, double gamma, int j5, double dt, const double* __restrict__ M,
+template <typename TM>
+__global__ void k_functional(Grid g, double gamma, int j5, double dt, const TM* __restrict__ M,
                              const double* __restrict__ Q, double* __restrict__ lam,
                              double* __restrict__ partials) {
   const int ni = g.n[0], nk = g.n[2];
@@ -720,8 +721,8 @@ __global__ void k_functional(Grid g, double gamma, int j5, double dt, const doub
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / nk), k = (int)(e % nk);
     const long long n = idx3(g, i, j5, k);
-    const double ex = M[3 * N + n], ey = M[4 * N + n], ez = M[5 * N + n];
-    const double dA = M[9 * N + n] * sqrt(ex * ex + ey * ey + ez * ez);
+    const double ex = (double)M[3 * N + n], ey = (double)M[4 * N + n], ez = (double)M[5 * N + n];
+    const double dA = (double)M[9 * N + n] * sqrt(ex * ex + ey * ey + ez * ez);
     const double rho = Q[n], u = Q[N + n] / rho, v = Q[2 * N + n] / rho, w = Q[3 * N + n] / rho;
     const double p = gm1 * (Q[4 * N + n] - 0.5 * rho * (u * u + v * v + w * w));
     const double dp = p - 1.0 / gamma;
@@ -858,7 +859,16 @@ void launch_functional(const Grid& g, const les_params& p, int j5, double dt, co
                        const Launch& L) {
   const long long count = (long long)g.n[0] * g.n[2];
   const int nb = nb_for(count) < kAdjBlocks ? nb_for(count) : kAdjBlocks;
-  k_functional<<<nb, 256, 0, L.s>>>(g, p.gamma, j5, dt, M, Q, lam, partials);
+  k_functional<double><<<nb, 256, 0, L.s>>>(g, p.gamma, j5, dt, M, Q, lam, partials);
+  k_sum_partials1<<<1, 32, 0, L.s>>>(partials, nb, Jout);
+  *L.counter += 2;
+}
+
+void launch_functional(const Grid& g, const les_params& p, int j5, double dt, const float* M,
+                       const double* Q, double* partials, double* Jout, const Launch& L) {
+  const long long count = (long long)g.n[0] * g.n[2];
+  const int nb = nb_for(count) < kAdjBlocks ? nb_for(count) : kAdjBlocks;
+  k_functional<float><<<nb, 256, 0, L.s>>>(g, p.gamma, j5, dt, M, Q, nullptr, partials);
   k_sum_partials1<<<1, 32, 0, L.s>>>(partials, nb, Jout);
   *L.counter += 2;
 }

@@ -923,6 +923,31 @@ int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps,
   return cuda_check(c, "les_adjoint_window");
 }
 
+int les_surface_functional(les_ctx* c, const double* Q, int j_surface, double w, double* J_out,
+                           les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || !J_out) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  if (j_surface < 0 || j_surface >= c->g.n[1]) return fail(c, LES_ERR_INVALID_ARG, "j_surface out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  double* part = at<double>(c, c->off_part);
+  double* out = part + 4 * (size_t)lesjet::kMaxPartials;  // past the block partials
+  cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (has_m64(c))
+    lesjet::launch_functional(c->g, c->p, j_surface, w, at<double>(c, c->off_m64), Q, nullptr, part,
+                              out, L);
+  else
+    lesjet::launch_functional(c->g, c->p, j_surface, w, at<float>(c, c->off_m32), Q, part, out, L);
+  if ((rc = cuda_check(c, "les_surface_functional")) != LES_OK) return rc;
+  double h = 0.0;
+  cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "les_surface_functional sync");
+  *J_out = h;
+  return cuda_check(c, "les_surface_functional");
+}
+
 }  // extern "C"
 
 // Read-only views of a context for other translation units of the library

@@ -85,6 +85,9 @@ void launch_bc_vjp(const Grid& g, const les_params& p, const double* M, const do
 void launch_functional(const Grid& g, const les_params& p, int j5, double dt, const double* M,
                        const double* Q, double* lam, double* partials, double* Jout,
                        const Launch& L);
+// the same term from FP32 metrics (mixed forms), value only
+void launch_functional(const Grid& g, const les_params& p, int j5, double dt, const float* M,
+                       const double* Q, double* partials, double* Jout, const Launch& L);
 void launch_pack_dual(long long count, const double* v, const double* d, Dual* out, const Launch& L);
 void launch_unpack_dual(long long count, const Dual* in, double* v, double* d, const Launch& L);
 

@@ -232,3 +232,34 @@ def test_window_gradient_against_torch_autograd(lj, torch, radius):
     # of dependence (about 1e-17 here), so it carries more relative round-off
     tol = 1e-9 if radius < 1.0 else 1e-6
     assert np.allclose(np.array(g), g_ref, rtol=0, atol=tol * gmax), (g, g_ref)
+
+
+def test_functional_along_fp64_and_mixed_forward_runs(lj, torch):
+    """les_surface_functional summed over a forward run: equal to the adjoint
+    window's J in FP64, and within 1e-5 of it with the FP32-mixed forward
+    (default and compact forms)."""
+    shape = (16, 14, 16)
+    amps = lj.synth.forcing_amplitudes(9, scale=2e-2)
+    xyz = torch.from_numpy(lj.synth.jet_grid(*shape)).cuda()
+    j5 = _j_surface(lj, shape, 0.5)
+    nsteps, dt = 6, 1e-3
+    out = {}
+    for prec in (lj.PREC_FP64, lj.PREC_MIXED, lj.PREC_MIXED_COMPACT):
+        ctx = lj.Context(lj.make_params(Re=500.0, dt_mode=lj.DT_FIXED, dt_fixed=dt, amp=tuple(amps),
+                                        precision=prec), shape, "cuda:0")
+        ctx.les_set_grid(xyz)
+        Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+        ctx.les_init_jet(xyz, 1, 1e-3, Q)
+        if prec == lj.PREC_FP64:
+            aw = ctx.adjoint_workspace(nsteps, 2)
+            out["window"], _ = ctx.les_adjoint_window(Q, 0.0, nsteps, 2, j5, aw)
+        ctx.les_set_time(0.0)
+        J = 0.0
+        for _ in range(nsteps):
+            ctx.les_run_n_steps(1, Q)
+            J += ctx.les_surface_functional(Q, j5, dt)
+        out[prec] = J
+    assert out["window"] > 0
+    assert math.isclose(out[lj.PREC_FP64], out["window"], rel_tol=1e-12)
+    for prec in (lj.PREC_MIXED, lj.PREC_MIXED_COMPACT):
+        assert math.isclose(out[prec], out["window"], rel_tol=1e-5), (prec, out)
