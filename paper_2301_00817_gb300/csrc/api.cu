@@ -610,7 +610,7 @@ namespace {
 
 struct AdjLayout {
   size_t acc, node, mk, lamMK, S, lamS, lamR, lamQ0, work, lam, Qnext, E, partials, scal;
-  size_t qd, mkd, noded, fluxd, rd, ckpt, segS, segMK, total;
+  size_t qd, mkd, noded, fluxd, rd, ckpt, segS, segMK, segN, total;
   int nckpt, K;
 };
 
@@ -650,6 +650,7 @@ AdjLayout adj_layout(const les_ctx* c, int nsteps, int K) {
   const int ks = nsteps > 0 ? L.K : 0;
   L.segS = take((size_t)ks * 6 * 5 * N * d);
   L.segMK = take((size_t)ks * 2 * N * d);
+  L.segN = take((size_t)ks * 5 * 8 * N * d);  // node quantities of the five stage inputs
   L.total = o;
   return L;
 }
@@ -686,19 +687,24 @@ lesjet::StageIO64 adj_io(les_ctx* c, void* aw, const AdjLayout& Ly, const double
 }
 
 // Forward recompute of one step from S[0] = Q^n: frozen viscosity mk of Q^n
-// and the stage states S[1..5] (S[5] before the boundary conditions).
+// and the stage states S[1..5] (S[5] before the boundary conditions).  With
+// nodes != nullptr ([5][8][N]) the node quantities of the five stage inputs
+// are kept there for the reverse sweep.
 void adj_forward(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], double* mk,
-                 cudaStream_t s) {
+                 double* nodes, cudaStream_t s) {
   lesjet::Launch L{s, &c->launches};
   const Grid& g = c->g;
   lesjet::StageIO64 io = adj_io(c, aw, Ly, S[0]);
   io.mk = mk;
+  auto node_of = [&](int l) { return nodes ? nodes + (size_t)(l - 1) * 8 * g.N : io.node; };
   lesjet::launch_dt_finalize(c->p, at<double>(c, c->off_part), at<DevScalars>(c, c->off_sc), 0, L);
-  lesjet::launch_node64(g, c->p, io, false, L);
+  io.node = node_of(1);
+  lesjet::launch_node64(g, c->p, io, false, L);  // node quantities of Q^n = stage-1 input
   lesjet::launch_mu64(g, c->p, io, L);
   for (int l = 1; l <= 5; ++l) {
     io.Qin = S[l - 1];
-    lesjet::launch_node64(g, c->p, io, false, L);
+    io.node = node_of(l);
+    if (l > 1) lesjet::launch_node64(g, c->p, io, false, L);
     for (int d = 0; d < 3; ++d) lesjet::launch_flux64(g, c->p, io, d, L);
     lesjet::launch_update64(g, io, S[0], kAlpha[l - 1], 1, S[l], L);
   }
@@ -708,8 +714,8 @@ void adj_forward(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], 
 // stored: lam_out = (dQ^{n+1}/dQ^n)^T lam_next; grad_dev[16] +=
 // (dQ^{n+1}/da)^T lam_next.  lam_out may alias lam_next.
 void adj_reverse(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], const double* mk,
-                 double t_n, const double* lam_next, double* lam_out, double* grad_dev,
-                 cudaStream_t s) {
+                 const double* nodes, double t_n, const double* lam_next, double* lam_out,
+                 double* grad_dev, cudaStream_t s) {
   lesjet::Launch L{s, &c->launches};
   const Grid& g = c->g;
   const size_t bytes = 5 * (size_t)g.N * sizeof(double);
@@ -738,7 +744,10 @@ void adj_reverse(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], 
   for (int l = 5; l >= 1; --l) {
     lesjet::launch_stage_prep(g, M, kAlpha[l - 1] * dt, lamS, lamR, lamQ0, L);
     io.Qin = S[l - 1];
-    lesjet::launch_node64(g, c->p, io, false, L);
+    if (nodes)
+      io.node = const_cast<double*>(nodes) + (size_t)(l - 1) * 8 * g.N;  // kept by adj_forward
+    else
+      lesjet::launch_node64(g, c->p, io, false, L);
     lesjet::launch_rhs_vjp(g, c->p, S[l - 1], M, io.node, io.mk, lamR, aw_at<double>(aw, Ly.acc),
                            lamS, lamMK, L);
   }
@@ -816,8 +825,8 @@ int les_adjoint_step(les_ctx* c, const double* Qn, double t_n, const double* lam
   for (int l = 0; l < 6; ++l) S[l] = aw_at<double>(aw, Ly.S) + (size_t)l * 5 * c->g.N;
   cudaMemcpyAsync(S[0], Qn, 5 * (size_t)c->g.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
   double* mk = aw_at<double>(aw, Ly.mk);
-  adj_forward(c, aw, Ly, S, mk, s);
-  adj_reverse(c, aw, Ly, S, mk, t_n, lam_next, lam_out, gdev, s);
+  adj_forward(c, aw, Ly, S, mk, nullptr, s);
+  adj_reverse(c, aw, Ly, S, mk, nullptr, t_n, lam_next, lam_out, gdev, s);
   if ((rc = cuda_check(c, "les_adjoint_step")) != LES_OK) return rc;
   double h[16];
   cudaMemcpyAsync(h, gdev, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -856,6 +865,7 @@ int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps,
     return aw_at<double>(aw, Ly.segS) + ((size_t)m * 6 + l) * 5 * g.N;
   };
   auto segMK = [&](int m) { return aw_at<double>(aw, Ly.segMK) + (size_t)m * 2 * g.N; };
+  auto segN = [&](int m) { return aw_at<double>(aw, Ly.segN) + (size_t)m * 5 * 8 * g.N; };
   cudaMemsetAsync(scal, 0, 64 * sizeof(double), s);
   DevScalars* sc = at<DevScalars>(c, c->off_sc);
   const int last = (nsteps - 1) / K;  // the last segment is kept by the forward sweep
@@ -863,7 +873,7 @@ int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps,
   auto kept_step = [&](int m, int n, double* dst) {
     double* S[6];
     for (int l = 0; l < 6; ++l) S[l] = segS(m, l);
-    adj_forward(c, aw, Ly, S, segMK(m), s);
+    adj_forward(c, aw, Ly, S, segMK(m), segN(m), s);
     cudaMemcpyAsync(dst, S[5], bytes, cudaMemcpyDeviceToDevice, s);
     if (c->p.bc == LES_BC_JET)
       lesjet::launch_bc_jet(g, c->p, dst, M, at<double>(c, c->off_rth), sc, 1, t0 + (n + 1) * dt, L);
@@ -900,7 +910,7 @@ int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps,
         } else {
           double* S[6];
           for (int l = 0; l < 6; ++l) S[l] = segS(m, l);
-          adj_forward(c, aw, Ly, S, segMK(m), s);
+          adj_forward(c, aw, Ly, S, segMK(m), segN(m), s);
         }
       }
     }
@@ -910,7 +920,7 @@ int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps,
       lesjet::launch_functional(g, c->p, j_surface, dt, M, Qn, lam, part, Jscratch, L);
       double* S[6];
       for (int l = 0; l < 6; ++l) S[l] = segS(m, l);
-      adj_reverse(c, aw, Ly, S, segMK(m), t0 + (n - 1) * dt, lam, lam, gdev, s);
+      adj_reverse(c, aw, Ly, S, segMK(m), segN(m), t0 + (n - 1) * dt, lam, lam, gdev, s);
     }
   }
   if ((rc = cuda_check(c, "les_adjoint_window")) != LES_OK) return rc;
