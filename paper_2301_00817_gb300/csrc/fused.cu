@@ -35,32 +35,10 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int NPEND>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
-  if (sizeof(T) == 8)
-    cp_async8(smem, gmem);
-  else
-    cp_async4(smem, gmem);
-}
-
-// Wrapped index along direction d, or -1 outside a non-periodic direction.
-__device__ __forceinline__ int wrap_idx(const Grid& g, int d, int v) {
-  const int n = g.n[d];
-  if (g.per[d]) {
-    v %= n;
-    return v < 0 ? v + n : v;
-  }
-  return (v >= 0 && v < n) ? v : -1;
 }
 
 // ----------------------------------------------------------- interface flux
@@ -420,7 +398,7 @@ __global__ void __launch_bounds__(FNT, 1)
   const bool jint = G.per[1] || (jown > 0 && jown < nj - 1);
   const bool kint = G.per[2] || (kown > 0 && kown < nk - 1);
   const bool per_i = G.per[0] != 0;
-  const int cm1 = colk(tx - 1), cm2 = colk(tx - 2);
+  const int cm1 = colk(tx - 1);
   const int o2 = (ty + 2) * SK + tx;  // own node, 2-node-halo planes
   const int o1 = (ty + 1) * SK + tx;  // own node, 1-node-halo planes
   const bool vec_ok = G.vec16 && (k0 + FTK <= nk);
