@@ -190,6 +190,14 @@ uint64_t les_launch_count(const les_ctx *ctx);
  * class k < 16, the summed device milliseconds ms[k] and launch groups
  * counts[k]; les_profile_name(k) names class k ("" past the last). */
 int les_profile(les_ctx *ctx, int enable);
+
+/* FMA throughput of the current device's CUDA cores, the roof of the
+ * ALU-bound kernels (the paper has no counterpart): every thread advances
+ * 16 independent FMA chains on a grid of 8 CTAs per SM, timed with CUDA
+ * events on `stream`.  precision LES_PREC_FP64 measures FP64, the mixed
+ * values FP32.  *tflops = 2 x FMAs / time / 1e12.  Needs no context.
+ * SYNCHRONISES; LES_ERR_INVALID_ARG or LES_ERR_CUDA on failure. */
+int les_measure_fma_peak(int precision, double *tflops, les_stream_t stream);
 int les_profile_read(les_ctx *ctx, double ms[16], uint64_t counts[16],
                      les_stream_t stream);
 const char *les_profile_name(int kind);

@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH):
     lib.les_profile_read.restype = C.c_int
     lib.les_profile_name.argtypes = [i]
     lib.les_profile_name.restype = C.c_char_p
+    lib.les_measure_fma_peak.argtypes = [i, C.POINTER(d), vp]
     lib.les_surface_functional.argtypes = [vp, vp, i, d, C.POINTER(d), vp]
     lib.les_time_step_static.argtypes = [vp, vp, vp, C.POINTER(d), vp]
     lib.les_time_step_static.restype = C.c_int
@@ -153,6 +154,17 @@ def _stream(stream=None):
     torch = _torch()
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def measure_fma_peak(precision: int, stream=None) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device: FP64 for
+    PREC_FP64, FP32 for the mixed precisions (les_measure_fma_peak)."""
+    lib = load_library()
+    out = C.c_double()
+    rc = lib.les_measure_fma_peak(precision, C.byref(out), _stream(stream))
+    if rc != LES_OK:
+        raise LesError(rc, "les_measure_fma_peak failed")
+    return out.value
 
 
 class Context:

@@ -333,3 +333,15 @@ def test_checkpoint_resume_is_bitwise(lj, torch, tmp_path, prec):
         # that is exact except on a half-ulp tie of the low word
         assert rel_linf(Q2.cpu().numpy(), Qref.cpu().numpy()) <= 1e-6
         assert abs(d.t - d8.t) <= 1e-12 * d8.t
+
+
+def test_measured_fma_peaks_are_plausible(lj, torch):
+    """les_measure_fma_peak: FP32 and FP64 CUDA-core FMA throughput of the
+    device (the roofs of the ALU-bound kernels).  On GB300 FP64 runs at a
+    small fraction of FP32."""
+    f64 = lj.measure_fma_peak(lj.PREC_FP64)
+    f32 = lj.measure_fma_peak(lj.PREC_MIXED)
+    assert 0.2 < f64 < 100.0 and 5.0 < f32 < 500.0, (f64, f32)
+    assert f32 > 4.0 * f64
+    with pytest.raises(lj.LesError):
+        lj.measure_fma_peak(7)
