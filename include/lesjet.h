@@ -101,6 +101,30 @@ typedef struct les_ctx les_ctx;
  * memory only; *out is owned by the caller and released by les_destroy. */
 int les_create(const les_params *p, int ni, int nj, int nk, les_ctx **out);
 int les_destroy(les_ctx *ctx);
+/* Synthetic annular jet grid (the stand-in for the paper's meshes, Table
+ * tab:mesh): Cartesian coordinates of node (i, j, k) into xyz (device [3][N]
+ * FP64, the layout les_set_grid reads):
+ *   x_i = length (q^i - 1)/(q^(ni-1) - 1), q = ratio, or length i/(ni-1) for
+ *         q = 1; ratio <= 0 selects 1.01 up to 288 planes and 1.01^(288/ni)
+ *         beyond (the same geometric mapping, refined);
+ *   r_j = r0 + (r1 - r0) g(s_j)/g(1), s_j = j/(nj-1),
+ *         g(s) = s - (A/beta)[tanh(beta (s - s_c)) + tanh(beta s_c)], s_c the
+ *         point the map sends to r_c (found by bisection; spacing is smallest
+ *         there, (1 - A) times the mean);
+ *   theta_k = 2 pi k/nk;  y = r cos theta, z = r sin theta.
+ * Needs no context.  ni, nj, nk >= 2, N < 2^40, length > 0, 0 <= r0 < r_c <
+ * r1, 0 <= A < 1, beta > 0; LES_ERR_SHAPE / LES_ERR_INVALID_ARG otherwise.
+ * Asynchronous. */
+typedef struct les_jet_grid {
+  double length;  /* axial extent (20 D) */
+  double ratio;   /* geometric axial stretching (<= 0: the refinement rule) */
+  double r0, r1;  /* radial extent (0.02 D, 10 D) */
+  double r_c;     /* clustering radius (0.5 D) */
+  double A, beta; /* clustering strength (0.9) and sharpness (8) */
+} les_jet_grid;
+int les_grid_jet(int ni, int nj, int nk, const les_jet_grid *grid, double *xyz,
+                 les_stream_t stream);
+
 /* Last error message of this context (never NULL; "" when none). */
 const char *les_last_error(const les_ctx *ctx);
 /* Replace the parameters (same grid and precision), e.g. new forcing. */

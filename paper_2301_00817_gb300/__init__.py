@@ -57,6 +57,13 @@ class LesDiag(C.Structure):
                 ("status", C.c_int), ("steps", C.c_int)]
 
 
+class LesJetGrid(C.Structure):
+    """Mirror of ``les_jet_grid`` in include/lesjet.h."""
+    _fields_ = [("length", C.c_double), ("ratio", C.c_double), ("r0", C.c_double),
+                ("r1", C.c_double), ("r_c", C.c_double), ("A", C.c_double),
+                ("beta", C.c_double)]
+
+
 def make_params(**kw) -> LesParams:
     """les_params with the jet workload's defaults, overridden by kw."""
     d = dict(gamma=1.4, Pr=0.72, Pr_sgs=0.9, Mj=1.4, Re=1.0e5, T_ref=288.15,
@@ -119,6 +126,8 @@ def load_library(path: str = LIB_PATH):
     lib.les_profile_name.argtypes = [i]
     lib.les_profile_name.restype = C.c_char_p
     lib.les_measure_fma_peak.argtypes = [i, C.POINTER(d), vp]
+    lib.les_grid_jet.argtypes = [i, i, i, C.POINTER(LesJetGrid), vp, vp]
+    lib.les_grid_jet.restype = C.c_int
     lib.les_surface_functional.argtypes = [vp, vp, i, d, C.POINTER(d), vp]
     lib.les_time_step_static.argtypes = [vp, vp, vp, C.POINTER(d), vp]
     lib.les_time_step_static.restype = C.c_int
@@ -165,6 +174,26 @@ def measure_fma_peak(precision: int, stream=None) -> float:
     if rc != LES_OK:
         raise LesError(rc, "les_measure_fma_peak failed")
     return out.value
+
+
+def grid_jet(shape, xyz=None, length: float = 20.0, ratio: float = 0.0, r0: float = 0.02,
+             r1: float = 10.0, r_c: float = 0.5, A: float = 0.9, beta: float = 8.0,
+             stream=None):
+    """The synthetic annular jet grid written on the device (les_grid_jet):
+    coordinates [3, ni, nj, nk] FP64, into ``xyz`` when given.  ratio <= 0
+    selects the axial stretching rule (1.01 up to 288 planes, 1.01^(288/ni)
+    beyond)."""
+    torch = _torch()
+    lib = load_library()
+    ni, nj, nk = (int(v) for v in shape)
+    if xyz is None:
+        xyz = torch.empty((3, ni, nj, nk), dtype=torch.float64, device="cuda")
+    assert xyz.dtype == torch.float64 and xyz.numel() == 3 * ni * nj * nk
+    g = LesJetGrid(length, ratio, r0, r1, r_c, A, beta)
+    rc = lib.les_grid_jet(ni, nj, nk, C.byref(g), _ptr(xyz), _stream(stream))
+    if rc != LES_OK:
+        raise LesError(rc, "les_grid_jet failed")
+    return xyz
 
 
 class Context:

@@ -933,6 +933,46 @@ int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps,
   return cuda_check(c, "les_adjoint_window");
 }
 
+int les_grid_jet(int ni, int nj, int nk, const les_jet_grid* gp, double* xyz, les_stream_t stream) {
+  if (!gp || !xyz) return LES_ERR_INVALID_ARG;
+  if (ni < 2 || nj < 2 || nk < 2) return LES_ERR_SHAPE;
+  const long long N = (long long)ni * nj * nk;
+  if (N >= (1LL << 40)) return LES_ERR_SHAPE;
+  const les_jet_grid G = *gp;
+  if (!(G.length > 0.0) || !(G.r0 >= 0.0) || !(G.r0 < G.r_c) || !(G.r_c < G.r1) || !(G.A >= 0.0) ||
+      !(G.A < 1.0) || !(G.beta > 0.0))
+    return LES_ERR_INVALID_ARG;
+  if (!aligned16(xyz)) return LES_ERR_ALIGN;
+  const double q = G.ratio > 0.0 ? G.ratio : (ni <= 288 ? 1.01 : std::pow(1.01, 288.0 / ni));
+  // s_c: the point the map r(s; s_c) sends to r_c (bisection on the monotone r(s_c; s_c))
+  auto gmap = [&](double s, double sc) {
+    return s - (G.A / G.beta) * (std::tanh(G.beta * (s - sc)) + std::tanh(G.beta * sc));
+  };
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double r = G.r0 + (G.r1 - G.r0) * gmap(mid, mid) / gmap(1.0, mid);
+    if (r < G.r_c)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  Grid g;
+  g.n[0] = ni;
+  g.n[1] = nj;
+  g.n[2] = nk;
+  g.per[0] = g.per[1] = 0;
+  g.per[2] = 1;
+  g.N = N;
+  g.stride[0] = (long long)nj * nk;
+  g.stride[1] = nk;
+  g.stride[2] = 1;
+  unsigned long long launches = 0;
+  lesjet::Launch L{(cudaStream_t)stream, &launches};
+  lesjet::launch_grid_jet(g, G.length, q, G.r0, G.r1, G.A, G.beta, 0.5 * (lo + hi), xyz, L);
+  return cudaGetLastError() == cudaSuccess ? LES_OK : LES_ERR_CUDA;
+}
+
 int les_surface_functional(les_ctx* c, const double* Q, int j_surface, double w, double* J_out,
                            les_stream_t stream) {
   int rc = ready(c);

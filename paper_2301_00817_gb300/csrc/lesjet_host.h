@@ -17,6 +17,9 @@ void launch_metrics(const Grid& g, const double* xyz, const double shift[9], flo
                     const Launch& L);
 void launch_to_float(long long count, const double* a, float* b, const Launch& L);
 void launch_inflow_geometry(const Grid& g, const double* xyz, double* rth, const Launch& L);
+// synthetic jet grid coordinates [3][N] (s_c: the clustering centre in s)
+void launch_grid_jet(const Grid& g, double length, double q, double r0, double r1, double A,
+                     double beta, double sc, double* xyz, const Launch& L);
 void launch_init_jet(const Grid& g, const double* xyz, uint64_t seed, double noise,
                      const les_params& p, double* Q, const Launch& L);
 

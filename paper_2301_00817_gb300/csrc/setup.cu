@@ -72,6 +72,40 @@ __global__ void k_to_float(long long count, const double* __restrict__ a, float*
     b[n] = (float)a[n];
 }
 
+// Synthetic annular jet grid (Table tab:mesh stand-in): node (i, j, k) at
+// x_i = L (q^i - 1)/(q^(ni-1) - 1) (L i/(ni-1) for q = 1), radius
+// r_j = r0 + (r1 - r0) g(s_j)/g(1) with s_j = j/(nj-1) and the clustering map
+// g(s) = s - (A/beta)[tanh(beta (s - s_c)) + tanh(beta s_c)], azimuth
+// theta_k = 2 pi k/nk; y = r cos theta, z = r sin theta.
+struct JetGridArgs {
+  double length, q, r0, r1, A, beta, sc;
+};
+
+__device__ __forceinline__ double jet_map(double s, const JetGridArgs& a) {
+  return s - (a.A / a.beta) * (tanh(a.beta * (s - a.sc)) + tanh(a.beta * a.sc));
+}
+
+__global__ void k_grid_jet(Grid g, JetGridArgs a, double* __restrict__ xyz) {
+  const long long N = g.N;
+  const int ni = g.n[0], nj = g.n[1], nk = g.n[2];
+  const double two_pi = 6.283185307179586476925286766559;
+  const double g1 = jet_map(1.0, a);
+  const double qn = pow(a.q, (double)(ni - 1)) - 1.0;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    const double x = (a.q == 1.0) ? a.length * c[0] / (double)(ni - 1)
+                                  : a.length * (pow(a.q, (double)c[0]) - 1.0) / qn;
+    const double r = a.r0 + (a.r1 - a.r0) * jet_map(c[1] / (double)(nj - 1), a) / g1;
+    double sn, cs;
+    sincos(two_pi * c[2] / (double)nk, &sn, &cs);
+    xyz[n] = x;
+    xyz[N + n] = r * cs;
+    xyz[2 * N + n] = r * sn;
+  }
+}
+
 // Radius and azimuth of the entrance-plane nodes (i = 0), used by the inflow
 // profile and forcing.
 __global__ void k_inflow_geometry(Grid g, const double* __restrict__ xyz, double* __restrict__ rth) {
@@ -167,6 +201,13 @@ void launch_init_jet(const Grid& g, const double* xyz, uint64_t seed, double noi
                      const les_params& p, double* Q, const Launch& L) {
   k_init_jet<<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, seed, noise, p.gamma, p.Mj, p.r_jet,
                                                       p.theta_m, Q);
+  ++*L.counter;
+}
+
+void launch_grid_jet(const Grid& g, double length, double q, double r0, double r1, double A,
+                     double beta, double sc, double* xyz, const Launch& L) {
+  JetGridArgs a{length, q, r0, r1, A, beta, sc};
+  k_grid_jet<<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, a, xyz);
   ++*L.counter;
 }
 

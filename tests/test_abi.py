@@ -28,7 +28,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("les_create", "les_set_grid", "les_init_jet", "les_rhs", "les_rk_step",
-                     "les_run_n_steps", "les_time_step", "les_apply_bc", "les_mu_eff"):
+                     "les_run_n_steps", "les_time_step", "les_apply_bc", "les_mu_eff",
+                     "les_grid_jet"):
         assert required in names
 
 
@@ -84,3 +85,18 @@ def test_calls_before_grid_are_rejected_without_touching_the_device(lib):
     assert b"les_set_grid" in lib.les_last_error(h)
     assert lib.les_set_grid(h, C.c_void_p(3), None, C.c_void_p(16), None) == lj.LES_ERR_ALIGN
     lib.les_destroy(h)
+
+
+def test_grid_jet_validates_before_touching_the_device(lib):
+    import paper_2301_00817_gb300 as lj
+    good = lj.LesJetGrid(20.0, 0.0, 0.02, 10.0, 0.5, 0.9, 8.0)
+    ptr = C.c_void_p(16)
+    assert lib.les_grid_jet(1, 8, 8, C.byref(good), ptr, None) == lj.LES_ERR_SHAPE
+    assert lib.les_grid_jet(8, 8, 8, None, ptr, None) == lj.LES_ERR_INVALID_ARG
+    assert lib.les_grid_jet(8, 8, 8, C.byref(good), None, None) == lj.LES_ERR_INVALID_ARG
+    assert lib.les_grid_jet(8, 8, 8, C.byref(good), C.c_void_p(24), None) == lj.LES_ERR_ALIGN
+    for field, value in (("length", 0.0), ("r_c", 0.01), ("r_c", 10.0), ("A", 1.0),
+                         ("beta", 0.0), ("r0", -1.0)):
+        bad = lj.LesJetGrid(20.0, 0.0, 0.02, 10.0, 0.5, 0.9, 8.0)
+        setattr(bad, field, value)
+        assert lib.les_grid_jet(8, 8, 8, C.byref(bad), ptr, None) == lj.LES_ERR_INVALID_ARG, field

@@ -75,6 +75,35 @@ def test_metrics(orc, lj, torch, case):
         assert np.abs(Mg[r] - Mo[r]).max() <= 1e-14 * scale, r
 
 
+@pytest.mark.parametrize("shape,ratio", [((12, 9, 8), 0.0), ((13, 9, 7), 1.0), ((40, 17, 6), 1.02),
+                                         ((301, 33, 12), 0.0), ((2, 2, 2), 0.0)])
+def test_grid_jet_matches_the_input_generator(lj, torch, shape, ratio):
+    xyz = lj.grid_jet(shape, ratio=ratio).cpu().numpy()
+    ref = lj.synth.jet_grid(*shape)
+    if ratio > 0.0:
+        ref[0] = lj.synth.jet_axial(shape[0], ratio=ratio)[:, None, None]
+    # the same closed forms evaluated in another order: rounding only
+    assert np.abs(xyz - ref).max() <= 1e-14 * 20.0
+    assert xyz[0, 0].max() == 0.0 and abs(xyz[0, -1] - 20.0).max() <= 1e-13
+
+
+def test_grid_jet_drives_one_step(orc, lj, torch):
+    shape = C1
+    kw = dict(periodic=(0, 0, 1), bc=1, sgs_model=1)
+    ctx = lj.Context(lj.make_params(**kw), shape, "cuda:0")
+    xyz_d = lj.grid_jet(shape)
+    ctx.les_set_grid(xyz_d)
+    Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_init_jet(xyz_d, 9, 1e-3, Q)
+    d = ctx.les_run_n_steps(1, Q)
+    P = oracle_params(orc, **kw)
+    xyz = lj.synth.jet_grid(*shape)
+    Q0 = orc.init_jet(P, xyz, seed=9, noise=1e-3)
+    Q1, dt1 = orc.rk_step(P, Q0, orc.metrics(xyz, (0, 0, 1)), xyz, 0.0)
+    assert abs(d.dt - dt1) <= 1e-13 * dt1
+    assert rel_linf(Q.cpu().numpy(), Q1) <= 1e-12
+
+
 def test_init_jet(orc, lj, torch):
     shape = C1
     xyz = lj.synth.jet_grid(*shape)
