@@ -85,6 +85,7 @@ def _lib_handle():
             P = C.POINTER(OrcParams)
             i = C.c_int
             lib.orc_metrics.argtypes = [i, i, i, C.POINTER(C.c_int), _dp, _dp, _dp]
+            lib.orc_metrics_conservative.argtypes = [i, i, i, C.POINTER(C.c_int), _dp, _dp, _dp]
             lib.orc_prim_to_cons.argtypes = [P, C.c_size_t, _dp, _dp]
             lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                                C.POINTER(C.c_uint32)]
@@ -121,14 +122,16 @@ def num_threads() -> int:
     return int(_lib_handle().orc_num_threads())
 
 
-def metrics(xyz, periodic=(0, 0, 1), shift=None) -> np.ndarray:
-    """xyz [3, ni, nj, nk] -> M [10, ni, nj, nk] (metrics then J^-1)."""
+def metrics(xyz, periodic=(0, 0, 1), shift=None, form: int = 0) -> np.ndarray:
+    """xyz [3, ni, nj, nk] -> M [10, ni, nj, nk] (metrics then J^-1).
+    form 0: the cross-product formulas; 1: the conservative form."""
     xyz = _f64(xyz)
     _, ni, nj, nk = xyz.shape
     sh = _f64(np.zeros(9) if shift is None else np.asarray(shift).reshape(9))
     per = (C.c_int * 3)(*periodic)
     M = np.empty((10, ni, nj, nk))
-    _lib_handle().orc_metrics(ni, nj, nk, per, _ptr(sh), _ptr(xyz), _ptr(M))
+    fn = _lib_handle().orc_metrics_conservative if form == 1 else _lib_handle().orc_metrics
+    fn(ni, nj, nk, per, _ptr(sh), _ptr(xyz), _ptr(M))
     return M
 
 

@@ -161,6 +161,98 @@ void orc_metrics(int ni, int nj, int nk, const int periodic[3],
   }
 }
 
+/* Coordinate component comp at node c, where c may lie one period outside a
+ * periodic direction: the stored value of the wrapped node plus one period's
+ * shift per wrap. */
+static double coord_at(const grid_t *g, const double *xyz,
+                       const double shift[9], const int c[3], int comp) {
+  int w[3] = {c[0], c[1], c[2]};
+  double v = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    if (w[d] < 0) { w[d] += g->n[d]; v -= shift[3 * d + comp]; }
+    if (w[d] >= g->n[d]) { w[d] -= g->n[d]; v += shift[3 * d + comp]; }
+  }
+  return xyz[(size_t)comp * g->N + lin(g, w)] + v;
+}
+
+/* The product (dp/ds) q at node c (c as in coord_at): coordinate p
+ * differentiated along s, times coordinate q. */
+static double metric_product(const grid_t *g, const double *xyz,
+                             const double shift[9], const int c[3], int p,
+                             int s, int q) {
+  int w[3] = {c[0], c[1], c[2]};
+  for (int d = 0; d < 3; ++d) {
+    if (w[d] < 0) w[d] += g->n[d];
+    if (w[d] >= g->n[d]) w[d] -= g->n[d];
+  }
+  return coord_deriv(g, xyz, shift, w, s, p) * coord_at(g, xyz, shift, c, q);
+}
+
+/* Derivative along t of metric_product(p, s, q) at node c, with the same
+ * second-order formulas as coord_deriv (central; one-sided at the faces of a
+ * non-periodic direction). */
+static double product_deriv(const grid_t *g, const double *xyz,
+                            const double shift[9], const int c[3], int t,
+                            int p, int s, int q) {
+  int a[3] = {c[0], c[1], c[2]}, b[3] = {c[0], c[1], c[2]},
+      e[3] = {c[0], c[1], c[2]};
+  int n = g->n[t];
+  if (g->per[t] || (c[t] > 0 && c[t] < n - 1)) {
+    a[t] = c[t] + 1; b[t] = c[t] - 1;
+    return 0.5 * (metric_product(g, xyz, shift, a, p, s, q) -
+                  metric_product(g, xyz, shift, b, p, s, q));
+  }
+  if (c[t] == 0) {
+    b[t] = 1; e[t] = 2;
+    return 0.5 * (-3.0 * metric_product(g, xyz, shift, a, p, s, q) +
+                  4.0 * metric_product(g, xyz, shift, b, p, s, q) -
+                  metric_product(g, xyz, shift, e, p, s, q));
+  }
+  b[t] = n - 2; e[t] = n - 3;
+  return 0.5 * (3.0 * metric_product(g, xyz, shift, a, p, s, q) -
+                4.0 * metric_product(g, xyz, shift, b, p, s, q) +
+                metric_product(g, xyz, shift, e, p, s, q));
+}
+
+/* Metric terms in the conservative (Thomas-Lombard) form, an alternative to
+ * the cross-product formulas of Sec. "Transformation of Coordinates".  For
+ * direction r with (r, s, t) a cyclic order of (xi, eta, zeta) and
+ * component c with (c, p, q) a cyclic order of (x, y, z):
+ *   J^-1 r_c = ((p_s) q)_t - ((p_t) q)_s,
+ * which equals the cofactor p_s q_t - p_t q_s of the continuous mapping and,
+ * written with central differences, makes sum_r delta_r (J^-1 r_c) vanish at
+ * every interior node (the discrete geometric conservation law: free-stream
+ * preservation on any grid).  J^-1 is the same determinant as in
+ * orc_metrics; the stored metric is (J^-1 r_c) / J^-1. */
+void orc_metrics_conservative(int ni, int nj, int nk, const int periodic[3],
+                              const double shift[9], const double *xyz,
+                              double *M) {
+  grid_t g = make_grid(ni, nj, nk, periodic);
+  size_t N = g.N;
+#pragma omp parallel for schedule(static)
+  for (long nn = 0; nn < (long)N; ++nn) {
+    int c[3];
+    unlin(&g, (size_t)nn, c);
+    double d[3][3];
+    for (int comp = 0; comp < 3; ++comp)
+      for (int dir = 0; dir < 3; ++dir)
+        d[comp][dir] = coord_deriv(&g, xyz, shift, c, dir, comp);
+    double Jinv = d[0][0] * d[1][1] * d[2][2] + d[0][1] * d[1][2] * d[2][0] +
+                  d[0][2] * d[1][0] * d[2][1] - d[0][0] * d[1][2] * d[2][1] -
+                  d[0][1] * d[1][0] * d[2][2] - d[0][2] * d[1][1] * d[2][0];
+    for (int r = 0; r < 3; ++r) {
+      int s = (r + 1) % 3, t = (r + 2) % 3;
+      for (int comp = 0; comp < 3; ++comp) {
+        int p = (comp + 1) % 3, q = (comp + 2) % 3;
+        double cof = product_deriv(&g, xyz, shift, c, t, p, s, q) -
+                     product_deriv(&g, xyz, shift, c, s, p, t, q);
+        M[(size_t)(3 * r + comp) * N + nn] = cof / Jinv;
+      }
+    }
+    M[9 * N + nn] = Jinv;
+  }
+}
+
 /* ------------------------------------------------------ state conversion */
 
 /* System I total energy e = p/(gamma-1) + rho u_i u_i / 2. */

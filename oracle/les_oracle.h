@@ -48,6 +48,9 @@ typedef struct {
 /* Grid metrics (Sec. "Transformation of Coordinates"); xyz is [3][N]. */
 void orc_metrics(int ni, int nj, int nk, const int periodic[3],
                  const double shift[9], const double *xyz, double *M);
+void orc_metrics_conservative(int ni, int nj, int nk, const int periodic[3],
+                              const double shift[9], const double *xyz,
+                              double *M);
 
 /* Primitive (rho,u,v,w,p) [5][N] -> conserved Q [5][N] (System I energy). */
 void orc_prim_to_cons(const orc_params *P, size_t N, const double *prim,

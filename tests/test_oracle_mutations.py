@@ -49,6 +49,15 @@ MUTATIONS = {
     "face_sensor": ("return fabs(pp - 2.0 * p0 + pm) / (pp + 2.0 * p0 + pm);\n  }",
                     "return fabs(pp - 2.0 * p0 + pm) / (pp + p0 + pm);\n  }",
                     ["test_one_dimensional_jst_reduction"]),
+    "conservative_outer_swap": ("double cof = product_deriv(&g, xyz, shift, c, t, p, s, q) -",
+                                "double cof = product_deriv(&g, xyz, shift, c, s, p, s, q) -",
+                                ["test_conservative_metrics_exact_on_affine_grid"]),
+    "conservative_period_shift": ("if (w[d] >= g->n[d]) { w[d] -= g->n[d]; v += shift[3 * d + comp]; }",
+                                  "if (w[d] >= g->n[d]) { w[d] -= g->n[d]; }",
+                                  ["test_conservative_metrics_converge_on_the_periodic_box"]),
+    "conservative_face_formula": ("return 0.5 * (-3.0 * metric_product(g, xyz, shift, a, p, s, q) +",
+                                  "return 0.5 * (-2.0 * metric_product(g, xyz, shift, a, p, s, q) +",
+                                  ["test_conservative_metrics_exact_on_affine_grid"]),
 }
 
 

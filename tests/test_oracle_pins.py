@@ -88,6 +88,142 @@ def test_metric_identity(orc, case):
     assert (M[9] > 0).all()
 
 
+def _central(f, d, periodic):
+    """Central difference along axis d at interior nodes (NaN elsewhere for a
+    non-periodic axis)."""
+    out = 0.5 * (np.roll(f, -1, axis=d) - np.roll(f, 1, axis=d))
+    if not periodic:
+        idx = [slice(None)] * 3
+        idx[d] = 0
+        out[tuple(idx)] = np.nan
+        idx[d] = -1
+        out[tuple(idx)] = np.nan
+    return out
+
+
+def _wavy_open_grid(n=(11, 10, 9), wave=0.3):
+    """The wavy box's coordinates taken as a grid with no periodic direction."""
+    xyz, _ = synth.box_grid(n, (1.0, 1.3, 0.7), wave=wave)
+    return xyz
+
+
+@pytest.mark.parametrize("periodic", [(0, 0, 0), (1, 1, 1), (0, 0, 1)])
+def test_conservative_metrics_geometric_conservation(orc, periodic):
+    """The conservative metric form satisfies the discrete geometric
+    conservation law sum_r delta_r (J^-1 r_c) = 0 at every interior node of a
+    non-separable grid, to round-off; the cross-product form does not (its
+    error is O(h^2), far above round-off here)."""
+    xyz, shift = synth.box_grid((11, 10, 9), (1.0, 1.3, 0.7), wave=0.3)
+    if not any(periodic):
+        shift = np.zeros(9)
+    gcl = {}
+    for form in (0, 1):
+        M = orc.metrics(xyz, periodic, shift, form=form)
+        cof = M[:9] * M[9]  # J^-1 r_c, row r = 3r + c
+        worst = 0.0
+        for c in range(3):
+            total = sum(_central(cof[3 * r + c], r, periodic[r]) for r in range(3))
+            inner = total[~np.isnan(total)]
+            worst = max(worst, np.abs(inner).max())
+        gcl[form] = worst / np.abs(cof).max()
+    assert gcl[1] < 1e-14, gcl
+    assert gcl[0] > 1e-5, gcl
+
+
+def test_conservative_metrics_exact_on_affine_grid(orc):
+    """On an affine grid x = A xi + b every second-order difference is exact:
+    both forms give A^-1 and det A at every node, faces included."""
+    rng = np.random.default_rng(4)
+    A = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+    n = (7, 6, 5)
+    I = np.stack(np.meshgrid(*[np.arange(m, dtype=np.float64) for m in n], indexing="ij"))
+    xyz = np.einsum("cd,d...->c...", A, I) + np.array([0.3, -1.0, 2.0])[:, None, None, None]
+    Ainv = np.linalg.inv(A)
+    for form in (0, 1):
+        M = orc.metrics(xyz, (0, 0, 0), None, form=form)
+        for r in range(3):
+            for c in range(3):
+                assert np.abs(M[3 * r + c] - Ainv[r, c]).max() < 1e-13, (form, r, c)
+        assert np.abs(M[9] - np.linalg.det(A)).max() < 1e-13
+
+
+def test_conservative_metrics_converge_to_the_mapping(orc):
+    """On a smooth non-separable mapping both forms approach the analytic
+    metrics at second order (the error falls about 4x per halving of h)."""
+    def grid(m):
+        s = np.arange(m, dtype=np.float64) / (m - 1)
+        S0, S1, S2 = np.meshgrid(s, s, s, indexing="ij")
+        x = S0 + 0.1 * np.sin(2.0 * S1) * np.cos(1.5 * S2)
+        y = S1 + 0.1 * np.sin(1.7 * S0) * np.sin(1.3 * S2)
+        z = S2 + 0.1 * np.cos(1.1 * S0) * np.sin(1.9 * S1)
+        h = 1.0 / (m - 1)
+        X = np.empty((3, 3) + S0.shape)  # analytic d x_c / d xi_d (xi = s/h)
+        X[0, 0], X[0, 1], X[0, 2] = 1.0, 0.2 * np.cos(2.0 * S1) * np.cos(1.5 * S2), \
+            -0.15 * np.sin(2.0 * S1) * np.sin(1.5 * S2)
+        X[1, 0], X[1, 1], X[1, 2] = 0.17 * np.cos(1.7 * S0) * np.sin(1.3 * S2), 1.0, \
+            0.13 * np.sin(1.7 * S0) * np.cos(1.3 * S2)
+        X[2, 0], X[2, 1], X[2, 2] = -0.11 * np.sin(1.1 * S0) * np.sin(1.9 * S1), \
+            0.19 * np.cos(1.1 * S0) * np.cos(1.9 * S1), 1.0
+        X *= h
+        Minv = np.linalg.inv(np.moveaxis(X, (0, 1), (-2, -1)))  # [..., d, c]
+        return np.stack([x, y, z]), np.moveaxis(Minv, (-2, -1), (0, 1))
+    for form in (0, 1):
+        errs = []
+        for m in (9, 17, 33):
+            xyz, exact = grid(m)
+            M = orc.metrics(xyz, (0, 0, 0), None, form=form)
+            h = 1.0 / (m - 1)
+            errs.append(max(np.abs(M[3 * r + c] - exact[r, c]).max() * h
+                            for r in range(3) for c in range(3)))
+        rates = [errs[i] / errs[i + 1] for i in range(2)]
+        assert all(3.3 < q < 4.8 for q in rates), (form, errs, rates)
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 1)])
+def test_conservative_metrics_converge_on_the_periodic_box(orc, periodic):
+    """The wavy box (coordinates jump by one period across each periodic
+    wrap): the conservative metrics approach the analytic inverse Jacobian at
+    second order at every node, wrapped neighbours included."""
+    L, wave, tp = (1.0, 1.3, 0.7), 0.2, 2.0 * math.pi
+    errs = []
+    for m in (8, 16, 32):
+        xyz, shift = synth.box_grid((m, m, m), L, wave=wave)
+        S = np.stack(np.meshgrid(*[np.arange(m) / m] * 3, indexing="ij"))
+        X = np.zeros((3, 3) + S.shape[1:])  # d x_c / d i_d of box_grid's mapping
+        X[0, 0] = L[0] / m
+        X[0, 1] = wave * L[0] * np.cos(tp * S[1]) * np.sin(tp * S[2]) / m
+        X[0, 2] = wave * L[0] * np.sin(tp * S[1]) * np.cos(tp * S[2]) / m
+        X[1, 0] = wave * L[1] * np.cos(tp * S[0]) * np.cos(tp * S[2]) / m
+        X[1, 1] = L[1] / m
+        X[1, 2] = -wave * L[1] * np.sin(tp * S[0]) * np.sin(tp * S[2]) / m
+        X[2, 0] = -wave * L[2] * np.sin(tp * S[0]) * np.sin(tp * S[1]) / m
+        X[2, 1] = wave * L[2] * np.cos(tp * S[0]) * np.cos(tp * S[1]) / m
+        X[2, 2] = L[2] / m
+        exact = np.moveaxis(np.linalg.inv(np.moveaxis(X, (0, 1), (-2, -1))), (-2, -1), (0, 1))
+        M = orc.metrics(xyz, periodic, shift, form=1)
+        errs.append(max(np.abs(M[3 * r + c] - exact[r, c]).max() / m
+                        for r in range(3) for c in range(3)))
+    rates = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.3 < q < 4.8 for q in rates), (errs, rates)
+
+
+@pytest.mark.parametrize("sgs", [0, 1])
+def test_free_stream_preservation_conservative_metrics(orc, sgs):
+    """With conservative metrics a uniform state on a non-separable grid has
+    zero residual to round-off, at all interior nodes (open faces, frozen);
+    with the cross-product form it does not."""
+    xyz = _wavy_open_grid()
+    P = orc.params(periodic=(0, 0, 0), bc=0, sgs_model=sgs, Re=300.0)
+    Q = orc.prim_to_cons(P, synth.uniform_prim(xyz.shape[1:], u=0.9, v=-0.3, w=0.2))
+    res = {}
+    for form in (0, 1):
+        M = orc.metrics(xyz, (0, 0, 0), None, form=form)
+        R = orc.rhs(P, Q, M)
+        res[form] = np.abs(R).max() / (np.abs(M[9]).max() * 10.0)
+    assert res[1] < 1e-14, res
+    assert res[0] > 1e-5, res
+
+
 # --------------------------------------------------------- jet grid and IC
 
 def test_jet_grid_recipe():
