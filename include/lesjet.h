@@ -54,6 +54,7 @@ enum { LES_SGS_NONE = 0, LES_SGS_SMAGORINSKY = 1, LES_SGS_VREMAN = 2 };
 enum { LES_PREC_FP64 = 0, LES_PREC_MIXED = 1, LES_PREC_MIXED_COMPACT = 2 };
 enum { LES_BC_FROZEN = 0, LES_BC_JET = 1 };
 enum { LES_DT_CFL = 0, LES_DT_FIXED = 1 };
+enum { LES_METRIC_CROSS = 0, LES_METRIC_CONSERVATIVE = 1 };
 
 /* Flow and scheme parameters (Sec. "Large Eddy Simulation Filtering" to
  * Sec. "Boundary Conditions").  Defaults used by the jet workloads:
@@ -84,6 +85,13 @@ typedef struct les_params {
   int freeze_visc;    /* 1: mu_eff, kappa_eff from Q^n held for 5 stages */
   int precision;      /* LES_PREC_FP64, LES_PREC_MIXED or
                          LES_PREC_MIXED_COMPACT */
+  int metric_form;    /* LES_METRIC_CROSS: the cross-product formulas of
+                         Sec. "Transformation of Coordinates";
+                         LES_METRIC_CONSERVATIVE: the same cofactors in the
+                         Thomas-Lombard form d_t((p_s) q) - d_s((p_t) q),
+                         whose central differences telescope, so a uniform
+                         flow stays uniform on any grid.  Read by
+                         les_set_grid. */
 } les_params;
 
 /* Diagnostics returned by the synchronising run calls. */

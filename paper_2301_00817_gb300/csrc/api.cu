@@ -125,6 +125,10 @@ int validate_params(const les_params* p, std::string& why) {
     why = "dt_mode CFL needs cfl > 0; dt_mode FIXED needs dt_fixed > 0";
     return LES_ERR_INVALID_ARG;
   }
+  if (p->metric_form != LES_METRIC_CROSS && p->metric_form != LES_METRIC_CONSERVATIVE) {
+    why = "metric_form must be LES_METRIC_CROSS or LES_METRIC_CONSERVATIVE";
+    return LES_ERR_INVALID_ARG;
+  }
   if (p->bc != LES_BC_FROZEN && p->bc != LES_BC_JET) {
     why = "bc must be LES_BC_FROZEN or LES_BC_JET";
     return LES_ERR_INVALID_ARG;
@@ -380,10 +384,10 @@ int les_set_grid(les_ctx* c, const double* xyz, const double shift[9], void* wor
   c->ws = (char*)workspace;
   if (has_m64(c)) {
     double* M64 = at<double>(c, c->off_m64);
-    lesjet::launch_metrics(c->g, xyz, shift, M64, L);
+    lesjet::launch_metrics(c->g, xyz, shift, c->p.metric_form, M64, L);
     if (is_mixed(c)) lesjet::launch_to_float(10 * c->g.N, M64, at<float>(c, c->off_m32), L);
   } else {
-    lesjet::launch_metrics(c->g, xyz, shift, at<float>(c, c->off_m32), L);
+    lesjet::launch_metrics(c->g, xyz, shift, c->p.metric_form, at<float>(c, c->off_m32), L);
   }
   lesjet::launch_inflow_geometry(c->g, xyz, at<double>(c, c->off_rth), L);
   lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), 0.0, L);

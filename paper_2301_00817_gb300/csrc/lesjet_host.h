@@ -11,9 +11,9 @@
 namespace lesjet {
 
 // setup.cu
-void launch_metrics(const Grid& g, const double* xyz, const double shift[9], double* M,
+void launch_metrics(const Grid& g, const double* xyz, const double shift[9], int form, double* M,
                     const Launch& L);
-void launch_metrics(const Grid& g, const double* xyz, const double shift[9], float* M,
+void launch_metrics(const Grid& g, const double* xyz, const double shift[9], int form, float* M,
                     const Launch& L);
 void launch_to_float(long long count, const double* a, float* b, const Launch& L);
 void launch_inflow_geometry(const Grid& g, const double* xyz, double* rth, const Launch& L);

@@ -66,6 +66,83 @@ __global__ void k_metrics(Grid g, const double* __restrict__ xyz, Shift sh,
   }
 }
 
+// Metric terms in the conservative (Thomas-Lombard) form: with (r, s, t) and
+// (c, p, q) cyclic orders of the directions and of the coordinates,
+//   J^-1 r_c = d/dt (p_s q) - d/ds (p_t q),
+// the cofactor of the continuous mapping written so that central
+// differences of the nine J^-1 r_c telescope (discrete geometric
+// conservation: a uniform flow has zero residual on any grid).  Each thread
+// walks the outer-difference stencil of its node along every direction e;
+// at each stencil node it forms the products (p_f q) for both inner
+// directions f != e and adds them, with the difference weight and the sign
+// of the pair (e, f), to the one row r that is neither e nor f.  J^-1 is the
+// same determinant as in k_metrics; the stored metric is (J^-1 r_c)/J^-1.
+template <typename TM>
+__global__ void k_metrics_conservative(Grid g, const double* __restrict__ xyz, Shift sh,
+                                       TM* __restrict__ M) {
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    double cof[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};  // [row][coordinate]
+#pragma unroll 1
+    for (int e = 0; e < 3; ++e) {
+      const int ne = g.n[e];
+      int cnt, off[3];
+      double wt[3];
+      if (g.per[e] || (c[e] > 0 && c[e] < ne - 1)) {
+        cnt = 2; off[0] = 1; off[1] = -1; off[2] = 0;
+        wt[0] = 0.5; wt[1] = -0.5; wt[2] = 0.0;
+      } else if (c[e] == 0) {
+        cnt = 3; off[0] = 0; off[1] = 1; off[2] = 2;
+        wt[0] = -1.5; wt[1] = 2.0; wt[2] = -0.5;
+      } else {
+        cnt = 3; off[0] = 0; off[1] = -1; off[2] = -2;
+        wt[0] = 1.5; wt[1] = -2.0; wt[2] = 0.5;
+      }
+#pragma unroll 1
+      for (int a = 0; a < cnt; ++a) {
+        int cm[3] = {c[0], c[1], c[2]};
+        int v = c[e] + off[a], wrap = 0;
+        if (v >= ne) { v -= ne; wrap = 1; }
+        if (v < 0) { v += ne; wrap = -1; }
+        cm[e] = v;
+        const long long m = n + (long long)(v - c[e]) * g.stride[e];
+        double xm[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) xm[k] = xyz[k * N + m] + wrap * sh.v[3 * e + k];
+#pragma unroll
+        for (int df = 1; df < 3; ++df) {
+          const int f = (e + df) % 3;
+          const int r = 3 - e - f;
+          const double sgn = (f == (r + 1) % 3) ? wt[a] : -wt[a];
+#pragma unroll
+          for (int comp = 0; comp < 3; ++comp) {
+            const int pc = (comp + 1) % 3, qc = (comp + 2) % 3;
+            const double dp = coord_deriv(g, xyz + pc * N, m, cm, f, sh.v[3 * f + pc]);
+            cof[r][comp] += sgn * (dp * xm[qc]);
+          }
+        }
+      }
+    }
+    double d[3][3];  // d[comp][dir] at the node itself, for J^-1
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir)
+        d[comp][dir] = coord_deriv(g, xyz + comp * N, n, c, dir, sh.v[3 * dir + comp]);
+    const double Jinv = d[0][0] * d[1][1] * d[2][2] + d[0][1] * d[1][2] * d[2][0] +
+                        d[0][2] * d[1][0] * d[2][1] - d[0][0] * d[1][2] * d[2][1] -
+                        d[0][1] * d[1][0] * d[2][2] - d[0][2] * d[1][1] * d[2][0];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) M[(3 * r + comp) * N + n] = (TM)(cof[r][comp] / Jinv);
+    M[9 * N + n] = (TM)Jinv;
+  }
+}
+
 __global__ void k_to_float(long long count, const double* __restrict__ a, float* __restrict__ b) {
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < count;
        n += (long long)gridDim.x * blockDim.x)
@@ -171,20 +248,26 @@ static int grid_blocks(long long count, int threads) {
   return (int)b;
 }
 
-void launch_metrics(const Grid& g, const double* xyz, const double shift[9], double* M,
-                    const Launch& L) {
+template <typename TM>
+static void metrics_any(const Grid& g, const double* xyz, const double shift[9], int form, TM* M,
+                        const Launch& L) {
   Shift sh;
   for (int i = 0; i < 9; ++i) sh.v[i] = shift ? shift[i] : 0.0;
-  k_metrics<double><<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, sh, M);
+  if (form == LES_METRIC_CONSERVATIVE)
+    k_metrics_conservative<TM><<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, sh, M);
+  else
+    k_metrics<TM><<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, sh, M);
   ++*L.counter;
 }
 
-void launch_metrics(const Grid& g, const double* xyz, const double shift[9], float* M,
+void launch_metrics(const Grid& g, const double* xyz, const double shift[9], int form, double* M,
                     const Launch& L) {
-  Shift sh;
-  for (int i = 0; i < 9; ++i) sh.v[i] = shift ? shift[i] : 0.0;
-  k_metrics<float><<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g, xyz, sh, M);
-  ++*L.counter;
+  metrics_any(g, xyz, shift, form, M, L);
+}
+
+void launch_metrics(const Grid& g, const double* xyz, const double shift[9], int form, float* M,
+                    const Launch& L) {
+  metrics_any(g, xyz, shift, form, M, L);
 }
 
 void launch_to_float(long long count, const double* a, float* b, const Launch& L) {

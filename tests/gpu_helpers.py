@@ -35,6 +35,7 @@ def device_ctx(lj, torch, shape, xyz, shift=None, **kw):
 def oracle_params(orc, **kw):
     kw = dict(kw)
     kw.pop("precision", None)
+    kw.pop("metric_form", None)
     return orc.params(**kw)
 
 

@@ -100,3 +100,30 @@ def test_grid_jet_validates_before_touching_the_device(lib):
         bad = lj.LesJetGrid(20.0, 0.0, 0.02, 10.0, 0.5, 0.9, 8.0)
         setattr(bad, field, value)
         assert lib.les_grid_jet(8, 8, 8, C.byref(bad), ptr, None) == lj.LES_ERR_INVALID_ARG, field
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors have the C structs' sizes and field offsets (the
+    header compiled as plain C by gcc)."""
+    import paper_2301_00817_gb300 as lj
+    fields = {"les_params": (lj.LesParams, ["Re", "St", "amp", "sgs_model", "periodic", "bc",
+                                            "precision", "metric_form"]),
+              "les_diag": (lj.LesDiag, ["dt", "totals", "status", "steps"]),
+              "les_jet_grid": (lj.LesJetGrid, ["ratio", "r_c", "beta"])}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    for st, (_, names) in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in names:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        st, what, value = line.split()
+        cls = fields[st][0]
+        got = C.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert got == int(value), (st, what, got, value)

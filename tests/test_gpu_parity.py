@@ -104,6 +104,51 @@ def test_grid_jet_drives_one_step(orc, lj, torch):
     assert rel_linf(Q.cpu().numpy(), Q1) <= 1e-12
 
 
+@pytest.mark.parametrize("case", ["jet_c1", "wavy_box", "wavy_open"])
+def test_metrics_conservative_form(orc, lj, torch, case):
+    if case == "wavy_open":
+        shape = (11, 10, 9)
+        xyz, _ = lj.synth.box_grid(shape, (1.0, 1.3, 0.7), wave=0.3)
+        shift, kw = None, dict(periodic=(0, 0, 0), bc=0)
+    else:
+        shape, xyz, shift, kw = _grid(lj, case)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, metric_form=lj.METRIC_CONSERVATIVE, **kw)
+    Mg = ctx.les_metrics().cpu().numpy()
+    Mo = orc.metrics(xyz, kw["periodic"], shift, form=1)
+    assert np.abs(Mg[9] - Mo[9]).max() <= 1e-14 * np.abs(Mo[9]).max()
+    # each conservative metric is a difference of products (dp/ds) q over
+    # J^-1: rounding scales with max|q| max|dp/ds| / J^-1 at the node, not with
+    # the metric (which cancels to ~0 in rows such as xi_y on the jet grid)
+    D = max(np.abs(np.gradient(xyz[c], axis=d)).max() for c in range(3) for d in range(3))
+    S = np.abs(xyz).max() * D / np.abs(Mo[9])
+    for r in range(9):
+        assert (np.abs(Mg[r] - Mo[r]) <= 1e-14 * S).all(), r
+
+
+@pytest.mark.parametrize("sgs", [0, 1, 2])
+def test_conservative_metrics_free_stream_and_steps(orc, lj, torch, sgs):
+    """A non-separable open grid: with conservative metrics the GPU residual
+    of a uniform flow is round-off, and 10 steps of a smooth state match the
+    oracle."""
+    shape = (19, 17, 15)
+    xyz, _ = lj.synth.box_grid(shape, (1.0, 1.3, 0.7), wave=0.3)
+    kw = dict(periodic=(0, 0, 0), bc=0, sgs_model=sgs, Re=300.0)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, None, metric_form=lj.METRIC_CONSERVATIVE, **kw)
+    P = oracle_params(orc, **kw)
+    M = orc.metrics(xyz, (0, 0, 0), None, form=1)
+    Qu = torch.from_numpy(orc.prim_to_cons(
+        P, lj.synth.uniform_prim(shape, u=0.9, v=-0.3, w=0.2))).cuda()
+    R = torch.empty_like(Qu)
+    ctx.les_rhs(Qu, R)
+    assert float(R.abs().max()) / (np.abs(M[9]).max() * 10.0) < 1e-14
+    prim = lj.synth.smooth_periodic_prim(xyz, (1.0, 1.3, 0.7), amp=0.2, seed=3)
+    Q0 = orc.prim_to_cons(P, prim)
+    Qd = torch.from_numpy(Q0).cuda()
+    ctx.les_run_n_steps(10, Qd)
+    Qo, _ = orc.run(P, Q0, M, xyz, 10)
+    assert rel_linf(Qd.cpu().numpy(), Qo) <= 1e-11
+
+
 def test_init_jet(orc, lj, torch):
     shape = C1
     xyz = lj.synth.jet_grid(*shape)
