@@ -103,7 +103,8 @@ def _lib_handle():
             lib.orc_num_threads.restype = C.c_int
             RHSFN = C.CFUNCTYPE(None, C.c_void_p, _dp, _dp)
             lib.orc_rk5.argtypes = [i, C.c_size_t, _dp, C.POINTER(C.c_ubyte), _dp,
-                                    C.c_double, RHSFN, C.c_void_p]
+                                    C.c_double, _dp, RHSFN, C.c_void_p]
+            lib.orc_dt_local.argtypes = [P, i, i, i, _dp, _dp, _dp]
             lib._RHSFN = RHSFN
             _lib = lib
     return _lib
@@ -199,6 +200,15 @@ def dt(P: OrcParams, Q, M) -> float:
     return float(_lib_handle().orc_dt(C.byref(P), ni, nj, nk, _ptr(Q), _ptr(M)))
 
 
+def dt_local(P: OrcParams, Q, M) -> np.ndarray:
+    """Per-node local time steps [ni, nj, nk]."""
+    Q, M = _f64(Q), _f64(M)
+    _, ni, nj, nk = Q.shape
+    out = np.empty((ni, nj, nk))
+    _lib_handle().orc_dt_local(C.byref(P), ni, nj, nk, _ptr(Q), _ptr(M), _ptr(out))
+    return out
+
+
 def bc_jet(P: OrcParams, Q, M, xyz, t: float) -> np.ndarray:
     Q = _f64(Q).copy()
     M, xyz = _f64(M), _f64(xyz)
@@ -207,7 +217,7 @@ def bc_jet(P: OrcParams, Q, M, xyz, t: float) -> np.ndarray:
     return Q
 
 
-def rk5(Q, rhs_fn, dt: float, update=None, Jinv=None) -> np.ndarray:
+def rk5(Q, rhs_fn, dt: float, update=None, Jinv=None, dtn=None) -> np.ndarray:
     """Generic 5-stage driver; rhs_fn(Q_array) -> R_array of Q's shape."""
     Q = _f64(Q).copy()
     shape = Q.shape
@@ -230,7 +240,12 @@ def rk5(Q, rhs_fn, dt: float, update=None, Jinv=None) -> np.ndarray:
     if Jinv is not None:
         Jinv = _f64(Jinv)
         jp = _ptr(Jinv)
-    lib.orc_rk5(ncomp, N, _ptr(Q), upd, jp, dt, fn, None)
+    dp = None
+    if dtn is not None:
+        dtn = _f64(dtn)
+        assert dtn.size == N
+        dp = _ptr(dtn)
+    lib.orc_rk5(ncomp, N, _ptr(Q), upd, jp, dt, dp, fn, None)
     return Q
 
 

@@ -775,6 +775,24 @@ double orc_dt(const orc_params *P, int ni, int nj, int nk, const double *Q,
   return P->cfl * best;
 }
 
+/* Local time stepping, the literal form of Eq. localdt: each node n advances
+ * with its own step, the CFL limit of that node alone,
+ * dtn[n] = cfl / (lam_xi + lam_eta + lam_zeta)(n). */
+void orc_dt_local(const orc_params *P, int ni, int nj, int nk, const double *Q,
+                  const double *M, double *dtn) {
+  state_t S;
+  memset(&S, 0, sizeof(S));
+  S.P = P;
+  S.g = make_grid(ni, nj, nk, P->periodic);
+  S.Q = Q; S.M = M;
+  state_alloc(&S);
+  node_primitives(&S);
+  node_radii(&S);
+  for (size_t n = 0; n < S.g.N; ++n)
+    dtn[n] = P->cfl / (S.lam[0][n] + S.lam[1][n] + S.lam[2][n]);
+  state_free(&S);
+}
+
 /* ---------------------------------------------------------- jet boundary */
 
 static void cons_from(double gam, double rho, double u, double v, double w,
@@ -912,7 +930,8 @@ void orc_bc_jet(const orc_params *P, int ni, int nj, int nk, double *Q,
  * RHS^(l-1) (the paper's Q is J^-1-scaled; for the stored unscaled Q the
  * update carries J = 1/J^-1), Q^(n+1) = Q^(5). */
 void orc_rk5(int ncomp, size_t N, double *Q, const unsigned char *update,
-             const double *Jinv, double dt, orc_rhs_fn rhs, void *user) {
+             const double *Jinv, double dt, const double *dtn, orc_rhs_fn rhs,
+             void *user) {
   static const double alpha[5] = {1.0 / 4.0, 1.0 / 6.0, 3.0 / 8.0, 1.0 / 2.0,
                                   1.0};
   size_t tot = (size_t)ncomp * N;
@@ -928,7 +947,8 @@ void orc_rk5(int ncomp, size_t N, double *Q, const unsigned char *update,
           Q[idx] = Q0[idx];
         } else {
           double Jn = Jinv ? 1.0 / Jinv[n] : 1.0;
-          Q[idx] = Q0[idx] - alpha[l] * dt * (Jn * R[idx]);
+          double h = dtn ? dtn[n] : dt;
+          Q[idx] = Q0[idx] - alpha[l] * h * (Jn * R[idx]);
         }
       }
   }
@@ -967,9 +987,17 @@ double orc_rk_step(const orc_params *P, int ni, int nj, int nk, double *Q,
   }
   orc_mu_eff(P, ni, nj, nk, Q, M, MK);
   double dt = orc_dt(P, ni, nj, nk, Q, M);
+  /* Reading: with local steps the clock (and so the inflow forcing phase)
+   * advances by the smallest local step, the global CFL step */
+  double *dtn = NULL;
+  if (P->dt_mode == 2) {
+    dtn = (double *)malloc(N * sizeof(double));
+    orc_dt_local(P, ni, nj, nk, Q, M, dtn);
+  }
   flow_user_t U = {P, ni, nj, nk, M, MK};
-  orc_rk5(5, N, Q, upd, M + 9 * N, dt, flow_rhs, &U);
+  orc_rk5(5, N, Q, upd, M + 9 * N, dt, dtn, flow_rhs, &U);
   if (P->bc == 1) orc_bc_jet(P, ni, nj, nk, Q, M, xyz, t + dt);
+  free(dtn);
   free(MK);
   free(upd);
   return dt;

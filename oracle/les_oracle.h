@@ -40,7 +40,7 @@ typedef struct {
   int sgs_model;     /* 0 none, 1 Smagorinsky, 2 Vreman */
   int periodic[3];   /* per direction xi, eta, zeta */
   int bc;            /* 0 non-periodic boundary nodes frozen, 1 jet BCs */
-  int dt_mode;       /* 0 CFL-limited global step, 1 fixed */
+  int dt_mode;       /* 0 CFL-limited global step, 1 fixed, 2 local steps */
   int freeze_visc;   /* 1: mu_eff/kappa_eff from Q^n held over 5 stages */
   int pad_;
 } orc_params;
@@ -83,6 +83,9 @@ void orc_interface_flux(const orc_params *P, int ni, int nj, int nk,
 /* Global CFL time step: cfl * min 1/(lam_xi + lam_eta + lam_zeta). */
 double orc_dt(const orc_params *P, int ni, int nj, int nk, const double *Q,
               const double *M);
+/* Local time steps dtn[n] = cfl / (lam_xi + lam_eta + lam_zeta) at node n. */
+void orc_dt_local(const orc_params *P, int ni, int nj, int nk, const double *Q,
+                  const double *M, double *dtn);
 
 /* Jet boundary conditions at time t (Sec. "Boundary Conditions"). */
 void orc_bc_jet(const orc_params *P, int ni, int nj, int nk, double *Q,
@@ -90,10 +93,12 @@ void orc_bc_jet(const orc_params *P, int ni, int nj, int nk, double *Q,
 
 /* Generic 5-stage driver: Q^(l) = Q^(0) - alpha_l dt J RHS(Q^(l-1)).
  * rhs(user, Qs, R) fills R [ncomp][N]; nodes with update[n]==0 keep Q^(0);
- * Jinv may be NULL (J = 1). */
+ * Jinv may be NULL (J = 1); dtn, when not NULL, gives node n its own step
+ * dtn[n] in place of dt. */
 typedef void (*orc_rhs_fn)(void *user, const double *Q, double *R);
 void orc_rk5(int ncomp, size_t N, double *Q, const unsigned char *update,
-             const double *Jinv, double dt, orc_rhs_fn rhs, void *user);
+             const double *Jinv, double dt, const double *dtn, orc_rhs_fn rhs,
+             void *user);
 
 /* One full time step (mu_eff, dt, 5 stages, BCs).  Returns dt used. */
 double orc_rk_step(const orc_params *P, int ni, int nj, int nk, double *Q,

@@ -58,6 +58,11 @@ MUTATIONS = {
     "conservative_face_formula": ("return 0.5 * (-3.0 * metric_product(g, xyz, shift, a, p, s, q) +",
                                   "return 0.5 * (-2.0 * metric_product(g, xyz, shift, a, p, s, q) +",
                                   ["test_conservative_metrics_exact_on_affine_grid"]),
+    "local_step_index": ("double h = dtn ? dtn[n] : dt;", "double h = dtn ? dtn[0] : dt;",
+                         ["test_rk5_local_steps_per_node"]),
+    "local_step_radii": ("dtn[n] = P->cfl / (S.lam[0][n] + S.lam[1][n] + S.lam[2][n]);",
+                         "dtn[n] = P->cfl / (S.lam[0][n] + S.lam[1][n] + S.lam[1][n]);",
+                         ["test_local_time_steps_closed_form"]),
 }
 
 

@@ -624,6 +624,23 @@ def test_rk5_amplification_polynomial(orc):
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
 
 
+def test_rk5_local_steps_per_node(orc):
+    """Local steps (Eq. localdt with a node-dependent dt): decoupled
+    y_n' = -lam_n y_n advanced with dt_n gives G(-lam_n dt_n) at every node,
+    so each node sees its own step (a transposed or shared index fails)."""
+    lam = np.array([0.3, 1.7, 0.5, 2.5, 0.9, 1.1])
+    dtn = np.array([1.0, 0.4, 2.0, 0.7, 1.3, 0.25])
+    y0 = np.ones((2, lam.size))
+
+    def rhs_fn(q):
+        return lam[None, :] * q
+
+    y1 = orc.rk5(y0, rhs_fn, 123.0, dtn=dtn)
+    z = -lam * dtn
+    G = 1 + z + z ** 2 / 2 + 3 * z ** 3 / 16 + z ** 4 / 32 + z ** 5 / 128
+    assert np.allclose(y1, G[None, :], rtol=1e-15, atol=1e-15)
+
+
 def test_rk5_linear_stability_bound():
     """The paper states linear stability up to CFL 2 sqrt(2): |G(iy)| <= 1 on
     the imaginary axis for |y| <= 2 sqrt(2) (and up to ~4)."""
@@ -662,6 +679,45 @@ def test_time_step_closed_form(orc):
     Q = orc.prim_to_cons(P, synth.uniform_prim(n, u=vel[0], v=vel[1], w=vel[2]))
     expect = 0.7 / sum((abs(vel[d]) + 1.0) / hs[d] for d in range(3))
     assert abs(orc.dt(P, Q, M) - expect) < 1e-15 * expect * 10
+
+
+def test_local_time_steps_closed_form(orc):
+    """Local steps on a Cartesian grid with a non-uniform state:
+    dt_n = CFL / sum_d (|u_d| + a)/h_d node by node; their minimum is the
+    global CFL step, and a step in local mode advances the clock by it."""
+    n = (6, 7, 5)
+    hs = (0.1, 0.2, 0.05)
+    xyz, shift = synth.box_grid(n, tuple(m * h for m, h in zip(n, hs)))
+    P = orc.params(periodic=(1, 1, 1), bc=0, cfl=0.7, dt_mode=2)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    prim = synth.smooth_periodic_prim(xyz, tuple(m * h for m, h in zip(n, hs)), amp=0.3, seed=5)
+    Q = orc.prim_to_cons(P, prim)
+    rho, u, v, w, p = prim
+    a = np.sqrt(1.4 * p / rho)
+    expect = 0.7 / ((np.abs(u) + a) / hs[0] + (np.abs(v) + a) / hs[1] + (np.abs(w) + a) / hs[2])
+    got = orc.dt_local(P, Q, M)
+    assert np.allclose(got, expect, rtol=1e-14, atol=0)
+    assert orc.dt(P, Q, M) == got.min()
+    _, dt = orc.rk_step(P, Q, M, xyz, 0.0)
+    assert dt == got.min()
+
+
+def test_local_steps_keep_the_free_stream_and_differ_from_global(orc):
+    """A free stream is a fixed point of the local-step march as of the
+    global one; on a non-uniform state the two marches differ (node-dependent
+    steps), while a uniform-lambda state would make them agree."""
+    xyz = synth.jet_grid(12, 10, 8)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Pl = orc.params(dt_mode=2, bc=0)
+    Pg = orc.params(dt_mode=0, bc=0)
+    Qu = orc.prim_to_cons(Pl, synth.uniform_prim(xyz.shape[1:], u=0.6, v=0.1, w=-0.2))
+    Q1, _ = orc.rk_step(Pl, Qu, M, xyz, 0.0)
+    assert np.abs(Q1 - Qu).max() < 1e-13
+    Q0 = orc.init_jet(Pl, xyz, seed=2, noise=1e-2)
+    Ql, dtl = orc.rk_step(Pl, Q0, M, xyz, 0.0)
+    Qg, dtg = orc.rk_step(Pg, Q0, M, xyz, 0.0)
+    assert dtl == dtg
+    assert np.abs(Ql - Qg).max() > 1e-6
 
 
 # --------------------------------------------------------- boundaries
