@@ -45,18 +45,21 @@ BYTES_PER_POINT = {
 }
 
 
-# DRAM bytes per grid point of one k_stage_fused launch, mean over the five
-# stages of a step, from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the 96 x 160 x 128 jet (traffic grows in
-# proportion to the points).  It describes the kernel source it was taken on
-# only: bench.py reports it when the hash of that source still matches.
-NCU_TRAFFIC = {
-    "stage_fused": {"bytes_per_point": 109.4, "fp32_flop_per_point": 1162,
-                    "sources": ("paper_2301_00817_gb300/csrc/fused.cu",
-                                "paper_2301_00817_gb300/csrc/lesjet_dev.cuh"),
-                    "sha256": "522d6c7839c49619d4b809b27368b8f170239bc6efc641abcd50778a88523ebd",
-                    "capture": "profiles/stage_fused_jet96x160x128.md"},
+# Counters of k_stage_fused from ncu captures on the 96 x 160 x 128 jet
+# (per grid point; traffic and instruction counts grow in proportion to the
+# points): DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum), mean
+# over the five stages of a step, and FP32 add + mul + 2 x FMA.  Each figure
+# describes the kernel source it was taken on only: bench.py reports it
+# while the hash of that source still matches.
+NCU_SOURCES = {"stage_fused": ("paper_2301_00817_gb300/csrc/fused.cu",
+                               "paper_2301_00817_gb300/csrc/lesjet_dev.cuh")}
+NCU_COUNTS = {
+    ("stage_fused", "bytes_per_point"):
+        (109.6, "9c21be518eb536a3a5de6a15f7fc5a07c3c88d2aad6c672505f46f5aa0442e8f"),
+    ("stage_fused", "fp32_flop_per_point"):
+        (1162, "522d6c7839c49619d4b809b27368b8f170239bc6efc641abcd50778a88523ebd"),
 }
+NCU_CAPTURE = {"stage_fused": "profiles/stage_fused_jet96x160x128.md"}
 # FP64 flop per grid point of one residual's flux launches (three
 # directions), counted by ncu (dadd + 2 dfma + dmul) on the xi-direction
 # kernel of the same case: 350 per interface.
@@ -68,17 +71,17 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 def traffic_per_point(kernel, field="bytes_per_point"):
     import hashlib
-    rec = NCU_TRAFFIC.get(kernel)
-    if rec is None or field not in rec:
+    rec = NCU_COUNTS.get((kernel, field))
+    if rec is None:
         return None
     h = hashlib.sha256()
     try:
-        for f in rec["sources"]:
+        for f in NCU_SOURCES[kernel]:
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(fh.read())
     except OSError:
         return None
-    return rec[field] if h.hexdigest() == rec["sha256"] else None
+    return rec[0] if h.hexdigest() == rec[1] else None
 
 
 def load_peaks():
@@ -550,7 +553,7 @@ def run_ours(args, world, rank, local):
         return {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": tpp * N if tpp is not None else None,
-                "traffic_source": NCU_TRAFFIC[top]["capture"] if tpp is not None else None,
+                "traffic_source": NCU_CAPTURE.get(top) if tpp is not None else None,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
                 "bytes_per_point": bpp, "avg_launch_us": per_launch_s * 1e6,
                 "share_of_step": share}

@@ -53,7 +53,7 @@ enum { LES_SGS_NONE = 0, LES_SGS_SMAGORINSKY = 1, LES_SGS_VREMAN = 2 };
  * read; les_metrics() returns NULL.  It is the form for the largest grids. */
 enum { LES_PREC_FP64 = 0, LES_PREC_MIXED = 1, LES_PREC_MIXED_COMPACT = 2 };
 enum { LES_BC_FROZEN = 0, LES_BC_JET = 1 };
-enum { LES_DT_CFL = 0, LES_DT_FIXED = 1 };
+enum { LES_DT_CFL = 0, LES_DT_FIXED = 1, LES_DT_LOCAL = 2 };
 enum { LES_METRIC_CROSS = 0, LES_METRIC_CONSERVATIVE = 1 };
 
 /* Flow and scheme parameters (Sec. "Large Eddy Simulation Filtering" to
@@ -81,7 +81,14 @@ typedef struct les_params {
   int periodic[3];    /* per direction xi, eta, zeta: 1 = periodic */
   int bc;             /* LES_BC_FROZEN (non-periodic faces never change)
                          or LES_BC_JET (needs periodic = {0,0,1}) */
-  int dt_mode;        /* LES_DT_CFL or LES_DT_FIXED */
+  int dt_mode;        /* LES_DT_CFL, LES_DT_FIXED or LES_DT_LOCAL (Eq.
+                         localdt taken literally: node n advances with its
+                         own CFL step cfl/(lambda_xi + lambda_eta +
+                         lambda_zeta)(n) of Q^n, for steady problems; the
+                         clock and les_diag.dt use the smallest of them).
+                         LES_DT_LOCAL must be chosen at les_create (its
+                         per-node steps live in the workspace); the adjoint
+                         calls reject it. */
   int freeze_visc;    /* 1: mu_eff, kappa_eff from Q^n held for 5 stages */
   int precision;      /* LES_PREC_FP64, LES_PREC_MIXED or
                          LES_PREC_MIXED_COMPACT */

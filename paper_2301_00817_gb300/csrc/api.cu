@@ -38,8 +38,9 @@ struct les_ctx {
   Grid g;
   // workspace layout (byte offsets, 256-byte aligned)
   size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_hi, off_lo, off_node, off_flux, off_rth,
-      off_sc, off_part;
+      off_sc, off_part, off_dtl;
   size_t total;
+  bool local_dt;  // the workspace holds per-node steps (dt_mode LOCAL at creation)
   char* ws;
   bool grid_set;
   std::string err;
@@ -121,8 +122,10 @@ int validate_params(const les_params* p, std::string& why) {
     why = "precision must be LES_PREC_FP64, LES_PREC_MIXED or LES_PREC_MIXED_COMPACT";
     return LES_ERR_INVALID_ARG;
   }
-  if (p->dt_mode == LES_DT_CFL ? !(p->cfl > 0.0) : (p->dt_mode != LES_DT_FIXED || !(p->dt_fixed > 0.0))) {
-    why = "dt_mode CFL needs cfl > 0; dt_mode FIXED needs dt_fixed > 0";
+  if (p->dt_mode == LES_DT_CFL || p->dt_mode == LES_DT_LOCAL
+          ? !(p->cfl > 0.0)
+          : (p->dt_mode != LES_DT_FIXED || !(p->dt_fixed > 0.0))) {
+    why = "dt_mode CFL or LOCAL needs cfl > 0; dt_mode FIXED needs dt_fixed > 0";
     return LES_ERR_INVALID_ARG;
   }
   if (p->metric_form != LES_METRIC_CROSS && p->metric_form != LES_METRIC_CONSERVATIVE) {
@@ -162,6 +165,8 @@ void layout(les_ctx* c) {
   c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
   c->off_sc = o; o = align256(o + sizeof(DevScalars));
   c->off_part = o; o = align256(o + 5 * (size_t)lesjet::kMaxPartials * sizeof(double));
+  c->off_dtl = o; o = align256(o + (c->p.dt_mode == LES_DT_LOCAL ? N * rs : 0));
+  c->local_dt = c->p.dt_mode == LES_DT_LOCAL;
   c->total = o;
 }
 
@@ -191,6 +196,7 @@ lesjet::StageIO64 io64(les_ctx* c, const double* Qin) {
   io.flux = at<double>(c, c->off_flux);
   io.partials = at<double>(c, c->off_part);
   io.sc = at<DevScalars>(c, c->off_sc);
+  io.dtl = c->p.dt_mode == LES_DT_LOCAL ? at<double>(c, c->off_dtl) : nullptr;
   return io;
 }
 
@@ -226,8 +232,11 @@ void join_state(les_ctx* c, double* Q, const lesjet::Launch& L) {
 // minima of the CFL step; sc == nullptr leaves the status word alone.
 void prestep32(les_ctx* c, const float* Qs, DevScalars* sc, const lesjet::Launch& L) {
   ProfScope ps(c, PK_PRESTEP, L.s);
+  // the per-node steps are those of Q^n: written only by the step's first
+  // prestep (the one that also takes the CFL minima, sc != nullptr)
+  float* dtl = (sc && c->p.dt_mode == LES_DT_LOCAL) ? at<float>(c, c->off_dtl) : nullptr;
   lesjet::launch_prestep(c->g, c->p, Qs, at<float>(c, c->off_m32), at<float>(c, c->off_mk),
-                         at<double>(c, c->off_part), sc, L);
+                         at<double>(c, c->off_part), sc, dtl, L);
 }
 
 lesjet::FusedIO fused_io(les_ctx* c, const void* Qin, void* out) {
@@ -238,6 +247,7 @@ lesjet::FusedIO fused_io(les_ctx* c, const void* Qin, void* out) {
   io.M = at<float>(c, c->off_m32);
   io.mk = at<float>(c, c->off_mk);
   io.sc = at<DevScalars>(c, c->off_sc);
+  io.dtl = c->p.dt_mode == LES_DT_LOCAL ? at<float>(c, c->off_dtl) : nullptr;
   io.out = out;
   return io;
 }
@@ -365,6 +375,8 @@ int les_set_params(les_ctx* c, const les_params* p) {
   int rc = validate_params(p, why);
   if (rc != LES_OK) return fail(c, rc, why.c_str());
   if (p->precision != c->p.precision) return fail(c, LES_ERR_INVALID_ARG, "precision is fixed at creation");
+  if (p->dt_mode == LES_DT_LOCAL && !c->local_dt)
+    return fail(c, LES_ERR_INVALID_ARG, "local time stepping must be chosen at creation");
   for (int d = 0; d < 3; ++d)
     if ((p->periodic[d] ? 1 : 0) != c->g.per[d])
       return fail(c, LES_ERR_INVALID_ARG, "periodicity is fixed at creation");

@@ -157,7 +157,8 @@ template <typename R, typename TQ, typename TM>
 __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* __restrict__ Q,
                                                  const TM* __restrict__ M, R* __restrict__ mk,
                                                  double* __restrict__ partials,
-                                                 DevScalars* __restrict__ sc) {
+                                                 DevScalars* __restrict__ sc,
+                                                 R* __restrict__ dtl, R cfl) {
   const long long N = g.N;
   R local_min = R(1e30);
   int bad = 0;
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
     const R inv = R(1) / lsum;
     if (!(rho > R(0)) || !(p > R(0)) || !(inv > R(0)) || !(inv < R(1e30))) bad = 1;
     local_min = inv < local_min ? inv : local_min;
+    if (dtl) dtl[n] = cfl * inv;  // local step of Eq. localdt
 
     const R mu_l = K.mu_scale * T * dev_sqrt(T) * (R(1) + K.S_suth) / (T + K.S_suth);
     R mu_s = R(0);
@@ -353,6 +355,7 @@ struct FusedPtrs {
   const float* mk[2];   // mu_eff, kappa_eff
   float* out[5];        // stage output
   double* outd[5];      // residual output (RHS mode)
+  const float* dtl;     // local steps (dt_mode LOCAL) or nullptr: global dt
 };
 
 struct FusedGeom {
@@ -779,6 +782,7 @@ __global__ void __launch_bounds__(FNT, 1)
       const int n = (ig * nj + jown) * nk + kown;
       if (iint && jint && kint) {
         const float Jn = __frcp_rn(sM[(s_c * 10 + 9) * PL1 + o1]);
+        const float an = (MODE != FMODE_RHS && P.dtl) ? (float)alpha * P.dtl[n] : adt;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           float r = 0.f;
@@ -788,11 +792,11 @@ __global__ void __launch_bounds__(FNT, 1)
           if (MODE == FMODE_RHS) {
             P.outd[c][n] = (double)r;
           } else if (MODE == FMODE_STAGE) {
-            P.out[c][n] = hc[c] - adt * (Jn * r);
+            P.out[c][n] = hc[c] - an * (Jn * r);
           } else {
             // compensated update of the pair (hi, lo) by d (TwoSum, then
             // renormalisation), all in FP32
-            const float d = -adt * (Jn * r);
+            const float d = -an * (Jn * r);
             const float hi = hc[c], lo = P.lo[c][n];
             const float s = hi + d;
             const float bb = s - hi;
@@ -875,9 +879,9 @@ static Consts<R> fused_consts(const les_params& p) {
 }
 
 void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
-                    float* mk, double* partials, DevScalars* sc, const Launch& L) {
+                    float* mk, double* partials, DevScalars* sc, float* dtl, const Launch& L) {
   k_prestep<float, float, float><<<kRedBlocks, kRedThreads, 0, L.s>>>(
-      g, fused_consts<float>(p), Q0, M, mk, partials, sc);
+      g, fused_consts<float>(p), Q0, M, mk, partials, sc, dtl, (float)p.cfl);
   ++*L.counter;
 }
 
@@ -971,6 +975,7 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   }
   for (int t = 0; t < 10; ++t) P.m[t] = (const float*)io.M + t * N;
   for (int t = 0; t < 2; ++t) P.mk[t] = (const float*)io.mk + t * N;
+  P.dtl = io.dtl;
   const Consts<float> K = fused_consts<float>(p);
   if (mode == FMODE_RHS)
     launch_stage_t<FMODE_RHS>(G, K, P, io.sc, alpha, L);

@@ -39,6 +39,7 @@ struct StageIO64 {
   double* flux;        // [3][5][N] interface fluxes
   double* partials;    // [kRedBlocks] block minima (dt)
   DevScalars* sc;
+  double* dtl = nullptr;  // [N] local steps (dt_mode LOCAL), else nullptr
 };
 void launch_node64(const Grid& g, const les_params& p, const StageIO64& io, bool with_dt,
                    const Launch& L);
@@ -57,11 +58,12 @@ struct FusedIO {
   const void* M;        // metrics [10][N] (double or float)
   const void* mk;       // mu_eff, kappa_eff [2][N] (compute type)
   const DevScalars* sc; // device scalars (dt)
+  const float* dtl = nullptr;  // [N] local steps (dt_mode LOCAL), else nullptr
   void* out;            // RHS mode: double [5][N]; stage mode: stage type [5][N]
 };
 // mixed form: mu_eff/kappa_eff and CFL block minima of the float state
 void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
-                    float* mk, double* partials, DevScalars* sc, const Launch& L);
+                    float* mk, double* partials, DevScalars* sc, float* dtl, const Launch& L);
 // mode 0: residual into io.out (double); 1: stage update into io.out;
 // 2: last stage, Q^(0) (hi, lo) updated in place with compensated sums
 void launch_stage_fused(int mode, const Grid& g, const les_params& p, const FusedIO& io,

@@ -26,7 +26,7 @@ void launch_node64(const Grid& g, const les_params& p, const StageIO64& io, bool
   auto K = make_consts<double>(p);
   if (with_dt)
     k_node<double, double, double, true><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node,
-                                                             io.partials, io.sc);
+                                                             io.partials, io.sc, io.dtl, p.cfl);
   else
     k_node<double, double, double, false><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node,
                                                               io.partials, io.sc);
@@ -58,11 +58,11 @@ void launch_update64(const Grid& g, const StageIO64& io, const double* Q0, doubl
                      double* out, const Launch& L) {
   const int th = 256, nb = blocks_for(g.N, th);
   if (mode == 0)
-    k_update<double, double, double, 0><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out);
+    k_update<double, double, double, 0><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out, io.dtl);
   else if (mode == 1)
-    k_update<double, double, double, 1><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out);
+    k_update<double, double, double, 1><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out, io.dtl);
   else
-    k_update<double, double, double, 2><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out);
+    k_update<double, double, double, 2><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out, io.dtl);
   ++*L.counter;
 }
 

@@ -41,7 +41,9 @@ template <typename R, typename TQ, typename TM, bool WITH_DT>
 __global__ void __launch_bounds__(256) k_node(Grid g, Consts<R> K, const TQ* __restrict__ Q,
                                               const TM* __restrict__ M, R* __restrict__ node,
                                               double* __restrict__ partials,
-                                              DevScalars* __restrict__ sc) {
+                                              DevScalars* __restrict__ sc,
+                                              double* __restrict__ dtl = nullptr,
+                                              double cfl = 0.0) {
   const long long N = g.N;
   double local_min = 1.0e300;
   int bad = 0;
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(256) k_node(Grid g, Consts<R> K, const TQ* __r
       const double inv = 1.0 / ((double)lam[0] + (double)lam[1] + (double)lam[2]);
       if (!(rho > R(0)) || !(p > R(0)) || !(inv > 0.0) || !(inv < 1.0e300)) bad = 1;
       local_min = inv < local_min ? inv : local_min;
+      if (dtl) dtl[n] = cfl * inv;  // local step of Eq. localdt
     }
   }
   if (WITH_DT) {
@@ -350,7 +353,8 @@ __global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
                                                 const double* __restrict__ Q0,
                                                 const TM* __restrict__ M,
                                                 const DevScalars* __restrict__ sc, double alpha,
-                                                TO* __restrict__ out) {
+                                                TO* __restrict__ out,
+                                                const double* __restrict__ dtl = nullptr) {
   const long long N = g.N;
   const R* F0 = F;
   const R* F1 = F + 5 * N;
@@ -383,7 +387,8 @@ __global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
       if (MODE == 0) {
         out[q * N + n] = (TO)r;
       } else {
-        out[q * N + n] = (TO)(Q0[q * N + n] - adt * ((double)r / Jinv));
+        const double a = dtl ? alpha * dtl[n] : adt;
+        out[q * N + n] = (TO)(Q0[q * N + n] - a * ((double)r / Jinv));
       }
     }
   }

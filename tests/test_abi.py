@@ -127,3 +127,29 @@ def test_binding_structs_match_the_header(tmp_path):
         cls = fields[st][0]
         got = C.sizeof(cls) if what == "size" else getattr(cls, what).offset
         assert got == int(value), (st, what, got, value)
+
+
+def test_local_time_steps_are_chosen_at_creation(lib):
+    """Per-node steps need workspace: a context created with a global step
+    cannot switch to LES_DT_LOCAL, and creating with it grows the workspace
+    by one value per point."""
+    import paper_2301_00817_gb300 as lj
+    h = C.c_void_p()
+    p = lj.make_params()
+    assert lib.les_create(C.byref(p), 16, 12, 8, C.byref(h)) == lj.LES_OK
+    base = lib.les_workspace_bytes(h)
+    q = lj.make_params(dt_mode=lj.DT_LOCAL)
+    assert lib.les_set_params(h, C.byref(q)) == lj.LES_ERR_INVALID_ARG
+    assert b"creation" in lib.les_last_error(h)
+    lib.les_destroy(h)
+    for prec, size in ((lj.PREC_FP64, 8), (lj.PREC_MIXED, 4)):
+        h0, h1 = C.c_void_p(), C.c_void_p()
+        a, b = lj.make_params(precision=prec), lj.make_params(precision=prec, dt_mode=lj.DT_LOCAL)
+        assert lib.les_create(C.byref(a), 16, 12, 8, C.byref(h0)) == lj.LES_OK
+        assert lib.les_create(C.byref(b), 16, 12, 8, C.byref(h1)) == lj.LES_OK
+        grow = lib.les_workspace_bytes(h1) - lib.les_workspace_bytes(h0)
+        assert size * 16 * 12 * 8 <= grow <= size * 16 * 12 * 8 + 256
+        assert lib.les_set_params(h1, C.byref(a)) == lj.LES_OK  # and back is fine
+        lib.les_destroy(h0)
+        lib.les_destroy(h1)
+    assert base > 0

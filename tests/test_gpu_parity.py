@@ -149,6 +149,39 @@ def test_conservative_metrics_free_stream_and_steps(orc, lj, torch, sgs):
     assert rel_linf(Qd.cpu().numpy(), Qo) <= 1e-11
 
 
+@pytest.mark.parametrize("sgs", [0, 1])
+def test_local_time_steps(orc, lj, torch, sgs):
+    """dt_mode LOCAL (per-node CFL steps of Q^n): FP64 against the oracle over
+    1 and 10 steps on the jet grid with its boundary conditions, and the
+    mixed form against FP64 after 20 steps."""
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    kw = dict(periodic=(0, 0, 1), bc=1, sgs_model=sgs, dt_mode=lj.DT_LOCAL)
+    ctx, xyz_d = device_ctx(lj, torch, shape, xyz, **kw)
+    P = oracle_params(orc, **kw)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Q0 = orc.init_jet(P, xyz, seed=4, noise=1e-2)
+    Qd = torch.from_numpy(Q0).cuda()
+    d1 = ctx.les_run_n_steps(1, Qd)
+    Q1, dt1 = orc.rk_step(P, Q0, M, xyz, 0.0)
+    assert abs(d1.dt - dt1) <= 1e-13 * dt1
+    assert rel_linf(Qd.cpu().numpy(), Q1) <= 1e-12
+    d10 = ctx.les_run_n_steps(9, Qd)
+    Q10, t10 = orc.run(P, Q1, M, xyz, 9, t=dt1)
+    assert abs(d10.t - t10) <= 1e-12 * t10
+    assert rel_linf(Qd.cpu().numpy(), Q10) <= 1e-11
+    out = {}
+    for prec in (lj.PREC_FP64, lj.PREC_MIXED):
+        c, _ = device_ctx(lj, torch, shape, xyz, precision=prec, **kw)
+        Q = torch.from_numpy(Q0).cuda()
+        assert c.les_run_n_steps(20, Q).status == 0
+        out[prec] = Q
+    a, b = out[lj.PREC_MIXED], out[lj.PREC_FP64]
+    for comp in (0, 1, 4):
+        err = float(torch.linalg.vector_norm(a[comp] - b[comp]) / torch.linalg.vector_norm(b[comp]))
+        assert err <= 1e-5, (comp, err)
+
+
 def test_init_jet(orc, lj, torch):
     shape = C1
     xyz = lj.synth.jet_grid(*shape)
