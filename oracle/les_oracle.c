@@ -808,13 +808,62 @@ static void prim_of(double gam, const double *Q, size_t N, long n,
   *p = (gam - 1.0) * (Q[4 * N + n] - 0.5 * *rho * (*u * *u + *v * *v + *w * *w));
 }
 
+/* Riemann-invariant far-field state (Sec. "Far Field Boundary", Reading
+ * A13) of a boundary node whose adjacent interior node holds (rho, u, v, w,
+ * p), for the unit outward normal (nx, ny, nz) and the free stream at rest
+ * (rho = 1, p = 1/gamma, a = 1): R+ = q_n,e + 2 a_e/(gamma-1) from the
+ * interior, R- = q_n,inf - 2 a_inf/(gamma-1) from the free stream, and the
+ * four branches chosen by q_n,e/a_e (0 counts as exit).  Returns 1 for the
+ * supersonic exit, where the caller copies the interior node's conserved
+ * values (q is then left unset), else 0 with the state in q. */
+static int riemann_far_field(double gam, double rho, double u, double v,
+                             double w, double p, double nx, double ny,
+                             double nz, double q[5]) {
+  double gm1 = gam - 1.0;
+  const double rho_inf = 1.0, p_inf = 1.0 / gam, a_inf = 1.0;
+  double a_e = sqrt(gam * p / rho);
+  double qne = u * nx + v * ny + w * nz;
+  double qninf = 0.0;
+  double Rp = qne + 2.0 * a_e / gm1;
+  double Rm = qninf - 2.0 * a_inf / gm1;
+  double qnf = 0.5 * (Rp + Rm);
+  double af = 0.25 * gm1 * (Rp - Rm);
+  double Mn = qne / a_e;
+  if (Mn >= 1.0) {
+    return 1;
+  } else if (Mn >= 0.0) {
+    double uf = u + (qnf - qne) * nx, vf = v + (qnf - qne) * ny,
+           wf = w + (qnf - qne) * nz;
+    double rf = pow(pow(rho, gam) * af * af / (gam * p), 1.0 / gm1);
+    double pf = rf * af * af / gam;
+    cons_from(gam, rf, uf, vf, wf, pf, q);
+  } else if (Mn > -1.0) {
+    double uf = 0.0 + (qnf - qninf) * nx, vf = 0.0 + (qnf - qninf) * ny,
+           wf = 0.0 + (qnf - qninf) * nz;
+    double rf = pow(pow(rho_inf, gam) * af * af / (gam * p_inf), 1.0 / gm1);
+    double pf = rf * af * af / gam;
+    cons_from(gam, rf, uf, vf, wf, pf, q);
+  } else {
+    cons_from(gam, rho_inf, 0.0, 0.0, 0.0, p_inf, q);
+  }
+  return 0;
+}
+
 /* Jet boundary conditions applied after the fifth stage.  The free stream is
  * at rest with rho = 1, p = 1/gamma, a = 1.  Phase 1 reads only the state
  * left by the stages:
- *  - entrance i = 0 (Reading A14): Dirichlet jet profile plus forcing,
- *    u = u(r) + sum_{m,f} a_{mf} g(r) cos(m theta - 2 pi St_f U_j t),
- *    g(r) = exp(-((r - r_jet)/w)^2), v = w = 0, rho = 1, p = 1/gamma
- *    (the paper's supersonic-entrance rule applied over the whole plane);
+ *  - entrance i = 0.  bc = 1 (Reading A14): Dirichlet jet profile plus
+ *    forcing, u = u(r) + sum_{m,f} a_{mf} g(r) cos(m theta - 2 pi St_f U_j
+ *    t), g(r) = exp(-((r - r_jet)/w)^2), v = w = 0, rho = 1, p = 1/gamma
+ *    (the paper's supersonic-entrance rule applied over the whole plane).
+ *    bc = 2 (Sec. "Entrance Boundary", Reading A25): the plane is split at
+ *    r = r_jet.  Above the jet, the far-field rule with the unit outward
+ *    normal -grad(xi)/|grad(xi)| and the adjacent node (1, j, k).  In the jet
+ *    area, a supersonic jet (Mj >= 1) gets the Dirichlet jet state as for
+ *    bc = 1; a subsonic one the 1-D characteristic relations: u = the target
+ *    u(r) plus forcing, v, w copied from (1, j, k), T = T_t/(1 + (gamma-1)
+ *    |u|^2/2) with T_t = 1 + (gamma-1) Mj^2/2, p = T^(gamma/(gamma-1))/gamma,
+ *    rho = gamma p/T;
  *  - far field j = nj-1, 0 < i < ni-1 (Sec. "Far Field Boundary", Reading
  *    A13): R- = q_n,inf - 2 a_inf/(gamma-1), R+ = q_n,e + 2 a_e/(gamma-1)
  *    (the printed R+ sign cannot give the printed a_f), unit normal
@@ -831,7 +880,7 @@ void orc_bc_jet(const orc_params *P, int ni, int nj, int nk, double *Q,
                 const double *M, const double *xyz, double t) {
   size_t N = (size_t)ni * nj * nk;
   double gam = P->gamma, gm1 = gam - 1.0;
-  const double rho_inf = 1.0, p_inf = 1.0 / gam, a_inf = 1.0;
+  const double p_inf = 1.0 / gam;
   const double two_pi = 6.283185307179586476925286766559;
   double *Qs = (double *)malloc(5 * N * sizeof(double));
   memcpy(Qs, Q, 5 * N * sizeof(double));
@@ -850,7 +899,25 @@ void orc_bc_jet(const orc_params *P, int ni, int nj, int nk, double *Q,
           u += P->amp[m * 4 + f] * gr *
                cos(m * th - two_pi * P->St[f] * P->Mj * t);
       double q[5];
-      cons_from(gam, 1.0, u, 0.0, 0.0, p_inf, q);
+      if (P->bc == 2 && r > P->r_jet) {
+        size_t ne = ID(1, j, k);
+        double ex = M[0 * N + n], ey = M[1 * N + n], ez = M[2 * N + n];
+        double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
+        double rho, ue, ve, we, p;
+        prim_of(gam, Qs, N, (long)ne, &rho, &ue, &ve, &we, &p);
+        if (riemann_far_field(gam, rho, ue, ve, we, p, -ex * inv, -ey * inv,
+                              -ez * inv, q))
+          for (int c = 0; c < 5; ++c) q[c] = Qs[c * N + ne];
+      } else if (P->bc == 2 && P->Mj < 1.0) {
+        double rho, ue, ve, we, p;
+        prim_of(gam, Qs, N, (long)ID(1, j, k), &rho, &ue, &ve, &we, &p);
+        double Tt = 1.0 + 0.5 * gm1 * P->Mj * P->Mj;
+        double T = Tt / (1.0 + 0.5 * gm1 * (u * u + ve * ve + we * we));
+        double pf = pow(T, gam / gm1) / gam;
+        cons_from(gam, gam * pf / T, u, ve, we, pf, q);
+      } else {
+        cons_from(gam, 1.0, u, 0.0, 0.0, p_inf, q);
+      }
       for (int c = 0; c < 5; ++c) Q[c * N + n] = q[c];
     }
   /* far field */
@@ -859,35 +926,11 @@ void orc_bc_jet(const orc_params *P, int ni, int nj, int nk, double *Q,
       size_t nf = ID(i, nj - 1, k), ne = ID(i, nj - 2, k);
       double ex = M[3 * N + nf], ey = M[4 * N + nf], ez = M[5 * N + nf];
       double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
-      double nx = ex * inv, ny = ey * inv, nz = ez * inv;
       double rho, u, v, w, p;
       prim_of(gam, Qs, N, (long)ne, &rho, &u, &v, &w, &p);
-      double a_e = sqrt(gam * p / rho);
-      double qne = u * nx + v * ny + w * nz;
-      double qninf = 0.0;
-      double Rp = qne + 2.0 * a_e / gm1;
-      double Rm = qninf - 2.0 * a_inf / gm1;
-      double qnf = 0.5 * (Rp + Rm);
-      double af = 0.25 * gm1 * (Rp - Rm);
-      double Mn = qne / a_e;
       double q[5];
-      if (Mn >= 1.0) {
+      if (riemann_far_field(gam, rho, u, v, w, p, ex * inv, ey * inv, ez * inv, q))
         for (int c = 0; c < 5; ++c) q[c] = Qs[c * N + ne];
-      } else if (Mn >= 0.0) {
-        double uf = u + (qnf - qne) * nx, vf = v + (qnf - qne) * ny,
-               wf = w + (qnf - qne) * nz;
-        double rf = pow(pow(rho, gam) * af * af / (gam * p), 1.0 / gm1);
-        double pf = rf * af * af / gam;
-        cons_from(gam, rf, uf, vf, wf, pf, q);
-      } else if (Mn > -1.0) {
-        double uf = 0.0 + (qnf - qninf) * nx, vf = 0.0 + (qnf - qninf) * ny,
-               wf = 0.0 + (qnf - qninf) * nz;
-        double rf = pow(pow(rho_inf, gam) * af * af / (gam * p_inf), 1.0 / gm1);
-        double pf = rf * af * af / gam;
-        cons_from(gam, rf, uf, vf, wf, pf, q);
-      } else {
-        cons_from(gam, rho_inf, 0.0, 0.0, 0.0, p_inf, q);
-      }
       for (int c = 0; c < 5; ++c) Q[c * N + nf] = q[c];
     }
   /* inner ring */
@@ -996,7 +1039,7 @@ double orc_rk_step(const orc_params *P, int ni, int nj, int nk, double *Q,
   }
   flow_user_t U = {P, ni, nj, nk, M, MK};
   orc_rk5(5, N, Q, upd, M + 9 * N, dt, dtn, flow_rhs, &U);
-  if (P->bc == 1) orc_bc_jet(P, ni, nj, nk, Q, M, xyz, t + dt);
+  if (P->bc == 1 || P->bc == 2) orc_bc_jet(P, ni, nj, nk, Q, M, xyz, t + dt);
   free(dtn);
   free(MK);
   free(upd);

@@ -39,7 +39,8 @@ typedef struct {
   double amp[16];    /* forcing amplitudes a_{m f}, index m*4 + f */
   int sgs_model;     /* 0 none, 1 Smagorinsky, 2 Vreman */
   int periodic[3];   /* per direction xi, eta, zeta */
-  int bc;            /* 0 non-periodic boundary nodes frozen, 1 jet BCs */
+  int bc;            /* 0 non-periodic boundary nodes frozen, 1 jet BCs,
+                        2 jet BCs with the characteristic entrance */
   int dt_mode;       /* 0 CFL-limited global step, 1 fixed, 2 local steps */
   int freeze_visc;   /* 1: mu_eff/kappa_eff from Q^n held over 5 stages */
   int pad_;

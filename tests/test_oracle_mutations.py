@@ -63,6 +63,12 @@ MUTATIONS = {
     "local_step_radii": ("dtn[n] = P->cfl / (S.lam[0][n] + S.lam[1][n] + S.lam[2][n]);",
                          "dtn[n] = P->cfl / (S.lam[0][n] + S.lam[1][n] + S.lam[1][n]);",
                          ["test_local_time_steps_closed_form"]),
+    "entrance_normal_sign": ("if (riemann_far_field(gam, rho, ue, ve, we, p, -ex * inv, -ey * inv,",
+                             "if (riemann_far_field(gam, rho, ue, ve, we, p, ex * inv, -ey * inv,",
+                             ["test_characteristic_entrance_above_the_jet"]),
+    "subsonic_jet_total_T": ("double Tt = 1.0 + 0.5 * gm1 * P->Mj * P->Mj;",
+                             "double Tt = 1.0 + 0.5 * gm1 * P->Mj;",
+                             ["test_subsonic_jet_characteristic_entrance"]),
 }
 
 

@@ -778,6 +778,86 @@ def test_far_field_riemann_invariants(orc):
     assert np.allclose(tan(uf, vf, wf, qf)[:, inn], 0.0, atol=1e-12)
 
 
+def _entrance_split(xyz, r_jet=0.5):
+    r = np.sqrt(xyz[1, 0] ** 2 + xyz[2, 0] ** 2)
+    return r > r_jet
+
+
+def test_characteristic_entrance_above_the_jet(orc):
+    """bc = 2, entrance above the jet: the far-field rule with the outward
+    normal -x (the jet grid's xi is the axial direction).  A quiescent
+    interior stays quiescent; otherwise R+ comes from the node (1, j, k),
+    R- from the free stream, and the entropy and tangential velocity from the
+    source state of the branch (interior for outflow through the plane,
+    free stream for inflow)."""
+    P, xyz, M = _jet_setup(orc, bc=2)
+    n = xyz.shape[1:]
+    above = _entrance_split(xyz)
+    assert above.sum() > 10 and (~above).sum() > 10
+    Qr = orc.prim_to_cons(P, synth.uniform_prim(n))
+    Qb = orc.bc_jet(P, Qr, M, xyz, 0.0)
+    assert np.abs(Qb[:, 0][:, above] - Qr[:, 0][:, above]).max() < 1e-14
+    rng = np.random.default_rng(6)
+    prim = synth.uniform_prim(n)
+    prim[0] = 1.0 + 0.05 * rng.standard_normal(n)
+    prim[1] = 0.4 * rng.standard_normal(n)
+    prim[2:4] = 0.2 * rng.standard_normal((2,) + n)
+    prim[4] = (1 / GAMMA) * (1.0 + 0.05 * rng.standard_normal(n))
+    Q = orc.prim_to_cons(P, prim)
+    Qb = orc.bc_jet(P, Q, M, xyz, 0.0)
+    rho, u, v, w, p = (a[above] for a in _prim(Q[:, 1]))
+    rf, uf, vf, wf, pf = (a[above] for a in _prim(Qb[:, 0]))
+    qe, qf = -u, -uf  # outward normal -x
+    ae, af = np.sqrt(GAMMA * p / rho), np.sqrt(GAMMA * pf / rf)
+    assert np.abs(M[1:3, 0]).max() < 1e-14  # the normal is exactly -x
+    sub = np.abs(qe / ae) < 1
+    out, inn = sub & (qe >= 0), sub & (qe < 0)
+    assert out.sum() > 3 and inn.sum() > 3
+    assert np.allclose((qf + 5 * af)[sub], (qe + 5 * ae)[sub], atol=1e-12)
+    assert np.allclose((qf - 5 * af)[sub], -5.0, atol=1e-12)
+    assert np.allclose((pf / rf ** GAMMA)[out], (p / rho ** GAMMA)[out], rtol=1e-12)
+    assert np.allclose((pf / rf ** GAMMA)[inn], 1 / GAMMA, rtol=1e-12)
+    assert np.allclose(vf[out], v[out], atol=1e-13) and np.allclose(wf[out], w[out], atol=1e-13)
+    assert np.abs(vf[inn]).max() < 1e-13 and np.abs(wf[inn]).max() < 1e-13
+    # the jet area of a supersonic jet keeps the Dirichlet jet state (bc = 1)
+    P1, _, _ = _jet_setup(orc, bc=1)
+    Q1 = orc.bc_jet(P1, Q, M, xyz, 0.0)
+    assert np.array_equal(Qb[:, 0][:, ~above], Q1[:, 0][:, ~above])
+    # the rest of the boundary is the same as with bc = 1
+    assert np.array_equal(Qb[:, 1:], Q1[:, 1:])
+
+
+def test_subsonic_jet_characteristic_entrance(orc):
+    """bc = 2 with a subsonic jet (Mj = 0.9): in the jet area u is the target
+    profile, v and w come from the node (1, j, k), and T, p follow the jet's
+    total temperature and the isentropic relation; at the target's own
+    design point (u = Mj, v = w = 0) that is exactly T = 1, p = 1/gamma."""
+    P, xyz, M = _jet_setup(orc, bc=2, Mj=0.9)
+    n = xyz.shape[1:]
+    jet = ~_entrance_split(xyz)
+    rng = np.random.default_rng(9)
+    prim = synth.uniform_prim(n)
+    prim[2:4] = 0.1 * rng.standard_normal((2,) + n)
+    Q = orc.prim_to_cons(P, prim)
+    Qb = orc.bc_jet(P, Q, M, xyz, 0.0)
+    rf, uf, vf, wf, pf = (a[jet] for a in _prim(Qb[:, 0]))
+    r = np.sqrt(xyz[1, 0] ** 2 + xyz[2, 0] ** 2)[jet]
+    ut = 0.45 * (1.0 + np.tanh((0.5 - r) / 0.1))
+    assert np.allclose(uf, ut, rtol=1e-14, atol=1e-15)
+    assert np.allclose(vf, prim[2, 1][jet], atol=1e-15)
+    assert np.allclose(wf, prim[3, 1][jet], atol=1e-15)
+    Tt = 1.0 + 0.2 * 0.81
+    T = Tt / (1.0 + 0.2 * (ut ** 2 + vf ** 2 + wf ** 2))
+    assert np.allclose(GAMMA * pf / rf, T, rtol=1e-13)
+    assert np.allclose(pf, T ** 3.5 / GAMMA, rtol=1e-13)
+    prim0 = synth.uniform_prim(n, u=0.9)
+    P0, _, _ = _jet_setup(orc, bc=2, Mj=0.9, theta_m=1e-6)
+    Qb0 = orc.bc_jet(P0, orc.prim_to_cons(P0, prim0), M, xyz, 0.0)
+    rf0, uf0, _, _, pf0 = (a[jet] for a in _prim(Qb0[:, 0]))
+    assert np.allclose(uf0, 0.9, rtol=1e-15) and np.allclose(pf0, 1 / GAMMA, rtol=1e-14)
+    assert np.allclose(rf0, 1.0, rtol=1e-14)
+
+
 def test_exit_and_inner_ring(orc):
     P, xyz, M = _jet_setup(orc)
     n = xyz.shape[1:]
