@@ -52,7 +52,7 @@ enum { LES_SGS_NONE = 0, LES_SGS_SMAGORINSKY = 1, LES_SGS_VREMAN = 2 };
  * once rounded to FP32, which the boundary conditions and the totals then
  * read; les_metrics() returns NULL.  It is the form for the largest grids. */
 enum { LES_PREC_FP64 = 0, LES_PREC_MIXED = 1, LES_PREC_MIXED_COMPACT = 2 };
-enum { LES_BC_FROZEN = 0, LES_BC_JET = 1 };
+enum { LES_BC_FROZEN = 0, LES_BC_JET = 1, LES_BC_JET_CHAR = 2 };
 enum { LES_DT_CFL = 0, LES_DT_FIXED = 1, LES_DT_LOCAL = 2 };
 enum { LES_METRIC_CROSS = 0, LES_METRIC_CONSERVATIVE = 1 };
 
@@ -79,8 +79,16 @@ typedef struct les_params {
   double amp[16];     /* forcing amplitudes a_{m f}, index m*4 + f */
   int sgs_model;      /* LES_SGS_* */
   int periodic[3];    /* per direction xi, eta, zeta: 1 = periodic */
-  int bc;             /* LES_BC_FROZEN (non-periodic faces never change)
-                         or LES_BC_JET (needs periodic = {0,0,1}) */
+  int bc;             /* LES_BC_FROZEN (non-periodic faces never change),
+                         LES_BC_JET (Dirichlet jet state over the whole
+                         entrance plane) or LES_BC_JET_CHAR (Sec. "Entrance
+                         Boundary": above r = r_jet the far-field Riemann
+                         rule with the xi normal; in the jet area the jet
+                         state if Mj >= 1, else the 1-D characteristic
+                         relations: target u, v and w from the next plane,
+                         T from the jet's total temperature, isentropic p).
+                         Both jet modes need periodic = {0,0,1}; the adjoint
+                         calls support LES_BC_FROZEN and LES_BC_JET. */
   int dt_mode;        /* LES_DT_CFL, LES_DT_FIXED or LES_DT_LOCAL (Eq.
                          localdt taken literally: node n advances with its
                          own CFL step cfl/(lambda_xi + lambda_eta +
@@ -191,7 +199,7 @@ int les_time_step(les_ctx *ctx, const double *Q, double *dt_out,
                   les_stream_t stream);
 
 /* Jet boundary conditions on Q at time t (entrance, far field, inner ring,
- * then exit).  Requires bc == LES_BC_JET.  Asynchronous. */
+ * then exit).  Requires bc == LES_BC_JET or LES_BC_JET_CHAR.  Asynchronous. */
 int les_apply_bc(les_ctx *ctx, double *Q, double t, les_stream_t stream);
 
 /* Set the device-resident simulation time used by the stepping calls. */

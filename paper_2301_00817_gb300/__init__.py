@@ -28,7 +28,7 @@ LES_ERR_STATE = -7
 
 SGS_NONE, SGS_SMAGORINSKY, SGS_VREMAN = 0, 1, 2
 PREC_FP64, PREC_MIXED, PREC_MIXED_COMPACT = 0, 1, 2
-BC_FROZEN, BC_JET = 0, 1
+BC_FROZEN, BC_JET, BC_JET_CHAR = 0, 1, 2
 DT_CFL, DT_FIXED, DT_LOCAL = 0, 1, 2
 METRIC_CROSS, METRIC_CONSERVATIVE = 0, 1
 

@@ -132,15 +132,16 @@ int validate_params(const les_params* p, std::string& why) {
     why = "metric_form must be LES_METRIC_CROSS or LES_METRIC_CONSERVATIVE";
     return LES_ERR_INVALID_ARG;
   }
-  if (p->bc != LES_BC_FROZEN && p->bc != LES_BC_JET) {
-    why = "bc must be LES_BC_FROZEN or LES_BC_JET";
+  if (p->bc != LES_BC_FROZEN && p->bc != LES_BC_JET && p->bc != LES_BC_JET_CHAR) {
+    why = "bc must be LES_BC_FROZEN, LES_BC_JET or LES_BC_JET_CHAR";
     return LES_ERR_INVALID_ARG;
   }
-  if (p->bc == LES_BC_JET && !(p->periodic[0] == 0 && p->periodic[1] == 0 && p->periodic[2] == 1)) {
+  const bool jet = p->bc == LES_BC_JET || p->bc == LES_BC_JET_CHAR;
+  if (jet && !(p->periodic[0] == 0 && p->periodic[1] == 0 && p->periodic[2] == 1)) {
     why = "jet boundary conditions need periodic = {0, 0, 1}";
     return LES_ERR_INVALID_ARG;
   }
-  if (p->bc == LES_BC_JET && !(p->theta_m > 0.0 && p->force_width > 0.0)) {
+  if (jet && !(p->theta_m > 0.0 && p->force_width > 0.0)) {
     why = "jet boundary conditions need theta_m > 0 and force_width > 0";
     return LES_ERR_INVALID_ARG;
   }
@@ -182,6 +183,7 @@ int ready(les_ctx* c) {
 }
 
 bool is_mixed(const les_ctx* c) { return c->p.precision != LES_PREC_FP64; }
+bool jet_bc(const les_ctx* c) { return c->p.bc == LES_BC_JET || c->p.bc == LES_BC_JET_CHAR; }
 // The compact mixed form keeps no FP64 copy of the metrics: its boundary
 // conditions and totals read the FP32 metrics.
 bool has_m64(const les_ctx* c) { return c->p.precision != LES_PREC_MIXED_COMPACT; }
@@ -269,7 +271,7 @@ void rk_step(les_ctx* c, double* Q, cudaStream_t s) {
       ProfScope ps(c, PK_UPDATE, s);
       lesjet::launch_update64(c->g, io, Q, kAlpha[l - 1], l == 5 ? 2 : 1, out, L);
     }
-    if (c->p.bc == LES_BC_JET) {
+    if (jet_bc(c)) {
       ProfScope ps(c, PK_BC, s);
       lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth),
                             sc, 0, 0.0, L);
@@ -291,7 +293,7 @@ void rk_step(les_ctx* c, double* Q, cudaStream_t s) {
     ProfScope ps(c, PK_STAGE, s);
     lesjet::launch_stage_fused(l == 5 ? 2 : 1, c->g, c->p, fused_io(c, in, out), kAlpha[l - 1], L);
   }
-  if (c->p.bc == LES_BC_JET) {
+  if (jet_bc(c)) {
     ProfScope ps(c, PK_BC, s);
     if (has_m64(c))
       lesjet::launch_bc_jet_hl(c->g, c->p, hi, at<float>(c, c->off_lo), at<double>(c, c->off_m64),
@@ -488,7 +490,7 @@ int les_apply_bc(les_ctx* c, double* Q, double t, les_stream_t stream) {
   if (rc != LES_OK) return rc;
   if (!Q) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
   if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
-  if (c->p.bc != LES_BC_JET) return fail(c, LES_ERR_STATE, "bc is not LES_BC_JET");
+  if (!jet_bc(c)) return fail(c, LES_ERR_STATE, "bc is not LES_BC_JET or LES_BC_JET_CHAR");
   lesjet::Launch L{(cudaStream_t)stream, &c->launches};
   if (has_m64(c))
     lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth),
@@ -678,6 +680,8 @@ int adj_check(les_ctx* c) {
     return fail(c, LES_ERR_UNSUPPORTED, "the adjoint is provided for the FP64 form");
   if (c->p.sgs_model != LES_SGS_NONE)
     return fail(c, LES_ERR_UNSUPPORTED, "the adjoint supports sgs_model = LES_SGS_NONE");
+  if (c->p.bc == LES_BC_JET_CHAR)
+    return fail(c, LES_ERR_UNSUPPORTED, "the adjoint supports bc = LES_BC_FROZEN or LES_BC_JET");
   if (c->p.dt_mode != LES_DT_FIXED)
     return fail(c, LES_ERR_UNSUPPORTED, "the adjoint needs dt_mode = LES_DT_FIXED");
   if (!c->p.freeze_visc)
@@ -746,7 +750,7 @@ void adj_reverse(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], 
   lesjet::StageIO64 io = adj_io(c, aw, Ly, S[0]);
   io.mk = const_cast<double*>(mk);
   // boundary conditions at t^{n+1}
-  if (c->p.bc == LES_BC_JET) {
+  if (jet_bc(c)) {
     cudaMemcpyAsync(Qnext, S[5], bytes, cudaMemcpyDeviceToDevice, s);
     lesjet::launch_bc_jet(g, c->p, Qnext, M, at<double>(c, c->off_rth), sc, 1, t_n + dt, L);
     lesjet::launch_bc_vjp(g, c->p, M, at<double>(c, c->off_rth), S[5], Qnext, lam_next, t_n + dt,
@@ -891,7 +895,7 @@ int les_adjoint_window(les_ctx* c, const double* Q_start, double t0, int nsteps,
     for (int l = 0; l < 6; ++l) S[l] = segS(m, l);
     adj_forward(c, aw, Ly, S, segMK(m), segN(m), s);
     cudaMemcpyAsync(dst, S[5], bytes, cudaMemcpyDeviceToDevice, s);
-    if (c->p.bc == LES_BC_JET)
+    if (jet_bc(c))
       lesjet::launch_bc_jet(g, c->p, dst, M, at<double>(c, c->off_rth), sc, 1, t0 + (n + 1) * dt, L);
   };
   // forward window, checkpoints every K steps

@@ -25,6 +25,7 @@ struct AccHL {
 };
 
 struct JetBC {
+  int mode;  // LES_BC_JET or LES_BC_JET_CHAR
   double gamma, Mj, r_jet, theta_m, force_width;
   double St[4];
   double amp[16];
@@ -51,13 +52,62 @@ __device__ __forceinline__ void load_prim(const Acc& Q, long long N, long long n
   p = (gamma - 1.0) * (Q.ld(4 * N + n) - 0.5 * rho * (u * u + v * v + w * w));
 }
 
-// Entrance i = 0: rho = 1, p = 1/gamma, v = w = 0, u = jet profile plus the
+// Riemann-invariant state of a far-field node from its interior neighbour's
+// primitives and the unit outward normal, the free stream at rest (rho = 1,
+// p = 1/gamma, a = 1): R+ = q_n,e + 2 a_e/(gamma-1), R- = -2/(gamma-1), four
+// branches by q_n,e/a_e.  Returns true for the supersonic exit (the caller
+// copies the neighbour's conserved values); otherwise the primitives of the
+// boundary state are in f = (rho, u, v, w, p).
+__device__ __forceinline__ bool far_field_state(double gamma, double rho, double u, double v,
+                                                double w, double p, double nx, double ny,
+                                                double nz, double f[5]) {
+  const double gm1 = gamma - 1.0;
+  const double ae = sqrt(gamma * p / rho);
+  const double qne = u * nx + v * ny + w * nz;
+  const double Rp = qne + 2.0 * ae / gm1;
+  const double Rm = 0.0 - 2.0 * 1.0 / gm1;
+  const double qnf = 0.5 * (Rp + Rm);
+  const double af = 0.25 * gm1 * (Rp - Rm);
+  const double Mn = qne / ae;
+  if (Mn >= 1.0) return true;
+  if (Mn >= 0.0) {
+    const double dq = qnf - qne;
+    const double rf = pow(pow(rho, gamma) * af * af / (gamma * p), 1.0 / gm1);
+    f[0] = rf;
+    f[1] = u + dq * nx;
+    f[2] = v + dq * ny;
+    f[3] = w + dq * nz;
+    f[4] = rf * af * af / gamma;
+  } else if (Mn > -1.0) {
+    const double rf = pow(af * af / (gamma * (1.0 / gamma)), 1.0 / gm1);
+    f[0] = rf;
+    f[1] = qnf * nx;
+    f[2] = qnf * ny;
+    f[3] = qnf * nz;
+    f[4] = rf * af * af / gamma;
+  } else {
+    f[0] = 1.0;
+    f[1] = f[2] = f[3] = 0.0;
+    f[4] = 1.0 / gamma;
+  }
+  return false;
+}
+
+// Entrance i = 0.  The target axial velocity is the jet profile plus the
 // 16-mode forcing sum a_{mf} g(r) cos(m theta - 2 pi St_f Mj t).
-template <class Acc>
+// LES_BC_JET: rho = 1, p = 1/gamma, v = w = 0, u = target on the whole plane.
+// LES_BC_JET_CHAR (Sec. "Entrance Boundary"): above r_jet the far-field rule
+// with the outward normal -grad(xi)/|grad(xi)| and the node (1, j, k); in the
+// jet area the same jet state when Mj >= 1, else the 1-D characteristic
+// relations (u = target, v and w from (1, j, k), T = T_t/(1 + (gamma-1)
+// |u|^2/2) with the jet's T_t = 1 + (gamma-1) Mj^2/2, p = T^(gamma/(gamma-1))
+// /gamma).  The plane i = 1 is read before any other boundary kernel runs.
+template <class Acc, typename TM>
 __global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
-                            const DevScalars* __restrict__ sc, int use_host_t, double t_host,
-                            Acc Q) {
+                            const TM* __restrict__ M, const DevScalars* __restrict__ sc,
+                            int use_host_t, double t_host, Acc Q) {
   const long long plane = (long long)g.n[1] * g.n[2];
+  const long long N = g.N;
   const double t = use_host_t ? t_host : sc->t;
   const double two_pi = 6.283185307179586476925286766559;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < plane;
@@ -71,7 +121,29 @@ __global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
 #pragma unroll
       for (int f = 0; f < 4; ++f)
         u += b.amp[m * 4 + f] * gr * cos(m * th - two_pi * b.St[f] * b.Mj * t);
-    store_prim(Q, g.N, n, b.gamma, 1.0, u, 0.0, 0.0, 1.0 / b.gamma);
+    const long long ne = n + plane;  // node (1, j, k)
+    if (b.mode == LES_BC_JET_CHAR && r > b.r_jet) {
+      const double ex = (double)M[n], ey = (double)M[N + n], ez = (double)M[2 * N + n];
+      const double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
+      double rho, ue, ve, we, p, f[5];
+      load_prim(Q, N, ne, b.gamma, rho, ue, ve, we, p);
+      if (far_field_state(b.gamma, rho, ue, ve, we, p, -ex * inv, -ey * inv, -ez * inv, f)) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Q.st(q * N + n, Q.ld(q * N + ne));
+      } else {
+        store_prim(Q, N, n, b.gamma, f[0], f[1], f[2], f[3], f[4]);
+      }
+    } else if (b.mode == LES_BC_JET_CHAR && b.Mj < 1.0) {
+      const double gm1 = b.gamma - 1.0;
+      double rho, ue, ve, we, p;
+      load_prim(Q, N, ne, b.gamma, rho, ue, ve, we, p);
+      const double Tt = 1.0 + 0.5 * gm1 * b.Mj * b.Mj;
+      const double T = Tt / (1.0 + 0.5 * gm1 * (u * u + ve * ve + we * we));
+      const double pf = pow(T, b.gamma / gm1) / b.gamma;
+      store_prim(Q, N, n, b.gamma, b.gamma * pf / T, u, ve, we, pf);
+    } else {
+      store_prim(Q, N, n, b.gamma, 1.0, u, 0.0, 0.0, 1.0 / b.gamma);
+    }
   }
 }
 
@@ -83,35 +155,19 @@ __global__ void k_bc_farfield(Grid g, double gamma, const TM* __restrict__ M, Ac
   const int ni = g.n[0], nj = g.n[1], nk = g.n[2];
   const long long count = (long long)(ni - 2) * nk;
   const long long N = g.N;
-  const double gm1 = gamma - 1.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = 1 + (int)(e / nk), k = (int)(e % nk);
     const long long nf = idx3(g, i, nj - 1, k), ne = idx3(g, i, nj - 2, k);
     const double ex = (double)M[3 * N + nf], ey = (double)M[4 * N + nf], ez = (double)M[5 * N + nf];
     const double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
-    const double nx = ex * inv, ny = ey * inv, nz = ez * inv;
-    double rho, u, v, w, p;
+    double rho, u, v, w, p, f[5];
     load_prim(Q, N, ne, gamma, rho, u, v, w, p);
-    const double ae = sqrt(gamma * p / rho);
-    const double qne = u * nx + v * ny + w * nz;
-    const double Rp = qne + 2.0 * ae / gm1;
-    const double Rm = 0.0 - 2.0 * 1.0 / gm1;
-    const double qnf = 0.5 * (Rp + Rm);
-    const double af = 0.25 * gm1 * (Rp - Rm);
-    const double Mn = qne / ae;
-    if (Mn >= 1.0) {
+    if (far_field_state(gamma, rho, u, v, w, p, ex * inv, ey * inv, ez * inv, f)) {
 #pragma unroll
       for (int q = 0; q < 5; ++q) Q.st(q * N + nf, Q.ld(q * N + ne));
-    } else if (Mn >= 0.0) {
-      const double dq = qnf - qne;
-      const double rf = pow(pow(rho, gamma) * af * af / (gamma * p), 1.0 / gm1);
-      store_prim(Q, N, nf, gamma, rf, u + dq * nx, v + dq * ny, w + dq * nz, rf * af * af / gamma);
-    } else if (Mn > -1.0) {
-      const double rf = pow(af * af / (gamma * (1.0 / gamma)), 1.0 / gm1);
-      store_prim(Q, N, nf, gamma, rf, qnf * nx, qnf * ny, qnf * nz, rf * af * af / gamma);
     } else {
-      store_prim(Q, N, nf, gamma, 1.0, 0.0, 0.0, 0.0, 1.0 / gamma);
+      store_prim(Q, N, nf, gamma, f[0], f[1], f[2], f[3], f[4]);
     }
   }
 }
@@ -240,6 +296,7 @@ static void bc_jet(const Grid& g, const les_params& p, Acc Q, const TM* M,
                    const double* rth, const DevScalars* sc, int use_host_t, double t_host,
                    const Launch& L) {
   JetBC b;
+  b.mode = p.bc;
   b.gamma = p.gamma;
   b.Mj = p.Mj;
   b.r_jet = p.r_jet;
@@ -248,7 +305,7 @@ static void bc_jet(const Grid& g, const les_params& p, Acc Q, const TM* M,
   for (int i = 0; i < 4; ++i) b.St[i] = p.St[i];
   for (int i = 0; i < 16; ++i) b.amp[i] = p.amp[i];
   const long long plane = (long long)g.n[1] * g.n[2];
-  k_bc_inflow<Acc><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, sc, use_host_t, t_host, Q);
+  k_bc_inflow<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, M, sc, use_host_t, t_host, Q);
   k_bc_farfield<Acc, TM><<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M, Q);
   k_bc_ring<Acc><<<g.n[0] - 2, 256, 0, L.s>>>(g, Q);
   k_bc_exit<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M, Q);

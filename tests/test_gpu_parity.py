@@ -259,6 +259,63 @@ def test_boundary_conditions(orc, lj, torch):
     assert rel_linf(Qd.cpu().numpy(), Qo) <= 1e-14
 
 
+@pytest.mark.parametrize("Mj", [1.4, 0.9])
+def test_characteristic_entrance_bc(orc, lj, torch, Mj):
+    """bc = LES_BC_JET_CHAR on a state with in- and outflow through the
+    entrance above the jet (all far-field branches) and, for Mj = 0.9, the
+    subsonic jet branch."""
+    shape, xyz, shift, kw = _grid(lj, "jet_c1")
+    kw = dict(kw, bc=lj.BC_JET_CHAR, Mj=Mj)
+    amp = lj.synth.forcing_amplitudes(9, scale=0.05)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, amp=tuple(amp), **kw)
+    P = oracle_params(orc, amp=tuple(amp), **kw)
+    M = orc.metrics(xyz, (0, 0, 1))
+    rng = np.random.default_rng(5)
+    prim = lj.synth.uniform_prim(shape)
+    prim[0] = 1.0 + 0.05 * rng.standard_normal(shape)
+    prim[1] = 0.6 * rng.standard_normal(shape)
+    prim[1, 1, ::3] = 1.5  # a few supersonic exits through the far field
+    prim[2:4] = 0.3 * rng.standard_normal((2,) + shape)
+    prim[4] = (1 / 1.4) * (1.0 + 0.05 * rng.standard_normal(shape))
+    Q = orc.prim_to_cons(P, prim)
+    Qd = torch.from_numpy(Q).cuda()
+    ctx.les_apply_bc(Qd, 0.731)
+    Qo = orc.bc_jet(P, Q, M, xyz, 0.731)
+    assert rel_linf(Qd.cpu().numpy(), Qo) <= 1e-14
+
+
+@pytest.mark.parametrize("Mj", [1.4, 0.9])
+def test_characteristic_entrance_steps(orc, lj, torch, Mj):
+    shape = C1
+    xyz = lj.synth.jet_grid(*shape)
+    kw = dict(periodic=(0, 0, 1), bc=lj.BC_JET_CHAR, sgs_model=1, Mj=Mj)
+    amp = tuple(lj.synth.forcing_amplitudes(2, scale=0.02))
+    ctx, _ = device_ctx(lj, torch, shape, xyz, amp=amp, **kw)
+    P = oracle_params(orc, amp=amp, **kw)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Q0 = orc.init_jet(P, xyz, seed=6, noise=1e-2)
+    Qd = torch.from_numpy(Q0).cuda()
+    d1 = ctx.les_run_n_steps(1, Qd)
+    Q1, dt1 = orc.rk_step(P, Q0, M, xyz, 0.0)
+    assert abs(d1.dt - dt1) <= 1e-13 * dt1
+    assert rel_linf(Qd.cpu().numpy(), Q1) <= 1e-12
+    ctx.les_run_n_steps(19, Qd)
+    Q20, _ = orc.run(P, Q1, M, xyz, 19, t=dt1)
+    assert rel_linf(Qd.cpu().numpy(), Q20) <= 1e-10
+    Qm = torch.from_numpy(Q0).cuda()
+    cm, _ = device_ctx(lj, torch, shape, xyz, amp=amp, precision=lj.PREC_MIXED, **kw)
+    assert cm.les_run_n_steps(20, Qm).status == 0
+    for comp in (0, 1, 4):
+        err = float(torch.linalg.vector_norm(Qm[comp] - Qd[comp]) / torch.linalg.vector_norm(Qd[comp]))
+        assert err <= 1e-5, (comp, err)
+    # the adjoint supports the Dirichlet entrance only
+    ca, _ = device_ctx(lj, torch, shape, xyz, periodic=(0, 0, 1), bc=lj.BC_JET_CHAR,
+                       dt_mode=lj.DT_FIXED, dt_fixed=1e-4)
+    with pytest.raises(lj.LesError) as e:
+        ca.les_adjoint_step(Qd, 0.0, Qd.clone(), torch.empty_like(Qd), ca.adjoint_workspace(1, 1))
+    assert e.value.code == lj.LES_ERR_UNSUPPORTED and "bc" in str(e.value)
+
+
 # ------------------------------------------------------------- time steps
 
 @pytest.mark.parametrize("sgs", [0, 1, 2])
