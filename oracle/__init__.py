@@ -105,6 +105,8 @@ def _lib_handle():
             lib.orc_rk5.argtypes = [i, C.c_size_t, _dp, C.POINTER(C.c_ubyte), _dp,
                                     C.c_double, _dp, RHSFN, C.c_void_p]
             lib.orc_dt_local.argtypes = [P, i, i, i, _dp, _dp, _dp]
+            lib.orc_dynamic_coefficients.argtypes = [P, i, i, i, _dp, _dp, _dp]
+            lib.orc_test_filter.argtypes = [i, i, i, C.POINTER(C.c_int), _dp, _dp]
             lib._RHSFN = RHSFN
             _lib = lib
     return _lib
@@ -166,9 +168,10 @@ def init_jet(P: OrcParams, xyz, seed: int, noise: float = 1.0e-3) -> np.ndarray:
 
 
 def mu_eff(P: OrcParams, Q, M) -> np.ndarray:
+    """[mu_eff, kappa_eff] (and sigma_ll for the dynamic model)."""
     Q, M = _f64(Q), _f64(M)
     _, ni, nj, nk = Q.shape
-    MK = np.empty((2, ni, nj, nk))
+    MK = np.empty((3 if P.sgs_model == 3 else 2, ni, nj, nk))
     _lib_handle().orc_mu_eff(C.byref(P), ni, nj, nk, _ptr(Q), _ptr(M), _ptr(MK))
     return MK
 
@@ -198,6 +201,26 @@ def dt(P: OrcParams, Q, M) -> float:
     Q, M = _f64(Q), _f64(M)
     _, ni, nj, nk = Q.shape
     return float(_lib_handle().orc_dt(C.byref(P), ni, nj, nk, _ptr(Q), _ptr(M)))
+
+
+def test_filter(f, periodic=(1, 1, 1)) -> np.ndarray:
+    """The dynamic model's test filter applied to the node field f."""
+    f = _f64(f)
+    ni, nj, nk = f.shape
+    out = np.empty_like(f)
+    _lib_handle().orc_test_filter(ni, nj, nk, (C.c_int * 3)(*periodic), _ptr(f), _ptr(out))
+    return out
+
+
+def dynamic_coefficients(P: OrcParams, Q, M) -> dict:
+    """The dynamic Smagorinsky procedure on Q: the averaged numerators and
+    denominators and the coefficients C_ds, C_I, Pr_sgs."""
+    Q, M = _f64(Q), _f64(M)
+    _, ni, nj, nk = Q.shape
+    out = np.empty(9)
+    _lib_handle().orc_dynamic_coefficients(C.byref(P), ni, nj, nk, _ptr(Q), _ptr(M), _ptr(out))
+    keys = ("numC", "denC", "numI", "denI", "numP", "denP", "Cd", "CI", "Prt")
+    return dict(zip(keys, out.tolist()))
 
 
 def dt_local(P: OrcParams, Q, M) -> np.ndarray:

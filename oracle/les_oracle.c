@@ -501,6 +501,197 @@ static double mu_laminar(const orc_params *P, double T) {
   return (P->Mj / P->Re) * pow(T, 1.5) * (1.0 + S) / (T + S);
 }
 
+/* ------------------------------------------------- dynamic Smagorinsky */
+
+/* Weight of offset off (-1, 0, 1) along direction d of the test filter at
+ * node c (Reading A26): the trapezoidal (1/4, 1/2, 1/4) filter of width two
+ * cells, the identity along a non-periodic direction at its faces. */
+static double filter_weight(const grid_t *g, const int c[3], int d, int off) {
+  if (!g->per[d] && (c[d] == 0 || c[d] == g->n[d] - 1)) return off == 0 ? 1.0 : 0.0;
+  return off == 0 ? 0.5 : 0.25;
+}
+
+/* Test filter of the field f at every node: the 27-point tensor product of
+ * the one-dimensional weights. */
+static void test_filter(const grid_t *g, const double *f, double *out) {
+#pragma omp parallel for schedule(static)
+  for (long n = 0; n < (long)g->N; ++n) {
+    int c[3];
+    unlin(g, (size_t)n, c);
+    double s = 0.0;
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b)
+        for (int e = -1; e <= 1; ++e) {
+          double wgt = filter_weight(g, c, 0, a) * filter_weight(g, c, 1, b) *
+                       filter_weight(g, c, 2, e);
+          if (wgt == 0.0) continue;
+          int cc[3] = {c[0] + a, c[1] + b, c[2] + e};
+          for (int d = 0; d < 3; ++d) cc[d] = (cc[d] + g->n[d]) % g->n[d];
+          s += wgt * f[lin(g, cc)];
+        }
+    out[n] = s;
+  }
+}
+
+/* Cartesian gradient of the node field f at node c (node-centred
+ * differences through the node's metrics, as for the static models). */
+static void cart_grad(const grid_t *g, const double *M, const double *f,
+                      const int c[3], double out[3]) {
+  size_t N = g->N, n = lin(g, c);
+  double dd[3];
+  for (int d = 0; d < 3; ++d) dd[d] = node_deriv(g, f, c, d);
+  for (int x = 0; x < 3; ++x)
+    out[x] = M[x * N + n] * dd[0] + M[(3 + x) * N + n] * dd[1] +
+             M[(6 + x) * N + n] * dd[2];
+}
+
+/* Strain rate S_ij = (d_j u_i + d_i u_j)/2 of the velocity fields (u, v, w)
+ * at node c, and |S| = (2 S_ij S_ij)^(1/2). */
+static double strain_at(const grid_t *g, const double *M, const double *u,
+                        const double *v, const double *w, const int c[3],
+                        double Sij[3][3]) {
+  const double *vel[3] = {u, v, w};
+  double gr[3][3];
+  for (int q = 0; q < 3; ++q) cart_grad(g, M, vel[q], c, gr[q]);
+  double ss = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Sij[i][j] = 0.5 * (gr[i][j] + gr[j][i]);
+      ss += Sij[i][j] * Sij[i][j];
+    }
+  return sqrt(2.0 * ss);
+}
+
+/* The dynamic procedure (Sec. "Dynamic Smagorinsky Model", Eqs. av_ci,
+ * av_cd, av_Pr_sgs) on the state Q with node primitives (u, v, w, T).
+ * Readings (A26): the test filter is test_filter, of width Delta^ = 2 Delta;
+ * Favre-filtered fields are u^_i = (rho u_i)^/rho^, T^ = (rho T)^/rho^, and
+ * S^ is the strain of u^; by the Germano identity the trace term
+ * T_ll - sigma^_ll of Eq. av_cd is L_kk, L_ij = (rho u_i u_j)^ -
+ * (rho u_i)^ (rho u_j)^/rho^; the second term of Eq. av_Pr_sgs contracts the
+ * gradient of T^ with that of T; <.> is the J^-1-weighted mean over the
+ * interior nodes.  out = {<num>, <den>} of C_ds, C_I and Pr_sgs/C_ds, then
+ * C_ds, C_I, Pr_sgs: C_ds and C_I are clipped at 0 (and are 0 when their
+ * denominator vanishes); Pr_sgs falls back to the configured value when it
+ * is not positive and finite. */
+static void dynamic_procedure(const orc_params *P, const grid_t *g,
+                              const double *Q, const double *M,
+                              const double *u, const double *v,
+                              const double *w, const double *T,
+                              double out[9]) {
+  size_t N = g->N;
+  enum { NF = 25 };
+  double *f = (double *)malloc(NF * N * sizeof(double));
+  double *fh = (double *)malloc(NF * N * sizeof(double));
+  /* node products: rho, rho u_i, rho T, rho u_i u_j (xx yy zz xy xz yz),
+   * rho|S| S_ij (same order), rho|S| S_mm, rho|S|^2, rho u_j T,
+   * rho|S| dT/dx_j */
+  static const int I6[6] = {0, 1, 2, 0, 0, 1}, J6[6] = {0, 1, 2, 1, 2, 2};
+  for (size_t n = 0; n < N; ++n) {
+    int c[3];
+    unlin(g, n, c);
+    double rho = Q[n], vel[3] = {u[n], v[n], w[n]}, Sij[3][3], dT[3];
+    double Sm = strain_at(g, M, u, v, w, c, Sij);
+    cart_grad(g, M, T, c, dT);
+    f[0 * N + n] = rho;
+    for (int i = 0; i < 3; ++i) f[(1 + i) * N + n] = rho * vel[i];
+    f[4 * N + n] = rho * T[n];
+    for (int k = 0; k < 6; ++k) {
+      f[(5 + k) * N + n] = rho * vel[I6[k]] * vel[J6[k]];
+      f[(11 + k) * N + n] = rho * Sm * Sij[I6[k]][J6[k]];
+    }
+    f[17 * N + n] = rho * Sm * (Sij[0][0] + Sij[1][1] + Sij[2][2]);
+    f[18 * N + n] = rho * Sm * Sm;
+    for (int j = 0; j < 3; ++j) {
+      f[(19 + j) * N + n] = rho * vel[j] * T[n];
+      f[(22 + j) * N + n] = rho * Sm * dT[j];
+    }
+  }
+  for (int q = 0; q < NF; ++q) test_filter(g, f + (size_t)q * N, fh + (size_t)q * N);
+  /* Favre-filtered velocity and temperature */
+  double *uh = (double *)malloc(4 * N * sizeof(double));
+  for (size_t n = 0; n < N; ++n) {
+    for (int i = 0; i < 3; ++i) uh[i * N + n] = fh[(1 + i) * N + n] / fh[n];
+    uh[3 * N + n] = fh[4 * N + n] / fh[n];
+  }
+  double sum[7] = {0, 0, 0, 0, 0, 0, 0}; /* 6 weighted sums, then sum of J^-1 */
+  for (size_t n = 0; n < N; ++n) {
+    int c[3];
+    unlin(g, n, c);
+    if (!is_interior(g, c)) continue;
+    double wgt = M[9 * N + n];
+    double Delta = cbrt(M[9 * N + n]), D2 = Delta * Delta, Dh2 = 4.0 * D2;
+    double Sij[3][3], dT[3], Sh[3][3], dTh[3];
+    double Sm = strain_at(g, M, u, v, w, c, Sij);
+    cart_grad(g, M, T, c, dT);
+    double Shm = strain_at(g, M, uh, uh + N, uh + 2 * N, c, Sh);
+    cart_grad(g, M, uh + 3 * N, c, dTh);
+    (void)Sm;
+    double rh = fh[n], mh[3] = {fh[N + n], fh[2 * N + n], fh[3 * N + n]};
+    double L[3][3], Fs[3][3];
+    for (int k = 0; k < 6; ++k) {
+      int i = I6[k], j = J6[k];
+      L[i][j] = L[j][i] = fh[(5 + k) * N + n] - mh[i] * mh[j] / rh;
+      Fs[i][j] = Fs[j][i] = fh[(11 + k) * N + n];
+    }
+    double trS = Sij[0][0] + Sij[1][1] + Sij[2][2];
+    double trSh = Sh[0][0] + Sh[1][1] + Sh[2][2];
+    double LS = 0.0, FS = 0.0, ShS = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        LS += L[i][j] * Sij[i][j];
+        FS += Fs[i][j] * Sij[i][j];
+        ShS += Sh[i][j] * Sij[i][j];
+      }
+    double Lkk = L[0][0] + L[1][1] + L[2][2];
+    double numC = LS - Lkk * trS / 3.0;
+    double denC = 2.0 * D2 * (FS - fh[17 * N + n] * trS / 3.0) -
+                  2.0 * Dh2 * (rh * Shm * ShS - rh * Shm * trSh * trS / 3.0);
+    double numI = Lkk;
+    double denI = 2.0 * Dh2 * rh * Shm * Shm - 2.0 * D2 * fh[18 * N + n];
+    double numP = 0.0, denP = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      double K = fh[(19 + j) * N + n] - mh[j] * fh[4 * N + n] / rh;
+      numP += D2 * fh[(22 + j) * N + n] * dT[j] - Dh2 * rh * Shm * dTh[j] * dT[j];
+      denP += K * dT[j];
+    }
+    sum[0] += wgt * numC; sum[1] += wgt * denC;
+    sum[2] += wgt * numI; sum[3] += wgt * denI;
+    sum[4] += wgt * numP; sum[5] += wgt * denP;
+    sum[6] += wgt;
+  }
+  for (int q = 0; q < 6; ++q) out[q] = sum[q] / sum[6];
+  double Cd = out[1] != 0.0 ? out[0] / out[1] : 0.0;
+  if (!(Cd > 0.0)) Cd = 0.0;
+  double CI = out[3] != 0.0 ? out[2] / out[3] : 0.0;
+  if (!(CI > 0.0)) CI = 0.0;
+  double Pr = out[5] != 0.0 ? Cd * out[4] / out[5] : 0.0;
+  if (!(Pr > 0.0) || !(Pr < 1e300)) Pr = P->Pr_sgs;
+  out[6] = Cd; out[7] = CI; out[8] = Pr;
+  free(uh);
+  free(fh);
+  free(f);
+}
+
+void orc_test_filter(int ni, int nj, int nk, const int periodic[3],
+                     const double *f, double *out) {
+  grid_t g = make_grid(ni, nj, nk, periodic);
+  test_filter(&g, f, out);
+}
+
+void orc_dynamic_coefficients(const orc_params *P, int ni, int nj, int nk,
+                              const double *Q, const double *M, double out[9]) {
+  state_t S;
+  memset(&S, 0, sizeof(S));
+  S.P = P;
+  S.g = make_grid(ni, nj, nk, P->periodic);
+  S.Q = Q; S.M = M;
+  state_alloc(&S);
+  node_primitives(&S);
+  dynamic_procedure(P, &S.g, Q, M, S.u, S.v, S.w, S.T, out);
+  state_free(&S);
+}
+
 /* Effective viscosity/conductivity (Sec. "Large Eddy Simulation Filtering",
  * "Subgrid Scale Modeling").  Reading A6: Smagorinsky is
  * mu_sgs = rho (Cs Delta)^2 |S| (the printed (rho Cs Delta)^2 squares rho),
@@ -522,6 +713,9 @@ void orc_mu_eff(const orc_params *P, int ni, int nj, int nk, const double *Q,
   node_primitives(&S);
   size_t N = S.g.N;
   double gm1 = P->gamma - 1.0;
+  double dyn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (P->sgs_model == 3)
+    dynamic_procedure(P, &S.g, Q, M, S.u, S.v, S.w, S.T, dyn);
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < (long)N; ++n) {
     int c[3];
@@ -529,6 +723,20 @@ void orc_mu_eff(const orc_params *P, int ni, int nj, int nk, const double *Q,
     double rho = Q[n];
     double mu_l = mu_laminar(P, S.T[n]);
     double mu_s = 0.0;
+    if (P->sgs_model == 3) {
+      /* dynamic model: mu_sgs = C_ds rho Delta^2 |S| (Reading A26: C_ds
+       * takes the place of Cs^2, as the dimensions of Eq. av_cd show),
+       * kappa_sgs with the dynamic Pr_sgs, and the Yoshizawa isotropic part
+       * sigma_ll = 2 C_I rho Delta^2 |S|^2 (Eq. yoshizawa) */
+      double Sij[3][3];
+      double Smag = strain_at(&S.g, M, S.u, S.v, S.w, c, Sij);
+      double D2 = cbrt(M[9 * N + n]) * cbrt(M[9 * N + n]);
+      mu_s = dyn[6] * rho * D2 * Smag;
+      MK[n] = mu_l + mu_s;
+      MK[N + n] = mu_l / (gm1 * P->Pr) + mu_s / (gm1 * dyn[8]);
+      MK[2 * N + n] = 2.0 * dyn[7] * rho * D2 * Smag * Smag;
+      continue;
+    }
     if (P->sgs_model != 0) {
       const double *vel[3] = {S.u, S.v, S.w};
       double g[3][3]; /* g[i][c] = d u_i / d x_c */
@@ -688,6 +896,14 @@ static void interface_flux(const state_t *S, int d, const int ca[3],
   double txx = mu * (2.0 * gr[0][0] - (2.0 / 3.0) * div);
   double tyy = mu * (2.0 * gr[1][1] - (2.0 / 3.0) * div);
   double tzz = mu * (2.0 * gr[2][2] - (2.0 / 3.0) * div);
+  if (S->P->sgs_model == 3) {
+    /* the modelled isotropic SGS stress sigma_ll/3 delta_ij (Eq. yoshizawa)
+     * is subtracted from the resolved stress, at the interface mean */
+    double iso = 0.5 * (S->MK[2 * N + a] + S->MK[2 * N + b]) / 3.0;
+    txx -= iso;
+    tyy -= iso;
+    tzz -= iso;
+  }
   double txy = mu * (gr[0][1] + gr[1][0]);
   double txz = mu * (gr[0][2] + gr[2][0]);
   double tyz = mu * (gr[1][2] + gr[2][1]);
@@ -1021,7 +1237,7 @@ double orc_rk_step(const orc_params *P, int ni, int nj, int nk, double *Q,
                    const double *M, const double *xyz, double t) {
   grid_t g = make_grid(ni, nj, nk, P->periodic);
   size_t N = g.N;
-  double *MK = (double *)malloc(2 * N * sizeof(double));
+  double *MK = (double *)malloc(3 * N * sizeof(double));
   unsigned char *upd = (unsigned char *)malloc(N);
   for (size_t n = 0; n < N; ++n) {
     int c[3];

@@ -37,7 +37,9 @@ typedef struct {
   double force_width;/* radial width of the inflow forcing (0.05 D) */
   double St[4];      /* forcing Strouhal numbers */
   double amp[16];    /* forcing amplitudes a_{m f}, index m*4 + f */
-  int sgs_model;     /* 0 none, 1 Smagorinsky, 2 Vreman */
+  int sgs_model;     /* 0 none, 1 Smagorinsky, 2 Vreman, 3 dynamic
+                        Smagorinsky (MK then holds a third field,
+                        sigma_ll) */
   int periodic[3];   /* per direction xi, eta, zeta */
   int bc;            /* 0 non-periodic boundary nodes frozen, 1 jet BCs,
                         2 jet BCs with the characteristic entrance */
@@ -84,6 +86,14 @@ void orc_interface_flux(const orc_params *P, int ni, int nj, int nk,
 /* Global CFL time step: cfl * min 1/(lam_xi + lam_eta + lam_zeta). */
 double orc_dt(const orc_params *P, int ni, int nj, int nk, const double *Q,
               const double *M);
+/* Test filter of the dynamic model applied to the node field f. */
+void orc_test_filter(int ni, int nj, int nk, const int periodic[3],
+                     const double *f, double *out);
+/* Dynamic Smagorinsky procedure on state Q: out = {<num>, <den>} of C_ds,
+ * C_I and Pr_sgs/C_ds, then C_ds, C_I, Pr_sgs. */
+void orc_dynamic_coefficients(const orc_params *P, int ni, int nj, int nk,
+                              const double *Q, const double *M, double out[9]);
+
 /* Local time steps dtn[n] = cfl / (lam_xi + lam_eta + lam_zeta) at node n. */
 void orc_dt_local(const orc_params *P, int ni, int nj, int nk, const double *Q,
                   const double *M, double *dtn);

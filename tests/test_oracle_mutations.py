@@ -69,6 +69,17 @@ MUTATIONS = {
     "subsonic_jet_total_T": ("double Tt = 1.0 + 0.5 * gm1 * P->Mj * P->Mj;",
                              "double Tt = 1.0 + 0.5 * gm1 * P->Mj;",
                              ["test_subsonic_jet_characteristic_entrance"]),
+    "dynamic_trace_term": ("double numC = LS - Lkk * trS / 3.0;", "double numC = LS;",
+                           ["test_dynamic_procedure_pure_shear_and_dilatation"]),
+    "dynamic_test_width": ("Dh2 = 4.0 * D2;", "Dh2 = 2.0 * D2;",
+                           ["test_dynamic_procedure_linear_fields_closed_form"]),
+    "leonard_favre": ("L[i][j] = L[j][i] = fh[(5 + k) * N + n] - mh[i] * mh[j] / rh;",
+                      "L[i][j] = L[j][i] = fh[(5 + k) * N + n] - mh[i] * mh[j];",
+                      ["test_dynamic_procedure_linear_fields_closed_form"]),
+    "yoshizawa_sign": ("    txx -= iso;", "    txx += iso;",
+                       ["test_yoshizawa_isotropic_stress_in_the_residual"]),
+    "filter_faces": ("return off == 0 ? 1.0 : 0.0;", "return off == 0 ? 0.5 : 0.25;",
+                     ["test_test_filter_transfer_function_and_faces"]),
 }
 
 

@@ -273,7 +273,7 @@ def test_free_stream_preservation_jet_grid(orc, sgs):
 
 
 @pytest.mark.parametrize("wave", [0.0, 0.25])
-@pytest.mark.parametrize("sgs", [1, 2])
+@pytest.mark.parametrize("sgs", [1, 2, 3])
 def test_discrete_conservation_periodic_box(orc, wave, sgs):
     """Interface fluxes telescope: sum J^-1 Q is constant in a periodic box."""
     P = orc.params(periodic=(1, 1, 1), bc=0, sgs_model=sgs, Re=200.0, cfl=0.8)
@@ -559,6 +559,157 @@ def test_sgs_closed_forms(orc):
     assert np.allclose(MK[0], mu_l + mu_v, rtol=1e-12)
     # kappa split with the two Prandtl numbers
     assert np.allclose(MK[1], mu_l / (0.4 * 0.72) + mu_v / (0.4 * 0.9), rtol=1e-12)
+
+
+# ------------------------------------------------------- dynamic model
+
+def _linear_state(orc, n, h, G, g, U0=(0.2, -0.1, 0.05), rho0=1.1, T0=1.0):
+    xyz, _ = synth.box_grid(n, tuple(m * hh for m, hh in zip(n, h)))
+    X = xyz.reshape(3, -1)
+    prim = np.empty((5,) + n)
+    prim[0] = rho0
+    prim[1:4] = (G @ X).reshape((3,) + n) + np.asarray(U0)[:, None, None, None]
+    prim[4] = rho0 * (T0 + (g @ X).reshape(n)) / GAMMA
+    return xyz, prim
+
+
+def test_dynamic_procedure_linear_fields_closed_form(orc):
+    """Constant velocity gradient G and temperature gradient g, uniform
+    density, on a Cartesian grid of spacings h: every difference and filter
+    is exact, the test filter's variance along d is h_d^2/2, so with
+    Sigma = diag(h_d^2/2), D = (h_x h_y h_z)^(1/3) and Delta^ = 2 Delta:
+    L = rho G Sigma G^T, K = rho G Sigma g, S^ = S, and
+      <num C_ds> = rho [L:S/rho - tr(L/rho) tr S/3],
+      <den C_ds> = -6 D^2 rho |S| (S:S - (tr S)^2/3),
+      C_I = tr(G Sigma G^T)/(6 D^2 |S|^2),
+      Pr_sgs = C_ds (-3 D^2 |S| |g|^2)/(g . G Sigma g)
+    (an asymmetric G: a transposed index or a dropped trace term fails)."""
+    n, h = (9, 8, 7), (0.1, 0.13, 0.07)
+    G = 0.5 * np.array([[1.0, 0.3, -0.2], [0.1, 0.8, 0.4], [-0.3, 0.2, -2.1]])
+    g = np.array([0.3, -0.5, 0.8])
+    xyz, prim = _linear_state(orc, n, h, G, g)
+    P = orc.params(periodic=(0, 0, 0), bc=0, sgs_model=3)
+    M = orc.metrics(xyz, (0, 0, 0), None)
+    out = orc.dynamic_coefficients(P, orc.prim_to_cons(P, prim), M)
+    rho0 = 1.1
+    Sig = np.diag([hh * hh / 2 for hh in h])
+    S = 0.5 * (G + G.T)
+    Smag = math.sqrt(2 * (S * S).sum())
+    D2 = (h[0] * h[1] * h[2]) ** (2.0 / 3.0)
+    GSG, trS = G @ Sig @ G.T, np.trace(S)
+    expect = dict(numC=rho0 * ((GSG * S).sum() - np.trace(GSG) * trS / 3),
+                  denC=-6 * D2 * rho0 * Smag * ((S * S).sum() - trS ** 2 / 3),
+                  numI=rho0 * np.trace(GSG), denI=6 * D2 * rho0 * Smag ** 2,
+                  numP=-3 * D2 * rho0 * Smag * (g @ g), denP=rho0 * g @ (G @ Sig @ g))
+    expect["Cd"] = expect["numC"] / expect["denC"]
+    expect["CI"] = expect["numI"] / expect["denI"]
+    expect["Prt"] = expect["Cd"] * expect["numP"] / expect["denP"]
+    assert expect["Cd"] > 0 and expect["CI"] > 0 and expect["Prt"] > 0
+    for k, v in expect.items():
+        assert abs(out[k] - v) <= 1e-12 * abs(v), (k, out[k], v)
+
+
+def test_dynamic_procedure_pure_shear_and_dilatation(orc):
+    """A unidirectional linear shear has L:S = 0 (C_ds = 0); a pure
+    dilatation has no deviatoric part, so numerator and denominator of C_ds
+    both vanish: the model acts on the deviatoric strain only."""
+    n, h = (8, 9, 7), (0.1, 0.1, 0.1)
+    P = orc.params(periodic=(0, 0, 0), bc=0, sgs_model=3)
+    for G, both_zero in ((np.array([[0.0, 0.7, 0.0], [0, 0, 0], [0, 0, 0]]), False),
+                         (0.4 * np.eye(3), True)):
+        xyz, prim = _linear_state(orc, n, h, G, np.zeros(3))
+        out = orc.dynamic_coefficients(P, orc.prim_to_cons(P, prim), orc.metrics(xyz, (0, 0, 0)))
+        assert abs(out["numC"]) < 1e-15
+        assert out["Cd"] == 0.0
+        if both_zero:
+            assert abs(out["denC"]) < 1e-14
+        else:
+            assert out["denC"] < -1e-4
+
+
+def test_test_filter_transfer_function_and_faces(orc):
+    """Periodic: a Fourier mode is multiplied by prod_d cos^2(pi m_d/n_d).
+    Open directions: linear fields pass unchanged (the face nodes filter only
+    along their own face)."""
+    n = (12, 10, 8)
+    I = np.meshgrid(*[np.arange(m, dtype=float) for m in n], indexing="ij")
+    m = (2, 3, 1)
+    f = np.cos(2 * np.pi * m[0] * I[0] / n[0] + 0.3) * np.cos(2 * np.pi * m[1] * I[1] / n[1]) \
+        * np.sin(2 * np.pi * m[2] * I[2] / n[2] + 1.1)
+    gain = np.prod([math.cos(math.pi * m[d] / n[d]) ** 2 for d in range(3)])
+    assert np.abs(orc.test_filter(f, (1, 1, 1)) - gain * f).max() < 1e-14
+    lin = 0.3 + 1.7 * I[0] - 0.4 * I[1] + 0.9 * I[2]
+    assert np.abs(orc.test_filter(lin, (0, 0, 0)) - lin).max() < 1e-13
+    q = I[1] ** 2  # curvature along eta: + h^2/2 inside, unchanged on the eta faces
+    fq = orc.test_filter(q, (0, 0, 0))
+    assert np.abs(fq[:, 1:-1] - (q[:, 1:-1] + 0.5)).max() < 1e-13
+    assert np.abs(fq[:, [0, -1]] - q[:, [0, -1]]).max() < 1e-13
+
+
+def test_dynamic_procedure_invariances(orc):
+    """On a non-separable periodic grid with a smooth 3-D state: adding a
+    uniform velocity changes nothing (Galilean invariance of L, K and the
+    strains); scaling the velocity by s scales the C_ds terms by s^3, the C_I
+    terms by s^2 and the Pr_sgs terms by s, leaving the coefficients; a
+    uniform temperature shift changes nothing."""
+    Lb = (1.0, 1.2, 0.9)
+    xyz, shift = synth.box_grid((12, 10, 9), Lb, wave=0.25)
+    P = orc.params(periodic=(1, 1, 1), bc=0, sgs_model=3)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    prim = synth.smooth_periodic_prim(xyz, Lb, amp=0.3, seed=4)
+    base = orc.dynamic_coefficients(P, orc.prim_to_cons(P, prim), M)
+    assert base["Cd"] > 0 and base["denP"] != 0
+    moved = prim.copy()
+    moved[1:4] += np.array([0.7, -0.4, 0.25])[:, None, None, None]
+    gal = orc.dynamic_coefficients(P, orc.prim_to_cons(P, moved), M)
+    for k in base:
+        assert abs(gal[k] - base[k]) <= 1e-11 * max(abs(base[k]), 1e-300), k
+    s = 1.7
+    scaled = prim.copy()
+    scaled[1:4] *= s
+    sc = orc.dynamic_coefficients(P, orc.prim_to_cons(P, scaled), M)
+    for k, e in (("numC", 3), ("denC", 3), ("numI", 2), ("denI", 2), ("numP", 1), ("denP", 1)):
+        assert abs(sc[k] - s ** e * base[k]) <= 1e-12 * abs(s ** e * base[k]), k
+    for k in ("Cd", "CI", "Prt"):
+        assert abs(sc[k] - base[k]) <= 1e-12 * abs(base[k]), k
+    hot = prim.copy()
+    hot[4] = prim[4] + 0.3 * prim[0] / GAMMA  # T + 0.3 at the same rho
+    ht = orc.dynamic_coefficients(P, orc.prim_to_cons(P, hot), M)
+    for k in base:
+        assert abs(ht[k] - base[k]) <= 1e-11 * max(abs(base[k]), 1e-300), k
+
+
+def test_yoshizawa_isotropic_stress_in_the_residual(orc):
+    """The isotropic SGS stress sigma_ll/3 enters the interface flux like a
+    pressure: on a uniform Cartesian periodic grid the residual changes by
+    A_d (s_{+1/2} - s_{-1/2}) in momentum d and by sum_d A_d ((s u_d)_{+1/2} -
+    (s u_d)_{-1/2}) in energy, s = sigma/3 and u_d at the interface means,
+    A_d = J^-1/h_d."""
+    n, h = (10, 9, 8), (0.1, 0.15, 0.2)
+    Lb = tuple(m * hh for m, hh in zip(n, h))
+    xyz, shift = synth.box_grid(n, Lb)
+    P = orc.params(periodic=(1, 1, 1), bc=0, sgs_model=3, k2=0.0, k4=0.0)
+    M = orc.metrics(xyz, (1, 1, 1), shift)
+    prim = synth.smooth_periodic_prim(xyz, Lb, amp=0.2, seed=1)
+    Q = orc.prim_to_cons(P, prim)
+    rng = np.random.default_rng(3)
+    MK0 = np.concatenate([orc.mu_eff(orc.params(periodic=(1, 1, 1), bc=0), Q, M),
+                          np.zeros((1,) + n)])
+    MK1 = MK0.copy()
+    MK1[2] = 0.05 * rng.random(n)
+    dR = orc.rhs(P, Q, M, MK1) - orc.rhs(P, Q, M, MK0)
+    s = MK1[2] / 3.0
+    Jinv = h[0] * h[1] * h[2]
+    vel = prim[1:4]
+    expect = np.zeros((5,) + n)
+    for d in range(3):
+        A = Jinv / h[d]
+        sp = 0.5 * (s + np.roll(s, -1, axis=d))  # interface (n, n + e_d)
+        up = 0.5 * (vel[d] + np.roll(vel[d], -1, axis=d))
+        expect[1 + d] += A * (sp - np.roll(sp, 1, axis=d))
+        fe = sp * up
+        expect[4] += A * (fe - np.roll(fe, 1, axis=d))
+    assert np.abs(dR - expect).max() < 1e-15 * 50
 
 
 def test_sutherland_law(orc):
