@@ -440,6 +440,55 @@ def large_leg(lj, torch, local, hbm_peak, warmup):
     return out
 
 
+def extensions_leg(lj, torch, local, xyz, shape, base_ms, steps=10, warmup=2):
+    """Cost of the options beyond the configured workload, on the same grid:
+    the dynamic SGS model (FP64), local time steps and the characteristic
+    entrance (mixed), and the conservative metric setup."""
+    stream = torch.cuda.current_stream()
+    out = {"steps": steps}
+    cases = (("fp64_dynamic", dict(precision=lj.PREC_FP64, sgs_model=lj.SGS_DYNAMIC)),
+             ("mixed_local_dt", dict(precision=lj.PREC_MIXED, sgs_model=lj.SGS_SMAGORINSKY,
+                                     dt_mode=lj.DT_LOCAL)),
+             ("mixed_char_bc", dict(precision=lj.PREC_MIXED, sgs_model=lj.SGS_SMAGORINSKY,
+                                    bc=lj.BC_JET_CHAR)))
+    for name, kw in cases:
+        ctx = lj.Context(lj.make_params(**kw), shape, f"cuda:{local}")
+        ctx.les_set_grid(xyz)
+        Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+        ctx.les_init_jet(xyz, 0, 1e-3, Q)
+        ctx.les_run_n_steps(warmup, Q)
+        ctx.les_profile(True)
+        ms, diag = time_steps(lj, torch, ctx, Q, steps, stream)
+        prof = ctx.les_profile_read()
+        ctx.les_profile(False)
+        rec = {"ms_per_step": ms / steps, "status": diag.status,
+               "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]}}
+        ref = base_ms["fp64" if kw["precision"] == lj.PREC_FP64 else "mixed"]
+        rec["vs_configured_step"] = rec["ms_per_step"] / ref
+        if name == "fp64_dynamic":
+            co = ctx.les_dynamic_coefficients(Q)
+            rec["coefficients"] = {k: co[k] for k in ("Cd", "CI", "Prt")}
+        out[name] = rec
+        del ctx, Q
+        torch.cuda.empty_cache()
+    setup = {}
+    for name, form in (("cross", lj.METRIC_CROSS), ("conservative", lj.METRIC_CONSERVATIVE)):
+        ctx = lj.Context(lj.make_params(precision=lj.PREC_MIXED, metric_form=form), shape,
+                         f"cuda:{local}")
+        ctx.les_set_grid(xyz)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.les_set_grid(xyz)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        setup[name] = e0.elapsed_time(e1)
+        del ctx
+    out["set_grid_ms"] = setup
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -517,6 +566,10 @@ def run_ours(args, world, rank, local):
                for c, nm in ((0, "rho"), (1, "rho_u"), (4, "rho_E"))}
         err["steps"] = args.accuracy_steps
 
+    ext = None
+    if not args.no_extensions and world == 1:
+        base = {k: results[k]["ms"] / args.steps for k in ("mixed", "fp64")}
+        ext = extensions_leg(lj, torch, local, xyz, shape, base)
     adj = None
     if not args.no_adjoint:
         adj = adjoint_leg(lj, torch, local)
@@ -611,6 +664,7 @@ def run_ours(args, world, rank, local):
         "mixed_error_vs_fp64": err,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in mixed["prof"].items() if v[1]},
         "kernel_ms_per_step_fp64": {k: v[0] / args.steps for k, v in fp64["prof"].items() if v[1]},
+        "extensions": ext,
         "adjoint_fwd_ratio": adj["ratio"] if adj else None,
         "adjoint": adj,
         "large": large,
@@ -625,8 +679,9 @@ def run_ours(args, world, rank, local):
 
 def run_profile_case(which: str):
     """Small case for ncu captures: 96 x 160 x 128 jet (1.97M points, state
-    and metrics above the 129 MB L2), two full steps, one precision; or the
-    adjoint window on 96 x 96 x 128 (10 steps, checkpoint every 5)."""
+    and metrics above the 129 MB L2), two full steps, one precision (the
+    dynamic case: FP64 with the dynamic SGS model); or the adjoint window on
+    96 x 96 x 128 (10 steps, checkpoint every 5)."""
     import numpy as np
     import torch
 
@@ -651,8 +706,9 @@ def run_profile_case(which: str):
               f"launches={ctx.les_launch_count()}")
         return 0
     prec = lj.PREC_MIXED if which == "mixed" else lj.PREC_FP64
+    sgs = lj.SGS_DYNAMIC if which == "dynamic" else lj.SGS_SMAGORINSKY
     shape = (96, 160, 128)
-    ctx = lj.Context(lj.make_params(sgs_model=lj.SGS_SMAGORINSKY, precision=prec), shape)
+    ctx = lj.Context(lj.make_params(sgs_model=sgs, precision=prec), shape)
     xyz = torch.from_numpy(lj.synth.jet_grid(*shape)).cuda()
     ctx.les_set_grid(xyz)
     Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
@@ -672,9 +728,11 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip the dynamic-SGS / local-step / entrance / metric-form timings")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 1.02e9-point compact mixed leg")
-    ap.add_argument("--profile-case", choices=("fp64", "mixed", "adjoint"), default=None,
+    ap.add_argument("--profile-case", choices=("fp64", "mixed", "adjoint", "dynamic"), default=None,
                     help="run the small ncu case (two steps) and exit")
     args = ap.parse_args()
     if args.profile_case:

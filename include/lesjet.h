@@ -46,7 +46,7 @@ enum {
   LES_ERR_STATE = -7        /* call order violated (e.g. no grid set) */
 };
 
-enum { LES_SGS_NONE = 0, LES_SGS_SMAGORINSKY = 1, LES_SGS_VREMAN = 2 };
+enum { LES_SGS_NONE = 0, LES_SGS_SMAGORINSKY = 1, LES_SGS_VREMAN = 2, LES_SGS_DYNAMIC = 3 };
 /* LES_PREC_MIXED_COMPACT is the mixed form without the FP64 copy of the
  * metrics (80 bytes per point less): metrics are computed in FP64 and stored
  * once rounded to FP32, which the boundary conditions and the totals then
@@ -77,7 +77,10 @@ typedef struct les_params {
   double force_width; /* radial width of the inflow forcing */
   double St[4];       /* forcing Strouhal numbers */
   double amp[16];     /* forcing amplitudes a_{m f}, index m*4 + f */
-  int sgs_model;      /* LES_SGS_* */
+  int sgs_model;      /* LES_SGS_NONE, LES_SGS_SMAGORINSKY, LES_SGS_VREMAN,
+                         or LES_SGS_DYNAMIC (dynamic Smagorinsky with the
+                         Yoshizawa isotropic part and a dynamic Pr_sgs;
+                         FP64 form, chosen at les_create) */
   int periodic[3];    /* per direction xi, eta, zeta: 1 = periodic */
   int bc;             /* LES_BC_FROZEN (non-periodic faces never change),
                          LES_BC_JET (Dirichlet jet state over the whole
@@ -150,10 +153,14 @@ int les_grid_jet(int ni, int nj, int nk, const les_jet_grid *grid, double *xyz,
 
 /* Last error message of this context (never NULL; "" when none). */
 const char *les_last_error(const les_ctx *ctx);
-/* Replace the parameters (same grid and precision), e.g. new forcing. */
+/* Replace the parameters (same grid and precision), e.g. new forcing.
+ * dt_mode LES_DT_LOCAL and sgs_model LES_SGS_DYNAMIC are accepted only by a
+ * context created with them (their data live in the workspace). */
 int les_set_params(les_ctx *ctx, const les_params *p);
 
-/* Bytes of the caller-owned device workspace this context needs. */
+/* Bytes of the caller-owned device workspace this context needs: about
+ * 360 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
+ * per point with LES_DT_LOCAL and 248 B per point with LES_SGS_DYNAMIC. */
 size_t les_workspace_bytes(const les_ctx *ctx);
 
 /* Bind the workspace and compute the Jacobian and the nine metric terms on
@@ -181,8 +188,23 @@ int les_init_jet(les_ctx *ctx, const double *xyz, uint64_t seed,
 
 /* Effective viscosity/conductivity of state Q into MK (device [2][N] FP64):
  * Sutherland laminar part times Mj/Re plus the SGS model (Sec. "Subgrid
- * Scale Modeling").  Asynchronous. */
+ * Scale Modeling").  With LES_SGS_DYNAMIC, MK is [3][N]: the third field is
+ * the Yoshizawa isotropic SGS stress sigma_ll (Eq. yoshizawa).
+ * Asynchronous. */
 int les_mu_eff(les_ctx *ctx, const double *Q, double *MK, les_stream_t stream);
+
+/* The dynamic Smagorinsky procedure (Sec. "Dynamic Smagorinsky Model",
+ * Eqs. av_ci, av_cd, av_Pr_sgs) on state Q (device [5][N] FP64), into
+ * out[9] (host): the J^-1-weighted interior means of the numerator and
+ * denominator of C_ds, of C_I and of Pr_sgs/C_ds, then C_ds, C_I and
+ * Pr_sgs as the stepping calls use them (C_ds, C_I clipped at 0; Pr_sgs
+ * the configured value when the dynamic one is not positive).  Test filter:
+ * (1/4, 1/2, 1/4) along each direction, width 2 Delta, identity along a
+ * non-periodic direction at its faces.  Needs sgs_model LES_SGS_DYNAMIC at
+ * les_create (FP64 form only: the workspace then holds 30 scratch fields
+ * and a third viscosity field).  SYNCHRONISES the stream. */
+int les_dynamic_coefficients(les_ctx *ctx, const double *Q, double out[9],
+                             les_stream_t stream);
 
 /* Residual RHS of Eq. spatial_discret for state Q into R (device [5][N]
  * FP64): interior nodes get sum_d (F_{+1/2} - F_{-1/2}) with F = centred

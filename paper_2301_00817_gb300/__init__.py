@@ -26,7 +26,7 @@ LES_ERR_NONFINITE = -5
 LES_ERR_UNSUPPORTED = -6
 LES_ERR_STATE = -7
 
-SGS_NONE, SGS_SMAGORINSKY, SGS_VREMAN = 0, 1, 2
+SGS_NONE, SGS_SMAGORINSKY, SGS_VREMAN, SGS_DYNAMIC = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED, PREC_MIXED_COMPACT = 0, 1, 2
 BC_FROZEN, BC_JET, BC_JET_CHAR = 0, 1, 2
 DT_CFL, DT_FIXED, DT_LOCAL = 0, 1, 2
@@ -128,6 +128,8 @@ def load_library(path: str = LIB_PATH):
     lib.les_profile_name.argtypes = [i]
     lib.les_profile_name.restype = C.c_char_p
     lib.les_measure_fma_peak.argtypes = [i, C.POINTER(d), vp]
+    lib.les_dynamic_coefficients.argtypes = [vp, vp, C.POINTER(d), vp]
+    lib.les_dynamic_coefficients.restype = C.c_int
     lib.les_grid_jet.argtypes = [i, i, i, C.POINTER(LesJetGrid), vp, vp]
     lib.les_grid_jet.restype = C.c_int
     lib.les_surface_functional.argtypes = [vp, vp, i, d, C.POINTER(d), vp]
@@ -251,6 +253,14 @@ class Context:
 
     def les_mu_eff(self, Q, MK, stream=None):
         self._check(self.lib.les_mu_eff(self.h, _ptr(Q), _ptr(MK), _stream(stream)))
+
+    def les_dynamic_coefficients(self, Q, stream=None) -> dict:
+        """The dynamic SGS procedure on Q (les_dynamic_coefficients): the six
+        averaged terms and C_ds, C_I, Pr_sgs."""
+        out = (C.c_double * 9)()
+        self._check(self.lib.les_dynamic_coefficients(self.h, _ptr(Q), out, _stream(stream)))
+        keys = ("numC", "denC", "numI", "denI", "numP", "denP", "Cd", "CI", "Prt")
+        return dict(zip(keys, list(out)))
 
     def les_rhs(self, Q, R, stream=None):
         self._check(self.lib.les_rhs(self.h, _ptr(Q), _ptr(R), _stream(stream)))

@@ -38,9 +38,10 @@ struct les_ctx {
   Grid g;
   // workspace layout (byte offsets, 256-byte aligned)
   size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_hi, off_lo, off_node, off_flux, off_rth,
-      off_sc, off_part, off_dtl;
+      off_sc, off_part, off_dtl, off_dyn;
   size_t total;
   bool local_dt;  // the workspace holds per-node steps (dt_mode LOCAL at creation)
+  bool dyn_ws;    // the workspace holds the dynamic SGS scratch (sgs DYNAMIC at creation)
   char* ws;
   bool grid_set;
   std::string err;
@@ -113,8 +114,8 @@ int validate_params(const les_params* p, std::string& why) {
     why = "gamma > 1, Pr, Pr_sgs, Mj, T_ref > 0 and k2, k4, Cs >= 0 are required";
     return LES_ERR_INVALID_ARG;
   }
-  if (p->sgs_model < 0 || p->sgs_model > 2) {
-    why = "sgs_model must be LES_SGS_NONE, LES_SGS_SMAGORINSKY or LES_SGS_VREMAN";
+  if (p->sgs_model < 0 || p->sgs_model > 3) {
+    why = "sgs_model must be LES_SGS_NONE, LES_SGS_SMAGORINSKY, LES_SGS_VREMAN or LES_SGS_DYNAMIC";
     return LES_ERR_INVALID_ARG;
   }
   if (p->precision != LES_PREC_FP64 && p->precision != LES_PREC_MIXED &&
@@ -156,7 +157,8 @@ void layout(les_ctx* c) {
   size_t o = 0;
   c->off_m64 = o; o = align256(o + (m64 ? 10 * N * sizeof(double) : 0));
   c->off_m32 = o; o = align256(o + (mixed ? 10 * N * sizeof(float) : 0));
-  c->off_mk = o; o = align256(o + 2 * N * rs);
+  c->dyn_ws = c->p.sgs_model == LES_SGS_DYNAMIC;
+  c->off_mk = o; o = align256(o + (c->dyn_ws ? 3 : 2) * N * rs);
   c->off_sa = o; o = align256(o + 5 * N * rs);
   c->off_sb = o; o = align256(o + 5 * N * rs);
   c->off_hi = o; o = align256(o + (mixed ? 5 * N * sizeof(float) : 0));
@@ -165,7 +167,8 @@ void layout(les_ctx* c) {
   c->off_flux = o; o = align256(o + (mixed ? 0 : 15 * N * sizeof(double)));
   c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
   c->off_sc = o; o = align256(o + sizeof(DevScalars));
-  c->off_part = o; o = align256(o + 5 * (size_t)lesjet::kMaxPartials * sizeof(double));
+  c->off_part = o; o = align256(o + 8 * (size_t)lesjet::kMaxPartials * sizeof(double));
+  c->off_dyn = o; o = align256(o + (c->dyn_ws ? 30 * N * sizeof(double) : 0));
   c->off_dtl = o; o = align256(o + (c->p.dt_mode == LES_DT_LOCAL ? N * rs : 0));
   c->local_dt = c->p.dt_mode == LES_DT_LOCAL;
   c->total = o;
@@ -199,6 +202,7 @@ lesjet::StageIO64 io64(les_ctx* c, const double* Qin) {
   io.partials = at<double>(c, c->off_part);
   io.sc = at<DevScalars>(c, c->off_sc);
   io.dtl = c->p.dt_mode == LES_DT_LOCAL ? at<double>(c, c->off_dtl) : nullptr;
+  io.dyn = c->dyn_ws ? at<double>(c, c->off_dyn) : nullptr;
   return io;
 }
 
@@ -334,6 +338,7 @@ int les_create(const les_params* p, int ni, int nj, int nk, les_ctx** out) {
   if (N >= (1LL << 40)) return LES_ERR_SHAPE;
   // the mixed form indexes each field with 32 bits
   if (p->precision != LES_PREC_FP64 && N >= (1LL << 31)) return LES_ERR_SHAPE;
+  if (p->precision != LES_PREC_FP64 && p->sgs_model == LES_SGS_DYNAMIC) return LES_ERR_UNSUPPORTED;
   les_ctx* c = new (std::nothrow) les_ctx();
   if (!c) return LES_ERR_INVALID_ARG;
   c->p = *p;
@@ -379,6 +384,8 @@ int les_set_params(les_ctx* c, const les_params* p) {
   if (p->precision != c->p.precision) return fail(c, LES_ERR_INVALID_ARG, "precision is fixed at creation");
   if (p->dt_mode == LES_DT_LOCAL && !c->local_dt)
     return fail(c, LES_ERR_INVALID_ARG, "local time stepping must be chosen at creation");
+  if (p->sgs_model == LES_SGS_DYNAMIC && !c->dyn_ws)
+    return fail(c, LES_ERR_INVALID_ARG, "the dynamic SGS model must be chosen at creation");
   for (int d = 0; d < 3; ++d)
     if ((p->periodic[d] ? 1 : 0) != c->g.per[d])
       return fail(c, LES_ERR_INVALID_ARG, "periodicity is fixed at creation");
@@ -438,8 +445,27 @@ int les_mu_eff(les_ctx* c, const double* Q, double* MK, les_stream_t stream) {
     lesjet::launch_node64(c->g, c->p, io, false, L);
     lesjet::launch_mu64(c->g, c->p, io, L);
   }
-  lesjet::launch_mk_to_double(c->p.precision, c->g, c->ws + c->off_mk, MK, L);
+  lesjet::launch_mk_to_double(c->p.precision, c->g, c->ws + c->off_mk,
+                              c->p.sgs_model == LES_SGS_DYNAMIC ? 3 : 2, MK, L);
   return cuda_check(c, "les_mu_eff");
+}
+
+int les_dynamic_coefficients(les_ctx* c, const double* Q, double out[9], les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || !out) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  if (!c->dyn_ws)
+    return fail(c, LES_ERR_UNSUPPORTED, "the context was not created with LES_SGS_DYNAMIC");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  lesjet::StageIO64 io = io64(c, Q);
+  lesjet::launch_node64(c->g, c->p, io, false, L);
+  lesjet::launch_dynamic64(c->g, c->p, io, io.dyn, L);
+  DevScalars* sc = at<DevScalars>(c, c->off_sc);
+  cudaMemcpyAsync(out, sc->dyn, 9 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "les_dynamic_coefficients");
+  return cuda_check(c, "les_dynamic_coefficients");
 }
 
 int les_rhs(les_ctx* c, const double* Q, double* R, les_stream_t stream) {

@@ -1,0 +1,311 @@
+// dynamic.cu -- the dynamic Smagorinsky procedure (Sec. "Dynamic Smagorinsky
+// Model", Eqs. yoshizawa, av_ci, av_cd, av_Pr_sgs) for the FP64 form.
+//
+// Once per viscosity evaluation, from the node primitives of the state:
+//   k_dyn_products  per node: the 25 fields the test filter acts on (rho,
+//                   rho u_i, rho T, rho u_i u_j, rho|S| S_ij, rho|S| S_mm,
+//                   rho|S|^2, rho u_j T, rho|S| dT/dx_j);
+//   k_dyn_filter    the test filter of rho, rho u_i, rho T (the Favre
+//                   filtered velocity and temperature need them at the
+//                   neighbours of every node);
+//   k_dyn_sums      per interior node: the other 20 fields filtered on the
+//                   spot, the strain of the Favre-filtered velocity, the
+//                   Leonard-type terms, and the six J^-1-weighted sums of
+//                   the numerators and denominators; fixed-grid block
+//                   partials (deterministic);
+//   k_dyn_final     one block: fixed-order totals and the coefficients
+//                   C_ds, C_I (clipped at 0) and Pr_sgs (the configured
+//                   value when the dynamic one is not positive).
+// The viscosity pass (k_mu) then forms mu_sgs = C_ds rho Delta^2 |S|, the
+// dynamic kappa_sgs and the Yoshizawa sigma_ll = 2 C_I rho Delta^2 |S|^2.
+// Test filter: the (1/4, 1/2, 1/4) trapezoidal filter along each direction
+// (width 2 Delta), identity along a non-periodic direction at its faces.
+#include "stage64_kernels.cuh"
+
+namespace lesjet {
+
+namespace {
+
+constexpr int kDynFields = 25;
+constexpr int kDynSums = 7;  // six weighted sums and the sum of the weights
+
+// The 27 (index, weight) pairs of the test filter at node c; returns the
+// number of pairs with a non-zero weight.
+__device__ __forceinline__ int filter_stencil(const Grid& g, const int c[3], long long idx[27],
+                                              double wt[27]) {
+  int cm[3][3];
+  double w1[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int nd = g.n[d];
+    const bool face = !g.per[d] && (c[d] == 0 || c[d] == nd - 1);
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      int v = c[d] + o - 1;
+      v = v < 0 ? v + nd : (v >= nd ? v - nd : v);
+      cm[d][o] = v;
+      w1[d][o] = face ? (o == 1 ? 1.0 : 0.0) : (o == 1 ? 0.5 : 0.25);
+    }
+  }
+  int k = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int e = 0; e < 3; ++e) {
+        const double w = w1[0][a] * w1[1][b] * w1[2][e];
+        if (w == 0.0) continue;
+        idx[k] = ((long long)cm[0][a] * g.n[1] + cm[1][b]) * g.n[2] + cm[2][e];
+        wt[k] = w;
+        ++k;
+      }
+  return k;
+}
+
+// Cartesian gradient of a node field through the node's metrics.
+__device__ __forceinline__ void grad_of(const Grid& g, const double* __restrict__ M,
+                                        const double* __restrict__ f, long long n, const int c[3],
+                                        double out[3]) {
+  const long long N = g.N;
+  double dd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dd[d] = node_deriv(g, f, n, c, d);
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+    out[x] = M[x * N + n] * dd[0] + M[(3 + x) * N + n] * dd[1] + M[(6 + x) * N + n] * dd[2];
+}
+
+// Node-centred derivative along d of the Favre average Fh[q]/Fh[0].
+__device__ __forceinline__ double favre_deriv(const Grid& g, const double* __restrict__ Fh, int q,
+                                              long long n, const int c[3], int d) {
+  const long long N = g.N;
+  const long long s = g.stride[d];
+  const int nd = g.n[d];
+  auto f = [&](long long m) { return Fh[q * N + m] / Fh[m]; };
+  if (g.per[d]) {
+    const long long np = (c[d] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
+    const long long nm = (c[d] == 0) ? n + (long long)(nd - 1) * s : n - s;
+    return 0.5 * (f(np) - f(nm));
+  }
+  if (c[d] == 0) return 0.5 * (-3.0 * f(n) + 4.0 * f(n + s) - f(n + 2 * s));
+  if (c[d] == nd - 1) return 0.5 * (3.0 * f(n) - 4.0 * f(n - s) + f(n - 2 * s));
+  return 0.5 * (f(n + s) - f(n - s));
+}
+
+__device__ __forceinline__ void favre_grad(const Grid& g, const double* __restrict__ M,
+                                           const double* __restrict__ Fh, int q, long long n,
+                                           const int c[3], double out[3]) {
+  const long long N = g.N;
+  double dd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dd[d] = favre_deriv(g, Fh, q, n, c, d);
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+    out[x] = M[x * N + n] * dd[0] + M[(3 + x) * N + n] * dd[1] + M[(6 + x) * N + n] * dd[2];
+}
+
+// S_ij from a velocity gradient gr[i][x] = d u_i/d x_x; returns |S|.
+__device__ __forceinline__ double strain(const double gr[3][3], double S[3][3]) {
+  double ss = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      S[i][j] = 0.5 * (gr[i][j] + gr[j][i]);
+      ss += S[i][j] * S[i][j];
+    }
+  return sqrt(2.0 * ss);
+}
+
+__constant__ int kI6[6] = {0, 1, 2, 0, 0, 1};
+__constant__ int kJ6[6] = {0, 1, 2, 1, 2, 2};
+
+__global__ void __launch_bounds__(256) k_dyn_products(Grid g, const double* __restrict__ Q,
+                                                      const double* __restrict__ M,
+                                                      const double* __restrict__ node,
+                                                      double* __restrict__ D) {
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    const double rho = Q[n];
+    const double vel[3] = {node[n], node[N + n], node[2 * N + n]};
+    const double T = node[4 * N + n];
+    double gr[3][3], S[3][3], dT[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) grad_of(g, M, node + q * N, n, c, gr[q]);
+    grad_of(g, M, node + 4 * N, n, c, dT);
+    const double Sm = strain(gr, S);
+    D[n] = rho;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D[(1 + i) * N + n] = rho * vel[i];
+    D[4 * N + n] = rho * T;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int i = kI6[k], j = kJ6[k];
+      D[(5 + k) * N + n] = rho * vel[i] * vel[j];
+      D[(11 + k) * N + n] = rho * Sm * S[i][j];
+    }
+    D[17 * N + n] = rho * Sm * (S[0][0] + S[1][1] + S[2][2]);
+    D[18 * N + n] = rho * Sm * Sm;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      D[(19 + j) * N + n] = rho * vel[j] * T;
+      D[(22 + j) * N + n] = rho * Sm * dT[j];
+    }
+  }
+}
+
+// Filtered copies of fields [0, count) of D into F.
+__global__ void __launch_bounds__(256) k_dyn_filter(Grid g, const double* __restrict__ D, int count,
+                                                    double* __restrict__ F) {
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    long long idx[27];
+    double wt[27];
+    const int k = filter_stencil(g, c, idx, wt);
+    for (int q = 0; q < count; ++q) {
+      double s = 0.0;
+      for (int t = 0; t < k; ++t) s += wt[t] * D[q * N + idx[t]];
+      F[q * N + n] = s;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const double* __restrict__ M,
+                                                  const double* __restrict__ node,
+                                                  const double* __restrict__ D,
+                                                  const double* __restrict__ Fh,
+                                                  double* __restrict__ partials) {
+  const long long N = g.N;
+  double acc[kDynSums] = {0, 0, 0, 0, 0, 0, 0};
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    if (!is_interior(g, c)) continue;
+    const double wgt = M[9 * N + n];
+    const double Delta = cbrt(M[9 * N + n]);
+    const double D2 = Delta * Delta, Dh2 = 4.0 * D2;
+    double gr[3][3], S[3][3], dT[3], grh[3][3], Sh[3][3], dTh[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) grad_of(g, M, node + q * N, n, c, gr[q]);
+    grad_of(g, M, node + 4 * N, n, c, dT);
+    strain(gr, S);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) favre_grad(g, M, Fh, 1 + q, n, c, grh[q]);
+    favre_grad(g, M, Fh, 4, n, c, dTh);
+    const double Shm = strain(grh, Sh);
+    // the other 20 fields, filtered at this node
+    long long idx[27];
+    double wt[27];
+    const int kk = filter_stencil(g, c, idx, wt);
+    double fh[kDynFields];
+#pragma unroll 1
+    for (int q = 5; q < kDynFields; ++q) {
+      double s = 0.0;
+      for (int t = 0; t < kk; ++t) s += wt[t] * D[q * N + idx[t]];
+      fh[q] = s;
+    }
+    const double rh = Fh[n];
+    const double mh[3] = {Fh[N + n], Fh[2 * N + n], Fh[3 * N + n]};
+    double L[3][3], Fs[3][3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int i = kI6[k], j = kJ6[k];
+      L[i][j] = L[j][i] = fh[5 + k] - mh[i] * mh[j] / rh;
+      Fs[i][j] = Fs[j][i] = fh[11 + k];
+    }
+    const double trS = S[0][0] + S[1][1] + S[2][2];
+    const double trSh = Sh[0][0] + Sh[1][1] + Sh[2][2];
+    double LS = 0.0, FS = 0.0, ShS = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        LS += L[i][j] * S[i][j];
+        FS += Fs[i][j] * S[i][j];
+        ShS += Sh[i][j] * S[i][j];
+      }
+    const double Lkk = L[0][0] + L[1][1] + L[2][2];
+    const double numC = LS - Lkk * trS / 3.0;
+    const double denC = 2.0 * D2 * (FS - fh[17] * trS / 3.0) -
+                        2.0 * Dh2 * (rh * Shm * ShS - rh * Shm * trSh * trS / 3.0);
+    const double denI = 2.0 * Dh2 * rh * Shm * Shm - 2.0 * D2 * fh[18];
+    double numP = 0.0, denP = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double K = fh[19 + j] - mh[j] * Fh[4 * N + n] / rh;
+      numP += D2 * fh[22 + j] * dT[j] - Dh2 * rh * Shm * dTh[j] * dT[j];
+      denP += K * dT[j];
+    }
+    acc[0] += wgt * numC;
+    acc[1] += wgt * denC;
+    acc[2] += wgt * Lkk;
+    acc[3] += wgt * denI;
+    acc[4] += wgt * numP;
+    acc[5] += wgt * denP;
+    acc[6] += wgt;
+  }
+  __shared__ double red[kDynSums][32];
+#pragma unroll
+  for (int q = 0; q < kDynSums; ++q)
+    for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < kDynSums; ++q) red[q][threadIdx.x >> 5] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < kDynSums; ++q) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[q][threadIdx.x] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (threadIdx.x == 0) partials[q * kRedBlocks + blockIdx.x] = v;
+    }
+  }
+}
+
+// One block of kDynSums warps: warp q totals partial array q in a fixed order.
+__global__ void k_dyn_final(const double* __restrict__ partials, double pr_default,
+                            DevScalars* __restrict__ sc) {
+  __shared__ double tot[kDynSums];
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (q < kDynSums) {
+    double v = 0.0;
+    for (int b = lane; b < kRedBlocks; b += 32) v += partials[q * kRedBlocks + b];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) tot[q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double* out = sc->dyn;
+    for (int k = 0; k < 6; ++k) out[k] = tot[k] / tot[6];
+    double Cd = out[1] != 0.0 ? out[0] / out[1] : 0.0;
+    if (!(Cd > 0.0)) Cd = 0.0;
+    double CI = out[3] != 0.0 ? out[2] / out[3] : 0.0;
+    if (!(CI > 0.0)) CI = 0.0;
+    double Pr = out[5] != 0.0 ? Cd * out[4] / out[5] : 0.0;
+    if (!(Pr > 0.0) || !(Pr < 1e300)) Pr = pr_default;
+    out[6] = Cd;
+    out[7] = CI;
+    out[8] = Pr;
+  }
+}
+
+}  // namespace
+
+void launch_dynamic64(const Grid& g, const les_params& p, const StageIO64& io, double* scratch,
+                      const Launch& L) {
+  const int th = 256, nb = blocks_for(g.N, th);
+  double* D = scratch;
+  double* Fh = scratch + (long long)kDynFields * g.N;
+  k_dyn_products<<<nb, th, 0, L.s>>>(g, io.Qin, io.M, io.node, D);
+  k_dyn_filter<<<nb, th, 0, L.s>>>(g, D, 5, Fh);
+  k_dyn_sums<<<kRedBlocks, kRedThreads, 0, L.s>>>(g, io.M, io.node, D, Fh, io.partials);
+  k_dyn_final<<<1, 32 * kDynSums, 0, L.s>>>(io.partials, p.Pr_sgs, io.sc);
+  *L.counter += 4;
+}
+
+}  // namespace lesjet

@@ -38,6 +38,7 @@ struct DevScalars {
   int status;        // LES_OK or LES_ERR_NONFINITE (sticky)
   int steps;
   double totals[5];
+  double dyn[9];     // dynamic SGS procedure: 6 averaged terms, C_ds, C_I, Pr_sgs
 };
 
 constexpr int kRedBlocks = 1216;   // 152 SMs x 8: fixed, so reductions are

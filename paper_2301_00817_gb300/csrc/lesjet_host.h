@@ -26,7 +26,7 @@ void launch_init_jet(const Grid& g, const double* xyz, uint64_t seed, double noi
 // stage.cu
 void launch_dt_finalize(const les_params& p, double* partials, DevScalars* sc, int advance,
                         const Launch& L);
-void launch_mk_to_double(int precision, const Grid& g, const void* mk, double* out,
+void launch_mk_to_double(int precision, const Grid& g, const void* mk, int fields, double* out,
                          const Launch& L);
 
 // stage64.cu (FP64 form): node, viscosity, per-direction flux and update
@@ -40,10 +40,15 @@ struct StageIO64 {
   double* partials;    // [kRedBlocks] block minima (dt)
   DevScalars* sc;
   double* dtl = nullptr;  // [N] local steps (dt_mode LOCAL), else nullptr
+  double* dyn = nullptr;  // [30][N] scratch of the dynamic SGS procedure
 };
 void launch_node64(const Grid& g, const les_params& p, const StageIO64& io, bool with_dt,
                    const Launch& L);
 void launch_mu64(const Grid& g, const les_params& p, const StageIO64& io, const Launch& L);
+// the dynamic procedure on io.Qin (node quantities in io.node): coefficients
+// into io.sc->dyn; io.partials holds 7 x kRedBlocks block sums
+void launch_dynamic64(const Grid& g, const les_params& p, const StageIO64& io, double* scratch,
+                      const Launch& L);
 void launch_flux64(const Grid& g, const les_params& p, const StageIO64& io, int dir,
                    const Launch& L);
 // mode 0: RHS into out; 1: stage update into out; 2: last stage in place

@@ -57,9 +57,9 @@ void launch_dt_finalize(const les_params& p, double* partials, DevScalars* sc, i
   ++*L.counter;
 }
 
-void launch_mk_to_double(int precision, const Grid& g, const void* mk, double* out,
+void launch_mk_to_double(int precision, const Grid& g, const void* mk, int fields, double* out,
                          const Launch& L) {
-  const long long count = 2 * g.N;
+  const long long count = fields * g.N;
   if (precision == LES_PREC_FP64) {
     cudaMemcpyAsync(out, mk, count * sizeof(double), cudaMemcpyDeviceToDevice, L.s);
   } else {

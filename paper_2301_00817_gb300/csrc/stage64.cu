@@ -13,6 +13,8 @@
 // Each interface is computed once and read by its two nodes, so the scheme
 // telescopes exactly.  The kernels are written for a compute type R and are
 // instantiated for double only (the mixed form uses fused.cu).
+#include <cstddef>
+
 #include "stage64_kernels.cuh"
 
 namespace lesjet {
@@ -35,8 +37,14 @@ void launch_node64(const Grid& g, const les_params& p, const StageIO64& io, bool
 
 void launch_mu64(const Grid& g, const les_params& p, const StageIO64& io, const Launch& L) {
   const int th = 256, nb = blocks_for(g.N, th);
+  const double* dyn = nullptr;
+  if (p.sgs_model == LES_SGS_DYNAMIC) {
+    launch_dynamic64(g, p, io, io.dyn, L);
+    dyn = reinterpret_cast<const double*>(reinterpret_cast<const char*>(io.sc) +
+                                          offsetof(DevScalars, dyn));
+  }
   k_mu<double, double, double><<<nb, th, 0, L.s>>>(g, make_consts<double>(p), io.Qin, io.M,
-                                                    io.node, io.mk);
+                                                    io.node, io.mk, dyn);
   ++*L.counter;
 }
 

@@ -124,17 +124,22 @@ __device__ __forceinline__ R node_deriv(const Grid& g, const R* __restrict__ f, 
 // mu_eff = (Mj/Re) T^1.5 (1+S)/(T+S) + mu_sgs; kappa_eff = mu_lam/((g-1)Pr)
 // + mu_sgs/((g-1)Pr_sgs).  Smagorinsky: rho (Cs Delta)^2 |S|; Vreman:
 // rho c sqrt(B_beta/alpha:alpha) (0 when alpha:alpha = 0, B_beta >= 0);
-// Delta = (J^-1)^(1/3).
+// dynamic: C_ds rho Delta^2 |S| with the dynamic Pr_sgs and the Yoshizawa
+// sigma_ll = 2 C_I rho Delta^2 |S|^2 as a third field (coefficients dyn[6..8]
+// from the dynamic procedure); Delta = (J^-1)^(1/3).
 template <typename R, typename TQ, typename TM>
 __global__ void __launch_bounds__(256) k_mu(Grid g, Consts<R> K, const TQ* __restrict__ Q,
                                             const TM* __restrict__ M,
-                                            const R* __restrict__ node, R* __restrict__ mk) {
+                                            const R* __restrict__ node, R* __restrict__ mk,
+                                            const double* __restrict__ dyn = nullptr) {
   const long long N = g.N;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const R T = node[4 * N + n];
     const R mu_l = K.mu_scale * T * dev_sqrt(T) * (R(1) + K.S_suth) / (T + K.S_suth);
     R mu_s = R(0);
+    R kap_s = R(0);
+    bool kap_set = false;
     if (K.sgs != LES_SGS_NONE) {
       int c[3];
       decompose(g, n, c);
@@ -162,6 +167,21 @@ __global__ void __launch_bounds__(256) k_mu(Grid g, Consts<R> K, const TQ* __res
             ss += sij * sij;
           }
         mu_s = rho * (delta * delta) * K.cs2 * dev_sqrt(R(2) * ss);
+      } else if (K.sgs == LES_SGS_DYNAMIC) {
+        R ss = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const R sij = R(0.5) * (gr[i][j] + gr[j][i]);
+            ss += sij * sij;
+          }
+        const R smag = dev_sqrt(R(2) * ss);
+        const R d2 = delta * delta;
+        mu_s = R(dyn[6]) * rho * d2 * smag;
+        kap_s = mu_s / (K.gm1 * R(dyn[8]));
+        kap_set = true;
+        mk[2 * N + n] = R(2) * R(dyn[7]) * rho * d2 * smag * smag;
       } else {
         // alpha_ij = d u_j / d x_i = gr[j][i]; beta_ij = Delta^2 alpha_mi alpha_mj
         R aa = R(0);
@@ -183,7 +203,7 @@ __global__ void __launch_bounds__(256) k_mu(Grid g, Consts<R> K, const TQ* __res
       }
     }
     mk[n] = mu_l + mu_s;
-    mk[N + n] = mu_l * K.inv_gm1_pr + mu_s * K.inv_gm1_prs;
+    mk[N + n] = mu_l * K.inv_gm1_pr + (kap_set ? kap_s : mu_s * K.inv_gm1_prs);
   }
 }
 
@@ -326,9 +346,17 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
     const R kap = R(0.5) * (mk[N + a] + mk[N + b]);
     const R div = gr[0][0] + gr[1][1] + gr[2][2];
     const R two3 = R(2.0 / 3.0);
-    const R txx = mu * (R(2) * gr[0][0] - two3 * div);
-    const R tyy = mu * (R(2) * gr[1][1] - two3 * div);
-    const R tzz = mu * (R(2) * gr[2][2] - two3 * div);
+    R txx = mu * (R(2) * gr[0][0] - two3 * div);
+    R tyy = mu * (R(2) * gr[1][1] - two3 * div);
+    R tzz = mu * (R(2) * gr[2][2] - two3 * div);
+    if (K.sgs == LES_SGS_DYNAMIC) {
+      // the modelled isotropic SGS stress sigma_ll/3 (Eq. yoshizawa) at the
+      // interface mean, subtracted from the normal stresses
+      const R iso = R(0.5) * (mk[2 * N + a] + mk[2 * N + b]) / R(3);
+      txx -= iso;
+      tyy -= iso;
+      tzz -= iso;
+    }
     const R txy = mu * (gr[0][1] + gr[1][0]);
     const R txz = mu * (gr[0][2] + gr[2][0]);
     const R tyz = mu * (gr[1][2] + gr[2][1]);

@@ -182,6 +182,85 @@ def test_local_time_steps(orc, lj, torch, sgs):
         assert err <= 1e-5, (comp, err)
 
 
+def _dyn_case(orc, lj, case):
+    if case == "wavy_box":
+        shape, xyz, shift, kw = _grid(lj, "wavy_box")
+        P = oracle_params(orc, sgs_model=3, **kw)
+        prim = lj.synth.smooth_periodic_prim(xyz, (1.0, 1.3, 0.8), amp=0.3, seed=4)
+        return shape, xyz, shift, kw, orc.prim_to_cons(P, prim)
+    # the jet with smooth 3-D perturbations of every primitive
+    shape, xyz, shift, kw = _grid(lj, "jet_c1")
+    P = oracle_params(orc, sgs_model=3, **kw)
+    x, y, z = xyz
+    r, th = np.sqrt(y * y + z * z), np.arctan2(z, y)
+    bump = np.exp(-((r - 0.5) / 0.3) ** 2)
+    prim = np.empty((5,) + shape)
+    prim[0] = 1.0 + 0.1 * np.exp(-((r - 0.5) / 0.2) ** 2) * np.cos(2 * np.pi * x / 4)
+    prim[1] = 0.7 * (1.0 + np.tanh((0.5 - r) / 0.1)) * (1 + 0.2 * np.sin(2 * np.pi * x / 3)
+                                                         * np.cos(2 * th))
+    prim[2] = 0.2 * bump * np.sin(2 * np.pi * x / 5 + th)
+    prim[3] = 0.2 * bump * np.cos(2 * np.pi * x / 4 - 2 * th)
+    T = 1.0 + 0.2 * np.exp(-((r - 0.5) / 0.2) ** 2) * np.sin(2 * np.pi * x / 6)
+    prim[4] = prim[0] * T / 1.4
+    return shape, xyz, shift, kw, orc.prim_to_cons(P, prim)
+
+
+@pytest.mark.parametrize("case", ["wavy_box", "jet_c1"])
+def test_dynamic_model_coefficients_viscosity_and_residual(orc, lj, torch, case):
+    """The dynamic procedure on the device against the oracle: the six
+    averaged terms and C_ds, C_I, Pr_sgs; mu_eff, kappa_eff and sigma_ll;
+    the residual with the Yoshizawa term."""
+    shape, xyz, shift, kw, Q0 = _dyn_case(orc, lj, case)
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=lj.SGS_DYNAMIC, **kw)
+    P = oracle_params(orc, sgs_model=3, **kw)
+    M = orc.metrics(xyz, kw["periodic"], shift)
+    Qd = torch.from_numpy(Q0).cuda()
+    got = ctx.les_dynamic_coefficients(Qd)
+    want = orc.dynamic_coefficients(P, Q0, M)
+    assert want["CI"] > 0 and (want["Cd"] > 0 or case == "jet_c1")
+    # each mean is a sum of terms of either sign: rounding scales with the
+    # larger of the pair's two means
+    for num, den in (("numC", "denC"), ("numI", "denI"), ("numP", "denP")):
+        scale = max(abs(want[num]), abs(want[den]))
+        for k in (num, den):
+            assert abs(got[k] - want[k]) <= 1e-11 * scale, (k, got[k], want[k])
+    for k in ("Cd", "CI", "Prt"):
+        assert abs(got[k] - want[k]) <= 1e-10 * abs(want[k]), (k, got[k], want[k])
+    MK = torch.empty((3,) + shape, dtype=torch.float64, device="cuda")
+    ctx.les_mu_eff(Qd, MK)
+    MKo = orc.mu_eff(P, Q0, M)
+    for f in range(3):
+        assert np.abs(MK[f].cpu().numpy() - MKo[f]).max() <= 1e-11 * np.abs(MKo[f]).max(), f
+    R = torch.empty_like(Qd)
+    ctx.les_rhs(Qd, R)
+    assert rel_linf(R.cpu().numpy(), orc.rhs(P, Q0, M)) <= 1e-11
+
+
+def test_dynamic_model_steps(orc, lj, torch):
+    shape, xyz, shift, kw, Q0 = _dyn_case(orc, lj, "jet_c1")
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=lj.SGS_DYNAMIC, **kw)
+    P = oracle_params(orc, sgs_model=3, **kw)
+    M = orc.metrics(xyz, (0, 0, 1))
+    Qd = torch.from_numpy(Q0).cuda()
+    d1 = ctx.les_run_n_steps(1, Qd)
+    Q1, dt1 = orc.rk_step(P, Q0, M, xyz, 0.0)
+    assert abs(d1.dt - dt1) <= 1e-13 * dt1
+    assert rel_linf(Qd.cpu().numpy(), Q1) <= 1e-12
+    ctx.les_run_n_steps(9, Qd)
+    Q10, _ = orc.run(P, Q1, M, xyz, 9, t=dt1)
+    assert rel_linf(Qd.cpu().numpy(), Q10) <= 1e-11
+    # periodic box: the isotropic term telescopes like the rest
+    shape, xyz, shift, kw, Qb = _dyn_case(orc, lj, "wavy_box")
+    cb, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=lj.SGS_DYNAMIC, Re=300.0, **kw)
+    Qbd = torch.from_numpy(Qb).cuda()
+    tot0 = np.array(cb.les_totals(Qbd))
+    d = cb.les_run_n_steps(20, Qbd)
+    assert d.status == 0
+    Mb = orc.metrics(xyz, (1, 1, 1), shift)
+    scale = np.abs(orc.totals(np.abs(Qb), Mb)).max()
+    assert np.abs(np.array(d.totals) - tot0).max() / scale <= 1e-13
+
+
 def test_init_jet(orc, lj, torch):
     shape = C1
     xyz = lj.synth.jet_grid(*shape)
