@@ -378,7 +378,10 @@ __device__ __forceinline__ int wrap_fast(int v, int n, int per) {
   return (v >= 0 && v < n) ? v : -1;
 }
 
-template <int MODE>
+// LOCAL: node n advances with its own step P.dtl[n] (dt_mode LOCAL) in
+// place of the global one; a separate instantiation keeps the global-step
+// kernel free of the per-node load and its branch.
+template <int MODE, bool LOCAL>
 __global__ void __launch_bounds__(FNT, 1)
     k_stage_fused(const FusedGeom G, const Consts<float> K, const FusedPtrs P,
                   const DevScalars* __restrict__ sc, double alpha) {
@@ -782,7 +785,7 @@ __global__ void __launch_bounds__(FNT, 1)
       const int n = (ig * nj + jown) * nk + kown;
       if (iint && jint && kint) {
         const float Jn = __frcp_rn(sM[(s_c * 10 + 9) * PL1 + o1]);
-        const float an = (MODE != FMODE_RHS && P.dtl) ? (float)alpha * P.dtl[n] : adt;
+        const float an = LOCAL ? (float)alpha * P.dtl[n] : adt;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           float r = 0.f;
@@ -926,7 +929,7 @@ static int choose_nch(int ni, int tiles, int slots) {
   return best;
 }
 
-template <int MODE>
+template <int MODE, bool LOCAL>
 static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const FusedPtrs& P,
                            const DevScalars* sc, double alpha, const Launch& L) {
   FusedGeom G = G0;
@@ -938,7 +941,8 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-    cudaFuncSetAttribute(k_stage_fused<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_stage_fused<MODE, LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
@@ -950,7 +954,7 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
   }
   G.nch = choose_nch(G.ni, tk * tj, n_sm.load());  // one CTA per SM
   dim3 grid(tk, tj, G.nch);
-  k_stage_fused<MODE><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
+  k_stage_fused<MODE, LOCAL><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
   ++*L.counter;
 }
 
@@ -977,12 +981,17 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   for (int t = 0; t < 2; ++t) P.mk[t] = (const float*)io.mk + t * N;
   P.dtl = io.dtl;
   const Consts<float> K = fused_consts<float>(p);
+  const bool local = P.dtl != nullptr;
   if (mode == FMODE_RHS)
-    launch_stage_t<FMODE_RHS>(G, K, P, io.sc, alpha, L);
+    launch_stage_t<FMODE_RHS, false>(G, K, P, io.sc, alpha, L);
+  else if (mode == FMODE_STAGE && !local)
+    launch_stage_t<FMODE_STAGE, false>(G, K, P, io.sc, alpha, L);
   else if (mode == FMODE_STAGE)
-    launch_stage_t<FMODE_STAGE>(G, K, P, io.sc, alpha, L);
+    launch_stage_t<FMODE_STAGE, true>(G, K, P, io.sc, alpha, L);
+  else if (!local)
+    launch_stage_t<FMODE_LAST, false>(G, K, P, io.sc, alpha, L);
   else
-    launch_stage_t<FMODE_LAST>(G, K, P, io.sc, alpha, L);
+    launch_stage_t<FMODE_LAST, true>(G, K, P, io.sc, alpha, L);
 }
 
 void launch_split(long long count, const double* q, float* hi, float* lo, const Launch& L) {
