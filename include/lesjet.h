@@ -238,9 +238,13 @@ int les_rk_step(les_ctx *ctx, double *Q, les_stream_t stream);
 int les_run_n_steps(les_ctx *ctx, int n, double *Q, les_diag *diag,
                     les_stream_t stream);
 
-/* Same as les_run_n_steps for a HOST state: copies Q_host (pinned or
- * pageable host [5][N]) into the device buffer Q_dev, runs n steps and
- * copies the result back into Q_host.  SYNCHRONISES. */
+/* Same as les_run_n_steps for a HOST state Q_host (pinned or pageable host
+ * [5][N]); the result is written back into Q_host.  In the mixed forms,
+ * when Q_host is pinned memory mapped into the device's address space (as
+ * cudaHostAlloc/torch pin_memory gives), the split and join kernels read
+ * and write it directly over the host link and Q_dev is not touched;
+ * otherwise (and always in FP64) Q_host is copied into the device buffer
+ * Q_dev and back.  SYNCHRONISES. */
 int les_run_host(les_ctx *ctx, int n, double *Q_host, double *Q_dev,
                  les_diag *diag, les_stream_t stream);
 

@@ -548,20 +548,9 @@ int les_rk_step(les_ctx* c, double* Q, les_stream_t stream) {
   return cuda_check(c, "les_rk_step");
 }
 
-int les_run_n_steps(les_ctx* c, int n, double* Q, les_diag* diag, les_stream_t stream) {
-  int rc = ready(c);
-  if (rc != LES_OK) return rc;
-  if (!Q || n < 0) return fail(c, LES_ERR_INVALID_ARG, "null pointer or negative n");
-  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
-  cudaStream_t s = (cudaStream_t)stream;
-  lesjet::Launch L{s, &c->launches};
-  if (is_mixed(c)) split_state(c, Q, L);
-  for (int i = 0; i < n; ++i) rk_step(c, Q, s);
-  if (is_mixed(c)) join_state(c, Q, L);
-  {
-    ProfScope ps(c, PK_TOTALS, s);
-    totals(c, Q, L);
-  }
+// Totals and diagnostics after a run; reads the device scalars (synchronises).
+int finish_run(les_ctx* c, int n, les_diag* diag, cudaStream_t s) {
+  int rc;
   if ((rc = cuda_check(c, "les_run_n_steps")) != LES_OK) return rc;
   DevScalars h;
   if ((rc = read_scalars(c, &h, s)) != LES_OK) return rc;
@@ -576,6 +565,41 @@ int les_run_n_steps(les_ctx* c, int n, double* Q, les_diag* diag, les_stream_t s
   return LES_OK;
 }
 
+int les_run_n_steps(les_ctx* c, int n, double* Q, les_diag* diag, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || n < 0) return fail(c, LES_ERR_INVALID_ARG, "null pointer or negative n");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  if (is_mixed(c)) split_state(c, Q, L);
+  for (int i = 0; i < n; ++i) rk_step(c, Q, s);
+  if (is_mixed(c)) join_state(c, Q, L);
+  {
+    ProfScope ps(c, PK_TOTALS, s);
+    totals(c, Q, L);
+  }
+  return finish_run(c, n, diag, s);
+}
+
+// Device-side address of a host buffer when it is pinned host memory that
+// the driver maps into this device's address space; nullptr otherwise
+// (pageable or unknown memory goes through the staging copy).
+const void* mapped_host(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();  // clear the query's error state
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || (a.device >= 0 && a.device != dev)) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.devicePointer;
+}
+
 int les_run_host(les_ctx* c, int n, double* Q_host, double* Q_dev, les_diag* diag,
                  les_stream_t stream) {
   int rc = ready(c);
@@ -584,6 +608,30 @@ int les_run_host(les_ctx* c, int n, double* Q_host, double* Q_dev, les_diag* dia
   if (!aligned16(Q_dev)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = 5 * (size_t)c->g.N * sizeof(double);
+  if (is_mixed(c) && n >= 0) {
+    // mapped pinned memory: the split kernel reads the host state and the
+    // join kernel writes it back over the host link, with no FP64 staging
+    // copy (the float pair state lives in the workspace in between)
+    double* Qm = const_cast<double*>(static_cast<const double*>(mapped_host(Q_host)));
+    if (Qm && aligned16(Qm)) {
+      lesjet::Launch L{s, &c->launches};
+      split_state(c, Qm, L);
+      for (int i = 0; i < n; ++i) rk_step(c, Qm, s);
+      join_state(c, Qm, L);
+      {
+        ProfScope ps(c, PK_TOTALS, s);
+        if (has_m64(c))
+          lesjet::launch_totals_hl(c->g, at<float>(c, c->off_hi), at<float>(c, c->off_lo),
+                                   at<double>(c, c->off_m64), at<double>(c, c->off_part),
+                                   at<DevScalars>(c, c->off_sc), L);
+        else
+          lesjet::launch_totals_hl(c->g, at<float>(c, c->off_hi), at<float>(c, c->off_lo),
+                                   at<float>(c, c->off_m32), at<double>(c, c->off_part),
+                                   at<DevScalars>(c, c->off_sc), L);
+      }
+      return finish_run(c, n, diag, s);
+    }
+  }
   if (cudaMemcpyAsync(Q_dev, Q_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return cuda_check(c, "les_run_host upload");
   rc = les_run_n_steps(c, n, Q_dev, diag, stream);

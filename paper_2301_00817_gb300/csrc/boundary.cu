@@ -239,9 +239,21 @@ __global__ void k_bc_exit(Grid g, double gamma, const TM* __restrict__ M, Acc Q)
   }
 }
 
+// Read-only state views for the totals: FP64, or the float pair hi + lo
+// (the value the join writes, so both give the same totals).
+struct ViewD {
+  const double* q;
+  __device__ __forceinline__ double ld(long long i) const { return q[i]; }
+};
+struct ViewHL {
+  const float* hi;
+  const float* lo;
+  __device__ __forceinline__ double ld(long long i) const { return (double)hi[i] + (double)lo[i]; }
+};
+
 // Block partials of sum_n J^-1 Q_c (grid-stride order fixed by the launch).
-template <typename TM>
-__global__ void k_totals_partial(Grid g, const double* __restrict__ Q, const TM* __restrict__ M,
+template <class View, typename TM>
+__global__ void k_totals_partial(Grid g, View Q, const TM* __restrict__ M,
                                  double* __restrict__ partials) {
   const long long N = g.N;
   double s[5] = {0, 0, 0, 0, 0};
@@ -249,7 +261,7 @@ __global__ void k_totals_partial(Grid g, const double* __restrict__ Q, const TM*
        n += (long long)gridDim.x * blockDim.x) {
     const double jv = (double)M[9 * N + n];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) s[q] += jv * Q[q * N + n];
+    for (int q = 0; q < 5; ++q) s[q] += jv * Q.ld(q * N + n);
   }
   __shared__ double red[5][32];
 #pragma unroll
@@ -334,22 +346,32 @@ void launch_bc_jet_hl(const Grid& g, const les_params& p, float* hi, float* lo, 
   bc_jet(g, p, AccHL{hi, lo}, M32, rth, sc, 0, 0.0, L);
 }
 
-template <typename TM>
-static void totals_t(const Grid& g, const double* Q, const TM* M, double* partials, DevScalars* sc,
+template <class View, typename TM>
+static void totals_t(const Grid& g, View Q, const TM* M, double* partials, DevScalars* sc,
                      const Launch& L) {
-  k_totals_partial<TM><<<kRedBlocks, kRedThreads, 0, L.s>>>(g, Q, M, partials);
+  k_totals_partial<View, TM><<<kRedBlocks, kRedThreads, 0, L.s>>>(g, Q, M, partials);
   k_totals_final<<<1, 160, 0, L.s>>>(partials, sc);
   *L.counter += 2;
 }
 
 void launch_totals(const Grid& g, const double* Q, const double* M64, double* partials,
                    DevScalars* sc, const Launch& L) {
-  totals_t(g, Q, M64, partials, sc, L);
+  totals_t(g, ViewD{Q}, M64, partials, sc, L);
 }
 
 void launch_totals(const Grid& g, const double* Q, const float* M32, double* partials,
                    DevScalars* sc, const Launch& L) {
-  totals_t(g, Q, M32, partials, sc, L);
+  totals_t(g, ViewD{Q}, M32, partials, sc, L);
+}
+
+void launch_totals_hl(const Grid& g, const float* hi, const float* lo, const double* M64,
+                      double* partials, DevScalars* sc, const Launch& L) {
+  totals_t(g, ViewHL{hi, lo}, M64, partials, sc, L);
+}
+
+void launch_totals_hl(const Grid& g, const float* hi, const float* lo, const float* M32,
+                      double* partials, DevScalars* sc, const Launch& L) {
+  totals_t(g, ViewHL{hi, lo}, M32, partials, sc, L);
 }
 
 void launch_set_time(DevScalars* sc, double t, const Launch& L) {

@@ -116,6 +116,11 @@ void launch_totals(const Grid& g, const double* Q, const double* M64, double* pa
                    DevScalars* sc, const Launch& L);
 void launch_totals(const Grid& g, const double* Q, const float* M32, double* partials,
                    DevScalars* sc, const Launch& L);
+// totals of the mixed form's float pair state (hi + lo)
+void launch_totals_hl(const Grid& g, const float* hi, const float* lo, const double* M64,
+                      double* partials, DevScalars* sc, const Launch& L);
+void launch_totals_hl(const Grid& g, const float* hi, const float* lo, const float* M32,
+                      double* partials, DevScalars* sc, const Launch& L);
 void launch_set_time(DevScalars* sc, double t, const Launch& L);
 
 }  // namespace lesjet

@@ -507,18 +507,28 @@ def test_argument_errors(lj, torch):
     assert rc == lj.LES_ERR_INVALID_ARG
 
 
-def test_run_host_matches_device(orc, lj, torch):
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "compact"])
+def test_run_host_matches_device(orc, lj, torch, prec):
+    """les_run_host on pinned memory (mapped: the mixed forms read and write
+    it directly) and on pageable memory (staging copy) gives the device
+    run's state and totals bit for bit."""
     shape = C1
     xyz = lj.synth.jet_grid(*shape)
-    ctx, _ = device_ctx(lj, torch, shape, xyz)
+    pc = {"fp64": lj.PREC_FP64, "mixed": lj.PREC_MIXED, "compact": lj.PREC_MIXED_COMPACT}[prec]
+    ctx, _ = device_ctx(lj, torch, shape, xyz, precision=pc)
     Q0 = orc.init_jet(orc.params(), xyz, seed=2)
     Qd = torch.from_numpy(Q0).cuda()
-    ctx.les_run_n_steps(3, Qd)
-    ctx.les_set_time(0.0)
-    Qh = torch.from_numpy(Q0.copy()).pin_memory()
-    stage = torch.empty_like(Qd)
-    ctx.les_run_host(3, Qh, stage)
-    assert np.array_equal(Qh.numpy(), Qd.cpu().numpy())
+    dd = ctx.les_run_n_steps(3, Qd)
+    ref = Qd.cpu().numpy()
+    for pinned in (True, False):
+        ctx.les_set_time(0.0)
+        Qh = torch.from_numpy(Q0.copy())
+        if pinned:
+            Qh = Qh.pin_memory()
+        stage = torch.zeros_like(Qd)
+        dh = ctx.les_run_host(3, Qh, stage)
+        assert np.array_equal(Qh.numpy(), ref), pinned
+        assert list(dh.totals) == list(dd.totals) and dh.t == dd.t, pinned
 
 
 # ------------------------------------------------------------ mixed form
