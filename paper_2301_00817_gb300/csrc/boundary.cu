@@ -25,7 +25,8 @@ struct AccHL {
 };
 
 struct JetBC {
-  int mode;  // LES_BC_JET or LES_BC_JET_CHAR
+  int mode;     // LES_BC_JET or LES_BC_JET_CHAR
+  int forced;   // some forcing amplitude is non-zero
   double gamma, Mj, r_jet, theta_m, force_width;
   double St[4];
   double amp[16];
@@ -71,15 +72,18 @@ __device__ __forceinline__ bool far_field_state(double gamma, double rho, double
   const double Mn = qne / ae;
   if (Mn >= 1.0) return true;
   if (Mn >= 0.0) {
+    // entropy of the interior node: rho_f = (rho_e^gamma a_f^2/(gamma p_e))^(1/(gamma-1))
+    // = rho_e (a_f/a_e)^(2/(gamma-1)), one power instead of two
     const double dq = qnf - qne;
-    const double rf = pow(pow(rho, gamma) * af * af / (gamma * p), 1.0 / gm1);
+    const double rf = rho * pow(af / ae, 2.0 / gm1);
     f[0] = rf;
     f[1] = u + dq * nx;
     f[2] = v + dq * ny;
     f[3] = w + dq * nz;
     f[4] = rf * af * af / gamma;
   } else if (Mn > -1.0) {
-    const double rf = pow(af * af / (gamma * (1.0 / gamma)), 1.0 / gm1);
+    // free-stream entropy (rho = 1, p = 1/gamma): rho_f = a_f^(2/(gamma-1))
+    const double rf = pow(af, 2.0 / gm1);
     f[0] = rf;
     f[1] = qnf * nx;
     f[2] = qnf * ny;
@@ -114,13 +118,29 @@ __global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
        n += (long long)gridDim.x * blockDim.x) {
     const double r = rth[n], th = rth[plane + n];
     double u = 0.5 * b.Mj * (1.0 + tanh((b.r_jet - r) / (2.0 * b.theta_m)));
-    const double x = (r - b.r_jet) / b.force_width;
-    const double gr = exp(-(x * x));
+    if (b.forced) {
+      // cos(m theta - phi_f) = cos(m theta) cos(phi_f) + sin(m theta) sin(phi_f),
+      // with cos/sin(m theta) by the angle-addition recurrence from theta
+      const double x = (r - b.r_jet) / b.force_width;
+      const double gr = exp(-(x * x));
+      double s1, c1;
+      sincos(th, &s1, &c1);
+      double cm[4] = {1.0, c1, 0.0, 0.0}, sm[4] = {0.0, s1, 0.0, 0.0};
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+      for (int m = 2; m < 4; ++m) {
+        cm[m] = cm[m - 1] * c1 - sm[m - 1] * s1;
+        sm[m] = sm[m - 1] * c1 + cm[m - 1] * s1;
+      }
+      double sf[4], cf[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f)
-        u += b.amp[m * 4 + f] * gr * cos(m * th - two_pi * b.St[f] * b.Mj * t);
+      for (int f = 0; f < 4; ++f) sincos(two_pi * b.St[f] * b.Mj * t, &sf[f], &cf[f]);
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) acc += b.amp[m * 4 + f] * (cm[m] * cf[f] + sm[m] * sf[f]);
+      u += gr * acc;
+    }
     const long long ne = n + plane;  // node (1, j, k)
     if (b.mode == LES_BC_JET_CHAR && r > b.r_jet) {
       const double ex = (double)M[n], ey = (double)M[N + n], ez = (double)M[2 * N + n];
@@ -315,7 +335,11 @@ static void bc_jet(const Grid& g, const les_params& p, Acc Q, const TM* M,
   b.theta_m = p.theta_m;
   b.force_width = p.force_width;
   for (int i = 0; i < 4; ++i) b.St[i] = p.St[i];
-  for (int i = 0; i < 16; ++i) b.amp[i] = p.amp[i];
+  b.forced = 0;
+  for (int i = 0; i < 16; ++i) {
+    b.amp[i] = p.amp[i];
+    if (p.amp[i] != 0.0) b.forced = 1;
+  }
   const long long plane = (long long)g.n[1] * g.n[2];
   k_bc_inflow<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, M, sc, use_host_t, t_host, Q);
   k_bc_farfield<Acc, TM><<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M, Q);
