@@ -211,12 +211,16 @@ def aggregate_rate(world: int, points: int, steps: int, ms: float) -> float:
     return world * points * steps / (ms / 1e3) / 1e9
 
 
-def oracle_baseline(shape, steps: int, warmup: int):
+def oracle_baseline(shape, steps: int, warmup: int, threads: int = 0):
     """CPU oracle on an axial slab of the workload (same grid spacing and
-    flow), all host cores; returns (Gpt*steps/s, seconds per step, points)."""
+    flow), all host cores (or `threads`); returns (Gpt*steps/s, seconds per
+    step, points, threads used)."""
     import numpy as np
 
     import oracle
+    full = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(threads)
     from paper_2301_00817_gb300 import synth
     x, r, th = synth.jet_lines(*WORKLOAD)
     ns = shape
@@ -237,7 +241,9 @@ def oracle_baseline(shape, steps: int, warmup: int):
         t += d
     el = time.perf_counter() - t0
     npts = ns[0] * ns[1] * ns[2]
-    return npts * steps / el / 1e9, el / steps, npts, oracle.num_threads()
+    used = oracle.num_threads()
+    oracle.set_num_threads(full)
+    return npts * steps / el / 1e9, el / steps, npts, used
 
 
 def run_reference(args, world, rank):
@@ -586,10 +592,15 @@ def run_ours(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, sec, npts, cores = oracle_baseline(WORKLOAD, 1, 0)
+        slab = (24, WORKLOAD[1], WORKLOAD[2])
+        v1, s1, n1, _ = oracle_baseline(slab, 1, 0, threads=1)
         cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                "seconds": sec,
                "sample": f"1 full RK step of the whole workload ({npts} points), "
-                         "all host threads"}
+                         "all host threads",
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "seconds": s1,
+                                 "sample": f"1 full RK step of the axial slab {slab} "
+                                           f"({n1} points), one thread"}}
 
     def roofline(res, prec_idx):
         prof = res["prof"]

@@ -101,6 +101,7 @@ def _lib_handle():
             lib.orc_rk_step.restype = C.c_double
             lib.orc_totals.argtypes = [i, i, i, _dp, _dp, _dp]
             lib.orc_num_threads.restype = C.c_int
+            lib.orc_set_num_threads.argtypes = [i]
             RHSFN = C.CFUNCTYPE(None, C.c_void_p, _dp, _dp)
             lib.orc_rk5.argtypes = [i, C.c_size_t, _dp, C.POINTER(C.c_ubyte), _dp,
                                     C.c_double, _dp, RHSFN, C.c_void_p]
@@ -123,6 +124,11 @@ def _f64(a) -> np.ndarray:
 
 def num_threads() -> int:
     return int(_lib_handle().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (its results do not depend on it)."""
+    _lib_handle().orc_set_num_threads(int(n))
 
 
 def metrics(xyz, periodic=(0, 0, 1), shift=None, form: int = 0) -> np.ndarray:

@@ -35,6 +35,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the OpenMP loops (n >= 1); results do not depend on it. */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------ grid */
 
 typedef struct {

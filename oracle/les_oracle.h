@@ -120,5 +120,6 @@ void orc_totals(int ni, int nj, int nk, const double *Q, const double *M,
                 double out[5]);
 
 int orc_num_threads(void);
+void orc_set_num_threads(int n);
 
 #endif

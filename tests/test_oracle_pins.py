@@ -1069,3 +1069,26 @@ def test_azimuthal_rotation_equivariance(orc):
     Q2, dt2 = orc.rk_step(P, rotate(Q), M, xyz, 0.0)
     assert abs(dt1 - dt2) < 1e-12 * dt1
     assert np.allclose(rotate(Q1), Q2, rtol=0, atol=1e-12)
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count(orc):
+    """The OpenMP loops only split independent per-node work: one thread and
+    all threads give the same bits (one step with SGS and jet BCs, and the
+    dynamic procedure)."""
+    xyz = synth.jet_grid(16, 12, 8)
+    M = orc.metrics(xyz, (0, 0, 1))
+    outs = []
+    full = orc.num_threads()
+    for nt in (1, full):
+        orc.set_num_threads(nt)
+        try:
+            P = orc.params(sgs_model=1)
+            Q0 = orc.init_jet(P, xyz, seed=7, noise=1e-2)
+            Q1, dt = orc.rk_step(P, Q0, M, xyz, 0.0)
+            P3 = orc.params(sgs_model=3)
+            dyn = orc.dynamic_coefficients(P3, Q0, M)
+            outs.append((Q1, dt, dyn))
+        finally:
+            orc.set_num_threads(full)
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+    assert outs[0][2] == outs[1][2]
