@@ -48,7 +48,7 @@ def _vdot(a, b):
     return float((a * b).sum())
 
 
-@pytest.mark.parametrize("case", ["jet", "box"])
+@pytest.mark.parametrize("case", ["jet", "box", "box_conservative"])
 def test_residual_adjoint_dot_product(lj, torch, case):
     if case == "jet":
         shape = (13, 11, 8)
@@ -58,7 +58,9 @@ def test_residual_adjoint_dot_product(lj, torch, case):
     else:
         shape = (9, 11, 10)
         xyz_np, shift = lj.synth.box_grid(shape, (1.0, 1.3, 0.8), wave=0.25)
-        ctx = lj.Context(lj.make_params(periodic=(1, 1, 1), bc=0, Re=300.0), shape, "cuda:0")
+        form = lj.METRIC_CONSERVATIVE if case == "box_conservative" else lj.METRIC_CROSS
+        ctx = lj.Context(lj.make_params(periodic=(1, 1, 1), bc=0, Re=300.0, metric_form=form),
+                         shape, "cuda:0")
         ctx.les_set_grid(torch.from_numpy(xyz_np).cuda(), shift)
         import oracle
         P = oracle.params(periodic=(1, 1, 1), bc=0)
