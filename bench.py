@@ -676,7 +676,11 @@ def run_ours(args, world, rank, local):
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in mixed["prof"].items() if v[1]},
         "kernel_ms_per_step_fp64": {k: v[0] / args.steps for k, v in fp64["prof"].items() if v[1]},
         "extensions": ext,
-        "adjoint_fwd_ratio": adj["ratio"] if adj else None,
+        # the backward pass (segment recompute + reverse) over the forward
+        # pass, per step; the whole window including the forward sweep is
+        # adjoint_window_ratio
+        "adjoint_fwd_ratio": adj["step_ratio"] if adj else None,
+        "adjoint_window_ratio": adj["ratio"] if adj else None,
         "adjoint": adj,
         "large": large,
     }
