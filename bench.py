@@ -211,7 +211,7 @@ def aggregate_rate(world: int, points: int, steps: int, ms: float) -> float:
     return world * points * steps / (ms / 1e3) / 1e9
 
 
-def oracle_baseline(shape, steps: int, warmup: int, threads: int = 0):
+def oracle_baseline(shape, steps: int, warmup: int, threads: int = 0, grid=WORKLOAD, Re=1.0e5):
     """CPU oracle on an axial slab of the workload (same grid spacing and
     flow), all host cores (or `threads`); returns (Gpt*steps/s, seconds per
     step, points, threads used)."""
@@ -222,13 +222,13 @@ def oracle_baseline(shape, steps: int, warmup: int, threads: int = 0):
     if threads:
         oracle.set_num_threads(threads)
     from paper_2301_00817_gb300 import synth
-    x, r, th = synth.jet_lines(*WORKLOAD)
+    x, r, th = synth.jet_lines(*grid)
     ns = shape
     xyz = np.empty((3,) + ns)
     xyz[0] = x[:ns[0], None, None]
     xyz[1] = r[None, :, None] * np.cos(th)[None, None, :]
     xyz[2] = r[None, :, None] * np.sin(th)[None, None, :]
-    P = oracle.params(sgs_model=1)
+    P = oracle.params(sgs_model=1, Re=Re)
     M = oracle.metrics(xyz, (0, 0, 1))
     Q = oracle.init_jet(P, xyz, seed=0)
     t = 0.0
@@ -720,6 +720,41 @@ def run_profile_case(which: str):
         print(f"profile case adjoint: J={J:.6e} |grad|={float(np.linalg.norm(g)):.3e} "
               f"launches={ctx.les_launch_count()}")
         return 0
+    if which == "c3":
+        # 576 x 320 x 256 (47M points), Re_D = 1e6: both forms, 5 timed steps
+        # each after 2 warm-up steps, and one oracle step on the host cores
+        shape = (576, 320, 256)
+        N = shape[0] * shape[1] * shape[2]
+        xyz = lj.synth.jet_grid_torch(*shape, "cuda")
+        out = {"workload": "jet 576x320x256 (47.2M points), Re_D 1e6, Smagorinsky",
+               "points": N}
+        for name, prec in (("mixed", lj.PREC_MIXED), ("fp64", lj.PREC_FP64)):
+            ctx = lj.Context(lj.make_params(Re=1.0e6, sgs_model=lj.SGS_SMAGORINSKY,
+                                            precision=prec), shape)
+            ctx.les_set_grid(xyz)
+            Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+            ctx.les_init_jet(xyz, 0, 1e-3, Q)
+            ctx.les_run_n_steps(2, Q)
+            ctx.les_profile(True)
+            ms, diag = time_steps(lj, torch, ctx, Q, 5, torch.cuda.current_stream())
+            prof = ctx.les_profile_read()
+            ctx.les_profile(False)
+            rec = {"ms_per_step": ms / 5, "gpt_steps_per_s": N * 5 / (ms / 1e3) / 1e9,
+                   "status": diag.status,
+                   "kernel_ms_per_step": {k: v[0] / 5 for k, v in prof.items() if v[1]}}
+            if name == "mixed":
+                st = prof["stage_fused"]
+                per_launch_s = st[0] / st[1] / 1e3
+                rec["stage_fused_avg_launch_us"] = per_launch_s * 1e6
+                rec["stage_fused_algorithmic_gbs"] = 112.0 * N / per_launch_s / 1e9
+            out[name] = rec
+            del ctx, Q
+            torch.cuda.empty_cache()
+        del xyz
+        val, sec, npts, cores = oracle_baseline(shape, 1, 0, grid=shape, Re=1.0e6)
+        out["oracle_one_step"] = {"seconds": sec, "cores": cores, "gpt_steps_per_s": val}
+        print(json.dumps(out))
+        return 0
     prec = lj.PREC_MIXED if which == "mixed" else lj.PREC_FP64
     sgs = lj.SGS_DYNAMIC if which == "dynamic" else lj.SGS_SMAGORINSKY
     shape = (96, 160, 128)
@@ -747,7 +782,8 @@ def main():
                     help="skip the dynamic-SGS / local-step / entrance / metric-form timings")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 1.02e9-point compact mixed leg")
-    ap.add_argument("--profile-case", choices=("fp64", "mixed", "adjoint", "dynamic"), default=None,
+    ap.add_argument("--profile-case", choices=("fp64", "mixed", "adjoint", "dynamic", "c3"),
+                    default=None,
                     help="run the small ncu case (two steps) and exit")
     args = ap.parse_args()
     if args.profile_case:
