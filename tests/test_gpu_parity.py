@@ -309,6 +309,32 @@ def test_rhs(orc, lj, torch, case, sgs):
         assert np.abs(Rg[:, 0]).max() == 0.0 and np.abs(Rg[:, :, -1]).max() == 0.0
 
 
+@pytest.mark.parametrize("sgs", [0, 1, 2])
+@pytest.mark.parametrize("case", ["jet_c1", "wavy_box", "jet_ragged", "jet_min"])
+@pytest.mark.parametrize("prec", ["mixed", "compact"])
+def test_rhs_mixed_forms(orc, lj, torch, case, sgs, prec):
+    """The fused kernel's residual mode against the oracle on the same cases
+    as the FP64 residual: periodic xi (wavy box), ragged tiles and rows whose
+    length is not a multiple of four (13 x 9 x 7), the smallest grid (5^3).
+    FP32 arithmetic: within 2e-5 of each component's flux scale."""
+    shape, xyz, shift, kw = _grid(lj, case)
+    pc = lj.PREC_MIXED if prec == "mixed" else lj.PREC_MIXED_COMPACT
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=sgs, Re=2000.0, precision=pc, **kw)
+    P = oracle_params(orc, sgs_model=sgs, Re=2000.0, **kw)
+    M = orc.metrics(xyz, kw["periodic"], shift)
+    Q = _state(orc, lj, case, shape, xyz, P)
+    R = torch.empty_like(torch.from_numpy(Q)).cuda()
+    ctx.les_rhs(torch.from_numpy(Q).cuda(), R)
+    Ro = orc.rhs(P, Q, M)
+    Rg = R.cpu().numpy()
+    fscale = (np.abs(M[9]) * np.sqrt(M[0] ** 2 + M[1] ** 2 + M[2] ** 2)).max()
+    for c in range(5):
+        qs = np.abs(Q[c]).max() + (np.abs(Q[4]).max() if c in (1, 2, 3, 4) else 0.0)
+        assert np.abs(Rg[c] - Ro[c]).max() <= 2e-5 * fscale * qs, c
+    if not case.startswith("wavy"):
+        assert np.abs(Rg[:, 0]).max() == 0.0 and np.abs(Rg[:, :, -1]).max() == 0.0
+
+
 def test_time_step(orc, lj, torch):
     shape, xyz, shift, kw = _grid(lj, "jet_c1")
     ctx, _ = device_ctx(lj, torch, shape, xyz, shift, **kw)
