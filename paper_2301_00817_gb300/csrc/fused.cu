@@ -519,14 +519,23 @@ __global__ void __launch_bounds__(FNT, 1)
       for (int c = 0; c < 5; ++c) qn[c] = __ldg(P.qin[c] + n);
     }
   };
-  // Q^(0) hi part of the own node, fetched one plane ahead of its update
+  // Q^(0) of the own node (hi part; in the last stage also the lo part; with
+  // local steps also the node's step), fetched one plane ahead of its update
+  // so the epilogue never waits on a global load
   float h0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float l0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // lo part, last stage only
+  float d0 = 0.f;                            // local step (LOCAL only)
   auto fetch_h = [&](int x) {
     const int ig = wrap_fast(x, ni, G.per[0]);
     if (MODE != FMODE_RHS && own && ig >= 0) {
       const int n = (ig * nj + jown) * nk + kown;
 #pragma unroll
       for (int c = 0; c < 5; ++c) h0[c] = P.hi[c][n];
+      if (MODE == FMODE_LAST) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) l0[c] = P.lo[c][n];
+      }
+      if (LOCAL) d0 = P.dtl[n];
     }
   };
   auto finish_W = [&](float W[5], float& p, bool& valid) {
@@ -780,12 +789,16 @@ __global__ void __launch_bounds__(FNT, 1)
     float hc[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) hc[c] = h0[c];
+    float lc[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) lc[c] = l0[c];
+    const float dc = d0;
     fetch_h(i + 1);
     if (own && ig >= 0) {
       const int n = (ig * nj + jown) * nk + kown;
       if (iint && jint && kint) {
         const float Jn = __frcp_rn(sM[(s_c * 10 + 9) * PL1 + o1]);
-        const float an = LOCAL ? (float)alpha * P.dtl[n] : adt;
+        const float an = LOCAL ? (float)alpha * dc : adt;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           float r = 0.f;
@@ -800,7 +813,7 @@ __global__ void __launch_bounds__(FNT, 1)
             // compensated update of the pair (hi, lo) by d (TwoSum, then
             // renormalisation), all in FP32
             const float d = -an * (Jn * r);
-            const float hi = hc[c], lo = P.lo[c][n];
+            const float hi = hc[c], lo = lc[c];
             const float s = hi + d;
             const float bb = s - hi;
             const float e = (hi - (s - bb)) + (d - bb);
