@@ -559,7 +559,8 @@ __global__ void __launch_bounds__(FNT, 1)
   };
 
   // xi interface (x, x+1) of the own column: sPr/sPw/sM/sK/sL slots of both planes
-  auto xi_flux = [&](int x, int p0, int p1, int m0, int m1, int l0, int l1, float F[5]) {
+  auto xi_flux = [&](int x, int p0, int p1, int m0, int m1, int l0, int l1, const float* mown,
+                     float F[5]) {
     const float4* A0 = sPr + p0 * PL2;
     const float4* A1 = sPr + p1 * PL2;
     float nua, nub;
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(FNT, 1)
     float ma[10], mb[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
-      ma[t] = sM[(m0 * 10 + t) * PL1 + o1];
+      ma[t] = mown ? mown[t] : sM[(m0 * 10 + t) * PL1 + o1];
       mb[t] = sM[(m1 * 10 + t) * PL1 + o1];
     }
     const float* Ka = sK + m0 * 2 * PL1;
@@ -594,7 +595,8 @@ __global__ void __launch_bounds__(FNT, 1)
 
   // eta interface between tile rows ra and ra+1 (ra in [-1, FTJ-1]), own
   // column; plane i in slots qs (sQ), ps (sP, with pm/pp for i-1/i+1), ms, ls
-  auto eta_flux = [&](int ra, int qs, int pm, int ps, int pp, int ms, int ls, float F[5]) {
+  auto eta_flux = [&](int ra, int qs, int pm, int ps, int pp, int ms, int ls, const float* mown,
+                      float F[5]) {
     const float* Qs = sQ + qs * 5 * PL2;
     const float4* Pc = sPr + ps * PL2;
     const float4* Pm = sPr + pm * PL2;
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(FNT, 1)
     float ma[10], mb[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
-      ma[t] = sM[(ms * 10 + t) * PL1 + a1];
+      ma[t] = mown ? mown[t] : sM[(ms * 10 + t) * PL1 + a1];
       mb[t] = sM[(ms * 10 + t) * PL1 + b1];
     }
     const float* Kc = sK + ms * 2 * PL1;
@@ -648,7 +650,8 @@ __global__ void __launch_bounds__(FNT, 1)
 
   // zeta interface between tile columns ca and ca+1 (ca in [-1, FTK-1]) in
   // tile row rr
-  auto zeta_flux = [&](int rr, int ca, int qs, int pm, int ps, int pp, int ms, int ls, float F[5]) {
+  auto zeta_flux = [&](int rr, int ca, int qs, int pm, int ps, int pp, int ms, int ls,
+                       const float* mown, float F[5]) {
     const float* Qs = sQ + qs * 5 * PL2;
     const float4* Pc = sPr + ps * PL2;
     const float4* Pm = sPr + pm * PL2;
@@ -691,7 +694,7 @@ __global__ void __launch_bounds__(FNT, 1)
     float ma[10], mb[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
-      ma[t] = sM[(ms * 10 + t) * PL1 + a1];
+      ma[t] = mown ? mown[t] : sM[(ms * 10 + t) * PL1 + a1];
       mb[t] = sM[(ms * 10 + t) * PL1 + b1];
     }
     const float* Kc = sK + ms * 2 * PL1;
@@ -728,7 +731,7 @@ __global__ void __launch_bounds__(FNT, 1)
   __syncthreads();
   float Fx_prev[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   if (own && jint && kint && (per_i || ib - 1 >= 0))
-    xi_flux(ib - 1, s_m, s_c, s_m, s_c, l_p, l_c, Fx_prev);
+    xi_flux(ib - 1, s_m, s_c, s_m, s_c, l_p, l_c, nullptr, Fx_prev);
   const float adt = (MODE == FMODE_RHS) ? 0.f : (float)(alpha * sc->dt);
 
   for (int i = ib; i < ie; ++i) {
@@ -753,24 +756,28 @@ __global__ void __launch_bounds__(FNT, 1)
     const int ig = wrap_fast(i, ni, G.per[0]);
     const bool iint = per_i || (i > 0 && i < ni - 1);
     float Fx[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    // the own node's metrics, read once for its three interfaces
+    float mo[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) mo[t] = sM[(s_c * 10 + t) * PL1 + o1];
     if (own && jint && kint && (per_i || i + 1 <= ni - 1))
-      xi_flux(i, s_c, s_p, s_c, s_p, l_c, l_p, Fx);
+      xi_flux(i, s_c, s_p, s_c, s_p, l_c, l_p, mo, Fx);
     if (own && iint && kint) {
       float F[5];
       if (G.per[1] || jown + 1 <= nj - 1) {
-        eta_flux(ty, s_c, s_m, s_c, s_p, s_c, l_c, F);
+        eta_flux(ty, s_c, s_m, s_c, s_p, s_c, l_c, mo, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1) + ty + 1) * FTK + tx] = F[c];
       }
       if (ty == 0 && (G.per[1] || j0 - 1 >= 0)) {
-        eta_flux(-1, s_c, s_m, s_c, s_p, s_c, l_c, F);
+        eta_flux(-1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1)) * FTK + tx] = F[c];
       }
     }
     if (own && iint && jint && (G.per[2] || kown + 1 <= nk - 1)) {
       float F[5];
-      zeta_flux(ty, tx, s_c, s_m, s_c, s_p, s_c, l_c, F);
+      zeta_flux(ty, tx, s_c, s_m, s_c, s_p, s_c, l_c, mo, F);
 #pragma unroll
       for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] = F[c];
     }
@@ -780,7 +787,7 @@ __global__ void __launch_bounds__(FNT, 1)
       const bool rint = G.per[1] || (jr > 0 && jr < nj - 1);
       if (jr < nj && rint) {
         float F[5];
-        zeta_flux(rr, -1, s_c, s_m, s_c, s_p, s_c, l_c, F);
+        zeta_flux(rr, -1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFz[(c * FTJ + rr) * (FTK + 1)] = F[c];
       }
@@ -797,7 +804,7 @@ __global__ void __launch_bounds__(FNT, 1)
     if (own && ig >= 0) {
       const int n = (ig * nj + jown) * nk + kown;
       if (iint && jint && kint) {
-        const float Jn = __frcp_rn(sM[(s_c * 10 + 9) * PL1 + o1]);
+        const float Jn = __frcp_rn(mo[9]);
         const float an = LOCAL ? (float)alpha * dc : adt;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
