@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(FNT, 1)
 
   // xi interface (x, x+1) of the own column: sPr/sPw/sM/sK/sL slots of both planes
   auto xi_flux = [&](int x, int p0, int p1, int m0, int m1, int l0, int l1, const float* mown,
-                     const float4* rown, const float2* wown, float F[5]) {
+                     const float4* rown, const float4* rpm, const float2* wown, float F[5]) {
     const float4* A0 = sPr + p0 * PL2;
     const float4* A1 = sPr + p1 * PL2;
     float nua, nub;
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(FNT, 1)
       nub = sensor3(pq[0], pq[1], pq[2]);
     else
       nub = sensor3(pq[1], pq[2], pq[3]);
-    const float4 a0 = rown ? *rown : A0[o2], b0 = A1[o2];
+    const float4 a0 = rown ? rown[0] : A0[o2], b0 = rpm ? rpm[0] : A1[o2];
     const float4 an = A0[o2 + SK], as = A0[o2 - SK], bn = A1[o2 + SK], bs = A1[o2 - SK];
     const float4 ae = A0[o2 + 1], aw = A0[o2 - tx + cm1], be = A1[o2 + 1], bw = A1[o2 - tx + cm1];
     float dphi[4][3];
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(FNT, 1)
   // eta interface between tile rows ra and ra+1 (ra in [-1, FTJ-1]), own
   // column; plane i in slots qs (sQ), ps (sP, with pm/pp for i-1/i+1), ms, ls
   auto eta_flux = [&](int ra, int qs, int pm, int ps, int pp, int ms, int ls, const float* mown,
-                      const float4* rown, const float2* wown, float F[5]) {
+                      const float4* rown, const float4* rpm, const float2* wown, float F[5]) {
     const float* Qs = sQ + qs * 5 * PL2;
     const float4* Pc = sPr + ps * PL2;
     const float4* Pm = sPr + pm * PL2;
@@ -631,10 +631,10 @@ __global__ void __launch_bounds__(FNT, 1)
     else
       nub = sensor3(wa.x, wb.x, wp.x);
     const int am1 = a2 - tx + cm1, bm1 = b2 - tx + cm1;
-    const float4 ca = rown ? *rown : Pc[a2], cb = Pc[b2];
+    const float4 ca = rown ? rown[0] : Pc[a2], cb = Pc[b2];
     float dphi[4][3];
     dphi_normal<1>(ca, cb, dphi);
-    dphi_tangent<0>(Pp[a2], Pm[a2], Pp[b2], Pm[b2], dphi);
+    dphi_tangent<0>(rpm ? rpm[0] : Pp[a2], rpm ? rpm[1] : Pm[a2], Pp[b2], Pm[b2], dphi);
     dphi_tangent<2>(Pc[a2 + 1], Pc[am1], Pc[b2 + 1], Pc[bm1], dphi);
     float ma[10], mb[10];
 #pragma unroll
@@ -652,7 +652,8 @@ __global__ void __launch_bounds__(FNT, 1)
   // zeta interface between tile columns ca and ca+1 (ca in [-1, FTK-1]) in
   // tile row rr
   auto zeta_flux = [&](int rr, int ca, int qs, int pm, int ps, int pp, int ms, int ls,
-                       const float* mown, const float4* rown, const float2* wown, float F[5]) {
+                       const float* mown, const float4* rown, const float4* rpm, const float2* wown,
+                       float F[5]) {
     const float* Qs = sQ + qs * 5 * PL2;
     const float4* Pc = sPr + ps * PL2;
     const float4* Pm = sPr + pm * PL2;
@@ -687,10 +688,10 @@ __global__ void __launch_bounds__(FNT, 1)
       nub = sensor3(wm.x, wa.x, wb.x);
     else
       nub = sensor3(wa.x, wb.x, wp.x);
-    const float4 pa = rown ? *rown : Pc[a2], pb = Pc[b2];
+    const float4 pa = rown ? rown[0] : Pc[a2], pb = Pc[b2];
     float dphi[4][3];
     dphi_normal<2>(pa, pb, dphi);
-    dphi_tangent<0>(Pp[a2], Pm[a2], Pp[b2], Pm[b2], dphi);
+    dphi_tangent<0>(rpm ? rpm[0] : Pp[a2], rpm ? rpm[1] : Pm[a2], Pp[b2], Pm[b2], dphi);
     dphi_tangent<1>(Pc[a2 + SK], Pc[a2 - SK], Pc[b2 + SK], Pc[b2 - SK], dphi);
     float ma[10], mb[10];
 #pragma unroll
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(FNT, 1)
   __syncthreads();
   float Fx_prev[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   if (own && jint && kint && (per_i || ib - 1 >= 0))
-    xi_flux(ib - 1, s_m, s_c, s_m, s_c, l_p, l_c, nullptr, nullptr, nullptr, Fx_prev);
+    xi_flux(ib - 1, s_m, s_c, s_m, s_c, l_p, l_c, nullptr, nullptr, nullptr, nullptr, Fx_prev);
   const float adt = (MODE == FMODE_RHS) ? 0.f : (float)(alpha * sc->dt);
 
   for (int i = ib; i < ie; ++i) {
@@ -761,26 +762,35 @@ __global__ void __launch_bounds__(FNT, 1)
     float mo[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) mo[t] = sM[(s_c * 10 + t) * PL1 + o1];
-    const float4 ro = sPr[s_c * PL2 + o2];  // and its node records
+    // and its node records; in the stage modes also those of planes i+1 and
+    // i-1 of the own column (the last stage keeps them in shared memory: its
+    // compensated update needs the registers)
+    const float4 ro = sPr[s_c * PL2 + o2];
     const float2 wo = sPw[s_c * PL2 + o2];
+    float4 rq[2];
+    if (MODE != FMODE_LAST) {
+      rq[0] = sPr[s_p * PL2 + o2];
+      rq[1] = sPr[s_m * PL2 + o2];
+    }
+    const float4* rpm = (MODE != FMODE_LAST) ? rq : nullptr;
     if (own && jint && kint && (per_i || i + 1 <= ni - 1))
-      xi_flux(i, s_c, s_p, s_c, s_p, l_c, l_p, mo, &ro, &wo, Fx);
+      xi_flux(i, s_c, s_p, s_c, s_p, l_c, l_p, mo, &ro, rpm, &wo, Fx);
     if (own && iint && kint) {
       float F[5];
       if (G.per[1] || jown + 1 <= nj - 1) {
-        eta_flux(ty, s_c, s_m, s_c, s_p, s_c, l_c, mo, &ro, &wo, F);
+        eta_flux(ty, s_c, s_m, s_c, s_p, s_c, l_c, mo, &ro, rpm, &wo, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1) + ty + 1) * FTK + tx] = F[c];
       }
       if (ty == 0 && (G.per[1] || j0 - 1 >= 0)) {
-        eta_flux(-1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, nullptr, nullptr, F);
+        eta_flux(-1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, nullptr, nullptr, nullptr, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1)) * FTK + tx] = F[c];
       }
     }
     if (own && iint && jint && (G.per[2] || kown + 1 <= nk - 1)) {
       float F[5];
-      zeta_flux(ty, tx, s_c, s_m, s_c, s_p, s_c, l_c, mo, &ro, &wo, F);
+      zeta_flux(ty, tx, s_c, s_m, s_c, s_p, s_c, l_c, mo, &ro, rpm, &wo, F);
 #pragma unroll
       for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] = F[c];
     }
@@ -790,7 +800,7 @@ __global__ void __launch_bounds__(FNT, 1)
       const bool rint = G.per[1] || (jr > 0 && jr < nj - 1);
       if (jr < nj && rint) {
         float F[5];
-        zeta_flux(rr, -1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, nullptr, nullptr, F);
+        zeta_flux(rr, -1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, nullptr, nullptr, nullptr, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFz[(c * FTJ + rr) * (FTK + 1)] = F[c];
       }
