@@ -160,7 +160,7 @@ int les_set_params(les_ctx *ctx, const les_params *p);
 
 /* Bytes of the caller-owned device workspace this context needs: about
  * 360 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
- * per point with LES_DT_LOCAL and 248 B per point with LES_SGS_DYNAMIC. */
+ * per point with LES_DT_LOCAL and 408 B per point with LES_SGS_DYNAMIC. */
 size_t les_workspace_bytes(const les_ctx *ctx);
 
 /* Bind the workspace and compute the Jacobian and the nine metric terms on
@@ -201,7 +201,7 @@ int les_mu_eff(les_ctx *ctx, const double *Q, double *MK, les_stream_t stream);
  * the configured value when the dynamic one is not positive).  Test filter:
  * (1/4, 1/2, 1/4) along each direction, width 2 Delta, identity along a
  * non-periodic direction at its faces.  Needs sgs_model LES_SGS_DYNAMIC at
- * les_create (FP64 form only: the workspace then holds 30 scratch fields
+ * les_create (FP64 form only: the workspace then holds 50 scratch fields
  * and a third viscosity field).  SYNCHRONISES the stream. */
 int les_dynamic_coefficients(les_ctx *ctx, const double *Q, double out[9],
                              les_stream_t stream);

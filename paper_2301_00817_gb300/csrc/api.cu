@@ -168,7 +168,7 @@ void layout(les_ctx* c) {
   c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
   c->off_sc = o; o = align256(o + sizeof(DevScalars));
   c->off_part = o; o = align256(o + 8 * (size_t)lesjet::kMaxPartials * sizeof(double));
-  c->off_dyn = o; o = align256(o + (c->dyn_ws ? 30 * N * sizeof(double) : 0));
+  c->off_dyn = o; o = align256(o + (c->dyn_ws ? 50 * N * sizeof(double) : 0));
   c->off_dtl = o; o = align256(o + (c->p.dt_mode == LES_DT_LOCAL ? N * rs : 0));
   c->local_dt = c->p.dt_mode == LES_DT_LOCAL;
   c->total = o;

@@ -5,14 +5,14 @@
 //   k_dyn_products  per node: the 25 fields the test filter acts on (rho,
 //                   rho u_i, rho T, rho u_i u_j, rho|S| S_ij, rho|S| S_mm,
 //                   rho|S|^2, rho u_j T, rho|S| dT/dx_j);
-//   k_dyn_filter    the test filter of rho, rho u_i, rho T (the Favre
-//                   filtered velocity and temperature need them at the
-//                   neighbours of every node);
-//   k_dyn_sums      per interior node: the other 20 fields filtered on the
-//                   spot, the strain of the Favre-filtered velocity, the
-//                   Leonard-type terms, and the six J^-1-weighted sums of
-//                   the numerators and denominators; fixed-grid block
-//                   partials (deterministic);
+//   k_dyn_filter1   the test filter, one direction per pass (zeta, eta, xi:
+//                   the filter is a tensor product, so three 3-point passes
+//                   replace the 27-point sum);
+//   k_dyn_favre     the Favre-filtered velocity and temperature per node;
+//   k_dyn_sums      per interior node: the strain of the Favre-filtered
+//                   velocity, the Leonard-type terms, and the six
+//                   J^-1-weighted sums of the numerators and denominators;
+//                   fixed-grid block partials (deterministic);
 //   k_dyn_final     one block: fixed-order totals and the coefficients
 //                   C_ds, C_I (clipped at 0) and Pr_sgs (the configured
 //                   value when the dynamic one is not positive).
@@ -29,37 +29,6 @@ namespace {
 constexpr int kDynFields = 25;
 constexpr int kDynSums = 7;  // six weighted sums and the sum of the weights
 
-// The 27 (index, weight) pairs of the test filter at node c; returns the
-// number of pairs with a non-zero weight.
-__device__ __forceinline__ int filter_stencil(const Grid& g, const int c[3], long long idx[27],
-                                              double wt[27]) {
-  int cm[3][3];
-  double w1[3][3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int nd = g.n[d];
-    const bool face = !g.per[d] && (c[d] == 0 || c[d] == nd - 1);
-#pragma unroll
-    for (int o = 0; o < 3; ++o) {
-      int v = c[d] + o - 1;
-      v = v < 0 ? v + nd : (v >= nd ? v - nd : v);
-      cm[d][o] = v;
-      w1[d][o] = face ? (o == 1 ? 1.0 : 0.0) : (o == 1 ? 0.5 : 0.25);
-    }
-  }
-  int k = 0;
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b)
-      for (int e = 0; e < 3; ++e) {
-        const double w = w1[0][a] * w1[1][b] * w1[2][e];
-        if (w == 0.0) continue;
-        idx[k] = ((long long)cm[0][a] * g.n[1] + cm[1][b]) * g.n[2] + cm[2][e];
-        wt[k] = w;
-        ++k;
-      }
-  return k;
-}
-
 // Cartesian gradient of a node field through the node's metrics.
 __device__ __forceinline__ void grad_of(const Grid& g, const double* __restrict__ M,
                                         const double* __restrict__ f, long long n, const int c[3],
@@ -68,35 +37,6 @@ __device__ __forceinline__ void grad_of(const Grid& g, const double* __restrict_
   double dd[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) dd[d] = node_deriv(g, f, n, c, d);
-#pragma unroll
-  for (int x = 0; x < 3; ++x)
-    out[x] = M[x * N + n] * dd[0] + M[(3 + x) * N + n] * dd[1] + M[(6 + x) * N + n] * dd[2];
-}
-
-// Node-centred derivative along d of the Favre average Fh[q]/Fh[0].
-__device__ __forceinline__ double favre_deriv(const Grid& g, const double* __restrict__ Fh, int q,
-                                              long long n, const int c[3], int d) {
-  const long long N = g.N;
-  const long long s = g.stride[d];
-  const int nd = g.n[d];
-  auto f = [&](long long m) { return Fh[q * N + m] / Fh[m]; };
-  if (g.per[d]) {
-    const long long np = (c[d] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
-    const long long nm = (c[d] == 0) ? n + (long long)(nd - 1) * s : n - s;
-    return 0.5 * (f(np) - f(nm));
-  }
-  if (c[d] == 0) return 0.5 * (-3.0 * f(n) + 4.0 * f(n + s) - f(n + 2 * s));
-  if (c[d] == nd - 1) return 0.5 * (3.0 * f(n) - 4.0 * f(n - s) + f(n - 2 * s));
-  return 0.5 * (f(n + s) - f(n - s));
-}
-
-__device__ __forceinline__ void favre_grad(const Grid& g, const double* __restrict__ M,
-                                           const double* __restrict__ Fh, int q, long long n,
-                                           const int c[3], double out[3]) {
-  const long long N = g.N;
-  double dd[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) dd[d] = favre_deriv(g, Fh, q, n, c, d);
 #pragma unroll
   for (int x = 0; x < 3; ++x)
     out[x] = M[x * N + n] * dd[0] + M[(3 + x) * N + n] * dd[1] + M[(6 + x) * N + n] * dd[2];
@@ -155,29 +95,47 @@ __global__ void __launch_bounds__(256) k_dyn_products(Grid g, const double* __re
   }
 }
 
-// Filtered copies of fields [0, count) of D into F.
-__global__ void __launch_bounds__(256) k_dyn_filter(Grid g, const double* __restrict__ D, int count,
-                                                    double* __restrict__ F) {
+// One pass of the test filter along direction D for `count` fields:
+// dst = (src_{-1} + 2 src_0 + src_{+1})/4 along D (periodic wrap), the
+// identity at the faces of a non-periodic D.
+template <int D>
+__global__ void __launch_bounds__(256) k_dyn_filter1(Grid g, const double* __restrict__ src,
+                                                     int count, double* __restrict__ dst) {
   const long long N = g.N;
+  const long long s = g.stride[D];
+  const int nd = g.n[D];
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     int c[3];
     decompose(g, n, c);
-    long long idx[27];
-    double wt[27];
-    const int k = filter_stencil(g, c, idx, wt);
-    for (int q = 0; q < count; ++q) {
-      double s = 0.0;
-      for (int t = 0; t < k; ++t) s += wt[t] * D[q * N + idx[t]];
-      F[q * N + n] = s;
+    const bool face = !g.per[D] && (c[D] == 0 || c[D] == nd - 1);
+    if (face) {
+      for (int q = 0; q < count; ++q) dst[q * N + n] = src[q * N + n];
+      continue;
     }
+    const long long np = (c[D] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
+    const long long nm = (c[D] == 0) ? n + (long long)(nd - 1) * s : n - s;
+    for (int q = 0; q < count; ++q)
+      dst[q * N + n] = 0.25 * src[q * N + nm] + 0.5 * src[q * N + n] + 0.25 * src[q * N + np];
+  }
+}
+
+// Favre-filtered velocity and temperature u^_i = (rho u_i)^/rho^,
+// T^ = (rho T)^/rho^ at every node, from the filtered fields F.
+__global__ void __launch_bounds__(256) k_dyn_favre(long long N, const double* __restrict__ F,
+                                                   double* __restrict__ H) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const double r = F[n];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) H[q * N + n] = F[(1 + q) * N + n] / r;
   }
 }
 
 __global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const double* __restrict__ M,
                                                   const double* __restrict__ node,
-                                                  const double* __restrict__ D,
                                                   const double* __restrict__ Fh,
+                                                  const double* __restrict__ H,
                                                   double* __restrict__ partials) {
   const long long N = g.N;
   double acc[kDynSums] = {0, 0, 0, 0, 0, 0, 0};
@@ -195,20 +153,13 @@ __global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const double* __restri
     grad_of(g, M, node + 4 * N, n, c, dT);
     strain(gr, S);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) favre_grad(g, M, Fh, 1 + q, n, c, grh[q]);
-    favre_grad(g, M, Fh, 4, n, c, dTh);
+    for (int q = 0; q < 3; ++q) grad_of(g, M, H + q * N, n, c, grh[q]);
+    grad_of(g, M, H + 3 * N, n, c, dTh);
     const double Shm = strain(grh, Sh);
-    // the other 20 fields, filtered at this node
-    long long idx[27];
-    double wt[27];
-    const int kk = filter_stencil(g, c, idx, wt);
+    // the filtered fields at this node (Fh holds all 25)
     double fh[kDynFields];
-#pragma unroll 1
-    for (int q = 5; q < kDynFields; ++q) {
-      double s = 0.0;
-      for (int t = 0; t < kk; ++t) s += wt[t] * D[q * N + idx[t]];
-      fh[q] = s;
-    }
+#pragma unroll
+    for (int q = 5; q < kDynFields; ++q) fh[q] = Fh[q * N + n];
     const double rh = Fh[n];
     const double mh[3] = {Fh[N + n], Fh[2 * N + n], Fh[3 * N + n]};
     double L[3][3], Fs[3][3];
@@ -299,13 +250,16 @@ __global__ void k_dyn_final(const double* __restrict__ partials, double pr_defau
 void launch_dynamic64(const Grid& g, const les_params& p, const StageIO64& io, double* scratch,
                       const Launch& L) {
   const int th = 256, nb = blocks_for(g.N, th);
-  double* D = scratch;
-  double* Fh = scratch + (long long)kDynFields * g.N;
+  double* D = scratch;                                 // products, then the eta pass
+  double* T = scratch + (long long)kDynFields * g.N;  // zeta pass, then the filtered fields
   k_dyn_products<<<nb, th, 0, L.s>>>(g, io.Qin, io.M, io.node, D);
-  k_dyn_filter<<<nb, th, 0, L.s>>>(g, D, 5, Fh);
-  k_dyn_sums<<<kRedBlocks, kRedThreads, 0, L.s>>>(g, io.M, io.node, D, Fh, io.partials);
+  k_dyn_filter1<2><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
+  k_dyn_filter1<1><<<nb, th, 0, L.s>>>(g, T, kDynFields, D);
+  k_dyn_filter1<0><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
+  k_dyn_favre<<<nb, th, 0, L.s>>>(g.N, T, D);  // D is free again: u^, v^, w^, T^
+  k_dyn_sums<<<kRedBlocks, kRedThreads, 0, L.s>>>(g, io.M, io.node, T, D, io.partials);
   k_dyn_final<<<1, 32 * kDynSums, 0, L.s>>>(io.partials, p.Pr_sgs, io.sc);
-  *L.counter += 4;
+  *L.counter += 7;
 }
 
 }  // namespace lesjet

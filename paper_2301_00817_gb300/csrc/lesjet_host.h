@@ -40,7 +40,7 @@ struct StageIO64 {
   double* partials;    // [kRedBlocks] block minima (dt)
   DevScalars* sc;
   double* dtl = nullptr;  // [N] local steps (dt_mode LOCAL), else nullptr
-  double* dyn = nullptr;  // [30][N] scratch of the dynamic SGS procedure
+  double* dyn = nullptr;  // [50][N] scratch of the dynamic SGS procedure
 };
 void launch_node64(const Grid& g, const les_params& p, const StageIO64& io, bool with_dt,
                    const Launch& L);
