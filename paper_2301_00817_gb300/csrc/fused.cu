@@ -735,6 +735,10 @@ __global__ void __launch_bounds__(FNT, 1)
   if (own && jint && kint && (per_i || ib - 1 >= 0))
     xi_flux(ib - 1, s_m, s_c, s_m, s_c, l_p, l_c, nullptr, nullptr, nullptr, nullptr, Fx_prev);
   const float adt = (MODE == FMODE_RHS) ? 0.f : (float)(alpha * sc->dt);
+  // plane ib+1 has landed (this thread's copies; the barrier makes everyone's
+  // visible) and the xi flux above is done with the slots of plane ib-1
+  cp_async_wait<0>();
+  __syncthreads();
 
   for (int i = ib; i < ie; ++i) {
     // own-column queue: planes i-1 .. i+2
@@ -747,9 +751,10 @@ __global__ void __launch_bounds__(FNT, 1)
     }
     finish_W(Wq[3], pq[3], vq[3]);  // plane i+2, fetched one iteration ago
     fetch_q(i + 3);
-    // plane i+1 has landed; reuse the slots of plane i-1 for plane i+2
-    cp_async_wait<0>();
-    __syncthreads();
+    // Plane i+1 has landed and is visible, and nothing reads the slots of
+    // plane i-1 any more: both were settled by the barrier that closed the
+    // previous flux phase (or the prologue), so plane i+2 is staged into
+    // those slots and plane i+1 derived without a barrier of their own.
     stage_plane(s_m, i + 2);
     cp_async_commit();
     derive_plane(s_p, s_p, s_p, l_p);
@@ -805,6 +810,10 @@ __global__ void __launch_bounds__(FNT, 1)
         for (int c = 0; c < 5; ++c) sFz[(c * FTJ + rr) * (FTK + 1)] = F[c];
       }
     }
+    // plane i+2, staged at the top of this iteration, must have landed before
+    // the next iteration derives it: wait here, and let this barrier (which
+    // also publishes the eta/zeta fluxes) make it visible
+    cp_async_wait<0>();
     __syncthreads();
     float hc[5];
 #pragma unroll
@@ -862,9 +871,10 @@ __global__ void __launch_bounds__(FNT, 1)
       l_c = l_p;
       l_p = u;
     }
-    // no barrier here: every shared slot read above is next written either by
-    // the staging or derivation after the next iteration's first barrier, or
-    // by the flux phase after its second
+    // no barrier here: the epilogue reads only the exchange fluxes and
+    // registers; the next iteration's staging and derivation write other
+    // slots, and its flux phase writes the exchange buffers only after the
+    // barrier that follows the derivation
   }
   cp_async_wait<0>();
   __syncthreads();

@@ -490,12 +490,17 @@ def test_full_size_step_c2(orc, lj, torch):
 
 # ------------------------------------------------------------- robustness
 
-def test_deterministic_bitwise(lj, torch):
-    shape = C1
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_deterministic_bitwise(lj, torch, prec):
+    """Two runs give the same bits: fixed-order reductions, and no race in the
+    fused kernel's shared-memory pipeline (the mixed case runs 96 x 160 x 128:
+    many CTAs and axial chunks)."""
+    shape = C1 if prec == "fp64" else (96, 160, 128)
+    pc = lj.PREC_FP64 if prec == "fp64" else lj.PREC_MIXED
     xyz = lj.synth.jet_grid(*shape)
     outs = []
     for _ in range(2):
-        ctx, xyz_d = device_ctx(lj, torch, shape, xyz, sgs_model=2)
+        ctx, xyz_d = device_ctx(lj, torch, shape, xyz, sgs_model=2, precision=pc)
         Q = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
         ctx.les_init_jet(xyz_d, 77, 1e-3, Q)
         d = ctx.les_run_n_steps(10, Q)
