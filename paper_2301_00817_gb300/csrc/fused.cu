@@ -413,7 +413,10 @@ __global__ void __launch_bounds__(FNT, 1)
   auto stage_plane = [&](int slot, int x) {
     const int ig = wrap_fast(x, ni, G.per[0]);
     constexpr int JQ = 5 * R2, JM = 10 * R1, JK = 2 * R1;
-    if (tid >= JQ + JM + JK) return;
+    // one row per thread, taken by the highest-numbered threads: the lowest
+    // ones derive a second node record in the same phase
+    const int tid = threadIdx.x - (FNT - (JQ + JM + JK));
+    if (tid < 0) return;
     const float* src;
     float* dst;
     int jj, halo;
