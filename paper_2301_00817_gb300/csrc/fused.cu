@@ -770,17 +770,19 @@ __global__ void __launch_bounds__(FNT, 1)
     float mo[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) mo[t] = sM[(s_c * 10 + t) * PL1 + o1];
-    // and its node records; in the stage modes also those of planes i+1 and
-    // i-1 of the own column (the last stage keeps them in shared memory: its
-    // compensated update needs the registers)
+    // and its node records; in the global-step stage and residual modes also
+    // those of planes i+1 and i-1 of the own column (the last stage and the
+    // local-step variants keep them in shared memory: their epilogues need
+    // the registers)
     const float4 ro = sPr[s_c * PL2 + o2];
     const float2 wo = sPw[s_c * PL2 + o2];
+    constexpr bool keep_pm = MODE != FMODE_LAST && !LOCAL;
     float4 rq[2];
-    if (MODE != FMODE_LAST) {
+    if (keep_pm) {
       rq[0] = sPr[s_p * PL2 + o2];
       rq[1] = sPr[s_m * PL2 + o2];
     }
-    const float4* rpm = (MODE != FMODE_LAST) ? rq : nullptr;
+    const float4* rpm = keep_pm ? rq : nullptr;
     if (own && jint && kint && (per_i || i + 1 <= ni - 1))
       xi_flux(i, s_c, s_p, s_c, s_p, l_c, l_p, mo, &ro, rpm, &wo, Fx);
     if (own && iint && kint) {
