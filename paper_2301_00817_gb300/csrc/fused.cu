@@ -556,10 +556,6 @@ __global__ void __launch_bounds__(FNT, 1)
     for (int c = 0; c < 4; ++c) W[c] = qn[c];
     W[4] = qn[4] + p;
   };
-  auto load_W = [&](int x, float W[5], float& p, bool& valid) {
-    fetch_q(x);
-    finish_W(W, p, valid);
-  };
 
   // xi interface (x, x+1) of the own column: sPr/sPw/sM/sK/sL slots of both planes
   auto xi_flux = [&](int x, int p0, int p1, int m0, int m1, int l0, int l1, const float* mown,
@@ -723,10 +719,30 @@ __global__ void __launch_bounds__(FNT, 1)
   cp_async_commit();
   stage_plane(s_p, ib + 1);
   cp_async_commit();
-  load_W(ib - 2, Wq[0], pq[0], vq[0]);
-  load_W(ib - 1, Wq[1], pq[1], vq[1]);
-  load_W(ib, Wq[2], pq[2], vq[2]);
-  load_W(ib + 1, Wq[3], pq[3], vq[3]);
+  // the own column's planes ib-2 .. ib+1: all loads issued before any is used
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int igq = wrap_fast(ib - 2 + q, ni, G.per[0]);
+    vq[q] = own && igq >= 0;
+    if (vq[q]) {
+      const int n = (igq * nj + jown) * nk + kown;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Wq[q][c] = __ldg(P.qin[c] + n);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!vq[q]) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Wq[q][c] = 0.f;
+      pq[q] = 1.f;
+      continue;
+    }
+    const float ir = __frcp_rn(Wq[q][0]);
+    const float u = Wq[q][1] * ir, v = Wq[q][2] * ir, w = Wq[q][3] * ir;
+    pq[q] = K.gm1 * (Wq[q][4] - 0.5f * Wq[q][0] * (u * u + v * v + w * w));
+    Wq[q][4] += pq[q];
+  }
   fetch_q(ib + 2);  // enters the queue in the first iteration
   fetch_h(ib);
   cp_async_wait<1>();
