@@ -58,6 +58,9 @@ NCU_COUNTS = {
         (111.3, "374d4b82a9a3e942a79633cc14971682d0c9743848d61dd0b0c371fe63110559"),
     ("stage_fused", "fp32_flop_per_point"):
         (1171, "374d4b82a9a3e942a79633cc14971682d0c9743848d61dd0b0c371fe63110559"),
+    # smsp__inst_executed.sum x 32 per point, mean of the five stages
+    ("stage_fused", "inst_per_point"):
+        (1857, "374d4b82a9a3e942a79633cc14971682d0c9743848d61dd0b0c371fe63110559"),
 }
 NCU_CAPTURE = {"stage_fused": "profiles/stage_fused_jet96x160x128.md"}
 # FP64 flop per grid point of one residual's flux launches (three
@@ -647,6 +650,24 @@ def run_ours(args, world, rank, local):
                 "peak_source": "measured FP32 FMA chains (les_measure_fma_peak)",
                 "flop_per_point": fpp}
 
+    def roofline_issue(res):
+        # instruction issue: every SM issues at most one warp-instruction per
+        # scheduler per clock (152 SMs x 4 schedulers on GB300), at the SM
+        # clock sampled during the timed region
+        ms_tot, n_launch = res["prof"].get("stage_fused", (0.0, 0))
+        ipp = traffic_per_point("stage_fused", "inst_per_point")
+        clk = (res.get("clocks") or {}).get("sm_mhz")
+        if not n_launch or ipp is None or not clk:
+            return None
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        peak = sms * 4 * clk * 1e6 / 1e9  # G warp-instructions/s
+        achieved = ipp / 32.0 * N / (ms_tot / n_launch / 1e3) / 1e9
+        return {"kernel": "stage_fused", "bound": "issue", "achieved": achieved, "peak": peak,
+                "unit": "G warp-instructions/s", "frac": achieved / peak,
+                "peak_source": f"{sms} SMs x 4 schedulers x {clk:.0f} MHz (sampled SM clock)",
+                "inst_per_point": ipp}
+
     mixed, fp64 = results["mixed"], results["fp64"]
     ms_step = mixed["ms"] / args.steps
     value = aggregate_rate(world, N, args.steps, mixed["ms"])
@@ -662,6 +683,7 @@ def run_ours(args, world, rank, local):
                    "l2": "state and metrics (~0.9 GB) exceed the 129 MB L2; no flush needed"},
         "roofline": roofline(mixed, 1),
         "roofline_alu": roofline_fp32_alu(mixed),
+        "roofline_issue": roofline_issue(mixed),
         "fma_peaks_tflops": fma_peaks,
         "cpu_baseline": cpu,
         "e2e": {"value": world * N * args.steps / e2e_s / 1e9, "unit": UNIT,
