@@ -604,11 +604,11 @@ int les_run_host(les_ctx* c, int n, double* Q_host, double* Q_dev, les_diag* dia
                  les_stream_t stream) {
   int rc = ready(c);
   if (rc != LES_OK) return rc;
-  if (!Q_host || !Q_dev) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!Q_host || !Q_dev || n < 0) return fail(c, LES_ERR_INVALID_ARG, "null pointer or negative n");
   if (!aligned16(Q_dev)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = 5 * (size_t)c->g.N * sizeof(double);
-  if (is_mixed(c) && n >= 0) {
+  if (is_mixed(c)) {
     // mapped pinned memory: the split kernel reads the host state and the
     // join kernel writes it back over the host link, with no FP64 staging
     // copy (the float pair state lives in the workspace in between)
