@@ -344,8 +344,9 @@ __global__ void k_adj_sensor(Grid g, const double* __restrict__ node, double* __
       const double s = P[xp] - 2.0 * P[xc] + P[xm];
       const double den = P[xp] + 2.0 * P[xc] + P[xm];
       // nu = |s| / den
-      const double ls = ln * sgn_abs(s) / den;
-      const double lden = -ln * fabs(s) / (den * den);
+      const double iden = 1.0 / den;
+      const double ls = ln * sgn_abs(s) * iden;
+      const double lden = -ln * fabs(s) * iden * iden;
       atomicAdd(A + AP * N + xp, ls + lden);
       atomicAdd(A + AP * N + xc, -2.0 * ls + 2.0 * lden);
       atomicAdd(A + AP * N + xm, ls + lden);
@@ -383,10 +384,12 @@ __global__ void __launch_bounds__(256, 2) k_adj_node(Grid g, Consts<double> K, c
       }
       const double s01 = sqrt(l[0] * l[1]), s02 = sqrt(l[0] * l[2]), s12 = sqrt(l[1] * l[2]);
       const double c01 = llb0 + llb1, c02 = llb0 + llb2, c12 = llb1 + llb2;
+      // d sqrt(l_a l_b)/d l_a = l_b/(2 sqrt(l_a l_b)): one reciprocal per pair
+      const double h01 = c01 / (2.0 * s01), h02 = c02 / (2.0 * s02), h12 = c12 / (2.0 * s12);
       double ll[3];
-      ll[0] = llb0 + c01 * l[1] / (2.0 * s01) + c02 * l[2] / (2.0 * s02);
-      ll[1] = llb1 + c01 * l[0] / (2.0 * s01) + c12 * l[2] / (2.0 * s12);
-      ll[2] = llb2 + c02 * l[0] / (2.0 * s02) + c12 * l[1] / (2.0 * s12);
+      ll[0] = llb0 + h01 * l[1] + h02 * l[2];
+      ll[1] = llb1 + h01 * l[0] + h12 * l[2];
+      ll[2] = llb2 + h02 * l[0] + h12 * l[1];
       double la = 0.0;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
