@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
     const long long m0 = step(g, n, c, 0, -1);
     const long long m1 = step(g, n, c, 1, -1);
     const long long m2 = step(g, n, c, 2, -1);
-    const double Jinv = (double)M[9 * N + n];
+    const double Jn = (MODE == 0) ? 0.0 : 1.0 / (double)M[9 * N + n];  // J, once per node
+    const double a = (MODE == 0) ? 0.0 : (dtl ? alpha * dtl[n] : adt);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       R r = R(0);
@@ -415,8 +416,7 @@ __global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
       if (MODE == 0) {
         out[q * N + n] = (TO)r;
       } else {
-        const double a = dtl ? alpha * dtl[n] : adt;
-        out[q * N + n] = (TO)(Q0[q * N + n] - a * ((double)r / Jinv));
+        out[q * N + n] = (TO)(Q0[q * N + n] - a * (Jn * (double)r));
       }
     }
   }
