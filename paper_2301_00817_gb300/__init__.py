@@ -390,6 +390,11 @@ class Solver:
         self.ctx.les_rhs(Q, R)
         return R
 
+    def step(self, Q):
+        """One time step in place (Delta t, five RK stages, boundary conditions)."""
+        self.ctx.les_rk_step(Q)
+        return Q
+
     def run(self, Q, n: int) -> LesDiag:
         return self.ctx.les_run_n_steps(n, Q)
 
