@@ -7,9 +7,12 @@
 //             radii lbar (optionally the block minima of the CFL step);
 //   k_mu      per node: mu_eff, kappa_eff (Sutherland + SGS);
 //   k_flux<D> per interface (n, n + e_D): centred inviscid flux minus J^-1
-//             times the Turkel-Vatsa dissipation minus the viscous flux;
+//             times the Turkel-Vatsa dissipation minus the viscous flux,
+//             stored as exactly twice its value (the interface means'
+//             factors 1/2 are folded away);
 //   k_update  per node: RHS = sum_D (F_{+1/2} - F_{-1/2}) and the stage
-//             update Q^(l) = Q^(0) - alpha_l dt J RHS (or RHS itself).
+//             update Q^(l) = Q^(0) - alpha_l dt J RHS (or RHS itself), with
+//             the factor 2 taken out once per node.
 // Each interface is computed once and read by its two nodes, so the scheme
 // telescopes exactly.  The kernels are written for a compute type R and are
 // instantiated for double only (the mixed form uses fused.cu).

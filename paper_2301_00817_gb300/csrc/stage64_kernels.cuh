@@ -239,6 +239,11 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
   const R* __restrict__ P = node + 3 * N;
   const R* __restrict__ Tt = node + 4 * N;
   const R* __restrict__ LB = node + (5 + D) * N;
+  // The interface means are left as sums of the two nodes' values and their
+  // powers of two are folded into a few factors (exact in binary floating
+  // point): F is written as exactly 2x the interface flux, and k_update
+  // halves J once per node.
+  const R k2h = R(0.5) * K.k2, k4h = R(0.5) * K.k4;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     int c[3];
@@ -283,11 +288,11 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
     // Turkel-Vatsa dissipation (Eqs. dissip_term, eps_2/4_dissip, W_dissip)
     const R nua = sensor<D>(g, P, a, c[D]);
     const R nub = sensor<D>(g, P, b, cb[D]);
-    const R eps2 = K.k2 * dev_max(nua, nub);
-    const R eps4 = dev_max(R(0), K.k4 - eps2);
-    const R lam = R(0.5) * (LB[a] + LB[b]);
-    const R Jh = R(0.5) * (Ja + Jb);
-    R Fq[5];
+    const R eps2 = k2h * dev_max(nua, nub);    // half of eps^(2)
+    const R eps4 = dev_max(R(0), k4h - eps2);  // half of eps^(4)
+    const R sJ = Ja + Jb;                      // 2 J^-1 at the interface
+    const R lJ = (LB[a] + LB[b]) * sJ;         // 4 lambda J^-1 at the interface
+    R Fq[5];                                   // 2x
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       const R wa = (q == 4) ? Qa[4] + pa : Qa[q];
@@ -307,11 +312,13 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
         Dp = -D1;
       }
       const R D3 = Dp - R(2) * D1 + Dm;
-      Fq[q] = R(0.5) * (Fa[q] + Fb[q]) - Jh * (lam * (eps2 * D1 - eps4 * D3));
+      Fq[q] = (Fa[q] + Fb[q]) - lJ * (eps2 * D1 - eps4 * D3);
     }
 
     // viscous + SGS flux with compact interface gradients (Eqs.
-    // hat-flux-Ev/Fv/Gv, tau_mod, q_mod with Fourier's sign)
+    // hat-flux-Ev/Fv/Gv, tau_mod, q_mod with Fourier's sign); the tangential
+    // derivatives are kept as 4x their value (the 1/4 of the mean of the two
+    // central differences is folded away)
     const R* phi[4] = {U, V, Wv, Tt};
     R dphi[4][3];
 #pragma unroll
@@ -321,38 +328,43 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
       const long long bpp = step(g, b, cb, T1, 1), bm = step(g, b, cb, T1, -1);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        dphi[q][T1] = R(0.25) * ((phi[q][ap] - phi[q][amm]) + (phi[q][bpp] - phi[q][bm]));
+        dphi[q][T1] = (phi[q][ap] - phi[q][amm]) + (phi[q][bpp] - phi[q][bm]);
     }
     {
       const long long ap = step(g, a, c, T2, 1), amm = step(g, a, c, T2, -1);
       const long long bpp = step(g, b, cb, T2, 1), bm = step(g, b, cb, T2, -1);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        dphi[q][T2] = R(0.25) * ((phi[q][ap] - phi[q][amm]) + (phi[q][bpp] - phi[q][bm]));
+        dphi[q][T2] = (phi[q][ap] - phi[q][amm]) + (phi[q][bpp] - phi[q][bm]);
     }
+    // interface metrics: 8x the mean along the normal, 2x along the
+    // tangents, so that every product with dphi is 8x its value
     R mh[3][3];
 #pragma unroll
     for (int t = 0; t < 3; ++t)
 #pragma unroll
       for (int x = 0; x < 3; ++x)
-        mh[t][x] = R(0.5) * ((R)M[(3 * t + x) * N + a] + (R)M[(3 * t + x) * N + b]);
-    R gr[4][3];
+        mh[t][x] = (R)M[(3 * t + x) * N + a] + (R)M[(3 * t + x) * N + b];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) mh[D][x] = R(4) * mh[D][x];
+    R gr[4][3];  // 8 grad(u, v, w, T)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int x = 0; x < 3; ++x)
         gr[q][x] = mh[0][x] * dphi[q][0] + mh[1][x] * dphi[q][1] + mh[2][x] * dphi[q][2];
-    const R mu = R(0.5) * (mk[a] + mk[b]);
-    const R kap = R(0.5) * (mk[N + a] + mk[N + b]);
+    const R mu = mk[a] + mk[b];                      // 2 mu
+    const R kap = R(2) * (mk[N + a] + mk[N + b]);    // 4 kappa
     const R div = gr[0][0] + gr[1][1] + gr[2][2];
     const R two3 = R(2.0 / 3.0);
+    // 16 tau
     R txx = mu * (R(2) * gr[0][0] - two3 * div);
     R tyy = mu * (R(2) * gr[1][1] - two3 * div);
     R tzz = mu * (R(2) * gr[2][2] - two3 * div);
     if (K.sgs == LES_SGS_DYNAMIC) {
       // the modelled isotropic SGS stress sigma_ll/3 (Eq. yoshizawa) at the
       // interface mean, subtracted from the normal stresses
-      const R iso = R(0.5) * (mk[2 * N + a] + mk[2 * N + b]) / R(3);
+      const R iso = R(8) * (mk[2 * N + a] + mk[2 * N + b]) / R(3);  // 16 sigma_ll / 3
       txx -= iso;
       tyy -= iso;
       tzz -= iso;
@@ -360,18 +372,21 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
     const R txy = mu * (gr[0][1] + gr[1][0]);
     const R txz = mu * (gr[0][2] + gr[2][0]);
     const R tyz = mu * (gr[1][2] + gr[2][1]);
-    const R uf = R(0.5) * (U[a] + U[b]);
-    const R vf = R(0.5) * (V[a] + V[b]);
-    const R wf = R(0.5) * (Wv[a] + Wv[b]);
+    const R uf = U[a] + U[b];  // 2 u at the interface
+    const R vf = V[a] + V[b];
+    const R wf = Wv[a] + Wv[b];
+    // 32 (tau u + kappa grad T)
     const R bx = txx * uf + txy * vf + txz * wf + kap * gr[3][0];
     const R by = txy * uf + tyy * vf + tyz * wf + kap * gr[3][1];
     const R bz = txz * uf + tyz * vf + tzz * wf + kap * gr[3][2];
     const R mx = mh[D][0], my = mh[D][1], mz = mh[D][2];
+    // 2 J^-1 m.tau = sJ (8 m).(16 tau) / 128 and 2 J^-1 m.b = sJ (8 m).(32 b) / 256
+    const R c1 = sJ * R(1.0 / 128.0), c2 = sJ * R(1.0 / 256.0);
     F[n] = Fq[0];
-    F[N + n] = Fq[1] - Jh * (mx * txx + my * txy + mz * txz);
-    F[2 * N + n] = Fq[2] - Jh * (mx * txy + my * tyy + mz * tyz);
-    F[3 * N + n] = Fq[3] - Jh * (mx * txz + my * tyz + mz * tzz);
-    F[4 * N + n] = Fq[4] - Jh * (mx * bx + my * by + mz * bz);
+    F[N + n] = Fq[1] - c1 * (mx * txx + my * txy + mz * txz);
+    F[2 * N + n] = Fq[2] - c1 * (mx * txy + my * tyy + mz * tyz);
+    F[3 * N + n] = Fq[3] - c1 * (mx * txz + my * tyz + mz * tzz);
+    F[4 * N + n] = Fq[4] - c2 * (mx * bx + my * by + mz * bz);
   }
 }
 
@@ -405,7 +420,8 @@ __global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
     const long long m0 = step(g, n, c, 0, -1);
     const long long m1 = step(g, n, c, 1, -1);
     const long long m2 = step(g, n, c, 2, -1);
-    const double Jn = (MODE == 0) ? 0.0 : 1.0 / (double)M[9 * N + n];  // J, once per node
+    // J once per node, halved: k_flux writes 2x the interface fluxes
+    const double Jn = (MODE == 0) ? 0.0 : 0.5 / (double)M[9 * N + n];
     const double a = (MODE == 0) ? 0.0 : (dtl ? alpha * dtl[n] : adt);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -414,7 +430,7 @@ __global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
       r += F1[q * N + n] - F1[q * N + m1];
       r += F2[q * N + n] - F2[q * N + m2];
       if (MODE == 0) {
-        out[q * N + n] = (TO)r;
+        out[q * N + n] = (TO)(R(0.5) * r);
       } else {
         out[q * N + n] = (TO)(Q0[q * N + n] - a * (Jn * (double)r));
       }
