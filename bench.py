@@ -52,7 +52,9 @@ BYTES_PER_POINT = {
 # describes the kernel source it was taken on only: bench.py reports it
 # while the hash of that source still matches.
 NCU_SOURCES = {"stage_fused": ("paper_2301_00817_gb300/csrc/fused.cu",
-                               "paper_2301_00817_gb300/csrc/lesjet_dev.cuh")}
+                               "paper_2301_00817_gb300/csrc/lesjet_dev.cuh"),
+               "flux64": ("paper_2301_00817_gb300/csrc/stage64_kernels.cuh",
+                          "paper_2301_00817_gb300/csrc/lesjet_dev.cuh")}
 NCU_COUNTS = {
     ("stage_fused", "bytes_per_point"):
         (111.3, "374d4b82a9a3e942a79633cc14971682d0c9743848d61dd0b0c371fe63110559"),
@@ -61,12 +63,13 @@ NCU_COUNTS = {
     # smsp__inst_executed.sum x 32 per point, mean of the five stages
     ("stage_fused", "inst_per_point"):
         (1857, "374d4b82a9a3e942a79633cc14971682d0c9743848d61dd0b0c371fe63110559"),
+    # FP64 flop (dadd + 2 x dfma + dmul) per grid point of one residual's
+    # three k_flux launches on the 96 x 160 x 128 jet: 324 + 323 + 321
+    ("flux64", "fp64_flop_per_point"):
+        (969, "b3db6249386596169f8fce9d98b5bfb633dea4fd73065c02a8754b9dcf183bb0"),
 }
-NCU_CAPTURE = {"stage_fused": "profiles/stage_fused_jet96x160x128.md"}
-# FP64 flop per grid point of one residual's flux launches (three
-# directions), counted by ncu (dadd + 2 dfma + dmul) on the xi-direction
-# kernel of the same case: 350 per interface.
-FP64_FLUX_FLOP_PER_POINT = 3 * 350
+NCU_CAPTURE = {"stage_fused": "profiles/stage_fused_jet96x160x128.md",
+               "flux64": "profiles/flux64_jet96x160x128.md"}
 # FP64 peak derived from the unit counts: 152 SMs x 2 DFMA per cycle x
 # 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -627,16 +630,17 @@ def run_ours(args, world, rank, local):
 
     def roofline_fp64_alu(res):
         ms_tot, n_group = res["prof"].get("flux", (0.0, 0))
-        if not n_group:
+        fpp = traffic_per_point("flux64", "fp64_flop_per_point")
+        if not n_group or fpp is None:
             return None
         per_group_s = ms_tot / n_group / 1e3
-        achieved = FP64_FLUX_FLOP_PER_POINT * N / per_group_s / 1e12
+        achieved = fpp * N / per_group_s / 1e12
         peak = fma_peaks["fp64"]
         return {"kernel": "flux (3 directions)", "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "measured FP64 FMA chains (les_measure_fma_peak); derived from unit "
                                f"counts: {FP64_PEAK_TFLOPS:.3f}",
-                "flop_per_point": FP64_FLUX_FLOP_PER_POINT,
+                "flop_per_point": fpp, "flop_source": NCU_CAPTURE["flux64"],
                 "avg_group_us": per_group_s * 1e6}
 
     def roofline_fp32_alu(res):
