@@ -100,6 +100,8 @@ def _lib_handle():
             lib.orc_rk_step.argtypes = [P, i, i, i, _dp, _dp, _dp, C.c_double]
             lib.orc_rk_step.restype = C.c_double
             lib.orc_totals.argtypes = [i, i, i, _dp, _dp, _dp]
+            lib.orc_surface_functional.argtypes = [P, i, i, i, _dp, _dp, i, C.c_double]
+            lib.orc_surface_functional.restype = C.c_double
             lib.orc_num_threads.restype = C.c_int
             lib.orc_set_num_threads.argtypes = [i]
             RHSFN = C.CFUNCTYPE(None, C.c_void_p, _dp, _dp)
@@ -293,6 +295,28 @@ def run(P: OrcParams, Q, M, xyz, nsteps: int, t: float = 0.0):
         Q, d = rk_step(P, Q, M, xyz, t)
         t += d
     return Q, t
+
+
+def surface_functional(P: OrcParams, Q, M, j_surface: int, w: float = 1.0) -> float:
+    """w sum_{i,k} (p - 1/gamma)^2 J^-1 |grad eta| on the ring j = j_surface."""
+    Q, M = _f64(Q), _f64(M)
+    _, ni, nj, nk = Q.shape
+    if not 0 <= j_surface < nj:
+        raise ValueError("j_surface out of range")
+    return float(_lib_handle().orc_surface_functional(C.byref(P), ni, nj, nk, _ptr(Q), _ptr(M),
+                                                      j_surface, w))
+
+
+def window_functional(P: OrcParams, Q, M, xyz, nsteps: int, t0: float, j_surface: int) -> float:
+    """The adjoint window's functional along an oracle run: the sum over the
+    steps n = 1..nsteps of dt times the surface functional of Q^n (the state
+    after step n and its boundary conditions)."""
+    J, t = 0.0, t0
+    for _ in range(nsteps):
+        Q, d = rk_step(P, Q, M, xyz, t)
+        t += d
+        J += surface_functional(P, Q, M, j_surface, d)
+    return J
 
 
 def totals(Q, M) -> np.ndarray:

@@ -1271,6 +1271,32 @@ double orc_rk_step(const orc_params *P, int ni, int nj, int nk, double *Q,
   return dt;
 }
 
+/* Far-field functional of the adjoint window (scope-table row a11; the
+ * paper has none): w times the sum over the ring j = js of
+ * (p - p_inf)^2 dA, with p_inf = 1/gamma (the free stream at rest), p from
+ * System I (Sec. "Large Eddy Simulation Filtering") and dA = J^-1 |grad eta|
+ * the area of the node's eta face (Sec. "Transformation of Coordinates":
+ * J^-1 grad eta is the cross product of the xi and zeta tangents).  Summed
+ * in increasing (i, k). */
+double orc_surface_functional(const orc_params *P, int ni, int nj, int nk,
+                              const double *Q, const double *M, int js,
+                              double w) {
+  size_t N = (size_t)ni * nj * nk;
+  double gam = P->gamma, s = 0.0;
+  for (int i = 0; i < ni; ++i) {
+    for (int k = 0; k < nk; ++k) {
+      long n = (long)(((size_t)i * nj + js) * nk + k);
+      double rho, u, v, wv, p;
+      prim_of(gam, Q, N, n, &rho, &u, &v, &wv, &p);
+      double ex = M[3 * N + n], ey = M[4 * N + n], ez = M[5 * N + n];
+      double dA = M[9 * N + n] * sqrt(ex * ex + ey * ey + ez * ez);
+      double dp = p - 1.0 / gam;
+      s += dp * dp * dA;
+    }
+  }
+  return w * s;
+}
+
 void orc_totals(int ni, int nj, int nk, const double *Q, const double *M,
                 double out[5]) {
   size_t N = (size_t)ni * nj * nk;

@@ -115,6 +115,12 @@ void orc_rk5(int ncomp, size_t N, double *Q, const unsigned char *update,
 double orc_rk_step(const orc_params *P, int ni, int nj, int nk, double *Q,
                    const double *M, const double *xyz, double t);
 
+/* w sum_{i,k} (p(i, js, k) - 1/gamma)^2 J^-1 |grad eta| (i, js, k): the
+ * far-field functional of the adjoint window, one state's term. */
+double orc_surface_functional(const orc_params *P, int ni, int nj, int nk,
+                              const double *Q, const double *M, int js,
+                              double w);
+
 /* sum_n J^-1_n Q_c(n) for c = 0..4, summed in increasing n. */
 void orc_totals(int ni, int nj, int nk, const double *Q, const double *M,
                 double out[5]);

@@ -205,7 +205,8 @@ def test_adjoint_rejects_unsupported_settings(lj, torch):
 def test_window_gradient_against_torch_autograd(lj, torch, radius):
     """The hand-written adjoint against torch.autograd through the independent
     FP64 torch restatement of the step (16 x 8 x 8 jet, 6 steps, checkpoint
-    every 2), on the shear-layer surface and on the stated r = 5 surface."""
+    every 2), on the shear-layer surface and on the stated r = 5 surface; the
+    window's J also against the C oracle's window."""
     import oracle
     from oracle import torch_ref
     shape = (16, 8, 8)
@@ -228,6 +229,10 @@ def test_window_gradient_against_torch_autograd(lj, torch, radius):
     aw = ctx.adjoint_workspace(nsteps, K)
     J, g = ctx.les_adjoint_window(torch.from_numpy(Q0).cuda(), 0.0, nsteps, K, js, aw)
     assert math.isclose(J, float(Jt.detach()), rel_tol=1e-11), (J, float(Jt.detach()))
+    # and the C oracle's window (its steps, then its functional term)
+    Po = oracle.params(Re=500.0, dt_mode=1, dt_fixed=dt, amp=tuple(amps))
+    J_orc = oracle.window_functional(Po, Q0, M, xyz, nsteps, 0.0, js)
+    assert math.isclose(J, J_orc, rel_tol=2e-11), (J, J_orc)
     gmax = np.abs(g_ref).max()
     assert gmax > 0
     # the r = 5 gradient reaches the surface only through the numerical domain

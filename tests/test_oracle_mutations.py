@@ -80,6 +80,11 @@ MUTATIONS = {
                        ["test_yoshizawa_isotropic_stress_in_the_residual"]),
     "filter_faces": ("return off == 0 ? 1.0 : 0.0;", "return off == 0 ? 0.5 : 0.25;",
                      ["test_test_filter_transfer_function_and_faces"]),
+    "functional_face_row": ("double ex = M[3 * N + n], ey = M[4 * N + n], ez = M[5 * N + n];",
+                            "double ex = M[0 * N + n], ey = M[1 * N + n], ez = M[2 * N + n];",
+                            ["test_surface_functional_ring_area_closed_form"]),
+    "functional_reference_p": ("double dp = p - 1.0 / gam;", "double dp = p - 1.0;",
+                               ["test_surface_functional_ring_area_closed_form"]),
 }
 
 

@@ -1071,6 +1071,45 @@ def test_azimuthal_rotation_equivariance(orc):
     assert np.allclose(rotate(Q1), Q2, rtol=0, atol=1e-12)
 
 
+# ------------------------------------------------- adjoint window functional
+
+def test_surface_functional_ring_area_closed_form(orc):
+    """The window functional's term for a state whose pressure exceeds 1/gamma
+    by c on the ring j is w c^2 times the ring's eta-face area.  On the
+    cylindrical jet grid J^-1 |grad eta| = |x_zeta x x_xi| = x_xi r_j
+    sin(2 pi / nk) exactly (x depends on i only, y and z on j and k only), so
+    the area is nk r_j sin(2 pi / nk) sum_i x_xi(i), with x_xi the metrics'
+    second-order differences (numpy's gradient with second-order edges).  The
+    pressure is the System I one: random density and velocity at p = 1/gamma
+    give 0.  The xi or zeta rows in place of the eta row, a missing J^-1, or
+    the kinetic energy left in p all fail here."""
+    P = orc.params()
+    ni, nj, nk = 20, 12, 16
+    xyz = synth.jet_grid(ni, nj, nk)
+    M = orc.metrics(xyz)
+    x, r, _ = synth.jet_lines(ni, nj, nk)
+    rng = np.random.default_rng(11)
+    prim = np.empty((5, ni, nj, nk))
+    prim[0] = 0.8 + 0.4 * rng.random((ni, nj, nk))
+    prim[1:4] = 0.5 * rng.standard_normal((3, ni, nj, nk))
+    for j in (0, 5, nj - 1):
+        ring = nk * r[j] * math.sin(2.0 * math.pi / nk) * np.gradient(x, edge_order=2).sum()
+        for c in (0.0, 0.03, -0.05):
+            prim[4] = 1.0 / GAMMA + c
+            Q = orc.prim_to_cons(P, prim)
+            for w in (1.0, 2.5e-4):
+                J = orc.surface_functional(P, Q, M, j, w)
+                assert J == pytest.approx(w * c * c * ring, rel=1e-12, abs=1e-28)
+    # only the ring j enters
+    prim[4] = 1.0 / GAMMA
+    prim[4][:, 4] += 0.1
+    Q = orc.prim_to_cons(P, prim)
+    assert orc.surface_functional(P, Q, M, 5, 1.0) < 1e-28
+    assert orc.surface_functional(P, Q, M, 4, 1.0) > 0.0
+    with pytest.raises(ValueError):
+        orc.surface_functional(P, Q, M, nj, 1.0)
+
+
 def test_oracle_results_do_not_depend_on_the_thread_count(orc):
     """The OpenMP loops only split independent per-node work: one thread and
     all threads give the same bits (one step with SGS and jet BCs, and the
