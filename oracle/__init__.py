@@ -50,7 +50,7 @@ class OrcParams(C.Structure):
         ("theta_m", C.c_double), ("force_width", C.c_double),
         ("St", C.c_double * 4), ("amp", C.c_double * 16),
         ("sgs_model", C.c_int), ("periodic", C.c_int * 3), ("bc", C.c_int),
-        ("dt_mode", C.c_int), ("freeze_visc", C.c_int), ("pad_", C.c_int),
+        ("dt_mode", C.c_int), ("freeze_visc", C.c_int), ("axis", C.c_int),
     ]
 
 
@@ -60,7 +60,7 @@ def params(**kw) -> OrcParams:
              k2=0.25, k4=0.016, Cs=0.148, cfl=0.5, dt_fixed=0.0, r_jet=0.5,
              theta_m=0.05, force_width=0.05, St=(0.25, 0.5, 0.75, 1.0),
              amp=(0.0,) * 16, sgs_model=0, periodic=(0, 0, 1), bc=1, dt_mode=0,
-             freeze_visc=1)
+             freeze_visc=1, axis=0)
     d.update(kw)
     p = OrcParams()
     for k, v in d.items():

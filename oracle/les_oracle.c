@@ -156,7 +156,11 @@ void orc_metrics(int ni, int nj, int nk, const int periodic[3],
     double Jinv = x_xi * y_eta * z_zeta + x_eta * y_zeta * z_xi +
                   x_zeta * y_xi * z_eta - x_xi * y_zeta * z_eta -
                   x_eta * y_xi * z_zeta - x_zeta * y_eta * z_xi;
-    double J = 1.0 / Jinv;
+    /* Reading A27 (a true centerline grid, r from 0): on the axis the zeta
+     * tangent vanishes, so J^-1 = 0 exactly and grad xi, grad eta, grad zeta
+     * are unbounded; an axis node stores the J^-1-scaled metrics (the
+     * cofactors themselves, finite) beside J^-1 = 0. */
+    double J = (Jinv == 0.0) ? 1.0 : 1.0 / Jinv;
     M[0 * N + nn] = J * (y_eta * z_zeta - y_zeta * z_eta);
     M[1 * N + nn] = J * (z_eta * x_zeta - z_zeta * x_eta);
     M[2 * N + nn] = J * (x_eta * y_zeta - x_zeta * y_eta);
@@ -255,7 +259,8 @@ void orc_metrics_conservative(int ni, int nj, int nk, const int periodic[3],
         int p = (comp + 1) % 3, q = (comp + 2) % 3;
         double cof = product_deriv(&g, xyz, shift, c, t, p, s, q) -
                      product_deriv(&g, xyz, shift, c, s, p, t, q);
-        M[(size_t)(3 * r + comp) * N + nn] = cof / Jinv;
+        /* an axis node (J^-1 = 0) keeps the scaled metric (Reading A27) */
+        M[(size_t)(3 * r + comp) * N + nn] = (Jinv == 0.0) ? cof : cof / Jinv;
       }
     }
     M[9 * N + nn] = Jinv;
@@ -416,6 +421,20 @@ static void node_radii(state_t *S) {
     S->lbar[0][n] = l[0] * (1.0 + sqrt(l[1] / l[0]) + sqrt(l[2] / l[0]));
     S->lbar[1][n] = l[1] * (1.0 + sqrt(l[0] / l[1]) + sqrt(l[2] / l[1]));
     S->lbar[2][n] = l[2] * (1.0 + sqrt(l[0] / l[2]) + sqrt(l[1] / l[2]));
+  }
+  /* Reading A27: an axis node (J^-1 = 0, on the face j = 0) has no radius of
+   * its own (its metrics are J^-1-scaled); like a face node's sensor
+   * (Reading A12) it takes the radii of its inward neighbour (i, 1, k). */
+  for (long n = 0; n < (long)N; ++n) {
+    if (S->M[9 * N + n] != 0.0) continue;
+    int c[3];
+    unlin(&S->g, (size_t)n, c);
+    int c1[3] = {c[0], 1, c[2]};
+    long n1 = (long)lin(&S->g, c1);
+    for (int d = 0; d < 3; ++d) {
+      S->lam[d][n] = S->lam[d][n1];
+      S->lbar[d][n] = S->lbar[d][n1];
+    }
   }
 }
 
@@ -725,6 +744,7 @@ void orc_mu_eff(const orc_params *P, int ni, int nj, int nk, const double *Q,
   double dyn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (P->sgs_model == 3)
     dynamic_procedure(P, &S.g, Q, M, S.u, S.v, S.w, S.T, dyn);
+  double *mus = (double *)malloc(N * sizeof(double));  /* mu_sgs per node */
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < (long)N; ++n) {
     int c[3];
@@ -741,6 +761,7 @@ void orc_mu_eff(const orc_params *P, int ni, int nj, int nk, const double *Q,
       double Smag = strain_at(&S.g, M, S.u, S.v, S.w, c, Sij);
       double D2 = cbrt(M[9 * N + n]) * cbrt(M[9 * N + n]);
       mu_s = dyn[6] * rho * D2 * Smag;
+      mus[n] = mu_s;
       MK[n] = mu_l + mu_s;
       MK[N + n] = mu_l / (gm1 * P->Pr) + mu_s / (gm1 * dyn[8]);
       MK[2 * N + n] = 2.0 * dyn[7] * rho * D2 * Smag * Smag;
@@ -788,9 +809,34 @@ void orc_mu_eff(const orc_params *P, int ni, int nj, int nk, const double *Q,
         mu_s = (aa == 0.0) ? 0.0 : rho * c_v * sqrt(B / aa);
       }
     }
+    mus[n] = mu_s;
     MK[n] = mu_l + mu_s;
     MK[N + n] = mu_l / (gm1 * P->Pr) + mu_s / (gm1 * P->Pr_sgs);
   }
+  /* Reading A27: an axis node (J^-1 = 0) has no velocity gradient of its own
+   * (its metrics are J^-1-scaled); like its state under the centerline rule,
+   * its mu_sgs (and sigma_ll) is the azimuthal mean over the ring j = 1 at
+   * its plane, summed in increasing k; mu_lam is its own. */
+  int nk_ = S.g.n[2];
+  for (long n = 0; n < (long)N; ++n) {
+    if (M[9 * N + n] != 0.0) continue;
+    int c[3];
+    unlin(&S.g, (size_t)n, c);
+    double sm = 0.0, ss = 0.0;
+    for (int k = 0; k < nk_; ++k) {
+      int c1[3] = {c[0], 1, k};
+      size_t n1 = lin(&S.g, c1);
+      sm += mus[n1];
+      if (P->sgs_model == 3) ss += MK[2 * N + n1];
+    }
+    double mu_s = sm / (double)nk_;
+    double mu_l = mu_laminar(P, S.T[n]);
+    double prs = (P->sgs_model == 3) ? dyn[8] : P->Pr_sgs;
+    MK[n] = mu_l + mu_s;
+    MK[N + n] = mu_l / (gm1 * P->Pr) + mu_s / (gm1 * prs);
+    if (P->sgs_model == 3) MK[2 * N + n] = ss / (double)nk_;
+  }
+  free(mus);
   state_free(&S);
 }
 
@@ -891,9 +937,27 @@ static void interface_flux(const state_t *S, int d, const int ca[3],
     }
   }
   double mh[3][3]; /* mh[t][c]: interface metric of direction t, comp c */
-  for (int t = 0; t < 3; ++t)
-    for (int cc = 0; cc < 3; ++cc)
-      mh[t][cc] = 0.5 * (S->M[(3 * t + cc) * N + a] + S->M[(3 * t + cc) * N + b]);
+  double Ja = S->M[9 * N + a], Jb = S->M[9 * N + b];
+  if (!P->axis && Ja != 0.0 && Jb != 0.0) {
+    for (int t = 0; t < 3; ++t)
+      for (int cc = 0; cc < 3; ++cc)
+        mh[t][cc] = 0.5 * (S->M[(3 * t + cc) * N + a] + S->M[(3 * t + cc) * N + b]);
+  } else {
+    /* Reading A27: on a grid with an axis (and at any interface touching an
+     * axis node, where the plain mean is unbounded) the interface metric is
+     * the J^-1-weighted mean, the mean of the scaled metrics J^-1 grad(t)
+     * over the mean J^-1.  Near the axis |grad zeta| ~ 1/r changes by O(1)
+     * between neighbours and the plain mean of 1/r misses 1/r at the
+     * interface by O(1) (0.75 against 0.67 of 1/dr between rings 1 and 2);
+     * the weighted mean gives 1/r there exactly on uniform radial spacing. */
+    for (int t = 0; t < 3; ++t)
+      for (int cc = 0; cc < 3; ++cc) {
+        double sa = S->M[(3 * t + cc) * N + a], sb = S->M[(3 * t + cc) * N + b];
+        if (Ja != 0.0) sa *= Ja;
+        if (Jb != 0.0) sb *= Jb;
+        mh[t][cc] = (sa + sb) / (Ja + Jb);
+      }
+  }
   double gr[4][3]; /* gr[q][c] = d phi_q / d x_c */
   for (int q = 0; q < 4; ++q)
     for (int cc = 0; cc < 3; ++cc)
@@ -1170,7 +1234,10 @@ void orc_bc_jet(const orc_params *P, int ni, int nj, int nk, double *Q,
   for (int j = 0; j < nj; ++j)
     for (int k = 0; k < nk; ++k) {
       size_t nx_ = ID(ni - 1, j, k), ne = ID(ni - 2, j, k);
-      double ex = M[0 * N + nx_], ey = M[1 * N + nx_], ez = M[2 * N + nx_];
+      /* an axis node (J^-1 = 0) has a zero xi row: it takes the outward
+       * normal of its neighbour (ni-1, 1, k) (Reading A27) */
+      size_t nm = (M[9 * N + nx_] == 0.0) ? ID(ni - 1, 1, k) : nx_;
+      double ex = M[0 * N + nm], ey = M[1 * N + nm], ez = M[2 * N + nm];
       double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
       double rho, u, v, w, p;
       prim_of(gam, Q, N, (long)ne, &rho, &u, &v, &w, &p);

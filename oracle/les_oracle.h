@@ -45,7 +45,7 @@ typedef struct {
                         2 jet BCs with the characteristic entrance */
   int dt_mode;       /* 0 CFL-limited global step, 1 fixed, 2 local steps */
   int freeze_visc;   /* 1: mu_eff/kappa_eff from Q^n held over 5 stages */
-  int pad_;
+  int axis;          /* 1: a true centerline grid (r from 0; Reading A27) */
 } orc_params;
 
 /* Grid metrics (Sec. "Transformation of Coordinates"); xyz is [3][N]. */

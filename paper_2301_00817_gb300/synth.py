@@ -67,14 +67,16 @@ def jet_azimuth(nk: int) -> np.ndarray:
     return 2.0 * math.pi * np.arange(nk, dtype=np.float64) / nk
 
 
-def jet_lines(ni: int, nj: int, nk: int):
+def jet_lines(ni: int, nj: int, nk: int, r0: float = 0.02):
     """The three 1-D coordinate lines (x_i, r_j, theta_k) of the jet grid."""
-    return jet_axial(ni), jet_radial(nj), jet_azimuth(nk)
+    return jet_axial(ni), jet_radial(nj, r0=r0), jet_azimuth(nk)
 
 
-def jet_grid(ni: int, nj: int, nk: int) -> np.ndarray:
-    """Cartesian coordinates [3, ni, nj, nk] (FP64) of the annular jet grid."""
-    x, r, th = jet_lines(ni, nj, nk)
+def jet_grid(ni: int, nj: int, nk: int, r0: float = 0.02) -> np.ndarray:
+    """Cartesian coordinates [3, ni, nj, nk] (FP64) of the jet grid: annular
+    for r0 > 0 (the default), a true centerline grid (r_0 = 0 exactly, the nk
+    nodes of ring j = 0 on the axis) for r0 = 0."""
+    x, r, th = jet_lines(ni, nj, nk, r0)
     xyz = np.empty((3, ni, nj, nk))
     xyz[0] = x[:, None, None]
     xyz[1] = r[None, :, None] * np.cos(th)[None, None, :]

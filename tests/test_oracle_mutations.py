@@ -85,6 +85,19 @@ MUTATIONS = {
                             ["test_surface_functional_ring_area_closed_form"]),
     "functional_reference_p": ("double dp = p - 1.0 / gam;", "double dp = p - 1.0;",
                                ["test_surface_functional_ring_area_closed_form"]),
+    "axis_unscaled_storage": ("double J = (Jinv == 0.0) ? 1.0 : 1.0 / Jinv;",
+                              "double J = 1.0 / Jinv;",
+                              ["test_axis_grid_metrics"]),
+    "axis_radii_copy": ("    if (S->M[9 * N + n] != 0.0) continue;\n    int c[3];\n    unlin(&S->g, (size_t)n, c);\n    int c1[3] = {c[0], 1, c[2]};",
+                        "    continue;\n    int c[3];\n    unlin(&S->g, (size_t)n, c);\n    int c1[3] = {c[0], 1, c[2]};",
+                        ["test_axis_free_stream_preservation"]),
+    "axis_plain_mean": ("if (!P->axis && Ja != 0.0 && Jb != 0.0) {", "if (Ja != 0.0 && Jb != 0.0) {",
+                        ["test_axis_residual_converges"]),
+    "axis_sgs_own": ("double mu_s = sm / (double)nk_;", "double mu_s = mus[n];",
+                     ["test_axis_viscosity_is_the_ring_mean"]),
+    "axis_exit_normal": ("size_t nm = (M[9 * N + nx_] == 0.0) ? ID(ni - 1, 1, k) : nx_;",
+                         "size_t nm = nx_;",
+                         ["test_axis_supersonic_exit"]),
 }
 
 

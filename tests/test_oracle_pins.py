@@ -1071,6 +1071,134 @@ def test_azimuthal_rotation_equivariance(orc):
     assert np.allclose(rotate(Q1), Q2, rtol=0, atol=1e-12)
 
 
+# ------------------------------------------- true centerline grid (A27)
+
+def _cylinder(ni, nj, nk, R=0.5, L=1.0):
+    """Uniform cylinder x in [0, L], r in [0, R] (r_0 = 0: the axis),
+    theta_k = 2 pi k / nk."""
+    x = np.linspace(0.0, L, ni)
+    r = np.linspace(0.0, R, nj)
+    th = 2.0 * math.pi * np.arange(nk) / nk
+    xyz = np.empty((3, ni, nj, nk))
+    xyz[0] = x[:, None, None]
+    xyz[1] = r[None, :, None] * np.cos(th)[None, None, :]
+    xyz[2] = r[None, :, None] * np.sin(th)[None, None, :]
+    return xyz
+
+
+def test_axis_grid_metrics(orc):
+    """On a true centerline grid (r_0 = 0) the zeta tangent vanishes on the
+    axis, so J^-1 = 0 there exactly and the axis nodes keep the J^-1-scaled
+    metrics: the xi and eta rows are 0 and the zeta row is x_xi x x_eta =
+    x_xi r_eta (0, -sin theta, cos theta), with r_eta the one-sided
+    second-order difference at j = 0.  Every other node satisfies the metric
+    identity and J^-1 = det, as on the annular grid."""
+    ni, nj, nk = 12, 10, 16
+    xyz = synth.jet_grid(ni, nj, nk, r0=0.0)
+    x, r, th = synth.jet_lines(ni, nj, nk, r0=0.0)
+    assert r[0] == 0.0
+    for form in (0, 1):
+        M = orc.metrics(xyz, form=form)
+        assert np.isfinite(M).all()
+        assert (M[9][:, 0] == 0.0).all() and (M[9][:, 1:] > 0.0).all()
+    M = orc.metrics(xyz)
+    assert (M[0:7][:, :, 0] == 0.0).all()
+    xd = np.gradient(x, edge_order=2)[:, None]
+    rd0 = np.gradient(r, edge_order=2)[0]
+    assert np.allclose(M[7][:, 0], -xd * rd0 * np.sin(th)[None, :], rtol=1e-13, atol=1e-15)
+    assert np.allclose(M[8][:, 0], xd * rd0 * np.cos(th)[None, :], rtol=1e-13, atol=1e-15)
+    X = _coord_jacobian(xyz, (0, 0, 1), np.zeros(9))
+    Mm = M[:9].reshape((3, 3) + xyz.shape[1:])
+    ident = np.einsum("dc...,ce...->de...", Mm, X)[:, :, :, 1:]
+    assert np.abs(ident - np.eye(3)[:, :, None, None, None]).max() < 1e-12
+    det = np.linalg.det(np.moveaxis(X, (0, 1), (-2, -1)))
+    assert np.allclose(det[:, 1:], M[9][:, 1:], rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("sgs", [0, 1, 2])
+@pytest.mark.parametrize("form", [0, 1])
+def test_axis_free_stream_preservation(orc, sgs, form):
+    """A uniform state on the centerline grid gives a zero residual at every
+    interior node, ring 1 included: the axis nodes' J^-1-scaled metrics and
+    the radii they take from ring 1 keep the central flux, the dissipation
+    (no NaN from the axis) and the weighted interface metrics exact."""
+    ni, nj, nk = 12, 10, 16
+    xyz = synth.jet_grid(ni, nj, nk, r0=0.0)
+    M = orc.metrics(xyz, form=form)
+    P = orc.params(sgs_model=sgs, Re=400.0, axis=1)
+    prim = np.empty((5,) + xyz.shape[1:])
+    prim[0], prim[1], prim[2], prim[3], prim[4] = 1.0, 0.3, 0.1, -0.2, 1.0 / GAMMA
+    Q = orc.prim_to_cons(P, prim)
+    R = orc.rhs(P, Q, M)
+    scale = np.abs(M[9]).max() * 1.5
+    assert np.isfinite(R).all()
+    assert np.abs(R).max() < 1e-13 * scale
+
+
+def test_axis_residual_converges(orc):
+    """J * RHS on uniform cylinders with an axis against the exact flux
+    divergence of the manufactured solution (viscous, Re = 20, no
+    dissipation, whose fourth difference meets the paper's boundary closure
+    at the faces): second order from ring 3 outward and convergent at ring 1.
+    The paper's plain mean of the two nodes' metrics makes ring 1 diverge
+    (|grad zeta| ~ 1/r changes by O(1) between rings 1 and 2); the weighted
+    mean of Reading A27 and the axis rules restore convergence."""
+    f_prim, f_res, _ = _mms_exact_divergence(20.0)
+    P = orc.params(periodic=(0, 0, 1), bc=0, Re=20.0, sgs_model=0, k2=0.0, k4=0.0, axis=1)
+    far, ring1 = [], []
+    for n in (8, 16, 32):
+        xyz = _cylinder(n, n, 2 * n)
+        M = orc.metrics(xyz, (0, 0, 1))
+        prim = np.array([np.broadcast_to(f, xyz.shape[1:]) for f in f_prim(*xyz)])
+        Q = orc.prim_to_cons(P, prim)
+        R = orc.rhs(P, Q, M)
+        inner = (slice(None), slice(1, -1), slice(1, -1), slice(None))
+        JR = R[inner] / M[9][1:-1, 1:-1][None]
+        exact = np.array([np.broadcast_to(f, xyz.shape[1:]) for f in f_res(*xyz)])[inner]
+        err = np.abs(JR - exact)
+        ring1.append(err[:, :, 0].max())
+        far.append(err[:, :, 2:].max())
+    assert far[0] / far[1] > 3.0 and far[1] / far[2] > 3.3, far
+    assert ring1[0] / ring1[1] > 2.0 and ring1[1] / ring1[2] > 2.0, ring1
+
+
+def test_axis_viscosity_is_the_ring_mean(orc):
+    """The SGS viscosity of an axis node is the azimuthal mean of ring 1's at
+    its plane (the centerline rule), its laminar part its own (Sutherland at
+    its temperature); kappa follows with Pr and Pr_sgs."""
+    ni, nj, nk = 12, 10, 16
+    xyz = synth.jet_grid(ni, nj, nk, r0=0.0)
+    M = orc.metrics(xyz)
+    for sgs in (1, 2):
+        P = orc.params(sgs_model=sgs, Re=400.0, axis=1)
+        Q = orc.init_jet(P, xyz, seed=5, noise=3e-2)
+        P0 = orc.params(sgs_model=0, Re=400.0, axis=1)
+        MK, MK0 = orc.mu_eff(P, Q, M), orc.mu_eff(P0, Q, M)
+        mu_sgs = MK[0] - MK0[0]
+        assert np.abs(mu_sgs[:, 1]).max() > 0.0
+        ring_mean = mu_sgs[:, 1].mean(axis=1)
+        assert np.allclose(mu_sgs[:, 0], ring_mean[:, None], rtol=1e-12, atol=1e-18)
+        kap_sgs = MK[1] - MK0[1]
+        assert np.allclose(kap_sgs[:, 0], ring_mean[:, None] / (0.4 * 0.9), rtol=1e-12, atol=1e-18)
+
+
+def test_axis_supersonic_exit(orc):
+    """A uniform supersonic axial stream leaves through the exit: every exit
+    node copies its upstream neighbour (as the other boundary rules left it),
+    the axis nodes too (their xi row is 0, so they take ring 1's outward
+    normal)."""
+    ni, nj, nk = 12, 10, 16
+    xyz = synth.jet_grid(ni, nj, nk, r0=0.0)
+    M = orc.metrics(xyz)
+    P = orc.params(axis=1)
+    prim = np.empty((5,) + xyz.shape[1:])
+    # p above the free stream's: the subsonic exit rule would change the state
+    prim[0], prim[1], prim[2], prim[3], prim[4] = 1.0, 1.6, 0.0, 0.0, 1.3 / GAMMA
+    Q = orc.prim_to_cons(P, prim)
+    Qb = orc.bc_jet(P, Q, M, xyz, 0.0)
+    assert np.array_equal(Qb[:, -1], Qb[:, -2])
+
+
 # ------------------------------------------------- adjoint window functional
 
 def test_surface_functional_ring_area_closed_form(orc):
