@@ -140,6 +140,8 @@ int les_destroy(les_ctx *ctx);
  *   theta_k = 2 pi k/nk;  y = r cos theta, z = r sin theta.
  * Needs no context.  ni, nj, nk >= 2, N < 2^40, length > 0, 0 <= r0 < r_c <
  * r1, 0 <= A < 1, beta > 0; LES_ERR_SHAPE / LES_ERR_INVALID_ARG otherwise.
+ * r0 = 0 writes a true centerline grid (ring j = 0 on the axis, J^-1 = 0
+ * there), which les_set_grid does not support yet (see there).
  * Asynchronous. */
 typedef struct les_jet_grid {
   double length;  /* axial extent (20 D) */
@@ -169,8 +171,11 @@ size_t les_workspace_bytes(const les_ctx *ctx);
  * FP64 Cartesian coordinates.  shift: host [3][3] coordinate jump over one
  * period of each periodic direction (shift[3*d + c]; zeros for the jet grid).
  * Derivatives are second-order central, one-sided second order at
- * non-periodic faces.  The workspace must stay allocated while the context
- * is used.  Asynchronous. */
+ * non-periodic faces.  Every node needs J^-1 > 0: on a grid with an axis
+ * (r = 0 on ring j = 0, the paper's centerline singularity) J^-1 is 0 there,
+ * the metrics of that ring come out non-finite and so does the state next to
+ * the axis once stepped; use an annular grid (r0 > 0).  The workspace must
+ * stay allocated while the context is used.  Asynchronous. */
 int les_set_grid(les_ctx *ctx, const double *xyz, const double shift[9],
                  void *workspace, les_stream_t stream);
 
