@@ -29,6 +29,12 @@ arrays.  The readings of the paper are the same:
 At non-differentiable points the derivative follows the branch the forward
 value takes: |x| is written x < 0 ? -x : x (slope +1 at 0) and max(a, b) as
 a > b ? a : b.
+
+With axis=True it restates, for the forward residual and step only, the
+rules of a true centerline grid (ring j = 0 on the axis, J^-1 = 0 there, its
+metrics J^-1-scaled): the axis nodes take ring 1's radii, every interface
+metric is the J^-1-weighted mean of the two nodes', and an exit node on the
+axis takes ring 1's outward normal.
 """
 from __future__ import annotations
 
@@ -56,7 +62,7 @@ class Case:
 
     def __init__(self, M, xyz, *, gamma=1.4, Pr=0.72, Mj=1.4, Re=1.0e5, T_ref=288.15,
                  k2=0.25, k4=0.016, r_jet=0.5, theta_m=0.05, force_width=0.05,
-                 St=(0.25, 0.5, 0.75, 1.0)):
+                 St=(0.25, 0.5, 0.75, 1.0), axis=False):
         self.M = torch.as_tensor(M, dtype=torch.float64)
         xyz = torch.as_tensor(xyz, dtype=torch.float64)
         self.shape = tuple(self.M.shape[1:])
@@ -67,6 +73,7 @@ class Case:
         self.k2, self.k4 = k2, k4
         self.r_jet, self.theta_m, self.force_width, self.St = r_jet, theta_m, force_width, St
         self.per = (False, False, True)
+        self.axis = axis
         ni, nj, nk = self.shape
         inter = torch.zeros(self.shape, dtype=torch.bool)
         inter[1:ni - 1, 1:nj - 1, :] = True
@@ -172,7 +179,13 @@ class Case:
         for t in range(3):
             for c in range(3):
                 ma, mb = P(M[3 * t + c])
-                mh[t][c] = 0.5 * (ma + mb)
+                if self.axis:
+                    # J^-1-weighted mean; axis nodes hold scaled metrics
+                    sa = torch.where(Ja == 0, ma, Ja * ma)
+                    sb = torch.where(Jb == 0, mb, Jb * mb)
+                    mh[t][c] = (sa + sb) / (Ja + Jb)
+                else:
+                    mh[t][c] = 0.5 * (ma + mb)
         gr = [[mh[0][c] * dphi[q][0] + mh[1][c] * dphi[q][1] + mh[2][c] * dphi[q][2]
                for c in range(3)] for q in range(4)]
         mua, mub = P(MK[0])
@@ -211,6 +224,8 @@ class Case:
         lbar = [lam[0] * (1.0 + torch.sqrt(lam[1] / lam[0]) + torch.sqrt(lam[2] / lam[0])),
                 lam[1] * (1.0 + torch.sqrt(lam[0] / lam[1]) + torch.sqrt(lam[2] / lam[1])),
                 lam[2] * (1.0 + torch.sqrt(lam[0] / lam[2]) + torch.sqrt(lam[1] / lam[2]))]
+        if self.axis:  # the axis nodes take ring 1's radii
+            lbar = [torch.cat([lb[:, 1:2], lb[:, 1:]], dim=1) for lb in lbar]
         nu = [self._sensor(p, d) for d in range(3)]
         R = [torch.zeros_like(rho) for _ in range(5)]
         for d in range(3):
@@ -273,6 +288,8 @@ class Case:
         Q1[:, 1:ni - 1, 0] = mean.expand(-1, -1, nk)
         # exit i = ni-1 from the updated column ni-2
         e = M[0:3, ni - 1]
+        if self.axis:  # an exit node on the axis takes ring 1's normal
+            e = torch.cat([e[:, 1:2], e[:, 1:]], dim=1)
         inv = 1.0 / torch.sqrt((e * e).sum(0))
         Qe = Q1[:, ni - 2]
         rho, u, v, w, p, T, a_e = self.primitives(Qe)
@@ -288,7 +305,8 @@ class Case:
     def step(self, Q, amps, t, dt):
         """Q^{n+1} = BC(RK5(Q^n)) with the boundary conditions at t + dt."""
         MK = self.viscosity(Q)
-        Jn = 1.0 / self.M[9]
+        J9 = self.M[9]
+        Jn = 1.0 / torch.where(J9 == 0, torch.ones_like(J9), J9)  # axis nodes are not advanced
         Q0, Qs = Q, Q
         for al in ALPHA:
             R = self.rhs(Qs, MK)

@@ -49,6 +49,31 @@ def test_forced_step_matches_oracle(orc):
     assert _rel(Q1t.numpy(), Q1) <= 1e-12
 
 
+def test_axis_grid_residual_and_step_match_oracle(orc):
+    """True centerline grid (reading A27): the torch restatement's residual
+    and forced step against the C oracle's axis mode, viscous, with the
+    dissipation on."""
+    shape = (12, 10, 8)
+    amps = synth.forcing_amplitudes(3, scale=2e-2)
+    xyz = synth.jet_grid(*shape, r0=0.0)
+    M = orc.metrics(xyz, (0, 0, 1))
+    P = orc.params(Re=300.0, dt_mode=1, dt_fixed=1e-3, amp=tuple(amps), axis=1)
+    Q = orc.init_jet(P, xyz, seed=6, noise=3e-2)
+    rng = np.random.default_rng(6)
+    Q[4] += 1e-2 / (P.gamma - 1.0) * rng.standard_normal(Q[4].shape)
+    MK = orc.mu_eff(P, Q, M)
+    R_orc = orc.rhs(P, Q, M, MK)
+    assert np.isfinite(R_orc).all() and np.abs(R_orc[:, :, 1]).max() > 0.0
+    case = torch_ref.Case(M, xyz, Re=300.0, axis=True)
+    R_t = case.rhs(torch.from_numpy(Q), tuple(torch.from_numpy(MK)))
+    assert _rel(R_t.numpy(), R_orc) <= 1e-12
+    t = 0.021
+    Q1, dt = orc.rk_step(P, Q, M, xyz, t)
+    Q1t = case.step(torch.from_numpy(Q), torch.from_numpy(amps), t, dt)
+    assert np.isfinite(Q1).all()
+    assert _rel(Q1t.numpy(), Q1) <= 1e-12
+
+
 def _functional_orc(orc, P, Q0, M, xyz, nsteps, j5):
     """The surface functional over a window of oracle steps (the C oracle's
     own window: dt times the functional term after every step)."""
