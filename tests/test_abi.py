@@ -129,6 +129,23 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got == int(value), (st, what, got, value)
 
 
+def test_plain_c_client(lib, tmp_path):
+    """tests/c_client.c, which includes only lesjet.h and links only
+    liblesjet.so, compiles as C11 without warnings and its host-only checks
+    (creation, validation, workspace sizes, call order, grid arguments)
+    hold."""
+    import subprocess
+    import paper_2301_00817_gb300 as lj
+    libdir = os.path.dirname(lj.LIB_PATH)
+    exe = tmp_path / "c_client"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), "-o", str(exe),
+                    os.path.join(ROOT, "tests", "c_client.c"), "-L", libdir, "-llesjet",
+                    "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
 def test_local_time_steps_are_chosen_at_creation(lib):
     """Per-node steps need workspace: a context created with a global step
     cannot switch to LES_DT_LOCAL, and creating with it grows the workspace
