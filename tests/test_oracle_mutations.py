@@ -31,7 +31,8 @@ MUTATIONS = {
                         "double bx = txx * uf + txy * wf + txz * vf - qx;",
                         ["test_manufactured_solution_second_order"]),
     "rk_alpha3": ("3.0 / 8.0, 1.0 / 2.0", "3.0 / 7.0, 1.0 / 2.0",
-                  ["test_rk5_amplification_polynomial"]),
+                  ["test_rk5_amplification_polynomial",
+                   "test_runge_kutta_coefficients_and_stability_statement"]),
     "closure_sign": ("double Dm = (am >= 0) ? W_of(S, a, q) - W_of(S, am, q) : -D1;",
                      "double Dm = (am >= 0) ? W_of(S, a, q) - W_of(S, am, q) : D1;",
                      ["test_fourth_difference_boundary_closure"]),
@@ -85,6 +86,8 @@ MUTATIONS = {
                             ["test_surface_functional_ring_area_closed_form"]),
     "functional_reference_p": ("double dp = p - 1.0 / gam;", "double dp = p - 1.0;",
                                ["test_surface_functional_ring_area_closed_form"]),
+    "sutherland_constant": ("double S = 110.4 / P->T_ref;", "double S = 110.0 / P->T_ref;",
+                            ["test_paper_constants_are_the_defaults"]),
     "axis_unscaled_storage": ("double J = (Jinv == 0.0) ? 1.0 : 1.0 / Jinv;",
                               "double J = 1.0 / Jinv;",
                               ["test_axis_grid_metrics"]),

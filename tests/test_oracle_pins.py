@@ -44,6 +44,68 @@ def test_box_muller_normals_are_standard(orc):
     assert abs(np.corrcoef(a[:, 0], a[:, 2])[0, 1]) < 0.06
 
 
+# ------------------------------------------------ constants the paper prints
+
+def _paper_constants():
+    """tests/golden/paper_constants.txt as {name: value}."""
+    from fractions import Fraction
+    out = {}
+    with open(os.path.join(HERE, "golden", "paper_constants.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            name, value = line.split()[:2]
+            if value.startswith("sqrt("):
+                out[name] = math.sqrt(float(value[5:-1]))
+            else:
+                out[name] = float(Fraction(value))
+    return out
+
+
+def test_paper_constants_are_the_defaults(orc):
+    """The oracle's and the library binding's default parameters are the
+    constants the paper prints (Pr, Pr_sgs, C_s, k2, k4), and the oracle's
+    laminar viscosity uses the printed Sutherland constant."""
+    c = _paper_constants()
+    import paper_2301_00817_gb300 as lj
+    for P in (orc.params(), lj.make_params()):
+        for name in ("Pr", "Pr_sgs", "Cs", "k2", "k4"):
+            assert getattr(P, name) == c[name], name
+    # mu_lam at a node of temperature T: (M_j/Re) T^1.5 (1 + S)/(T + S), S = S1/T_ref
+    P = orc.params(Re=1000.0)
+    prim = np.empty((5, 8, 8, 8))
+    prim[0], prim[1], prim[2], prim[3] = 1.3, 0.0, 0.0, 0.0
+    prim[4] = 1.3 * 1.7 / GAMMA  # T = gamma p / rho = 1.7
+    Q = orc.prim_to_cons(P, prim)
+    M = orc.metrics(synth.jet_grid(8, 8, 8))
+    S = c["S1_K"] / P.T_ref
+    mu = (P.Mj / 1000.0) * 1.7 ** 1.5 * (1.0 + S) / (1.7 + S)
+    assert np.allclose(orc.mu_eff(P, Q, M)[0], mu, rtol=1e-14, atol=0)
+
+
+def test_runge_kutta_coefficients_and_stability_statement(orc):
+    """The oracle's five-stage driver has the amplification factor of the
+    printed coefficients, G(z) = 1 + a5 z (1 + a4 z (1 + a3 z (1 + a2 z (1 +
+    a1 z)))) for dQ/dt = lambda Q, z = lambda dt; and |G(i y)| <= 1 for
+    |y| <= 2 sqrt 2, the paper's linear stability statement."""
+    c = _paper_constants()
+    alpha = [c[f"alpha{m}"] for m in range(1, 6)]
+
+    def G(z):
+        g = 1.0
+        for a in alpha:
+            g = 1.0 + a * z * g
+        return g
+
+    for lam_dt in (-0.3, -1.1, -2.5, 0.7):
+        Q = np.ones((1, 1))
+        out = orc.rk5(Q, lambda q: -lam_dt * q, 1.0)  # RHS = -lambda Q, dt = 1
+        assert out[0, 0] == pytest.approx(G(lam_dt), rel=1e-15, abs=1e-15)
+    y = np.linspace(0.0, c["cfl_max"], 2001)
+    assert np.abs(G(1j * y)).max() <= 1.0 + 1e-15
+
+
 # ----------------------------------------------------------------- metrics
 
 def _coord_jacobian(xyz, periodic, shift):
