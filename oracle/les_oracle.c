@@ -815,8 +815,10 @@ void orc_mu_eff(const orc_params *P, int ni, int nj, int nk, const double *Q,
   }
   /* Reading A27: an axis node (J^-1 = 0) has no velocity gradient of its own
    * (its metrics are J^-1-scaled); like its state under the centerline rule,
-   * its mu_sgs (and sigma_ll) is the azimuthal mean over the ring j = 1 at
-   * its plane, summed in increasing k; mu_lam is its own. */
+   * its mu_sgs is the azimuthal mean over the ring j = 1 at its plane, summed
+   * in increasing k; mu_lam is its own.  (The reading covers the static
+   * models: the dynamic model's test filter would carry the axis nodes'
+   * scaled data into ring 1, so it is not defined on a grid with an axis.) */
   int nk_ = S.g.n[2];
   for (long n = 0; n < (long)N; ++n) {
     if (M[9 * N + n] != 0.0) continue;
