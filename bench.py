@@ -683,7 +683,9 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "points": N, "global_batch": world,
                    "seq_len": 0, "parallelism": f"replicas x{world}",
-                   "precision": "FP32 fluxes/dissipation/SGS, FP64 metrics + RK accumulation",
+                   "precision": "FP32 arithmetic (fluxes, dissipation, SGS); metrics built in FP64 "
+                                "and stored FP32; Q^(0) as a compensated float pair (FP64-accurate "
+                                "RK accumulation)",
                    "l2": "state and metrics (~0.9 GB) exceed the 129 MB L2; no flush needed"},
         "roofline": roofline(mixed, 1),
         "roofline_alu": roofline_fp32_alu(mixed),
