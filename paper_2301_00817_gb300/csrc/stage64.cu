@@ -14,8 +14,9 @@
 //             update Q^(l) = Q^(0) - alpha_l dt J RHS (or RHS itself), with
 //             the factor 2 taken out once per node.
 // Each interface is computed once and read by its two nodes, so the scheme
-// telescopes exactly.  The kernels are written for a compute type R and are
-// instantiated for double only (the mixed form uses fused.cu).
+// telescopes exactly.  The kernels are written for a compute type R: double
+// here, and dual numbers in adjoint.cu (the exact tangent of the residual);
+// the mixed form uses fused.cu.
 #include <cstddef>
 
 #include "stage64_kernels.cuh"
