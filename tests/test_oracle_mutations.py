@@ -44,6 +44,23 @@ MUTATIONS = {
                        ["test_manufactured_solution_second_order"]),
     "riemann_plus": ("double Rp = qne + 2.0 * a_e / gm1;", "double Rp = qne - 2.0 * a_e / gm1;",
                      ["test_far_field_keeps_free_stream"]),
+    "far_field_exit_source_node": (
+        "if (riemann_far_field(gam, rho, u, v, w, p, ex * inv, ey * inv, ez * inv, q))\n"
+        "        for (int c = 0; c < 5; ++c) q[c] = Qs[c * N + ne];",
+        "if (riemann_far_field(gam, rho, u, v, w, p, ex * inv, ey * inv, ez * inv, q))\n"
+        "        for (int c = 0; c < 5; ++c) q[c] = Qs[c * N + nf];",
+        ["test_far_field_supersonic_branches"]),
+    "far_field_inflow_pressure": ("cons_from(gam, rho_inf, 0.0, 0.0, 0.0, p_inf, q);",
+                                  "cons_from(gam, rho_inf, 0.0, 0.0, 0.0, 1.0, q);",
+                                  ["test_far_field_supersonic_branches",
+                                   "test_characteristic_entrance_supersonic_branches"]),
+    "far_field_sonic_exit_edge": ("if (Mn >= 1.0) {", "if (Mn > 1.0) {",
+                                  ["test_characteristic_entrance_supersonic_branches"]),
+    "entrance_exit_source_node": ("                              -ez * inv, q))\n"
+                                  "          for (int c = 0; c < 5; ++c) q[c] = Qs[c * N + ne];",
+                                  "                              -ez * inv, q))\n"
+                                  "          for (int c = 0; c < 5; ++c) q[c] = Qs[c * N + n];",
+                                  ["test_characteristic_entrance_supersonic_branches"]),
     "energy_flux_p": ("F[4] = Jinv * ((S->Q[4 * N + n] + p) * Th);",
                       "F[4] = Jinv * ((S->Q[4 * N + n]) * Th);",
                       ["test_one_dimensional_jst_reduction"]),

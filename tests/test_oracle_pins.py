@@ -991,6 +991,88 @@ def test_far_field_riemann_invariants(orc):
     assert np.allclose(tan(uf, vf, wf, qf)[:, inn], 0.0, atol=1e-12)
 
 
+def _free_stream_cons():
+    # the far field's free stream at rest: rho = 1, u = v = w = 0, p = 1/gamma
+    return np.array([1.0, 0.0, 0.0, 0.0, (1.0 / GAMMA) / (GAMMA - 1.0)])
+
+
+def test_far_field_supersonic_branches(orc):
+    """Supersonic branches of the far-field rule (Sec. "Far Field Boundary"):
+    where the interior state leaves through the boundary faster than sound
+    (q_n/a >= 1 along the outward normal grad(eta)/|grad(eta)|) the boundary
+    node takes the adjacent interior node's conserved values unchanged; where
+    it enters faster than sound (q_n/a <= -1) the free-stream state is
+    imposed.  Interior nodes are given q_n = +-1.5 a plus a random tangential
+    velocity, and a density and pressure of their own."""
+    P, xyz, M = _jet_setup(orc)
+    n = xyz.shape[1:]
+    rng = np.random.default_rng(31)
+    e = M[3:6, :, -1]
+    nvec = e / np.sqrt((e ** 2).sum(axis=0))  # unit outward normal at (i, nj-1, k)
+    rho = 1.0 + 0.2 * rng.random((n[0], n[2]))
+    p = (1.0 / GAMMA) * (1.0 + 0.3 * rng.random((n[0], n[2])))
+    a = np.sqrt(GAMMA * p / rho)
+    sign = np.where(rng.random((n[0], n[2])) < 0.5, 1.5, -1.5)
+    t = rng.standard_normal((3, n[0], n[2]))
+    t -= (t * nvec).sum(axis=0) * nvec  # tangential part only
+    vel = sign * a * nvec + 0.3 * t
+    prim = synth.uniform_prim(n)
+    prim[0, :, -2], prim[4, :, -2] = rho, p
+    prim[1:4, :, -2] = vel
+    Q = orc.prim_to_cons(P, prim)
+    Qb = orc.bc_jet(P, Q, M, xyz, 0.0)
+    _, u, v, w, _ = _prim(Q[:, :, -2])
+    mach = (u * nvec[0] + v * nvec[1] + w * nvec[2]) / a
+    inner = np.zeros((n[0], n[2]), bool)
+    inner[1:-1] = True  # the far-field rule covers 0 < i < ni-1
+    out = inner & (mach >= 1.0)
+    inn = inner & (mach <= -1.0)
+    assert out.sum() > 5 and inn.sum() > 5 and (out | inn).sum() == inner.sum()
+    # supersonic exit: the interior node's conserved values, bit for bit
+    assert np.array_equal(Qb[:, :, -1][:, out], Q[:, :, -2][:, out])
+    # supersonic entrance: the free stream at rest
+    fs = _free_stream_cons()
+    got = Qb[:, :, -1][:, inn]
+    assert np.allclose(got, fs[:, None], rtol=1e-15, atol=1e-15)
+
+
+def test_characteristic_entrance_supersonic_branches(orc):
+    """The same two branches at the entrance above the jet (bc = 2), whose
+    outward normal is -x on the jet grid: u <= -a leaves the domain
+    supersonically (the node (1, j, k) is copied), u >= a enters it (free
+    stream).  The sonic edges are taken exactly with gamma = 2, rho = 1,
+    p = 1/2 (a = 1 and the conserved round trip are exact in binary) at the
+    nodes whose unit normal is exactly -1 in floating point: q_n/a = +1 is
+    an exit (q_n/a >= 1 copies), q_n/a = -1 the supersonic entrance."""
+    rng = np.random.default_rng(32)
+    for exact in (False, True):
+        gam = 2.0 if exact else GAMMA
+        P, xyz, M = _jet_setup(orc, bc=2, gamma=gam)
+        n = xyz.shape[1:]
+        above = _entrance_split(xyz)
+        assert np.abs(M[1:3, 0]).max() < 1e-14 and (M[0, 0] > 0).all()
+        prim = synth.uniform_prim(n, p=1.0 / gam)
+        if exact:
+            ex = M[0, 0]
+            above = above & (ex * (1.0 / np.sqrt(ex * ex)) == 1.0)
+            ux = np.where(rng.random((n[1], n[2])) < 0.5, -1.0, 1.0)
+        else:
+            prim[0, 1] = 1.0 + 0.2 * rng.random((n[1], n[2]))
+            prim[4, 1] = (1.0 / gam) * (1.0 + 0.3 * rng.random((n[1], n[2])))
+            a = np.sqrt(gam * prim[4, 1] / prim[0, 1])
+            ux = np.where(rng.random((n[1], n[2])) < 0.5, -1.5, 1.5) * a
+            prim[2:4, 1] = 0.3 * rng.standard_normal((2, n[1], n[2]))
+        prim[1, 1] = ux
+        Q = orc.prim_to_cons(P, prim)
+        Qb = orc.bc_jet(P, Q, M, xyz, 0.0)
+        leave = above & (ux < 0)
+        enter = above & (ux > 0)
+        assert leave.sum() > 3 and enter.sum() > 3
+        assert np.array_equal(Qb[:, 0][:, leave], Q[:, 1][:, leave])
+        fs = np.array([1.0, 0.0, 0.0, 0.0, (1.0 / gam) / (gam - 1.0)])
+        assert np.allclose(Qb[:, 0][:, enter], fs[:, None], rtol=1e-15, atol=1e-15)
+
+
 def _entrance_split(xyz, r_jet=0.5):
     r = np.sqrt(xyz[1, 0] ** 2 + xyz[2, 0] ** 2)
     return r > r_jet
