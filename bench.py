@@ -35,14 +35,20 @@ WORKLOAD_NAME = "jet 288x160x128 (5.9M pts, Mesh-A size), Re_D 1e5, M_j 1.4, CFL
 
 # Algorithmic bytes per grid point of one launch of each kernel class (what
 # the kernel must read and write at least once, halos assumed cached), as
-# (FP64, mixed).  stage_fused: mean over the five stages of state in (Q or
-# stage buffer), Q^(0) for the update, metrics (10), mu/kappa (2) and the
-# stage state out; mixed: float stage states and metrics, Q^(0) as float hi
-# (+ lo in the last stage).  prestep: Q^n + metrics in, mu/kappa out.
+# (FP64, mixed), mean over the five stages of a step.  stage_fused: state in
+# (Q or stage buffer), Q^(0) for the update, metrics (10), mu/kappa (2) and
+# the stage state out.  FP64: 176 (stage 1), 216 (stages 2-5).  Mixed, the
+# scope table's count: FP64 Q^(0) (40) read by every stage, float stage
+# states, metrics and mu/kappa: 108, 128 x 3, 148 -> 128.  prestep: Q^n +
+# metrics in, mu/kappa out.
 BYTES_PER_POINT = {
-    "stage_fused": ((176 + 4 * 216) / 5, (88 + 3 * 108 + 148) / 5),
+    "stage_fused": ((176 + 4 * 216) / 5, (108 + 3 * 128 + 148) / 5),
     "prestep": (40 + 80 + 16, 20 + 40 + 8),
 }
+# The mixed kernel's own floor: it holds Q^(0) as a float pair (hi, lo) and
+# stages 2-4 read only hi (20 B) for their update; the first stage reads no
+# Q^(0) and the last reads and writes both parts: 88, 108 x 3, 148 -> 112.
+BYTES_PER_POINT_FLOOR_MIXED = (88 + 3 * 108 + 148) / 5
 
 
 # Counters of k_stage_fused from ncu captures on the 96 x 160 x 128 jet
@@ -70,9 +76,14 @@ NCU_COUNTS = {
 }
 NCU_CAPTURE = {"stage_fused": "profiles/stage_fused_jet96x160x128.md",
                "flux64": "profiles/flux64_jet96x160x128.md"}
-# FP64 peak derived from the unit counts: 152 SMs x 2 DFMA per cycle x
-# 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def fp64_peak_from_units(clock_mhz=2070.0):
+    """FP64 peak derived from the unit counts: the device's SMs x 2 DFMA per
+    cycle x 2 flop x the SM clock (GB300: 152 SMs, 2.07 GHz maximum)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 2 * 2 * clock_mhz * 1e6 / 1e12
 
 
 def traffic_per_point(kernel, field="bytes_per_point"):
@@ -252,21 +263,30 @@ def oracle_baseline(shape, steps: int, warmup: int, threads: int = 0, grid=WORKL
     return npts * steps / el / 1e9, el / steps, npts, used
 
 
+def workload_config(world):
+    """The config object of both arms' JSON lines (the same workload)."""
+    N = WORKLOAD[0] * WORKLOAD[1] * WORKLOAD[2]
+    return {"workload": WORKLOAD_NAME, "points": N, "global_batch": world, "seq_len": 0,
+            "parallelism": f"replicas x{world}",
+            "l2": "state and metrics (~0.9 GB) exceed the 129 MB L2; no flush needed"}
+
+
 def run_reference(args, world, rank):
+    """The oracle (plain FP64 C, OpenMP over nodes) on the host cores, on the
+    whole workload: every timed step is one full RK step of all 5.9M points
+    (about 2.3 s on 16 Grace cores)."""
     if rank != 0:
         return 0
-    slab = (48, WORKLOAD[1], WORKLOAD[2])
-    val, sec, npts, cores = oracle_baseline(slab, args.steps, args.warmup)
+    val, sec, npts, cores = oracle_baseline(WORKLOAD, args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "sample": f"axial slab {slab} of the workload",
-                   "global_batch": 1, "seq_len": 0, "parallelism": "host cores"},
+        "config": workload_config(1),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} full RK steps on the axial slab {slab} "
-                                   f"({npts} points) of the workload"},
+                         "sample": f"{args.steps} full RK steps of the whole workload "
+                                   f"({npts} points), all host threads"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -620,13 +640,20 @@ def run_ours(args, world, rank, local):
         achieved = bpp * N / per_launch_s / 1e9
         share = ms_tot / sum(v[0] for v in prof.values())
         tpp = traffic_per_point(top) if prec_idx == 1 else None
-        return {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": tpp * N if tpp is not None else None,
-                "traffic_source": NCU_CAPTURE.get(top) if tpp is not None else None,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-                "bytes_per_point": bpp, "avg_launch_us": per_launch_s * 1e6,
-                "share_of_step": share}
+        out = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+               "unit": "GB/s", "frac": achieved / hbm_peak,
+               "traffic": tpp * N if tpp is not None else None,
+               "traffic_source": NCU_CAPTURE.get(top) if tpp is not None else None,
+               "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+               "bytes_per_point": bpp, "avg_launch_us": per_launch_s * 1e6,
+               "share_of_step": share}
+        if prec_idx == 1 and top == "stage_fused":
+            fl = BYTES_PER_POINT_FLOOR_MIXED
+            out["bytes_per_point_floor"] = fl
+            out["frac_at_floor"] = fl * N / per_launch_s / 1e9 / hbm_peak
+            out["floor_note"] = ("this kernel's own minimum: Q^(0) held as a float pair, stages "
+                                 "2-4 read only its hi part")
+        return out
 
     def roofline_fp64_alu(res):
         ms_tot, n_group = res["prof"].get("flux", (0.0, 0))
@@ -639,7 +666,7 @@ def run_ours(args, world, rank, local):
         return {"kernel": "flux (3 directions)", "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "measured FP64 FMA chains (les_measure_fma_peak); derived from unit "
-                               f"counts: {FP64_PEAK_TFLOPS:.3f}",
+                               f"counts: {fp64_peak_from_units():.3f}",
                 "flop_per_point": fpp, "flop_source": NCU_CAPTURE["flux64"],
                 "avg_group_us": per_group_s * 1e6}
 
@@ -681,12 +708,9 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "points": N, "global_batch": world,
-                   "seq_len": 0, "parallelism": f"replicas x{world}",
-                   "precision": "FP32 arithmetic (fluxes, dissipation, SGS); metrics built in FP64 "
-                                "and stored FP32; Q^(0) as a compensated float pair (FP64-accurate "
-                                "RK accumulation)",
-                   "l2": "state and metrics (~0.9 GB) exceed the 129 MB L2; no flush needed"},
+        "config": workload_config(world),
+        "precision": "FP32 arithmetic (fluxes, dissipation, SGS); metrics built in FP64 and stored "
+                     "FP32; Q^(0) as a compensated float pair (FP64-accurate RK accumulation)",
         "roofline": roofline(mixed, 1),
         "roofline_alu": roofline_fp32_alu(mixed),
         "roofline_issue": roofline_issue(mixed),
@@ -774,7 +798,8 @@ def run_profile_case(which: str):
                 st = prof["stage_fused"]
                 per_launch_s = st[0] / st[1] / 1e3
                 rec["stage_fused_avg_launch_us"] = per_launch_s * 1e6
-                rec["stage_fused_algorithmic_gbs"] = 112.0 * N / per_launch_s / 1e9
+                rec["stage_fused_algorithmic_gbs"] = (BYTES_PER_POINT["stage_fused"][1] * N /
+                                                      per_launch_s / 1e9)
             out[name] = rec
             del ctx, Q
             torch.cuda.empty_cache()

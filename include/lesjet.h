@@ -348,9 +348,11 @@ int les_surface_functional(les_ctx *ctx, const double *Q, int j_surface, double 
  * is one static device array inside the library, sized for ni <=
  * LES_STATIC_MAX_NI axial planes (256 KiB, held on every GPU that loads the
  * library until the process exits); larger grids are rejected with
- * LES_ERR_SHAPE.  The first call on each device looks up that array's device
- * address with the device current; make that first call before any stream
- * capture.  All calls share the array, so calls that overlap on the GPU race.
+ * LES_ERR_SHAPE.  The array's device address differs between CUDA contexts
+ * (a second context on a device, or the primary context re-created after
+ * cudaDeviceReset), so the first call in each context looks it up with that
+ * context current; make that first call before any stream capture.  All
+ * calls share the array, so calls that overlap on the GPU race.
  * Always FP64.  SYNCHRONISES the stream; LES_ERR_NONFINITE as les_time_step. */
 #define LES_STATIC_MAX_NI 16384
 int les_time_step_static(les_ctx *ctx, const double *Q, const double *M,

@@ -774,11 +774,12 @@ __global__ void k_unpack_dual(long long count, const Dual* __restrict__ in, doub
 }
 
 // ------------------------------------------------------------- launchers
-constexpr int kAdjBlocks = 152 * 8;
+constexpr int kAdjBlocks = kRedBlocks;  // fixed reduction grid (deterministic sums)
 
 static int nb_for(long long count) {
   long long b = (count + 255) / 256;
-  if (b > 152LL * 32) b = 152LL * 32;
+  const long long cap = 32LL * sm_count();
+  if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
 

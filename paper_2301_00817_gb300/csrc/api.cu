@@ -2,11 +2,13 @@
 // workspace layout and the order of kernel launches of one time step
 // (Table tab:JAZzY: viscosity, time step, five Runge-Kutta stages, boundary
 // conditions).  The library allocates no device memory.
+#include <cuda.h>  // driver types only (entry points come through the runtime)
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -582,10 +584,37 @@ int les_run_n_steps(les_ctx* c, int n, double* Q, les_diag* diag, les_stream_t s
   return finish_run(c, n, diag, s);
 }
 
-// Device-side address of a host buffer when it is pinned host memory that
-// the driver maps into this device's address space; nullptr otherwise
-// (pageable or unknown memory goes through the staging copy).
-const void* mapped_host(const void* host) {
+// True when the pinned host range [host, host + bytes) lies inside one
+// allocation or registration known to the driver (cuPointerGetAttribute's
+// range start and size, fetched through the runtime); false when it does not
+// or the driver cannot tell.
+bool host_range_covers(const void* host, size_t bytes) {
+  typedef CUresult (*PfnPointerGetAttribute)(void*, CUpointer_attribute, CUdeviceptr);
+  static PfnPointerGetAttribute get_attr = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_attr = (PfnPointerGetAttribute)f;
+  });
+  if (!get_attr) return false;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  const CUdeviceptr p = (CUdeviceptr)(uintptr_t)host;
+  if (get_attr(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, p) != CUDA_SUCCESS ||
+      get_attr(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, p) != CUDA_SUCCESS)
+    return false;
+  return start <= p && (unsigned long long)(p - start) + bytes <= (unsigned long long)size;
+}
+
+// Device-side address of a host buffer of `bytes` bytes when all of it is
+// pinned host memory that the driver maps into this device's address space;
+// nullptr otherwise (pageable, partly registered or unknown memory goes
+// through the staging copy).
+const void* mapped_host(const void* host, size_t bytes) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
     cudaGetLastError();  // clear the query's error state
@@ -597,6 +626,7 @@ const void* mapped_host(const void* host) {
     cudaGetLastError();
     return nullptr;
   }
+  if (!host_range_covers(host, bytes)) return nullptr;
   return a.devicePointer;
 }
 
@@ -612,7 +642,7 @@ int les_run_host(les_ctx* c, int n, double* Q_host, double* Q_dev, les_diag* dia
     // mapped pinned memory: the split kernel reads the host state and the
     // join kernel writes it back over the host link, with no FP64 staging
     // copy (the float pair state lives in the workspace in between)
-    double* Qm = const_cast<double*>(static_cast<const double*>(mapped_host(Q_host)));
+    double* Qm = const_cast<double*>(static_cast<const double*>(mapped_host(Q_host, bytes)));
     if (Qm && aligned16(Qm)) {
       lesjet::Launch L{s, &c->launches};
       split_state(c, Qm, L);
@@ -727,7 +757,7 @@ AdjLayout adj_layout(const les_ctx* c, int nsteps, int K) {
   L.lam = take(5 * N * d);
   L.Qnext = take(5 * N * d);
   L.E = take(5 * (size_t)c->g.n[1] * c->g.n[2] * d);
-  L.partials = take(((size_t)152 * 8 * 16 + 64) * d);
+  L.partials = take(((size_t)lesjet::kRedBlocks * 16 + 64) * d);
   L.scal = take(64 * d);
   L.qd = take(5 * N * dd);
   L.mkd = take(2 * N * dd);

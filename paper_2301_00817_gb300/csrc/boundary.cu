@@ -319,7 +319,8 @@ __global__ void k_set_time(DevScalars* sc, double t) {
 
 static int nblocks(long long count) {
   long long b = (count + 255) / 256;
-  if (b > 152LL * 16) b = 152LL * 16;
+  const long long cap = 16LL * sm_count();
+  if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
 

@@ -925,7 +925,8 @@ __global__ void k_join(long long count, const float* __restrict__ hi, const floa
 
 static int fblocks(long long count) {
   long long b = (count + 255) / 256;
-  if (b > 152LL * 32) b = 152LL * 32;
+  const long long cap = 32LL * sm_count();
+  if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -1010,13 +1011,7 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
-  static std::atomic<int> n_sm{0};
-  if (n_sm.load() == 0) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    n_sm.store(sms > 0 ? sms : 152);
-  }
-  G.nch = choose_nch(G.ni, tk * tj, n_sm.load());  // one CTA per SM
+  G.nch = choose_nch(G.ni, tk * tj, sm_count());  // one CTA per SM
   dim3 grid(tk, tj, G.nch);
   k_stage_fused<MODE, LOCAL><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
   ++*L.counter;

@@ -41,9 +41,26 @@ struct DevScalars {
   double dyn[9];     // dynamic SGS procedure: 6 averaged terms, C_ds, C_I, Pr_sgs
 };
 
-constexpr int kRedBlocks = 1216;   // 152 SMs x 8: fixed, so reductions are
-constexpr int kRedThreads = 256;   // deterministic run to run
+// Reductions run on a fixed grid (whatever the GPU's SM count), so their
+// block partials and summation order, hence their bits, never change.
+constexpr int kRedBlocks = 1216;
+constexpr int kRedThreads = 256;
 constexpr int kMaxPartials = kRedBlocks;
+
+// Multiprocessor count of the current device (cached per device), for
+// sizing grid-stride launches in whole waves.
+inline int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+    cache[dev] = sms;
+  }
+  return cache[dev];
+}
 
 __host__ __device__ inline long long idx3(const Grid& g, int i, int j, int k) {
   return ((long long)i * g.n[1] + j) * g.n[2] + k;

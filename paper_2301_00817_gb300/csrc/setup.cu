@@ -243,7 +243,8 @@ __global__ void k_init_jet(Grid g, const double* __restrict__ xyz, uint64_t seed
 
 static int grid_blocks(long long count, int threads) {
   long long b = (count + threads - 1) / threads;
-  if (b > 152LL * 32) b = 152LL * 32;
+  const long long cap = 32LL * sm_count();
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
 }

@@ -5,7 +5,8 @@
 
 namespace lesjet {
 
-static int blocks_for(long long count, int threads, long long cap = 152LL * 64) {
+static int blocks_for(long long count, int threads, long long cap = 0) {
+  if (cap <= 0) cap = 64LL * sm_count();
   long long b = (count + threads - 1) / threads;
   if (b > cap) b = cap;
   if (b < 1) b = 1;

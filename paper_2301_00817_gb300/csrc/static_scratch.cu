@@ -14,6 +14,14 @@
 // call's contents, so calls that overlap on the GPU (on different streams or
 // host threads) race; each call overwrites every slot it reads, so nothing
 // has to be cleared between calls.
+//
+// Set-up: the device address of the array is looked up with
+// cudaGetSymbolAddress with the caller's device current, once per CUDA
+// context (the module holding the array is loaded afresh, at another
+// address, into every context: a second context on the same device, or the
+// primary context re-created after cudaDeviceReset).  The first call in a
+// context does this lookup, so it should come before any stream capture.
+#include <cuda.h>  // driver types only: the two entry points below come through the runtime
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -31,8 +39,43 @@ namespace {
 constexpr int kStaticMaxNi = LES_STATIC_MAX_NI;
 constexpr int kMaxDevices = 64;
 
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+// Address of g_static_scratch as seen in one context of a device.
+struct ScratchSlot {
+  double* ptr = nullptr;
+  unsigned long long ctx_id = 0;  // cuCtxGetId of the context the address belongs to
+  bool keyed = false;             // ctx_id is valid
+};
+ScratchSlot g_slots[kMaxDevices];
 std::mutex g_setup_mutex;
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+// Unique id of the context current to this thread (ids are never reused,
+// unlike context handles); false if the driver cannot tell.
+bool current_context_id(unsigned long long* id) {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = (PfnCtxGetCurrent)f1;
+      get_id = (PfnCtxGetId)f2;
+    }
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || c == nullptr) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
 
 // One block per axial plane i: FP64 spectral radii of every node of the plane
 // (same formulas as the time step of les_time_step) and the plane minimum.
@@ -123,21 +166,31 @@ __global__ void k_static_final(int ni, int mode, double cfl, double dt_fixed,
   }
 }
 
-// Device address of g_static_scratch on the current device, looked up once
-// per device with that device current.
-cudaError_t scratch_for_current_device(double** out) {
+// Device address of g_static_scratch in the context current to this thread
+// (the runtime's primary context of the current device unless the caller
+// made another one current), looked up once per context.
+cudaError_t scratch_for_current_context(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    double* ptr = nullptr;
-    e = cudaGetSymbolAddress((void**)&ptr, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = ptr;
+  ScratchSlot& slot = g_slots[dev];
+  unsigned long long id = 0;
+  bool keyed = current_context_id(&id);
+  if (keyed && slot.keyed && slot.ptr && slot.ctx_id == id) {
+    *out = slot.ptr;
+    return cudaSuccess;
   }
-  *out = g_scratch_ptr[dev];
+  double* ptr = nullptr;
+  e = cudaGetSymbolAddress((void**)&ptr, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  // the lookup makes the runtime's context current if none was: key on it
+  if (!keyed) keyed = current_context_id(&id);
+  slot.ptr = ptr;
+  slot.ctx_id = id;
+  slot.keyed = keyed;  // unkeyed: looked up again on every call
+  *out = ptr;
   return cudaSuccess;
 }
 
@@ -166,7 +219,7 @@ extern "C" int les_time_step_static(les_ctx* ctx, const double* Q, const double*
     return LES_ERR_SHAPE;
   }
   double* scratch = nullptr;
-  cudaError_t e = scratch_for_current_device(&scratch);
+  cudaError_t e = scratch_for_current_context(&scratch);
   if (e != cudaSuccess) {
     lesjet::ctx_set_error(ctx, cudaGetErrorString(e));
     return LES_ERR_CUDA;
@@ -181,12 +234,22 @@ extern "C" int les_time_step_static(les_ctx* ctx, const double* Q, const double*
   g.stride[1] = shape[2];
   g.stride[2] = 1;
   cudaStream_t s = (cudaStream_t)stream;
-  k_static_plane_min<<<shape[0], 256, 0, s>>>(g, p->gamma, Q, M, scratch);
-  k_static_final<<<1, 1024, 0, s>>>(shape[0], p->dt_mode, p->cfl, p->dt_fixed, scratch);
+  // cudaLaunchKernel returns each launch's own error: the thread's sticky
+  // last-error state (which may hold another component's error) is neither
+  // read nor cleared here
+  double gamma = p->gamma;
+  void* args1[] = {&g, &gamma, (void*)&Q, (void*)&M, &scratch};
+  e = cudaLaunchKernel((const void*)k_static_plane_min, dim3(shape[0]), dim3(256), args1, 0, s);
+  int ni = shape[0], mode = p->dt_mode;
+  double cfl = p->cfl, dt_fixed = p->dt_fixed;
+  void* args2[] = {&ni, &mode, &cfl, &dt_fixed, &scratch};
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel((const void*)k_static_final, dim3(1), dim3(1024), args2, 0, s);
   double host[2] = {0.0, 0.0};
-  cudaMemcpyAsync(host, scratch + 2 * kStaticMaxNi, sizeof(host), cudaMemcpyDeviceToHost, s);
-  e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host, scratch + 2 * kStaticMaxNi, sizeof(host), cudaMemcpyDeviceToHost, s);
+  // errors raised while the kernels run surface here
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     lesjet::ctx_set_error(ctx, cudaGetErrorString(e));
     return LES_ERR_CUDA;
