@@ -110,6 +110,18 @@ typedef struct les_params {
                          whose central differences telescope, so a uniform
                          flow stays uniform on any grid.  Read by
                          les_set_grid. */
+  int axis;           /* 1: a true centerline grid (Sec. "Centerline Boundary
+                         Condition", Reading A27): ring j = 0 lies on the
+                         axis r = 0, where J^-1 = 0.  Its nodes store the
+                         J^-1-scaled metrics (finite cofactors) beside
+                         J^-1 = 0, take the spectral radii of (i, 1, k) and,
+                         as SGS viscosity, the azimuthal mean of ring 1's at
+                         their plane; every interface metric is the
+                         J^-1-weighted mean of its two nodes; the exit takes
+                         ring 1's normal on the axis; the centerline rule sets
+                         the axis state.  Needs periodic = {0, 0, 1} and a
+                         static SGS model (not LES_SGS_DYNAMIC); the adjoint
+                         calls reject it.  0: every node has J^-1 > 0. */
 } les_params;
 
 /* Diagnostics returned by the synchronising run calls. */
@@ -171,11 +183,11 @@ size_t les_workspace_bytes(const les_ctx *ctx);
  * FP64 Cartesian coordinates.  shift: host [3][3] coordinate jump over one
  * period of each periodic direction (shift[3*d + c]; zeros for the jet grid).
  * Derivatives are second-order central, one-sided second order at
- * non-periodic faces.  Every node needs J^-1 > 0: on a grid with an axis
- * (r = 0 on ring j = 0, the paper's centerline singularity) J^-1 is 0 there,
- * the metrics of that ring come out non-finite and so does the state next to
- * the axis once stepped; use an annular grid (r0 > 0).  The workspace must
- * stay allocated while the context is used.  Asynchronous. */
+ * non-periodic faces.  Every node needs J^-1 > 0, except on a grid with an
+ * axis (r = 0 on ring j = 0, the paper's centerline singularity; params.axis
+ * = 1), where the axis nodes have J^-1 = 0 exactly and store the J^-1-scaled
+ * metrics.  The workspace must stay allocated while the context is used.
+ * Asynchronous. */
 int les_set_grid(les_ctx *ctx, const double *xyz, const double shift[9],
                  void *workspace, les_stream_t stream);
 

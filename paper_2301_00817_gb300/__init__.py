@@ -51,6 +51,7 @@ class LesParams(C.Structure):
         ("sgs_model", C.c_int), ("periodic", C.c_int * 3), ("bc", C.c_int),
         ("dt_mode", C.c_int), ("freeze_visc", C.c_int), ("precision", C.c_int),
         ("metric_form", C.c_int),
+        ("axis", C.c_int),
     ]
 
 
@@ -72,7 +73,8 @@ def make_params(**kw) -> LesParams:
              k2=0.25, k4=0.016, Cs=0.148, cfl=0.5, dt_fixed=0.0, r_jet=0.5,
              theta_m=0.05, force_width=0.05, St=(0.25, 0.5, 0.75, 1.0),
              amp=(0.0,) * 16, sgs_model=SGS_NONE, periodic=(0, 0, 1), bc=BC_JET,
-             dt_mode=DT_CFL, freeze_visc=1, precision=PREC_FP64, metric_form=METRIC_CROSS)
+             dt_mode=DT_CFL, freeze_visc=1, precision=PREC_FP64, metric_form=METRIC_CROSS,
+             axis=0)
     d.update(kw)
     p = LesParams()
     for k, v in d.items():

@@ -148,6 +148,19 @@ int validate_params(const les_params* p, std::string& why) {
     why = "jet boundary conditions need theta_m > 0 and force_width > 0";
     return LES_ERR_INVALID_ARG;
   }
+  if (p->axis != 0 && p->axis != 1) {
+    why = "axis must be 0 or 1";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (p->axis && !(p->periodic[0] == 0 && p->periodic[1] == 0 && p->periodic[2] == 1)) {
+    why = "a grid with an axis needs periodic = {0, 0, 1} (ring j = 0 on the axis)";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (p->axis && p->sgs_model == LES_SGS_DYNAMIC) {
+    why = "the dynamic SGS model is not defined on a grid with an axis (its test filter would "
+          "carry the axis nodes' scaled data into ring 1)";
+    return LES_ERR_UNSUPPORTED;
+  }
   return LES_OK;
 }
 
@@ -336,6 +349,8 @@ int les_create(const les_params* p, int ni, int nj, int nk, les_ctx** out) {
   int rc = validate_params(p, why);
   if (rc != LES_OK) return rc;
   if (ni < 5 || nj < 5 || nk < 5) return LES_ERR_SHAPE;
+  // the axis viscosity rule averages a ring in shared memory
+  if (p->axis && nk > 4096) return LES_ERR_SHAPE;
   const long long N = (long long)ni * nj * nk;
   if (N >= (1LL << 40)) return LES_ERR_SHAPE;
   // the mixed form indexes each field with 32 bits
@@ -790,6 +805,8 @@ int adj_check(les_ctx* c) {
     return fail(c, LES_ERR_UNSUPPORTED, "the adjoint needs dt_mode = LES_DT_FIXED");
   if (!c->p.freeze_visc)
     return fail(c, LES_ERR_UNSUPPORTED, "the adjoint needs freeze_visc = 1");
+  if (c->p.axis)
+    return fail(c, LES_ERR_UNSUPPORTED, "the adjoint is provided for grids without an axis");
   return LES_OK;
 }
 

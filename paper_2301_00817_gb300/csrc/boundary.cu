@@ -238,7 +238,10 @@ __global__ void k_bc_exit(Grid g, double gamma, const TM* __restrict__ M, Acc Q)
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane;
        e += (long long)gridDim.x * blockDim.x) {
     const long long nx_ = (long long)(ni - 1) * plane + e, ne = nx_ - plane;
-    const double ex = (double)M[nx_], ey = (double)M[N + nx_], ez = (double)M[2 * N + nx_];
+    // an axis node (J^-1 = 0, ring j = 0) has a zero xi row: it takes the
+    // outward normal of (ni-1, 1, k) (Reading A27)
+    const long long nm = (e < g.n[2] && (double)M[9 * N + nx_] == 0.0) ? nx_ + g.n[2] : nx_;
+    const double ex = (double)M[nm], ey = (double)M[N + nm], ez = (double)M[2 * N + nm];
     const double inv = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
     double rho, u, v, w, p;
     load_prim(Q, N, ne, gamma, rho, u, v, w, p);

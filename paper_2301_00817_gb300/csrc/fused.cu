@@ -49,7 +49,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // q_mod with Fourier's sign) from compact interface gradients.
 // m*[0..8] = xi_x .. zeta_z, m*[9] = J^-1; W* = (rho, rho u, rho v, rho w,
 // e + p); dphi[q][t] = computational derivative of u, v, w, T along t.
-template <int D, typename R>
+template <int D, typename R, bool AXIS>
 __device__ __forceinline__ void iface_flux(const Consts<R>& K, const R* Wm, const R* Wa,
                                            const R* Wb, const R* Wp, bool has_m, bool has_p,
                                            R nua, R nub, R lba, R lbb, const R* ma, const R* mb,
@@ -79,8 +79,17 @@ __device__ __forceinline__ void iface_flux(const Consts<R>& K, const R* Wm, cons
     F[q] = R(0.5) * Fc[q] - lJ * (eps2 * D1 - eps4 * D3);
   }
   R mh[9];
+  if (AXIS) {
+    // a grid with an axis (Reading A27): the J^-1-weighted mean of the two
+    // nodes' metrics; an axis node (J^-1 = 0) stores J^-1 m already
+    const R wa = (Ja == R(0)) ? R(1) : Ja, wb = (Jb == R(0)) ? R(1) : Jb;
+    const R s = R(1) / (Ja + Jb);
 #pragma unroll
-  for (int t = 0; t < 9; ++t) mh[t] = R(0.5) * (ma[t] + mb[t]);
+    for (int t = 0; t < 9; ++t) mh[t] = (wa * ma[t] + wb * mb[t]) * s;
+  } else {
+#pragma unroll
+    for (int t = 0; t < 9; ++t) mh[t] = R(0.5) * (ma[t] + mb[t]);
+  }
   R gr[4][3];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -173,10 +182,27 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
     R m[10];
     load_metrics(M, N, n, m);
     R lsum = R(0);
+    if (K.axis && m[9] == R(0) && (n / g.n[2]) % g.n[1] == 0) {
+      // an axis node (Reading A27) takes the radii of (i, 1, k)
+      const long long n1 = n + g.stride[1];
+      const R rho1 = (R)Q[n1];
+      const R ir1 = R(1) / rho1;
+      const R u1 = (R)Q[N + n1] * ir1, v1 = (R)Q[2 * N + n1] * ir1, w1 = (R)Q[3 * N + n1] * ir1;
+      const R p1 = K.gm1 * ((R)Q[4 * N + n1] - R(0.5) * rho1 * (u1 * u1 + v1 * v1 + w1 * w1));
+      const R a1 = dev_sqrt(K.gamma * p1 * ir1);
+      R m1[10];
+      load_metrics(M, N, n1, m1);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const R mx = m[3 * d], my = m[3 * d + 1], mz = m[3 * d + 2];
-      lsum += dev_abs(mx * u + my * v + mz * w) + a * dev_sqrt(mx * mx + my * my + mz * mz);
+      for (int d = 0; d < 3; ++d) {
+        const R mx = m1[3 * d], my = m1[3 * d + 1], mz = m1[3 * d + 2];
+        lsum += dev_abs(mx * u1 + my * v1 + mz * w1) + a1 * dev_sqrt(mx * mx + my * my + mz * mz);
+      }
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const R mx = m[3 * d], my = m[3 * d + 1], mz = m[3 * d + 2];
+        lsum += dev_abs(mx * u + my * v + mz * w) + a * dev_sqrt(mx * mx + my * my + mz * mz);
+      }
     }
     const R inv = R(1) / lsum;
     if (!(rho > R(0)) || !(p > R(0)) || !(inv > R(0)) || !(inv < R(1e30))) bad = 1;
@@ -381,7 +407,7 @@ __device__ __forceinline__ int wrap_fast(int v, int n, int per) {
 // LOCAL: node n advances with its own step P.dtl[n] (dt_mode LOCAL) in
 // place of the global one; a separate instantiation keeps the global-step
 // kernel free of the per-node load and its branch.
-template <int MODE, bool LOCAL>
+template <int MODE, bool LOCAL, bool AXIS>
 __global__ void __launch_bounds__(FNT, 1)
     k_stage_fused(const FusedGeom G, const Consts<float> K, const FusedPtrs P,
                   const DevScalars* __restrict__ sc, double alpha) {
@@ -498,7 +524,21 @@ __global__ void __launch_bounds__(FNT, 1)
 #pragma unroll
         for (int t = 0; t < 10; ++t) m[t] = mm[t * PL1 + r1];
         float lb[3];
-        node_lbar(m, u, v, w, T, lb);
+        if (AXIS && m[9] == 0.f && j0 + row - 2 == 0) {
+          // an axis node (Reading A27) takes the radii of its inward
+          // neighbour (i, 1, k): the next row of the same plane
+          const int s = r + SK;
+          const float rho1 = q[s];
+          const float ir1 = __frcp_rn(rho1);
+          const float u1 = q[PL2 + s] * ir1, v1 = q[2 * PL2 + s] * ir1, w1 = q[3 * PL2 + s] * ir1;
+          const float p1 = K.gm1 * (q[4 * PL2 + s] - 0.5f * rho1 * (u1 * u1 + v1 * v1 + w1 * w1));
+          float m1[10];
+#pragma unroll
+          for (int t = 0; t < 10; ++t) m1[t] = mm[t * PL1 + r1 + SK];
+          node_lbar(m1, u1, v1, w1, K.gamma * p1 * ir1, lb);
+        } else {
+          node_lbar(m, u, v, w, T, lb);
+        }
         ll[r1] = lb[0];
         ll[PL1 + r1] = lb[1];
         ll[2 * PL1 + r1] = lb[2];
@@ -586,7 +626,7 @@ __global__ void __launch_bounds__(FNT, 1)
     }
     const float* Ka = sK + m0 * 2 * PL1;
     const float* Kb = sK + m1 * 2 * PL1;
-    iface_flux<0, float>(K, Wq[0], Wq[1], Wq[2], Wq[3], vq[0], vq[3], nua, nub,
+    iface_flux<0, float, AXIS>(K, Wq[0], Wq[1], Wq[2], Wq[3], vq[0], vq[3], nua, nub,
                          sL[l0 * 3 * PL1 + o1], sL[l1 * 3 * PL1 + o1], ma, mb,
                          wown ? wown->x : sPw[p0 * PL2 + o2].x,
                          sPw[p1 * PL2 + o2].x, a0.x, a0.y, a0.z, b0.x, b0.y, b0.z, dphi, Ka[o1],
@@ -643,7 +683,7 @@ __global__ void __launch_bounds__(FNT, 1)
     }
     const float* Kc = sK + ms * 2 * PL1;
     const float* L = sL + ls * 3 * PL1 + PL1;
-    iface_flux<1, float>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
+    iface_flux<1, float, AXIS>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
                          wb.x, ca.x, ca.y, ca.z, cb.x, cb.y, cb.z, dphi, Kc[a1], Kc[b1],
                          Kc[PL1 + a1], Kc[PL1 + b1], F);
   };
@@ -700,7 +740,7 @@ __global__ void __launch_bounds__(FNT, 1)
     }
     const float* Kc = sK + ms * 2 * PL1;
     const float* L = sL + ls * 3 * PL1 + 2 * PL1;
-    iface_flux<2, float>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
+    iface_flux<2, float, AXIS>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
                          wb.x, pa.x, pa.y, pa.z, pb.x, pb.y, pb.z, dphi, Kc[a1], Kc[b1],
                          Kc[PL1 + a1], Kc[PL1 + b1], F);
   };
@@ -943,14 +983,21 @@ static Consts<R> fused_consts(const les_params& p) {
   K.inv_gm1_pr = (R)(1.0 / ((p.gamma - 1.0) * p.Pr));
   K.inv_gm1_prs = (R)(1.0 / ((p.gamma - 1.0) * p.Pr_sgs));
   K.sgs = p.sgs_model;
+  K.axis = p.axis;
   return K;
 }
 
 void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
                     float* mk, double* partials, DevScalars* sc, float* dtl, const Launch& L) {
+  const Consts<float> K = fused_consts<float>(p);
   k_prestep<float, float, float><<<kRedBlocks, kRedThreads, 0, L.s>>>(
-      g, fused_consts<float>(p), Q0, M, mk, partials, sc, dtl, (float)p.cfl);
+      g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl);
   ++*L.counter;
+  if (p.axis) {
+    k_mu_axis<float, TempFromState<float, float>><<<g.n[0], 128, g.n[2] * sizeof(float), L.s>>>(
+        g, K, TempFromState<float, float>{Q0, g.N, K.gamma, K.gm1}, mk);
+    ++*L.counter;
+  }
 }
 
 // Number of axial chunks.  CTAs are dispatched chunk-major (all tiles of a
@@ -994,7 +1041,7 @@ static int choose_nch(int ni, int tiles, int slots) {
   return best;
 }
 
-template <int MODE, bool LOCAL>
+template <int MODE, bool LOCAL, bool AXIS>
 static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const FusedPtrs& P,
                            const DevScalars* sc, double alpha, const Launch& L) {
   FusedGeom G = G0;
@@ -1006,15 +1053,31 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-    cudaFuncSetAttribute(k_stage_fused<MODE, LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_stage_fused<MODE, LOCAL, AXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
   G.nch = choose_nch(G.ni, tk * tj, sm_count());  // one CTA per SM
   dim3 grid(tk, tj, G.nch);
-  k_stage_fused<MODE, LOCAL><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
+  k_stage_fused<MODE, LOCAL, AXIS><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
   ++*L.counter;
+}
+
+template <bool AXIS>
+static void launch_stage_dispatch(int mode, bool local, const FusedGeom& G, const Consts<float>& K,
+                                  const FusedPtrs& P, const DevScalars* sc, double alpha,
+                                  const Launch& L) {
+  if (mode == FMODE_RHS)
+    launch_stage_t<FMODE_RHS, false, AXIS>(G, K, P, sc, alpha, L);
+  else if (mode == FMODE_STAGE && !local)
+    launch_stage_t<FMODE_STAGE, false, AXIS>(G, K, P, sc, alpha, L);
+  else if (mode == FMODE_STAGE)
+    launch_stage_t<FMODE_STAGE, true, AXIS>(G, K, P, sc, alpha, L);
+  else if (!local)
+    launch_stage_t<FMODE_LAST, false, AXIS>(G, K, P, sc, alpha, L);
+  else
+    launch_stage_t<FMODE_LAST, true, AXIS>(G, K, P, sc, alpha, L);
 }
 
 void launch_stage_fused(int mode, const Grid& g, const les_params& p, const FusedIO& io,
@@ -1041,16 +1104,10 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   P.dtl = io.dtl;
   const Consts<float> K = fused_consts<float>(p);
   const bool local = P.dtl != nullptr;
-  if (mode == FMODE_RHS)
-    launch_stage_t<FMODE_RHS, false>(G, K, P, io.sc, alpha, L);
-  else if (mode == FMODE_STAGE && !local)
-    launch_stage_t<FMODE_STAGE, false>(G, K, P, io.sc, alpha, L);
-  else if (mode == FMODE_STAGE)
-    launch_stage_t<FMODE_STAGE, true>(G, K, P, io.sc, alpha, L);
-  else if (!local)
-    launch_stage_t<FMODE_LAST, false>(G, K, P, io.sc, alpha, L);
+  if (p.axis)
+    launch_stage_dispatch<true>(mode, local, G, K, P, io.sc, alpha, L);
   else
-    launch_stage_t<FMODE_LAST, true>(G, K, P, io.sc, alpha, L);
+    launch_stage_dispatch<false>(mode, local, G, K, P, io.sc, alpha, L);
 }
 
 void launch_split(long long count, const double* q, float* hi, float* lo, const Launch& L) {

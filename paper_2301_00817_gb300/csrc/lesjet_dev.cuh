@@ -29,6 +29,7 @@ struct Consts {
   R inv_gm1_pr;      // 1/((gamma-1) Pr)
   R inv_gm1_prs;     // 1/((gamma-1) Pr_sgs)
   int sgs;           // LES_SGS_*
+  int axis;          // 1: ring j = 0 on the axis (J^-1 = 0 there), Reading A27
 };
 
 // Device-resident scalars of a context (inside the workspace).
@@ -138,5 +139,66 @@ struct Launch {
   cudaStream_t s;
   unsigned long long* counter;
 };
+
+// On a grid with an axis (Reading A27) an axis node's SGS viscosity is the
+// azimuthal mean of ring 1's at its plane, summed in increasing k; its
+// laminar part is its own.  One block per plane i, after k_mu (or the mixed
+// prestep) has written mk for every node: ring 1's SGS part is mk minus its
+// laminar part.  T(n) gives a node's temperature.
+template <typename R>
+__device__ __forceinline__ R mu_laminar(const Consts<R>& K, R T) {
+  return K.mu_scale * T * dev_sqrt(T) * (R(1) + K.S_suth) / (T + K.S_suth);
+}
+
+template <typename R, class TempOf>
+__global__ void k_mu_axis(Grid g, Consts<R> K, TempOf T, R* __restrict__ mk) {
+  extern __shared__ __align__(16) unsigned char smu_raw[];
+  R* smu = reinterpret_cast<R*>(smu_raw);
+  const int nk = g.n[2];
+  const long long N = g.N;
+  const long long base0 = (long long)blockIdx.x * g.stride[0];  // (i, 0, 0)
+  const long long base1 = base0 + g.stride[1];                  // (i, 1, 0)
+  for (int k = threadIdx.x; k < nk; k += blockDim.x)
+    smu[k] = mk[base1 + k] - mu_laminar(K, T(base1 + k));
+  __syncthreads();
+  __shared__ R mean;
+  if (threadIdx.x == 0) {
+    R s = R(0);
+    for (int k = 0; k < nk; ++k) s += smu[k];
+    mean = s / R(nk);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    const long long n = base0 + k;
+    const R ml = mu_laminar(K, T(n));
+    mk[n] = ml + mean;
+    mk[N + n] = ml * K.inv_gm1_pr + mean * K.inv_gm1_prs;
+  }
+}
+
+// Temperature of a node from a node array (FP64 form: node[4 N + n]).
+template <typename R>
+struct TempFromNode {
+  const R* node;
+  long long N;
+  __device__ R operator()(long long n) const { return node[4 * N + n]; }
+};
+
+// Temperature of a node recovered from the conserved state (System I
+// energy), as the mixed prestep does.
+template <typename R, typename TQ>
+struct TempFromState {
+  const TQ* Q;
+  long long N;
+  R gamma, gm1;
+  __device__ R operator()(long long n) const {
+    const R rho = (R)Q[n];
+    const R ir = R(1) / rho;
+    const R u = (R)Q[N + n] * ir, v = (R)Q[2 * N + n] * ir, w = (R)Q[3 * N + n] * ir;
+    const R p = gm1 * ((R)Q[4 * N + n] - R(0.5) * rho * (u * u + v * v + w * w));
+    return gamma * p * ir;
+  }
+};
+
 
 }  // namespace lesjet

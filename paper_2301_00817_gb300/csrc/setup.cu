@@ -52,7 +52,9 @@ __global__ void k_metrics(Grid g, const double* __restrict__ xyz, Shift sh,
     const double c20 = ya * zb - yb * za, c21 = za * xb - zb * xa, c22 = xa * yb - xb * ya;
     const double Jinv = xa * yb * zc + xb * yc * za + xc * ya * zb - xa * yc * zb -
                         xb * ya * zc - xc * yb * za;
-    const double J = 1.0 / Jinv;
+    // an axis node (J^-1 = 0 exactly, Reading A27) stores the cofactors
+    // themselves, the J^-1-scaled metrics, which stay finite
+    const double J = (Jinv == 0.0) ? 1.0 : 1.0 / Jinv;
     M[0 * N + n] = (TM)(J * c00);
     M[1 * N + n] = (TM)(J * c01);
     M[2 * N + n] = (TM)(J * c02);
@@ -138,7 +140,8 @@ __global__ void k_metrics_conservative(Grid g, const double* __restrict__ xyz, S
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int comp = 0; comp < 3; ++comp) M[(3 * r + comp) * N + n] = (TM)(cof[r][comp] / Jinv);
+      for (int comp = 0; comp < 3; ++comp)
+        M[(3 * r + comp) * N + n] = (TM)((Jinv == 0.0) ? cof[r][comp] : cof[r][comp] / Jinv);
     M[9 * N + n] = (TM)Jinv;
   }
 }

@@ -50,6 +50,11 @@ void launch_mu64(const Grid& g, const les_params& p, const StageIO64& io, const 
   k_mu<double, double, double><<<nb, th, 0, L.s>>>(g, make_consts<double>(p), io.Qin, io.M,
                                                     io.node, io.mk, dyn);
   ++*L.counter;
+  if (p.axis) {
+    k_mu_axis<double, TempFromNode<double>><<<g.n[0], 128, g.n[2] * sizeof(double), L.s>>>(
+        g, make_consts<double>(p), TempFromNode<double>{io.node, g.N}, io.mk);
+    ++*L.counter;
+  }
 }
 
 void launch_flux64(const Grid& g, const les_params& p, const StageIO64& io, int dir,

@@ -18,6 +18,7 @@ inline Consts<R> make_consts(const les_params& p) {
   K.k4 = (R)p.k4;
   K.mu_scale = (R)(p.Re > 0.0 ? p.Mj / p.Re : 0.0);
   K.S_suth = (R)(110.4 / p.T_ref);
+  K.axis = p.axis;
   K.cs2 = (R)(p.sgs_model == LES_SGS_VREMAN ? 2.5 * p.Cs * p.Cs : p.Cs * p.Cs);
   K.inv_gm1_pr = (R)(1.0 / ((p.gamma - 1.0) * p.Pr));
   K.inv_gm1_prs = (R)(1.0 / ((p.gamma - 1.0) * p.Pr_sgs));
@@ -58,12 +59,26 @@ __global__ void __launch_bounds__(256) k_node(Grid g, Consts<R> K, const TQ* __r
     const R p = K.gm1 * ((R)Q[4 * N + n] - R(0.5) * rho * (u * u + v * v + w * w));
     const R T = K.gamma * p * inv_rho;
     const R a = dev_sqrt(T);
+    // the radii's node: itself, or for an axis node (J^-1 = 0 on ring j = 0,
+    // Reading A27) its inward neighbour (i, 1, k), whose radii it takes
+    long long nr = n;
+    R ur = u, vr = v, wr = w, ar = a;
+    if (K.axis && (R)M[9 * N + n] == R(0) && (n / g.n[2]) % g.n[1] == 0) {
+      nr = n + g.stride[1];
+      const R rho1 = (R)Q[nr];
+      const R ir1 = R(1) / rho1;
+      ur = (R)Q[N + nr] * ir1;
+      vr = (R)Q[2 * N + nr] * ir1;
+      wr = (R)Q[3 * N + nr] * ir1;
+      const R p1 = K.gm1 * ((R)Q[4 * N + nr] - R(0.5) * rho1 * (ur * ur + vr * vr + wr * wr));
+      ar = dev_sqrt(K.gamma * p1 * ir1);
+    }
     R lam[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const R mx = (R)M[(3 * d) * N + n], my = (R)M[(3 * d + 1) * N + n],
-              mz = (R)M[(3 * d + 2) * N + n];
-      lam[d] = dev_abs(mx * u + my * v + mz * w) + a * dev_sqrt(mx * mx + my * my + mz * mz);
+      const R mx = (R)M[(3 * d) * N + nr], my = (R)M[(3 * d + 1) * N + nr],
+              mz = (R)M[(3 * d + 2) * N + nr];
+      lam[d] = dev_abs(mx * ur + my * vr + mz * wr) + ar * dev_sqrt(mx * mx + my * my + mz * mz);
     }
     const R s01 = dev_sqrt(lam[0] * lam[1]);
     const R s02 = dev_sqrt(lam[0] * lam[2]);
@@ -341,11 +356,24 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
     // interface metrics: 8x the mean along the normal, 2x along the
     // tangents, so that every product with dphi is 8x its value
     R mh[3][3];
+    if (K.axis) {
+      // a grid with an axis (Reading A27): the J^-1-weighted mean
+      // (J^-1_a m_a + J^-1_b m_b)/(J^-1_a + J^-1_b), kept at 2x like the
+      // plain sum; an axis node's stored metric is J^-1 m already
+      const R wa = (Ja == R(0)) ? R(1) : Ja, wb = (Jb == R(0)) ? R(1) : Jb;
+      const R s2 = R(2) / sJ;
 #pragma unroll
-    for (int t = 0; t < 3; ++t)
+      for (int t = 0; t < 3; ++t)
 #pragma unroll
-      for (int x = 0; x < 3; ++x)
-        mh[t][x] = (R)M[(3 * t + x) * N + a] + (R)M[(3 * t + x) * N + b];
+        for (int x = 0; x < 3; ++x)
+          mh[t][x] = (wa * (R)M[(3 * t + x) * N + a] + wb * (R)M[(3 * t + x) * N + b]) * s2;
+    } else {
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+          mh[t][x] = (R)M[(3 * t + x) * N + a] + (R)M[(3 * t + x) * N + b];
+    }
 #pragma unroll
     for (int x = 0; x < 3; ++x) mh[D][x] = R(4) * mh[D][x];
     R gr[4][3];  // 8 grad(u, v, w, T)

@@ -45,6 +45,7 @@ static les_params jet_params(int precision) {
   p.freeze_visc = 1;
   p.precision = precision;
   p.metric_form = LES_METRIC_CROSS;
+  p.axis = 0;
   return p;
 }
 
