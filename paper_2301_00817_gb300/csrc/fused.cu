@@ -31,6 +31,15 @@
 
 namespace lesjet {
 
+// Approximate reciprocal (rcp.approx.ftz: relative error below 2^-22),
+// inside this form's FP32 error budget; cheaper than the correctly rounded
+// __frcp_rn.
+__device__ __forceinline__ float frcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -325,13 +334,16 @@ enum { FMODE_RHS = 0, FMODE_STAGE = 1, FMODE_LAST = 2 };
 
 // Tile of FTJ x FTK (eta, zeta) columns, one thread per column.
 constexpr int FTJ = 16, FTK = 32, FNT = FTJ * FTK;
-// Shared-memory rows are circular in zeta with period SK: tile column kk in
-// [-2, FTK+1] lives at column kk (kk >= 0) or SK + kk (kk < 0), so the 32
-// tile columns start 16-byte aligned and the halo wraps around the row end.
-constexpr int SK = 36;
+// Shared-memory rows hold the tile's FTK columns and a two-column halo on
+// each side: tile column kk in [-2, FTK+1] lives at row column kk + 2.  When
+// zeta is periodic and nk % 4 == 0 the tiles are shifted by two columns
+// (tile t owns the global columns 32 t + 2 .. 32 t + 33, wrapped), so a
+// whole row, halos included, is the 16-byte-aligned global range
+// [32 t, 32 t + 36): nine 16-byte copies and no separate halo copy.
+constexpr int SK = FTK + 4;
 constexpr int R2 = FTJ + 4, R1 = FTJ + 2;  // rows with a 2-node / 1-node halo
 constexpr int PL2 = R2 * SK, PL1 = R1 * SK;
-__host__ __device__ constexpr int colk(int kk) { return kk < 0 ? kk + SK : kk; }
+__host__ __device__ constexpr int colk(int kk) { return kk + 2; }
 
 // Shared-memory plan (floats):
 //   sQ[3][5][PL2]  conserved state of planes i, i+1, i+2 (2-node halo)
@@ -388,7 +400,8 @@ struct FusedGeom {
   int ni, nj, nk;
   int per[3];
   int nch;  // axial chunks; chunk z holds planes [z ni / nch, (z + 1) ni / nch)
-  int vec16;  // rows of every field start 16-byte aligned (nk % 4 == 0)
+  int vec16;  // zeta periodic, nk % 4 == 0 and nk >= FTK: tiles shifted by
+              // two columns, rows staged as 16-byte copies
 };
 
 __device__ __forceinline__ int wrap_fast(int v, int n, int per) {
@@ -422,18 +435,20 @@ __global__ void __launch_bounds__(FNT, 1)
   float* sFz = smem + OFF_FZ;
   const int ni = G.ni, nj = G.nj, nk = G.nk;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int k0 = blockIdx.x * FTK, j0 = blockIdx.y * FTJ;
+  // kt: first column of the unshifted tile; k0: global column of tile
+  // column 0 (kt + 2 with the shifted tiling; may exceed nk - 1, wrapped)
+  const bool vec_ok = G.vec16 != 0;
+  const int kt = blockIdx.x * FTK, k0 = kt + (vec_ok ? 2 : 0), j0 = blockIdx.y * FTJ;
   const int ib = (int)((long long)blockIdx.z * ni / G.nch);
   const int ie = (int)((long long)(blockIdx.z + 1) * ni / G.nch);
-  const int jown = j0 + ty, kown = k0 + tx;
-  const bool own = jown < nj && kown < nk;
+  const int jown = j0 + ty;
+  const int kown = (k0 + tx < nk) ? k0 + tx : k0 + tx - nk;  // wraps in the shifted case only
+  const bool own = jown < nj && kt + tx < nk;
   const bool jint = G.per[1] || (jown > 0 && jown < nj - 1);
   const bool kint = G.per[2] || (kown > 0 && kown < nk - 1);
   const bool per_i = G.per[0] != 0;
-  const int cm1 = colk(tx - 1);
-  const int o2 = (ty + 2) * SK + tx;  // own node, 2-node-halo planes
-  const int o1 = (ty + 1) * SK + tx;  // own node, 1-node-halo planes
-  const bool vec_ok = G.vec16 && (k0 + FTK <= nk);
+  const int o2 = (ty + 2) * SK + tx + 2;  // own node, 2-node-halo planes
+  const int o1 = (ty + 1) * SK + tx + 2;  // own node, 1-node-halo planes
 
   // ---- stage plane x (state: 2-node halo; metrics, mu/kappa: 1-node halo)
   auto stage_plane = [&](int slot, int x) {
@@ -476,28 +491,22 @@ __global__ void __launch_bounds__(FNT, 1)
     }
     const float* row = src + (ig * nj + jg) * nk;
     if (vec_ok) {
+      // the row's global columns kt .. kt + SK - 1, wrapped at nk (a
+      // multiple of 4, so no 16-byte piece straddles the wrap; kt + SK <
+      // 2 nk because nk >= FTK)
 #pragma unroll
-      for (int v = 0; v < FTK / 4; ++v) cp_async16(dst + 4 * v, row + k0 + 4 * v);
+      for (int v = 0; v < SK / 4; ++v) {
+        const int kg = (kt + 4 * v < nk) ? kt + 4 * v : kt + 4 * v - nk;
+        cp_async16(dst + 4 * v, row + kg);
+      }
     } else {
-      for (int kk = 0; kk < FTK; ++kk) {
+      for (int kk = -halo; kk < FTK + halo; ++kk) {
         const int kg = wrap_fast(k0 + kk, nk, G.per[2]);
         if (kg >= 0)
-          cp_async4(dst + kk, row + kg);
+          cp_async4(dst + colk(kk), row + kg);
         else
-          dst[kk] = benign;
+          dst[colk(kk)] = benign;
       }
-    }
-    for (int h = 1; h <= halo; ++h) {
-      const int kl = wrap_fast(k0 - h, nk, G.per[2]);
-      const int kr = wrap_fast(k0 + FTK - 1 + h, nk, G.per[2]);
-      if (kl >= 0)
-        cp_async4(dst + colk(-h), row + kl);
-      else
-        dst[colk(-h)] = benign;
-      if (kr >= 0)
-        cp_async4(dst + FTK - 1 + h, row + kr);
-      else
-        dst[FTK - 1 + h] = benign;
     }
   };
 
@@ -510,7 +519,7 @@ __global__ void __launch_bounds__(FNT, 1)
     float* ll = sL + ls * 3 * PL1;
     for (int r = tid; r < PL2; r += FNT) {
       const float rho = q[r];
-      const float ir = __frcp_rn(rho);
+      const float ir = frcp_fast(rho);
       const float u = q[PL2 + r] * ir, v = q[2 * PL2 + r] * ir, w = q[3 * PL2 + r] * ir;
       const float p = K.gm1 * (q[4 * PL2 + r] - 0.5f * rho * (u * u + v * v + w * w));
       const float T = K.gamma * p * ir;
@@ -518,7 +527,7 @@ __global__ void __launch_bounds__(FNT, 1)
       pw[r] = make_float2(p, q[4 * PL2 + r] + p);
       const int row = r / SK, col = r - row * SK;
       // 1-node halo: rows 1 .. R2-2 of the 2-node layout, columns kk in [-1, FTK]
-      if (row >= 1 && row <= R2 - 2 && (col <= FTK || col == SK - 1)) {
+      if (row >= 1 && row <= R2 - 2 && col >= colk(-1) && col <= colk(FTK)) {
         const int r1 = r - SK;
         float m[10];
 #pragma unroll
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(FNT, 1)
           // neighbour (i, 1, k): the next row of the same plane
           const int s = r + SK;
           const float rho1 = q[s];
-          const float ir1 = __frcp_rn(rho1);
+          const float ir1 = frcp_fast(rho1);
           const float u1 = q[PL2 + s] * ir1, v1 = q[2 * PL2 + s] * ir1, w1 = q[3 * PL2 + s] * ir1;
           const float p1 = K.gm1 * (q[4 * PL2 + s] - 0.5f * rho1 * (u1 * u1 + v1 * v1 + w1 * w1));
           float m1[10];
@@ -589,7 +598,7 @@ __global__ void __launch_bounds__(FNT, 1)
       p = 1.f;
       return;
     }
-    const float ir = __frcp_rn(qn[0]);
+    const float ir = frcp_fast(qn[0]);
     const float u = qn[1] * ir, v = qn[2] * ir, w = qn[3] * ir;
     p = K.gm1 * (qn[4] - 0.5f * qn[0] * (u * u + v * v + w * w));
 #pragma unroll
@@ -613,7 +622,7 @@ __global__ void __launch_bounds__(FNT, 1)
       nub = sensor3(pq[1], pq[2], pq[3]);
     const float4 a0 = rown ? rown[0] : A0[o2], b0 = rpm ? rpm[0] : A1[o2];
     const float4 an = A0[o2 + SK], as = A0[o2 - SK], bn = A1[o2 + SK], bs = A1[o2 - SK];
-    const float4 ae = A0[o2 + 1], aw = A0[o2 - tx + cm1], be = A1[o2 + 1], bw = A1[o2 - tx + cm1];
+    const float4 ae = A0[o2 + 1], aw = A0[o2 - 1], be = A1[o2 + 1], bw = A1[o2 - 1];
     float dphi[4][3];
     dphi_normal<0>(a0, b0, dphi);
     dphi_tangent<1>(an, as, bn, bs, dphi);
@@ -642,8 +651,8 @@ __global__ void __launch_bounds__(FNT, 1)
     const float4* Pm = sPr + pm * PL2;
     const float4* Pp = sPr + pp * PL2;
     const float2* Pw = sPw + ps * PL2;
-    const int a2 = (ra + 2) * SK + tx, b2 = a2 + SK;
-    const int a1 = (ra + 1) * SK + tx, b1 = a1 + SK;
+    const int a2 = (ra + 2) * SK + colk(tx), b2 = a2 + SK;
+    const int a1 = (ra + 1) * SK + colk(tx), b1 = a1 + SK;
     const int jga = j0 + ra;
     const bool has_m = G.per[1] || jga - 1 >= 0;
     const bool has_p = G.per[1] || jga + 2 <= nj - 1;
@@ -669,7 +678,7 @@ __global__ void __launch_bounds__(FNT, 1)
       nub = sensor3(wm.x, wa.x, wb.x);
     else
       nub = sensor3(wa.x, wb.x, wp.x);
-    const int am1 = a2 - tx + cm1, bm1 = b2 - tx + cm1;
+    const int am1 = a2 - 1, bm1 = b2 - 1;
     const float4 ca = rown ? rown[0] : Pc[a2], cb = Pc[b2];
     float dphi[4][3];
     dphi_normal<1>(ca, cb, dphi);
@@ -778,7 +787,7 @@ __global__ void __launch_bounds__(FNT, 1)
       pq[q] = 1.f;
       continue;
     }
-    const float ir = __frcp_rn(Wq[q][0]);
+    const float ir = frcp_fast(Wq[q][0]);
     const float u = Wq[q][1] * ir, v = Wq[q][2] * ir, w = Wq[q][3] * ir;
     pq[q] = K.gm1 * (Wq[q][4] - 0.5f * Wq[q][0] * (u * u + v * v + w * w));
     Wq[q][4] += pq[q];
@@ -887,7 +896,7 @@ __global__ void __launch_bounds__(FNT, 1)
     if (own && ig >= 0) {
       const int n = (ig * nj + jown) * nk + kown;
       if (iint && jint && kint) {
-        const float Jn = __frcp_rn(mo[9]);
+        const float Jn = frcp_fast(mo[9]);
         const float an = LOCAL ? (float)alpha * dc : adt;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
@@ -1088,7 +1097,7 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   G.nk = g.n[2];
   for (int d = 0; d < 3; ++d) G.per[d] = g.per[d];
   G.nch = 1;
-  G.vec16 = (g.n[2] % 4 == 0) ? 1 : 0;
+  G.vec16 = (g.per[2] && g.n[2] % 4 == 0 && g.n[2] >= FTK) ? 1 : 0;
   const long long N = g.N;
   FusedPtrs P;
   for (int c = 0; c < 5; ++c) {
