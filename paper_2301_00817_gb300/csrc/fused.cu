@@ -87,43 +87,50 @@ __device__ __forceinline__ void iface_flux(const Consts<R>& K, const R* Wm, cons
     const R D3 = Dp - R(2) * D1 + Dm;
     F[q] = R(0.5) * Fc[q] - lJ * (eps2 * D1 - eps4 * D3);
   }
-  R mh[9];
+  // Viscous part from the interface metric vectors m_t (kept at twice
+  // their mean): with m = m_D, the flux needs only m.tau and m.q, and
+  //   m.tau_i / mu = sum_t g_t dphi_i,t + sum_t m_t,i c_t - 2/3 m_i div,
+  //   m.grad T     = sum_t g_t dphi_T,t,
+  // where g_t = m . m_t, c_t = sum_j m_j dphi_j,t and div = sum_t m_t .
+  // dphi_.,t (every factor 2 of the sums is collected in the constants).
+  R mt[9];
   if (AXIS) {
     // a grid with an axis (Reading A27): the J^-1-weighted mean of the two
     // nodes' metrics; an axis node (J^-1 = 0) stores J^-1 m already
     const R wa = (Ja == R(0)) ? R(1) : Ja, wb = (Jb == R(0)) ? R(1) : Jb;
-    const R s = R(1) / (Ja + Jb);
+    const R s2 = R(2) / (Ja + Jb);
 #pragma unroll
-    for (int t = 0; t < 9; ++t) mh[t] = (wa * ma[t] + wb * mb[t]) * s;
+    for (int t = 0; t < 9; ++t) mt[t] = (wa * ma[t] + wb * mb[t]) * s2;
   } else {
 #pragma unroll
-    for (int t = 0; t < 9; ++t) mh[t] = R(0.5) * (ma[t] + mb[t]);
+    for (int t = 0; t < 9; ++t) mt[t] = ma[t] + mb[t];
   }
-  R gr[4][3];
+  const R mx = mt[3 * D], my = mt[3 * D + 1], mz = mt[3 * D + 2];  // 2 m
+  R g[3], c[3];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int t = 0; t < 3; ++t) {
+    g[t] = mx * mt[3 * t] + my * mt[3 * t + 1] + mz * mt[3 * t + 2];        // 4 g_t
+    c[t] = mx * dphi[0][t] + my * dphi[1][t] + mz * dphi[2][t];             // 2 c_t
+  }
+  R div = R(0);  // 2 div
 #pragma unroll
-    for (int x = 0; x < 3; ++x)
-      gr[q][x] = mh[x] * dphi[q][0] + mh[3 + x] * dphi[q][1] + mh[6 + x] * dphi[q][2];
-  const R mu = R(0.5) * (mua + mub);
-  const R kap = R(0.5) * (kaa + kab);
-  const R div = gr[0][0] + gr[1][1] + gr[2][2];
-  const R two3 = R(2.0 / 3.0);
-  const R txx = mu * (R(2) * gr[0][0] - two3 * div);
-  const R tyy = mu * (R(2) * gr[1][1] - two3 * div);
-  const R tzz = mu * (R(2) * gr[2][2] - two3 * div);
-  const R txy = mu * (gr[0][1] + gr[1][0]);
-  const R txz = mu * (gr[0][2] + gr[2][0]);
-  const R tyz = mu * (gr[1][2] + gr[2][1]);
-  const R uf = R(0.5) * (ua + ub), vf = R(0.5) * (va + vb), wf = R(0.5) * (wa + wb);
-  const R bx = txx * uf + txy * vf + txz * wf + kap * gr[3][0];
-  const R by = txy * uf + tyy * vf + tyz * wf + kap * gr[3][1];
-  const R bz = txz * uf + tyz * vf + tzz * wf + kap * gr[3][2];
-  const R mx = mh[3 * D], my = mh[3 * D + 1], mz = mh[3 * D + 2];
-  F[1] -= Jh * (mx * txx + my * txy + mz * txz);
-  F[2] -= Jh * (mx * txy + my * tyy + mz * tyz);
-  F[3] -= Jh * (mx * txz + my * tyz + mz * tzz);
-  F[4] -= Jh * (mx * bx + my * by + mz * bz);
+  for (int t = 0; t < 3; ++t)
+    div += mt[3 * t] * dphi[0][t] + mt[3 * t + 1] * dphi[1][t] + mt[3 * t + 2] * dphi[2][t];
+  const R d23 = R(2.0 / 3.0) * div;
+  const R mm[3] = {mx, my, mz};
+  R sv[3];  // 4 m.tau_i / mu
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    sv[i] = (g[0] * dphi[i][0] + g[1] * dphi[i][1] + g[2] * dphi[i][2]) +
+            (mt[i] * c[0] + mt[3 + i] * c[1] + mt[6 + i] * c[2]) - mm[i] * d23;
+  const R aT = g[0] * dphi[3][0] + g[1] * dphi[3][1] + g[2] * dphi[3][2];  // 4 m.grad T
+  const R sJ = Ja + Jb, smu = mua + mub, skap = kaa + kab;  // 2x the means
+  const R cf = sJ * smu * R(1.0 / 16.0);
+  F[1] -= cf * sv[0];
+  F[2] -= cf * sv[1];
+  F[3] -= cf * sv[2];
+  const R us = (ua + ub) * sv[0] + (va + vb) * sv[1] + (wa + wb) * sv[2];  // 8 u_f . m.tau / mu
+  F[4] -= sJ * (smu * us * R(1.0 / 32.0) + skap * aT * R(1.0 / 16.0));
 }
 
 // Pressure sensor from the three pressures around a (possibly shifted) node.
@@ -352,11 +359,13 @@ __host__ __device__ constexpr int colk(int kk) { return kk + 2; }
 //   sM[3][10][PL1] metrics of planes i, i+1, i+2 (1-node halo)
 //   sK[3][2][PL1]  mu_eff kappa_eff of planes i, i+1, i+2
 //   sL[2][3][PL1]  lbar of planes i, i+1
-//   sFe[5][FTJ+1][FTK], sFz[5][FTJ][FTK+1]  eta / zeta interface fluxes
+//   sFe[5][FTJ+1][FTK]  eta interface fluxes (rows -1 .. FTJ-1 of the tile)
+//   sFz[5][FTJ]         the tile's left-edge zeta interface fluxes (the
+//                       others pass between neighbouring lanes by shuffle)
 constexpr int OFF_PR = 3 * 5 * PL2, OFF_PW = OFF_PR + 3 * 4 * PL2,
               OFF_M = OFF_PW + 3 * 2 * PL2, OFF_K = OFF_M + 3 * 10 * PL1,
               OFF_L = OFF_K + 3 * 2 * PL1, OFF_FE = OFF_L + 2 * 3 * PL1,
-              OFF_FZ = OFF_FE + 5 * (FTJ + 1) * FTK, SMEM_FLOATS = OFF_FZ + 5 * FTJ * (FTK + 1);
+              OFF_FZ = OFF_FE + 5 * (FTJ + 1) * FTK, SMEM_FLOATS = OFF_FZ + 5 * FTJ;
 
 // Computational derivatives of (u, v, w, T) at an interface from node
 // records (float4 u, v, w, T): along the interface normal, phi_b - phi_a;
@@ -863,11 +872,19 @@ __global__ void __launch_bounds__(FNT, 1)
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1)) * FTK + tx] = F[c];
       }
     }
-    if (own && iint && jint && (G.per[2] || kown + 1 <= nk - 1)) {
-      float F[5];
-      zeta_flux(ty, tx, s_c, s_m, s_c, s_p, s_c, l_c, mo, &ro, rpm, &wo, F);
+    // zeta interfaces: this lane's (tx, tx+1) minus its left neighbour's,
+    // taken through the warp; lane 0's left interface is the tile edge,
+    // computed by warp 1 and read after the barrier
+    float dz[5];
+    {
+      float Fz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      if (own && iint && jint && (G.per[2] || kown + 1 <= nk - 1))
+        zeta_flux(ty, tx, s_c, s_m, s_c, s_p, s_c, l_c, mo, &ro, rpm, &wo, Fz);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] = F[c];
+      for (int c = 0; c < 5; ++c) {
+        const float left = __shfl_up_sync(0xffffffffu, Fz[c], 1);
+        dz[c] = Fz[c] - (tx == 0 ? 0.f : left);
+      }
     }
     // left-edge zeta interfaces (k0-1, k0) of the FTJ rows: lanes of warp 1
     if (ty == 1 && tx < FTJ && iint && (G.per[2] || k0 - 1 >= 0)) {
@@ -877,7 +894,7 @@ __global__ void __launch_bounds__(FNT, 1)
         float F[5];
         zeta_flux(rr, -1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, nullptr, nullptr, nullptr, F);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) sFz[(c * FTJ + rr) * (FTK + 1)] = F[c];
+        for (int c = 0; c < 5; ++c) sFz[c * FTJ + rr] = F[c];
       }
     }
     // plane i+2, staged at the top of this iteration, must have landed before
@@ -903,7 +920,8 @@ __global__ void __launch_bounds__(FNT, 1)
           float r = 0.f;
           r += Fx[c] - Fx_prev[c];
           r += sFe[(c * (FTJ + 1) + ty + 1) * FTK + tx] - sFe[(c * (FTJ + 1) + ty) * FTK + tx];
-          r += sFz[(c * FTJ + ty) * (FTK + 1) + tx + 1] - sFz[(c * FTJ + ty) * (FTK + 1) + tx];
+          r += dz[c];
+          if (tx == 0) r -= sFz[c * FTJ + ty];
           if (MODE == FMODE_RHS) {
             P.outd[c][n] = (double)r;
           } else if (MODE == FMODE_STAGE) {
