@@ -173,7 +173,7 @@ const char *les_last_error(const les_ctx *ctx);
 int les_set_params(les_ctx *ctx, const les_params *p);
 
 /* Bytes of the caller-owned device workspace this context needs: about
- * 360 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
+ * 384 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
  * per point with LES_DT_LOCAL and 408 B per point with LES_SGS_DYNAMIC. */
 size_t les_workspace_bytes(const les_ctx *ctx);
 

@@ -39,7 +39,7 @@ struct les_ctx {
   les_params p;
   Grid g;
   // workspace layout (byte offsets, 256-byte aligned)
-  size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_hi, off_lo, off_node, off_flux, off_rth,
+  size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_hi, off_lo, off_node, off_flux, off_nu, off_rth,
       off_sc, off_part, off_dtl, off_dyn;
   size_t total;
   bool local_dt;  // the workspace holds per-node steps (dt_mode LOCAL at creation)
@@ -180,6 +180,7 @@ void layout(les_ctx* c) {
   c->off_lo = o; o = align256(o + (mixed ? 5 * N * sizeof(float) : 0));
   c->off_node = o; o = align256(o + (mixed ? 0 : 8 * N * sizeof(double)));
   c->off_flux = o; o = align256(o + (mixed ? 0 : 15 * N * sizeof(double)));
+  c->off_nu = o; o = align256(o + (mixed ? 0 : 3 * N * sizeof(double)));
   c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
   c->off_sc = o; o = align256(o + sizeof(DevScalars));
   c->off_part = o; o = align256(o + 8 * (size_t)lesjet::kMaxPartials * sizeof(double));
@@ -218,6 +219,7 @@ lesjet::StageIO64 io64(les_ctx* c, const double* Qin) {
   io.sc = at<DevScalars>(c, c->off_sc);
   io.dtl = c->p.dt_mode == LES_DT_LOCAL ? at<double>(c, c->off_dtl) : nullptr;
   io.dyn = c->dyn_ws ? at<double>(c, c->off_dyn) : nullptr;
+  io.nu = at<double>(c, c->off_nu);
   return io;
 }
 
@@ -236,6 +238,7 @@ void residual64(les_ctx* c, const lesjet::StageIO64& io, bool with_mu, bool with
     lesjet::launch_mu64(c->g, c->p, io, L);
   }
   ProfScope ps(c, PK_FLUX, L.s);
+  lesjet::launch_sensor64(c->g, io, L);
   for (int d = 0; d < 3; ++d) lesjet::launch_flux64(c->g, c->p, io, d, L);
 }
 

@@ -40,6 +40,8 @@ struct StageIO64 {
   double* partials;    // [kRedBlocks] block minima (dt)
   DevScalars* sc;
   double* dtl = nullptr;  // [N] local steps (dt_mode LOCAL), else nullptr
+  double* nu = nullptr;   // [3][N] pressure sensors along xi, eta, zeta
+                          // (k_sensor), or nullptr: k_flux evaluates them
   double* dyn = nullptr;  // [50][N] scratch of the dynamic SGS procedure
 };
 void launch_node64(const Grid& g, const les_params& p, const StageIO64& io, bool with_dt,
@@ -51,6 +53,8 @@ void launch_dynamic64(const Grid& g, const les_params& p, const StageIO64& io, d
                       const Launch& L);
 void launch_flux64(const Grid& g, const les_params& p, const StageIO64& io, int dir,
                    const Launch& L);
+// the three pressure sensors of every node into io.nu (after launch_node64)
+void launch_sensor64(const Grid& g, const StageIO64& io, const Launch& L);
 // mode 0: RHS into out; 1: stage update into out; 2: last stage in place
 void launch_update64(const Grid& g, const StageIO64& io, const double* Q0, double alpha, int mode,
                      double* out, const Launch& L);

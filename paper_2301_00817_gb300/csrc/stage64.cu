@@ -63,11 +63,21 @@ void launch_flux64(const Grid& g, const les_params& p, const StageIO64& io, int 
   auto K = make_consts<double>(p);
   double* F = io.flux + 5 * g.N * dir;
   if (dir == 0)
-    k_flux<0, double, double, double><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node, io.mk, F);
+    k_flux<0, double, double, double><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node, io.mk, F,
+                                                          io.nu);
   else if (dir == 1)
-    k_flux<1, double, double, double><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node, io.mk, F);
+    k_flux<1, double, double, double><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node, io.mk, F,
+                                                          io.nu);
   else
-    k_flux<2, double, double, double><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node, io.mk, F);
+    k_flux<2, double, double, double><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node, io.mk, F,
+                                                          io.nu);
+  ++*L.counter;
+}
+
+void launch_sensor64(const Grid& g, const StageIO64& io, const Launch& L) {
+  if (!io.nu) return;
+  const int th = 256, nb = blocks_for(g.N, th);
+  k_sensor<double><<<nb, th, 0, L.s>>>(g, io.node + 3 * g.N, io.nu);
   ++*L.counter;
 }
 

@@ -242,11 +242,28 @@ __device__ __forceinline__ R sensor(const Grid& g, const R* __restrict__ P, long
   return dev_abs(pp - R(2) * p0 + pm) / (pp + R(2) * p0 + pm);
 }
 
+// The three sensors of every node, once per residual evaluation (each node's
+// sensor along D is read by its two interfaces along D).
+template <typename R>
+__global__ void __launch_bounds__(256) k_sensor(Grid g, const R* __restrict__ P,
+                                                R* __restrict__ NU) {
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    NU[n] = sensor<0>(g, P, n, c[0]);
+    NU[N + n] = sensor<1>(g, P, n, c[1]);
+    NU[2 * N + n] = sensor<2>(g, P, n, c[2]);
+  }
+}
+
 template <int D, typename R, typename TQ, typename TM>
 __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __restrict__ Q,
                                               const TM* __restrict__ M,
                                               const R* __restrict__ node,
-                                              const R* __restrict__ mk, R* __restrict__ F) {
+                                              const R* __restrict__ mk, R* __restrict__ F,
+                                              const R* __restrict__ NU = nullptr) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const long long N = g.N;
   const R* __restrict__ U = node;
@@ -302,8 +319,8 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
     Fb[4] = Jb * ((Qb[4] + pb) * thb);
 
     // Turkel-Vatsa dissipation (Eqs. dissip_term, eps_2/4_dissip, W_dissip)
-    const R nua = sensor<D>(g, P, a, c[D]);
-    const R nub = sensor<D>(g, P, b, cb[D]);
+    const R nua = NU ? NU[D * N + a] : sensor<D>(g, P, a, c[D]);
+    const R nub = NU ? NU[D * N + b] : sensor<D>(g, P, b, cb[D]);
     const R eps2 = k2h * dev_max(nua, nub);    // half of eps^(2)
     const R eps4 = dev_max(R(0), k4h - eps2);  // half of eps^(4)
     const R sJ = Ja + Jb;                      // 2 J^-1 at the interface
@@ -376,46 +393,59 @@ __global__ void __launch_bounds__(256) k_flux(Grid g, Consts<R> K, const TQ* __r
     }
 #pragma unroll
     for (int x = 0; x < 3; ++x) mh[D][x] = R(4) * mh[D][x];
-    R gr[4][3];  // 8 grad(u, v, w, T)
+    // The flux needs only m.tau and m.q (m = the interface metric of
+    // direction D), which follow from the contractions g_t = m . m_t and
+    // c_t = sum_j m_j dphi_j,t and the divergence without forming the
+    // gradient tensor:
+    //   m.tau_i / mu = sum_t g_t dphi_i,t + sum_t m_t,i c_t - 2/3 m_i div,
+    //   m.grad T     = sum_t g_t dphi_T,t.
+    // With mh (8 m_D, 2 m_t) and dphi (1x along D, 4x along the tangents)
+    // every term below is 64x its value.
+    const R mx = mh[D][0], my = mh[D][1], mz = mh[D][2];  // 8 m
+    R G[3], Cc[3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int x = 0; x < 3; ++x)
-        gr[q][x] = mh[0][x] * dphi[q][0] + mh[1][x] * dphi[q][1] + mh[2][x] * dphi[q][2];
-    const R mu = mk[a] + mk[b];                      // 2 mu
-    const R kap = R(2) * (mk[N + a] + mk[N + b]);    // 4 kappa
-    const R div = gr[0][0] + gr[1][1] + gr[2][2];
-    const R two3 = R(2.0 / 3.0);
-    // 16 tau
-    R txx = mu * (R(2) * gr[0][0] - two3 * div);
-    R tyy = mu * (R(2) * gr[1][1] - two3 * div);
-    R tzz = mu * (R(2) * gr[2][2] - two3 * div);
-    if (K.sgs == LES_SGS_DYNAMIC) {
-      // the modelled isotropic SGS stress sigma_ll/3 (Eq. yoshizawa) at the
-      // interface mean, subtracted from the normal stresses
-      const R iso = R(8) * (mk[2 * N + a] + mk[2 * N + b]) / R(3);  // 16 sigma_ll / 3
-      txx -= iso;
-      tyy -= iso;
-      tzz -= iso;
+    for (int t = 0; t < 3; ++t) {
+      G[t] = mx * mh[t][0] + my * mh[t][1] + mz * mh[t][2];
+      Cc[t] = mx * dphi[0][t] + my * dphi[1][t] + mz * dphi[2][t];
     }
-    const R txy = mu * (gr[0][1] + gr[1][0]);
-    const R txz = mu * (gr[0][2] + gr[2][0]);
-    const R tyz = mu * (gr[1][2] + gr[2][1]);
+    R div = R(0);  // 8 div
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+      div += mh[t][0] * dphi[0][t] + mh[t][1] * dphi[1][t] + mh[t][2] * dphi[2][t];
+    const R d23 = R(2.0 / 3.0) * div;
+    const R mv[3] = {mx, my, mz};
+    R sv[3];  // 64 m.tau_i / mu
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      sv[i] = (G[0] * dphi[i][0] + G[1] * dphi[i][1] + G[2] * dphi[i][2]) +
+              (mh[0][i] * Cc[0] + mh[1][i] * Cc[1] + mh[2][i] * Cc[2]) - mv[i] * d23;
+    const R aT = G[0] * dphi[3][0] + G[1] * dphi[3][1] + G[2] * dphi[3][2];  // 64 m.grad T
+    const R mu = mk[a] + mk[b];                    // 2 mu
+    const R kap = R(2) * (mk[N + a] + mk[N + b]);  // 4 kappa
     const R uf = U[a] + U[b];  // 2 u at the interface
     const R vf = V[a] + V[b];
     const R wf = Wv[a] + Wv[b];
-    // 32 (tau u + kappa grad T)
-    const R bx = txx * uf + txy * vf + txz * wf + kap * gr[3][0];
-    const R by = txy * uf + tyy * vf + tyz * wf + kap * gr[3][1];
-    const R bz = txz * uf + tyz * vf + tzz * wf + kap * gr[3][2];
-    const R mx = mh[D][0], my = mh[D][1], mz = mh[D][2];
-    // 2 J^-1 m.tau = sJ (8 m).(16 tau) / 128 and 2 J^-1 m.b = sJ (8 m).(32 b) / 256
-    const R c1 = sJ * R(1.0 / 128.0), c2 = sJ * R(1.0 / 256.0);
+    // 2 J^-1 m.tau_i = sJ mu sv_i / 128; 2 J^-1 m.(tau u_f + kappa grad T) =
+    // sJ (mu (u_f . sv) + kap aT) / 256
+    const R c1 = sJ * mu * R(1.0 / 128.0), c2 = sJ * R(1.0 / 256.0);
+    R f1 = c1 * sv[0], f2 = c1 * sv[1], f3 = c1 * sv[2];
+    R f4 = c2 * (mu * (uf * sv[0] + vf * sv[1] + wf * sv[2]) + kap * aT);
+    if (K.sgs == LES_SGS_DYNAMIC) {
+      // the modelled isotropic SGS stress sigma_ll/3 (Eq. yoshizawa) at the
+      // interface mean, subtracted from the normal stresses: m.tau_i gains
+      // -m_i sigma/3 and u_f.(m.tau) gains -(u_f . m) sigma/3
+      const R ss = mk[2 * N + a] + mk[2 * N + b];  // 2 sigma_ll
+      const R e1 = sJ * ss * R(1.0 / 48.0);
+      f1 -= e1 * mx;
+      f2 -= e1 * my;
+      f3 -= e1 * mz;
+      f4 -= e1 * R(0.5) * (uf * mx + vf * my + wf * mz);
+    }
     F[n] = Fq[0];
-    F[N + n] = Fq[1] - c1 * (mx * txx + my * txy + mz * txz);
-    F[2 * N + n] = Fq[2] - c1 * (mx * txy + my * tyy + mz * tyz);
-    F[3 * N + n] = Fq[3] - c1 * (mx * txz + my * tyz + mz * tzz);
-    F[4 * N + n] = Fq[4] - c2 * (mx * bx + my * by + mz * bz);
+    F[N + n] = Fq[1] - f1;
+    F[2 * N + n] = Fq[2] - f2;
+    F[3 * N + n] = Fq[3] - f3;
+    F[4 * N + n] = Fq[4] - f4;
   }
 }
 
