@@ -122,6 +122,21 @@ typedef struct les_params {
                          the axis state.  Needs periodic = {0, 0, 1} and a
                          static SGS model (not LES_SGS_DYNAMIC); the adjoint
                          calls reject it.  0: every node has J^-1 > 0. */
+  int slab_ghost[2];  /* axial domain decomposition (Sec. "Communication":
+                         axial partitions with two ghost layers): the number
+                         of ghost planes at the low and the high xi end of
+                         this context's grid, 0 at a physical face (the
+                         entrance, the exit) and 2 at a cut between slabs.
+                         A ghost plane belongs to the neighbouring slab: the
+                         stages neither update it nor count it in the CFL
+                         minimum or the totals, and the entrance (exit)
+                         conditions apply only with slab_ghost[0] ([1]) = 0.
+                         Stepping with ghost planes goes through the phase
+                         calls below (les_step_begin ...), which let a driver
+                         exchange the ghost planes and take the global time
+                         step between the phases.  Needs periodic[0] = 0;
+                         not with LES_SGS_DYNAMIC (its means are global) or
+                         the adjoint calls. {0, 0}: an undivided grid. */
 } les_params;
 
 /* Diagnostics returned by the synchronising run calls. */
@@ -348,6 +363,49 @@ int les_adjoint_window(les_ctx *ctx, const double *Q_start, double t0,
  * window (the paper has no counterpart).  SYNCHRONISES. */
 int les_surface_functional(les_ctx *ctx, const double *Q, int j_surface, double w,
                            double *J_out, les_stream_t stream);
+
+/* One Runge-Kutta step in phases (Table tab:JAZzY), for a driver of axial
+ * slabs (slab_ghost) that exchanges ghost planes between the phases; on an
+ * undivided grid the phases in order do exactly what les_rk_step does.  Per
+ * step:
+ *   les_step_begin   viscosity and the CFL step of this slab's own planes
+ *                    from the state Q^n; returns that step in dt_local
+ *                    (SYNCHRONISES; LES_ERR_NONFINITE as les_time_step);
+ *   les_step_set_dt  the step all slabs take (the minimum of their dt_local
+ *                    across slabs); advances the clock to t^{n+1};
+ *   les_step_stage   stage l = 1..5 (Eq. localdt): Q^(l) = Q^(0) -
+ *                    alpha_l dt J RHS(Q^(l-1)); exchange the ghost planes of
+ *                    the state after it before the next phase;
+ *   les_step_end     the boundary conditions at t^{n+1}; exchange again.
+ * Q: device [5][N] FP64, the caller's state.  The mixed forms keep the state
+ * as a float pair in the workspace between phases: les_state_load splits Q
+ * into it before the first step, les_state_store joins it back into Q (both
+ * no-ops in FP64).  les_state_buffer names the arrays that hold the state
+ * after stage l (l = 1..4: the stage buffer, FP64 or float, *a; l = 0 or 5,
+ * the state after stage 5 or after the boundary conditions: *a = NULL for
+ * FP64, meaning the caller's Q, else the float pair hi *a and lo *b); each
+ * is [5][N] with field stride N, elem_bytes 8 or 4; ghost plane i of field
+ * f is the nj*nk values from (f N + i nj nk).  Asynchronous except
+ * les_step_begin. */
+int les_step_begin(les_ctx *ctx, double *Q, double *dt_local, les_stream_t stream);
+int les_step_set_dt(les_ctx *ctx, double dt, les_stream_t stream);
+int les_step_stage(les_ctx *ctx, int l, double *Q, les_stream_t stream);
+int les_step_end(les_ctx *ctx, double *Q, les_stream_t stream);
+int les_state_load(les_ctx *ctx, const double *Q, les_stream_t stream);
+int les_state_store(les_ctx *ctx, double *Q, les_stream_t stream);
+int les_state_buffer(les_ctx *ctx, int l, void **a, void **b, int *elem_bytes);
+
+/* Ghost-plane exchange between two slab contexts of one process (the same
+ * or peer devices): copies src's two own planes next to the cut into dst's
+ * ghost planes, for the state after stage l (as in les_state_buffer; Qdst,
+ * Qsrc are the callers' states, used for l = 0 or 5 in FP64).  side 0: dst
+ * is the slab above src along xi (src planes [ni_src-4, ni_src-2) into dst
+ * planes [0, 2)); side 1: dst is the slab below (src planes [2, 4) into dst
+ * planes [ni_dst-2, ni_dst)).  One cudaMemcpy2DAsync per array (5 fields of
+ * 2 planes, field strides N_src, N_dst) on stream.  Both contexts need the
+ * same nj, nk and precision and the matching ghost planes.  Asynchronous. */
+int les_halo_copy(les_ctx *dst, double *Qdst, les_ctx *src, const double *Qsrc, int l, int side,
+                  les_stream_t stream);
 
 /* Global time step of state Q, like les_time_step, for callers that cannot
  * allocate device memory (the paper has no counterpart): for example a

@@ -52,6 +52,7 @@ class LesParams(C.Structure):
         ("dt_mode", C.c_int), ("freeze_visc", C.c_int), ("precision", C.c_int),
         ("metric_form", C.c_int),
         ("axis", C.c_int),
+        ("slab_ghost", C.c_int * 2),
     ]
 
 
@@ -74,11 +75,11 @@ def make_params(**kw) -> LesParams:
              theta_m=0.05, force_width=0.05, St=(0.25, 0.5, 0.75, 1.0),
              amp=(0.0,) * 16, sgs_model=SGS_NONE, periodic=(0, 0, 1), bc=BC_JET,
              dt_mode=DT_CFL, freeze_visc=1, precision=PREC_FP64, metric_form=METRIC_CROSS,
-             axis=0)
+             axis=0, slab_ghost=(0, 0))
     d.update(kw)
     p = LesParams()
     for k, v in d.items():
-        if k in ("St", "amp", "periodic"):
+        if k in ("St", "amp", "periodic", "slab_ghost"):
             arr = getattr(p, k)
             for i, x in enumerate(v):
                 arr[i] = float(x) if k != "periodic" else int(x)
@@ -144,6 +145,17 @@ def load_library(path: str = LIB_PATH):
     lib.les_adjoint_step.argtypes = [vp, vp, d, vp, vp, C.POINTER(d), vp, vp]
     lib.les_adjoint_window.argtypes = [vp, vp, d, i, i, i, vp, C.POINTER(d), C.POINTER(d), vp]
     for name in ("les_rhs_jvp", "les_rhs_vjp", "les_adjoint_step", "les_adjoint_window"):
+        getattr(lib, name).restype = C.c_int
+    lib.les_step_begin.argtypes = [vp, vp, C.POINTER(d), vp]
+    lib.les_step_set_dt.argtypes = [vp, d, vp]
+    lib.les_step_stage.argtypes = [vp, i, vp, vp]
+    lib.les_step_end.argtypes = [vp, vp, vp]
+    lib.les_state_load.argtypes = [vp, vp, vp]
+    lib.les_state_store.argtypes = [vp, vp, vp]
+    lib.les_state_buffer.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(i)]
+    lib.les_halo_copy.argtypes = [vp, vp, vp, vp, i, i, vp]
+    for name in ("les_step_begin", "les_step_set_dt", "les_step_stage", "les_step_end",
+                 "les_state_load", "les_state_store", "les_state_buffer", "les_halo_copy"):
         getattr(lib, name).restype = C.c_int
     for name in ("les_create", "les_destroy", "les_set_params", "les_set_grid", "les_init_jet",
                  "les_mu_eff", "les_rhs", "les_time_step", "les_apply_bc", "les_set_time",
@@ -329,6 +341,53 @@ class Context:
         diag = LesDiag()
         self._check(self.lib.les_run_n_steps(self.h, n, _ptr(Q), C.byref(diag), _stream(stream)))
         return diag
+
+    # --- one step in phases (axial slabs; see slabs.py) -------------------
+    def les_step_begin(self, Q, stream=None) -> float:
+        """Viscosity and the CFL step of this slab's own planes; synchronises."""
+        out = C.c_double()
+        self._check(self.lib.les_step_begin(self.h, _ptr(Q), C.byref(out), _stream(stream)))
+        return out.value
+
+    def les_step_set_dt(self, dt: float, stream=None):
+        self._check(self.lib.les_step_set_dt(self.h, dt, _stream(stream)))
+
+    def les_step_stage(self, l: int, Q, stream=None):
+        self._check(self.lib.les_step_stage(self.h, l, _ptr(Q), _stream(stream)))
+
+    def les_step_end(self, Q, stream=None):
+        self._check(self.lib.les_step_end(self.h, _ptr(Q), _stream(stream)))
+
+    def les_state_load(self, Q, stream=None):
+        self._check(self.lib.les_state_load(self.h, _ptr(Q), _stream(stream)))
+
+    def les_state_store(self, Q, stream=None):
+        self._check(self.lib.les_state_store(self.h, _ptr(Q), _stream(stream)))
+
+    def state_views(self, l: int, Q):
+        """The arrays holding the state after stage l (les_state_buffer), as
+        [5, ni, nj, nk] views: the caller's Q, a stage buffer of the
+        workspace, or the float pair (hi, lo) of the mixed forms."""
+        torch = _torch()
+        a, b, e = C.c_void_p(), C.c_void_p(), C.c_int()
+        self._check(self.lib.les_state_buffer(self.h, l, C.byref(a), C.byref(b), C.byref(e)))
+        if not a.value:
+            return [Q]
+        dt = torch.float32 if e.value == 4 else torch.float64
+        out = []
+        for ptr in (a.value, b.value):
+            if not ptr:
+                continue
+            off = ptr - self.workspace.data_ptr()
+            nbytes = 5 * self.N * e.value
+            out.append(self.workspace[off:off + nbytes].view(dt).view(5, *self.shape))
+        return out
+
+    def les_halo_copy(self, Q, src, Q_src, l: int, side: int, stream=None):
+        """Ghost planes of this slab from the neighbouring slab src (same
+        process): side 0, src lies below along xi; side 1, above."""
+        self._check(self.lib.les_halo_copy(self.h, _ptr(Q), src.h, _ptr(Q_src), l, side,
+                                           _stream(stream)))
 
     def les_run_host(self, n: int, Q_host, Q_dev, stream=None) -> LesDiag:
         assert not Q_host.is_cuda and Q_host.is_contiguous()

@@ -156,6 +156,20 @@ int validate_params(const les_params* p, std::string& why) {
     why = "a grid with an axis needs periodic = {0, 0, 1} (ring j = 0 on the axis)";
     return LES_ERR_INVALID_ARG;
   }
+  for (int e = 0; e < 2; ++e)
+    if (p->slab_ghost[e] != 0 && p->slab_ghost[e] != 2) {
+      why = "slab_ghost entries must be 0 (a physical face) or 2 (a cut between slabs)";
+      return LES_ERR_INVALID_ARG;
+    }
+  const bool slab = p->slab_ghost[0] || p->slab_ghost[1];
+  if (slab && p->periodic[0]) {
+    why = "axial slabs need a non-periodic xi (periodic[0] = 0)";
+    return LES_ERR_INVALID_ARG;
+  }
+  if (slab && p->sgs_model == LES_SGS_DYNAMIC) {
+    why = "the dynamic SGS model's volume means are global: not with axial slabs";
+    return LES_ERR_UNSUPPORTED;
+  }
   if (p->axis && p->sgs_model == LES_SGS_DYNAMIC) {
     why = "the dynamic SGS model is not defined on a grid with an axis (its test filter would "
           "carry the axis nodes' scaled data into ring 1)";
@@ -352,6 +366,8 @@ int les_create(const les_params* p, int ni, int nj, int nk, les_ctx** out) {
   int rc = validate_params(p, why);
   if (rc != LES_OK) return rc;
   if (ni < 5 || nj < 5 || nk < 5) return LES_ERR_SHAPE;
+  // a slab owns at least one plane besides its ghost planes
+  if (ni <= p->slab_ghost[0] + p->slab_ghost[1]) return LES_ERR_SHAPE;
   // the axis viscosity rule averages a ring in shared memory
   if (p->axis && nk > 4096) return LES_ERR_SHAPE;
   const long long N = (long long)ni * nj * nk;
@@ -370,6 +386,8 @@ int les_create(const les_params* p, int ni, int nj, int nk, les_ctx** out) {
   c->g.stride[0] = (long long)nj * nk;
   c->g.stride[1] = nk;
   c->g.stride[2] = 1;
+  c->g.glo = p->slab_ghost[0];
+  c->g.ghi = p->slab_ghost[1];
   c->ws = nullptr;
   c->grid_set = false;
   c->launches = 0;
@@ -409,6 +427,8 @@ int les_set_params(les_ctx* c, const les_params* p) {
   for (int d = 0; d < 3; ++d)
     if ((p->periodic[d] ? 1 : 0) != c->g.per[d])
       return fail(c, LES_ERR_INVALID_ARG, "periodicity is fixed at creation");
+  if (p->slab_ghost[0] != c->g.glo || p->slab_ghost[1] != c->g.ghi)
+    return fail(c, LES_ERR_INVALID_ARG, "the slab's ghost planes are fixed at creation");
   c->p = *p;
   return LES_OK;
 }
@@ -582,6 +602,185 @@ int finish_run(les_ctx* c, int n, les_diag* diag, cudaStream_t s) {
     diag->steps = n;
   }
   if (h.status != 0) return fail(c, LES_ERR_NONFINITE, "non-finite or non-positive state");
+  return LES_OK;
+}
+
+// ---- one step in phases (axial slabs: the driver exchanges ghost planes and
+// takes the global step between them)
+int les_step_begin(les_ctx* c, double* Q, double* dt_local, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || !dt_local) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  DevScalars* sc = at<DevScalars>(c, c->off_sc);
+  if (is_mixed(c)) {
+    prestep32(c, at<float>(c, c->off_hi), sc, L);
+    ProfScope ps(c, PK_DT, s);
+    lesjet::launch_dt_finalize(c->p, at<double>(c, c->off_part), sc, 0, L);
+  } else {
+    // node quantities (with the CFL minima), dt, viscosity of Q^n; stage 1
+    // reuses them
+    lesjet::StageIO64 io = io64(c, Q);
+    {
+      ProfScope ps(c, PK_NODE, s);
+      lesjet::launch_node64(c->g, c->p, io, true, L);
+    }
+    {
+      ProfScope ps(c, PK_DT, s);
+      lesjet::launch_dt_finalize(c->p, io.partials, io.sc, 0, L);
+    }
+    ProfScope ps(c, PK_MU, s);
+    lesjet::launch_mu64(c->g, c->p, io, L);
+  }
+  if ((rc = cuda_check(c, "les_step_begin")) != LES_OK) return rc;
+  DevScalars h;
+  if ((rc = read_scalars(c, &h, s)) != LES_OK) return rc;
+  *dt_local = h.dt;
+  if (h.status != 0) return fail(c, LES_ERR_NONFINITE, "non-finite or non-positive state");
+  return LES_OK;
+}
+
+int les_step_set_dt(les_ctx* c, double dt, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!(dt > 0.0) || !(dt < 1.0e300)) return fail(c, LES_ERR_INVALID_ARG, "dt must be positive and finite");
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  lesjet::launch_set_dt(at<DevScalars>(c, c->off_sc), dt, L);
+  return cuda_check(c, "les_step_set_dt");
+}
+
+int les_step_stage(les_ctx* c, int l, double* Q, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q || l < 1 || l > 5) return fail(c, LES_ERR_INVALID_ARG, "null pointer or stage outside 1..5");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  if (!is_mixed(c)) {
+    double* SA = at<double>(c, c->off_sa);
+    double* SB = at<double>(c, c->off_sb);
+    const double* in = (l == 1) ? Q : ((l % 2 == 0) ? SA : SB);
+    double* out = (l == 5) ? Q : ((l % 2 == 1) ? SA : SB);
+    lesjet::StageIO64 io = io64(c, in);
+    if (l == 1) {
+      // node quantities and viscosity of Q^n come from les_step_begin
+      ProfScope ps(c, PK_FLUX, s);
+      lesjet::launch_sensor64(c->g, io, L);
+      for (int d = 0; d < 3; ++d) lesjet::launch_flux64(c->g, c->p, io, d, L);
+    } else {
+      residual64(c, io, !c->p.freeze_visc, false, 0, L);
+    }
+    ProfScope ps(c, PK_UPDATE, s);
+    lesjet::launch_update64(c->g, io, Q, kAlpha[l - 1], l == 5 ? 2 : 1, out, L);
+  } else {
+    float* hi = at<float>(c, c->off_hi);
+    float* SA = at<float>(c, c->off_sa);
+    float* SB = at<float>(c, c->off_sb);
+    const float* in = (l == 1) ? hi : ((l % 2 == 0) ? SA : SB);
+    float* out = (l == 5) ? nullptr : ((l % 2 == 1) ? SA : SB);
+    if (l > 1 && !c->p.freeze_visc) prestep32(c, in, nullptr, L);  // Reading A17, unfrozen
+    ProfScope ps(c, PK_STAGE, s);
+    lesjet::launch_stage_fused(l == 5 ? 2 : 1, c->g, c->p, fused_io(c, in, out), kAlpha[l - 1], L);
+  }
+  return cuda_check(c, "les_step_stage");
+}
+
+int les_step_end(les_ctx* c, double* Q, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  lesjet::Launch L{s, &c->launches};
+  if (jet_bc(c)) {
+    ProfScope ps(c, PK_BC, s);
+    DevScalars* sc = at<DevScalars>(c, c->off_sc);
+    if (!is_mixed(c))
+      lesjet::launch_bc_jet(c->g, c->p, Q, at<double>(c, c->off_m64), at<double>(c, c->off_rth), sc,
+                            0, 0.0, L);
+    else if (has_m64(c))
+      lesjet::launch_bc_jet_hl(c->g, c->p, at<float>(c, c->off_hi), at<float>(c, c->off_lo),
+                               at<double>(c, c->off_m64), at<double>(c, c->off_rth), sc, L);
+    else
+      lesjet::launch_bc_jet_hl(c->g, c->p, at<float>(c, c->off_hi), at<float>(c, c->off_lo),
+                               at<float>(c, c->off_m32), at<double>(c, c->off_rth), sc, L);
+  }
+  return cuda_check(c, "les_step_end");
+}
+
+int les_state_load(les_ctx* c, const double* Q, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  if (is_mixed(c)) split_state(c, Q, L);
+  return cuda_check(c, "les_state_load");
+}
+
+int les_state_store(les_ctx* c, double* Q, les_stream_t stream) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!Q) return fail(c, LES_ERR_INVALID_ARG, "null pointer");
+  if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
+  lesjet::Launch L{(cudaStream_t)stream, &c->launches};
+  if (is_mixed(c)) join_state(c, Q, L);
+  return cuda_check(c, "les_state_store");
+}
+
+int les_state_buffer(les_ctx* c, int l, void** a, void** b, int* elem_bytes) {
+  int rc = ready(c);
+  if (rc != LES_OK) return rc;
+  if (!a || !b || !elem_bytes || l < 0 || l > 5)
+    return fail(c, LES_ERR_INVALID_ARG, "null pointer or stage outside 0..5");
+  *b = nullptr;
+  if (l >= 1 && l <= 4) {
+    *a = c->ws + ((l % 2 == 1) ? c->off_sa : c->off_sb);
+    *elem_bytes = is_mixed(c) ? 4 : 8;
+  } else if (!is_mixed(c)) {
+    *a = nullptr;  // the caller's Q
+    *elem_bytes = 8;
+  } else {
+    *a = c->ws + c->off_hi;
+    *b = c->ws + c->off_lo;
+    *elem_bytes = 4;
+  }
+  return LES_OK;
+}
+
+int les_halo_copy(les_ctx* dst, double* Qdst, les_ctx* src, const double* Qsrc, int l, int side,
+                  les_stream_t stream) {
+  int rc = ready(dst);
+  if (rc != LES_OK) return rc;
+  if ((rc = ready(src)) != LES_OK) return rc;
+  if (side != 0 && side != 1) return fail(dst, LES_ERR_INVALID_ARG, "side must be 0 or 1");
+  if (dst->g.n[1] != src->g.n[1] || dst->g.n[2] != src->g.n[2] || is_mixed(dst) != is_mixed(src))
+    return fail(dst, LES_ERR_INVALID_ARG, "slabs differ in nj, nk or precision");
+  // side 0: dst lies above src (dst's low ghosts from src's top own planes)
+  if (side == 0 ? (dst->g.glo != 2 || src->g.ghi != 2) : (dst->g.ghi != 2 || src->g.glo != 2))
+    return fail(dst, LES_ERR_INVALID_ARG, "the slabs have no ghost planes at this cut");
+  void *da, *db, *sa, *sb;
+  int de, se;
+  if ((rc = les_state_buffer(dst, l, &da, &db, &de)) != LES_OK) return rc;
+  if ((rc = les_state_buffer(src, l, &sa, &sb, &se)) != LES_OK) return fail(dst, rc, "source buffers");
+  if (!da) da = Qdst;
+  if (!sa) sa = const_cast<double*>(Qsrc);
+  if (!da || !sa) return fail(dst, LES_ERR_INVALID_ARG, "null state pointer");
+  const size_t e = (size_t)de;
+  const size_t plane = (size_t)dst->g.n[1] * dst->g.n[2] * e;
+  const size_t dp = (size_t)dst->g.N * e, sp = (size_t)src->g.N * e;
+  const size_t doff = (side == 0) ? 0 : (size_t)(dst->g.n[0] - 2) * plane;
+  const size_t soff = (side == 0) ? (size_t)(src->g.n[0] - 4) * plane : 2 * plane;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* dsts[2] = {da, db};
+  void* srcs[2] = {sa, sb};
+  for (int k = 0; k < 2; ++k) {
+    if (!dsts[k]) continue;
+    if (cudaMemcpy2DAsync((char*)dsts[k] + doff, dp, (const char*)srcs[k] + soff, sp, 2 * plane, 5,
+                          cudaMemcpyDefault, s) != cudaSuccess)
+      return cuda_check(dst, "les_halo_copy");
+  }
   return LES_OK;
 }
 
@@ -810,6 +1009,8 @@ int adj_check(les_ctx* c) {
     return fail(c, LES_ERR_UNSUPPORTED, "the adjoint needs freeze_visc = 1");
   if (c->p.axis)
     return fail(c, LES_ERR_UNSUPPORTED, "the adjoint is provided for grids without an axis");
+  if (c->g.glo || c->g.ghi)
+    return fail(c, LES_ERR_UNSUPPORTED, "the adjoint is provided for undivided grids");
   return LES_OK;
 }
 

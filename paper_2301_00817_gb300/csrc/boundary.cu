@@ -282,6 +282,7 @@ __global__ void k_totals_partial(Grid g, View Q, const TM* __restrict__ M,
   double s[5] = {0, 0, 0, 0, 0};
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
+    if ((g.glo | g.ghi) != 0 && !owned_plane(g, (int)(n / g.stride[0]))) continue;  // a slab sums its own planes
     const double jv = (double)M[9 * N + n];
 #pragma unroll
     for (int q = 0; q < 5; ++q) s[q] += jv * Q.ld(q * N + n);
@@ -345,11 +346,20 @@ static void bc_jet(const Grid& g, const les_params& p, Acc Q, const TM* M,
     if (p.amp[i] != 0.0) b.forced = 1;
   }
   const long long plane = (long long)g.n[1] * g.n[2];
-  k_bc_inflow<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, M, sc, use_host_t, t_host, Q);
+  // an axial slab has the entrance only if it starts at the physical face
+  // and the exit only if it ends there (its far field and inner ring cover
+  // its ghost planes too, which the next exchange overwrites)
+  if (g.glo == 0) {
+    k_bc_inflow<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, M, sc, use_host_t, t_host, Q);
+    ++*L.counter;
+  }
   k_bc_farfield<Acc, TM><<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M, Q);
   k_bc_ring<Acc><<<g.n[0] - 2, 256, 0, L.s>>>(g, Q);
-  k_bc_exit<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M, Q);
-  *L.counter += 4;
+  *L.counter += 2;
+  if (g.ghi == 0) {
+    k_bc_exit<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M, Q);
+    ++*L.counter;
+  }
 }
 
 void launch_bc_jet(const Grid& g, const les_params& p, double* Q, const double* M64,

@@ -221,8 +221,10 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
       }
     }
     const R inv = R(1) / lsum;
-    if (!(rho > R(0)) || !(p > R(0)) || !(inv > R(0)) || !(inv < R(1e30))) bad = 1;
-    local_min = inv < local_min ? inv : local_min;
+    if ((g.glo | g.ghi) == 0 || owned_plane(g, (int)(n / g.stride[0]))) {  // a slab's ghost planes are its neighbour's
+      if (!(rho > R(0)) || !(p > R(0)) || !(inv > R(0)) || !(inv < R(1e30))) bad = 1;
+      local_min = inv < local_min ? inv : local_min;
+    }
     if (dtl) dtl[n] = cfl * inv;  // local step of Eq. localdt
 
     const R mu_l = K.mu_scale * T * dev_sqrt(T) * (R(1) + K.S_suth) / (T + K.S_suth);
@@ -411,6 +413,7 @@ struct FusedGeom {
   int nch;  // axial chunks; chunk z holds planes [z ni / nch, (z + 1) ni / nch)
   int vec16;  // zeta periodic, nk % 4 == 0 and nk >= FTK: tiles shifted by
               // two columns, rows staged as 16-byte copies
+  int ilo, ihi;  // planes the stage updates along a non-periodic xi: [ilo, ihi)
 };
 
 __device__ __forceinline__ int wrap_fast(int v, int n, int per) {
@@ -838,7 +841,7 @@ __global__ void __launch_bounds__(FNT, 1)
     __syncthreads();
 
     const int ig = wrap_fast(i, ni, G.per[0]);
-    const bool iint = per_i || (i > 0 && i < ni - 1);
+    const bool iint = per_i || (i >= G.ilo && i < G.ihi);
     float Fx[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     // the own node's metrics, read once for its three interfaces
     float mo[10];
@@ -1116,6 +1119,9 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   for (int d = 0; d < 3; ++d) G.per[d] = g.per[d];
   G.nch = 1;
   G.vec16 = (g.per[2] && g.n[2] % 4 == 0 && g.n[2] >= FTK) ? 1 : 0;
+  // inside the physical faces and, for an axial slab, its own planes
+  G.ilo = g.glo > 0 ? g.glo : 1;
+  G.ihi = g.n[0] - (g.ghi > 0 ? g.ghi : 1);
   const long long N = g.N;
   FusedPtrs P;
   for (int c = 0; c < 5; ++c) {

@@ -16,7 +16,17 @@ struct Grid {
   int per[3];
   long long N;
   long long stride[3];  // {nj*nk, nk, 1}
+  // ghost planes at the low / high xi end of an axial slab (0 at a physical
+  // face): those planes belong to the neighbouring slab, which refreshes
+  // them between the stages; this grid updates, reduces and sums only its
+  // own planes [glo, n[0] - ghi)
+  int glo = 0, ghi = 0;
 };
+
+// Own planes of a slab (every plane of an undivided grid).
+__host__ __device__ inline bool owned_plane(const Grid& g, int i) {
+  return i >= g.glo && i < g.n[0] - g.ghi;
+}
 
 // Scheme constants in the compute precision R.
 template <typename R>
@@ -89,11 +99,13 @@ __device__ __forceinline__ long long step(const Grid& g, long long n, const int 
   return n + (long long)(v - c[d]) * g.stride[d];
 }
 
+// A node the stages update: inside every non-periodic face, and along xi
+// inside the slab's own planes (a ghost plane is refreshed by the exchange).
 __device__ __forceinline__ bool is_interior(const Grid& g, const int c[3]) {
 #pragma unroll
   for (int d = 0; d < 3; ++d)
     if (!g.per[d] && (c[d] == 0 || c[d] == g.n[d] - 1)) return false;
-  return true;
+  return c[0] >= g.glo && c[0] < g.n[0] - g.ghi;
 }
 
 template <typename T>

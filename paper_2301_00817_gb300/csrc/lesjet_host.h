@@ -24,6 +24,8 @@ void launch_init_jet(const Grid& g, const double* xyz, uint64_t seed, double noi
                      const les_params& p, double* Q, const Launch& L);
 
 // stage.cu
+// the step every slab takes (the minimum of their own): dt and t^{n+1}
+void launch_set_dt(DevScalars* sc, double dt, const Launch& L);
 void launch_dt_finalize(const les_params& p, double* partials, DevScalars* sc, int advance,
                         const Launch& L);
 void launch_mk_to_double(int precision, const Grid& g, const void* mk, int fields, double* out,

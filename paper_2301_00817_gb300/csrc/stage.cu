@@ -42,6 +42,19 @@ __global__ void k_dt_finalize(const double* __restrict__ partials, int nparts, i
   }
 }
 
+__global__ void k_set_dt(DevScalars* sc, double dt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    sc->dt = dt;
+    sc->t += dt;
+    sc->steps += 1;
+  }
+}
+
+void launch_set_dt(DevScalars* sc, double dt, const Launch& L) {
+  k_set_dt<<<1, 32, 0, L.s>>>(sc, dt);
+  ++*L.counter;
+}
+
 template <typename R>
 __global__ void k_cast_to_double(long long count, const R* __restrict__ a, double* __restrict__ b) {
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < count;

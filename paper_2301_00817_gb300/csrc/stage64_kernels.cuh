@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(256) k_node(Grid g, Consts<R> K, const TQ* __r
     node[7 * N + n] = lam[2] + s02 + s12;
     if (WITH_DT) {
       const double inv = 1.0 / ((double)lam[0] + (double)lam[1] + (double)lam[2]);
-      if (!(rho > R(0)) || !(p > R(0)) || !(inv > 0.0) || !(inv < 1.0e300)) bad = 1;
-      local_min = inv < local_min ? inv : local_min;
+      if ((g.glo | g.ghi) == 0 || owned_plane(g, (int)(n / g.stride[0]))) {  // a slab's ghost planes are its neighbour's
+        if (!(rho > R(0)) || !(p > R(0)) || !(inv > 0.0) || !(inv < 1.0e300)) bad = 1;
+        local_min = inv < local_min ? inv : local_min;
+      }
       if (dtl) dtl[n] = cfl * inv;  // local step of Eq. localdt
     }
   }

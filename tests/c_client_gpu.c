@@ -54,6 +54,7 @@ static les_params jet_params(int precision) {
   p.precision = precision;
   p.metric_form = LES_METRIC_CROSS;
   p.axis = 0;
+  p.slab_ghost[0] = p.slab_ghost[1] = 0;
   return p;
 }
 

@@ -107,7 +107,8 @@ def test_binding_structs_match_the_header(tmp_path):
     header compiled as plain C by gcc)."""
     import paper_2301_00817_gb300 as lj
     fields = {"les_params": (lj.LesParams, ["Re", "St", "amp", "sgs_model", "periodic", "bc",
-                                            "precision", "metric_form", "axis"]),
+                                            "precision", "metric_form", "axis",
+                                            "slab_ghost"]),
               "les_diag": (lj.LesDiag, ["dt", "totals", "status", "steps"]),
               "les_jet_grid": (lj.LesJetGrid, ["ratio", "r_c", "beta"])}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
