@@ -82,7 +82,7 @@ def make_params(**kw) -> LesParams:
         if k in ("St", "amp", "periodic", "slab_ghost"):
             arr = getattr(p, k)
             for i, x in enumerate(v):
-                arr[i] = float(x) if k != "periodic" else int(x)
+                arr[i] = int(x) if k in ("periodic", "slab_ghost") else float(x)
         else:
             setattr(p, k, v)
     return p
