@@ -80,7 +80,8 @@ typedef struct les_params {
   int sgs_model;      /* LES_SGS_NONE, LES_SGS_SMAGORINSKY, LES_SGS_VREMAN,
                          or LES_SGS_DYNAMIC (dynamic Smagorinsky with the
                          Yoshizawa isotropic part and a dynamic Pr_sgs;
-                         FP64 form, chosen at les_create) */
+                         chosen at les_create; in the mixed forms the
+                         procedure runs in FP32 with FP64 sums) */
   int periodic[3];    /* per direction xi, eta, zeta: 1 = periodic */
   int bc;             /* LES_BC_FROZEN (non-periodic faces never change),
                          LES_BC_JET (Dirichlet jet state over the whole
@@ -189,7 +190,8 @@ int les_set_params(les_ctx *ctx, const les_params *p);
 
 /* Bytes of the caller-owned device workspace this context needs: about
  * 384 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
- * per point with LES_DT_LOCAL and 408 B per point with LES_SGS_DYNAMIC. */
+ * per point with LES_DT_LOCAL and, with LES_SGS_DYNAMIC, 408 B per point
+ * (FP64) or 236 B per point (mixed). */
 size_t les_workspace_bytes(const les_ctx *ctx);
 
 /* Bind the workspace and compute the Jacobian and the nine metric terms on

@@ -192,13 +192,14 @@ void layout(les_ctx* c) {
   c->off_sb = o; o = align256(o + 5 * N * rs);
   c->off_hi = o; o = align256(o + (mixed ? 5 * N * sizeof(float) : 0));
   c->off_lo = o; o = align256(o + (mixed ? 5 * N * sizeof(float) : 0));
-  c->off_node = o; o = align256(o + (mixed ? 0 : 8 * N * sizeof(double)));
+  // node fields: FP64 form; FP32 for the mixed forms' dynamic procedure
+  c->off_node = o; o = align256(o + (mixed ? (c->dyn_ws ? 8 * N * sizeof(float) : 0) : 8 * N * sizeof(double)));
   c->off_flux = o; o = align256(o + (mixed ? 0 : 15 * N * sizeof(double)));
   c->off_nu = o; o = align256(o + (mixed ? 0 : 3 * N * sizeof(double)));
   c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
   c->off_sc = o; o = align256(o + sizeof(DevScalars));
   c->off_part = o; o = align256(o + 8 * (size_t)lesjet::kMaxPartials * sizeof(double));
-  c->off_dyn = o; o = align256(o + (c->dyn_ws ? 50 * N * sizeof(double) : 0));
+  c->off_dyn = o; o = align256(o + (c->dyn_ws ? 50 * N * rs : 0));
   c->off_dtl = o; o = align256(o + (c->p.dt_mode == LES_DT_LOCAL ? N * rs : 0));
   c->local_dt = c->p.dt_mode == LES_DT_LOCAL;
   c->total = o;
@@ -269,12 +270,22 @@ void join_state(les_ctx* c, double* Q, const lesjet::Launch& L) {
 // mu_eff/kappa_eff of the float state (frozen for the step) and the block
 // minima of the CFL step; sc == nullptr leaves the status word alone.
 void prestep32(les_ctx* c, const float* Qs, DevScalars* sc, const lesjet::Launch& L) {
+  const double* dyn = nullptr;
+  if (c->dyn_ws) {
+    // the dynamic procedure on the float state: coefficients into dyn[6..8]
+    ProfScope ps(c, PK_MU, L.s);
+    DevScalars* scd = at<DevScalars>(c, c->off_sc);
+    lesjet::launch_dynamic32(c->g, c->p, Qs, at<float>(c, c->off_m32), at<float>(c, c->off_node),
+                             at<float>(c, c->off_dyn), at<double>(c, c->off_part), scd, L);
+    dyn = reinterpret_cast<const double*>(reinterpret_cast<const char*>(scd) +
+                                          offsetof(DevScalars, dyn));
+  }
   ProfScope ps(c, PK_PRESTEP, L.s);
   // the per-node steps are those of Q^n: written only by the step's first
   // prestep (the one that also takes the CFL minima, sc != nullptr)
   float* dtl = (sc && c->p.dt_mode == LES_DT_LOCAL) ? at<float>(c, c->off_dtl) : nullptr;
   lesjet::launch_prestep(c->g, c->p, Qs, at<float>(c, c->off_m32), at<float>(c, c->off_mk),
-                         at<double>(c, c->off_part), sc, dtl, L);
+                         at<double>(c, c->off_part), sc, dtl, dyn, L);
 }
 
 lesjet::FusedIO fused_io(les_ctx* c, const void* Qin, void* out) {
@@ -374,7 +385,6 @@ int les_create(const les_params* p, int ni, int nj, int nk, les_ctx** out) {
   if (N >= (1LL << 40)) return LES_ERR_SHAPE;
   // the mixed form indexes each field with 32 bits
   if (p->precision != LES_PREC_FP64 && N >= (1LL << 31)) return LES_ERR_SHAPE;
-  if (p->precision != LES_PREC_FP64 && p->sgs_model == LES_SGS_DYNAMIC) return LES_ERR_UNSUPPORTED;
   les_ctx* c = new (std::nothrow) les_ctx();
   if (!c) return LES_ERR_INVALID_ARG;
   c->p = *p;
@@ -499,10 +509,17 @@ int les_dynamic_coefficients(les_ctx* c, const double* Q, double out[9], les_str
     return fail(c, LES_ERR_UNSUPPORTED, "the context was not created with LES_SGS_DYNAMIC");
   cudaStream_t s = (cudaStream_t)stream;
   lesjet::Launch L{s, &c->launches};
-  lesjet::StageIO64 io = io64(c, Q);
-  lesjet::launch_node64(c->g, c->p, io, false, L);
-  lesjet::launch_dynamic64(c->g, c->p, io, io.dyn, L);
   DevScalars* sc = at<DevScalars>(c, c->off_sc);
+  if (is_mixed(c)) {
+    split_state(c, Q, L);
+    lesjet::launch_dynamic32(c->g, c->p, at<float>(c, c->off_hi), at<float>(c, c->off_m32),
+                             at<float>(c, c->off_node), at<float>(c, c->off_dyn),
+                             at<double>(c, c->off_part), sc, L);
+  } else {
+    lesjet::StageIO64 io = io64(c, Q);
+    lesjet::launch_node64(c->g, c->p, io, false, L);
+    lesjet::launch_dynamic64(c->g, c->p, io, io.dyn, L);
+  }
   cudaMemcpyAsync(out, sc->dyn, 9 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "les_dynamic_coefficients");
   return cuda_check(c, "les_dynamic_coefficients");

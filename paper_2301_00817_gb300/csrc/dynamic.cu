@@ -1,5 +1,7 @@
 // dynamic.cu -- the dynamic Smagorinsky procedure (Sec. "Dynamic Smagorinsky
-// Model", Eqs. yoshizawa, av_ci, av_cd, av_Pr_sgs) for the FP64 form.
+// Model", Eqs. yoshizawa, av_ci, av_cd, av_Pr_sgs), for the FP64 form and,
+// with FP32 node fields, products, filter and per-node terms (the sums
+// still in FP64, fixed order), for the mixed forms.
 //
 // Once per viscosity evaluation, from the node primitives of the state:
 //   k_dyn_products  per node: the 25 fields the test filter acts on (rho,
@@ -30,51 +32,54 @@ constexpr int kDynFields = 25;
 constexpr int kDynSums = 7;  // six weighted sums and the sum of the weights
 
 // Cartesian gradient of a node field through the node's metrics.
-__device__ __forceinline__ void grad_of(const Grid& g, const double* __restrict__ M,
-                                        const double* __restrict__ f, long long n, const int c[3],
-                                        double out[3]) {
+template <typename R, typename TM>
+__device__ __forceinline__ void grad_of(const Grid& g, const TM* __restrict__ M,
+                                        const R* __restrict__ f, long long n, const int c[3],
+                                        R out[3]) {
   const long long N = g.N;
-  double dd[3];
+  R dd[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) dd[d] = node_deriv(g, f, n, c, d);
 #pragma unroll
   for (int x = 0; x < 3; ++x)
-    out[x] = M[x * N + n] * dd[0] + M[(3 + x) * N + n] * dd[1] + M[(6 + x) * N + n] * dd[2];
+    out[x] = (R)M[x * N + n] * dd[0] + (R)M[(3 + x) * N + n] * dd[1] + (R)M[(6 + x) * N + n] * dd[2];
 }
 
 // S_ij from a velocity gradient gr[i][x] = d u_i/d x_x; returns |S|.
-__device__ __forceinline__ double strain(const double gr[3][3], double S[3][3]) {
-  double ss = 0.0;
+template <typename R>
+__device__ __forceinline__ R strain(const R gr[3][3], R S[3][3]) {
+  R ss = R(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      S[i][j] = 0.5 * (gr[i][j] + gr[j][i]);
+      S[i][j] = R(0.5) * (gr[i][j] + gr[j][i]);
       ss += S[i][j] * S[i][j];
     }
-  return sqrt(2.0 * ss);
+  return dev_sqrt(R(2) * ss);
 }
 
 __constant__ int kI6[6] = {0, 1, 2, 0, 0, 1};
 __constant__ int kJ6[6] = {0, 1, 2, 1, 2, 2};
 
-__global__ void __launch_bounds__(256) k_dyn_products(Grid g, const double* __restrict__ Q,
-                                                      const double* __restrict__ M,
-                                                      const double* __restrict__ node,
-                                                      double* __restrict__ D) {
+template <typename R, typename TQ, typename TM>
+__global__ void __launch_bounds__(256) k_dyn_products(Grid g, const TQ* __restrict__ Q,
+                                                      const TM* __restrict__ M,
+                                                      const R* __restrict__ node,
+                                                      R* __restrict__ D) {
   const long long N = g.N;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     int c[3];
     decompose(g, n, c);
-    const double rho = Q[n];
-    const double vel[3] = {node[n], node[N + n], node[2 * N + n]};
-    const double T = node[4 * N + n];
-    double gr[3][3], S[3][3], dT[3];
+    const R rho = (R)Q[n];
+    const R vel[3] = {node[n], node[N + n], node[2 * N + n]};
+    const R T = node[4 * N + n];
+    R gr[3][3], S[3][3], dT[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) grad_of(g, M, node + q * N, n, c, gr[q]);
     grad_of(g, M, node + 4 * N, n, c, dT);
-    const double Sm = strain(gr, S);
+    const R Sm = strain(gr, S);
     D[n] = rho;
 #pragma unroll
     for (int i = 0; i < 3; ++i) D[(1 + i) * N + n] = rho * vel[i];
@@ -98,9 +103,9 @@ __global__ void __launch_bounds__(256) k_dyn_products(Grid g, const double* __re
 // One pass of the test filter along direction D for `count` fields:
 // dst = (src_{-1} + 2 src_0 + src_{+1})/4 along D (periodic wrap), the
 // identity at the faces of a non-periodic D.
-template <int D>
-__global__ void __launch_bounds__(256) k_dyn_filter1(Grid g, const double* __restrict__ src,
-                                                     int count, double* __restrict__ dst) {
+template <int D, typename R>
+__global__ void __launch_bounds__(256) k_dyn_filter1(Grid g, const R* __restrict__ src,
+                                                     int count, R* __restrict__ dst) {
   const long long N = g.N;
   const long long s = g.stride[D];
   const int nd = g.n[D];
@@ -116,26 +121,30 @@ __global__ void __launch_bounds__(256) k_dyn_filter1(Grid g, const double* __res
     const long long np = (c[D] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
     const long long nm = (c[D] == 0) ? n + (long long)(nd - 1) * s : n - s;
     for (int q = 0; q < count; ++q)
-      dst[q * N + n] = 0.25 * src[q * N + nm] + 0.5 * src[q * N + n] + 0.25 * src[q * N + np];
+      dst[q * N + n] = R(0.25) * src[q * N + nm] + R(0.5) * src[q * N + n] + R(0.25) * src[q * N + np];
   }
 }
 
 // Favre-filtered velocity and temperature u^_i = (rho u_i)^/rho^,
 // T^ = (rho T)^/rho^ at every node, from the filtered fields F.
-__global__ void __launch_bounds__(256) k_dyn_favre(long long N, const double* __restrict__ F,
-                                                   double* __restrict__ H) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_dyn_favre(long long N, const R* __restrict__ F,
+                                                   R* __restrict__ H) {
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const double r = F[n];
+    const R r = F[n];
 #pragma unroll
     for (int q = 0; q < 4; ++q) H[q * N + n] = F[(1 + q) * N + n] / r;
   }
 }
 
-__global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const double* __restrict__ M,
-                                                  const double* __restrict__ node,
-                                                  const double* __restrict__ Fh,
-                                                  const double* __restrict__ H,
+// Per interior node the six terms (numerators and denominators of the
+// three coefficients), in R; their J^-1-weighted sums in FP64.
+template <typename R, typename TM>
+__global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const TM* __restrict__ M,
+                                                  const R* __restrict__ node,
+                                                  const R* __restrict__ Fh,
+                                                  const R* __restrict__ H,
                                                   double* __restrict__ partials) {
   const long long N = g.N;
   double acc[kDynSums] = {0, 0, 0, 0, 0, 0, 0};
@@ -144,10 +153,10 @@ __global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const double* __restri
     int c[3];
     decompose(g, n, c);
     if (!is_interior(g, c)) continue;
-    const double wgt = M[9 * N + n];
-    const double Delta = cbrt(M[9 * N + n]);
-    const double D2 = Delta * Delta, Dh2 = 4.0 * D2;
-    double gr[3][3], S[3][3], dT[3], grh[3][3], Sh[3][3], dTh[3];
+    const double wgt = (double)M[9 * N + n];
+    const R Delta = cbrt((R)M[9 * N + n]);
+    const R D2 = Delta * Delta, Dh2 = R(4) * D2;
+    R gr[3][3], S[3][3], dT[3], grh[3][3], Sh[3][3], dTh[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) grad_of(g, M, node + q * N, n, c, gr[q]);
     grad_of(g, M, node + 4 * N, n, c, dT);
@@ -155,23 +164,23 @@ __global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const double* __restri
 #pragma unroll
     for (int q = 0; q < 3; ++q) grad_of(g, M, H + q * N, n, c, grh[q]);
     grad_of(g, M, H + 3 * N, n, c, dTh);
-    const double Shm = strain(grh, Sh);
+    const R Shm = strain(grh, Sh);
     // the filtered fields at this node (Fh holds all 25)
-    double fh[kDynFields];
+    R fh[kDynFields];
 #pragma unroll
     for (int q = 5; q < kDynFields; ++q) fh[q] = Fh[q * N + n];
-    const double rh = Fh[n];
-    const double mh[3] = {Fh[N + n], Fh[2 * N + n], Fh[3 * N + n]};
-    double L[3][3], Fs[3][3];
+    const R rh = Fh[n];
+    const R mh[3] = {Fh[N + n], Fh[2 * N + n], Fh[3 * N + n]};
+    R L[3][3], Fs[3][3];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const int i = kI6[k], j = kJ6[k];
       L[i][j] = L[j][i] = fh[5 + k] - mh[i] * mh[j] / rh;
       Fs[i][j] = Fs[j][i] = fh[11 + k];
     }
-    const double trS = S[0][0] + S[1][1] + S[2][2];
-    const double trSh = Sh[0][0] + Sh[1][1] + Sh[2][2];
-    double LS = 0.0, FS = 0.0, ShS = 0.0;
+    const R trS = S[0][0] + S[1][1] + S[2][2];
+    const R trSh = Sh[0][0] + Sh[1][1] + Sh[2][2];
+    R LS = R(0), FS = R(0), ShS = R(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -180,24 +189,24 @@ __global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const double* __restri
         FS += Fs[i][j] * S[i][j];
         ShS += Sh[i][j] * S[i][j];
       }
-    const double Lkk = L[0][0] + L[1][1] + L[2][2];
-    const double numC = LS - Lkk * trS / 3.0;
-    const double denC = 2.0 * D2 * (FS - fh[17] * trS / 3.0) -
-                        2.0 * Dh2 * (rh * Shm * ShS - rh * Shm * trSh * trS / 3.0);
-    const double denI = 2.0 * Dh2 * rh * Shm * Shm - 2.0 * D2 * fh[18];
-    double numP = 0.0, denP = 0.0;
+    const R Lkk = L[0][0] + L[1][1] + L[2][2];
+    const R numC = LS - Lkk * trS / R(3);
+    const R denC = R(2) * D2 * (FS - fh[17] * trS / R(3)) -
+                   R(2) * Dh2 * (rh * Shm * ShS - rh * Shm * trSh * trS / R(3));
+    const R denI = R(2) * Dh2 * rh * Shm * Shm - R(2) * D2 * fh[18];
+    R numP = R(0), denP = R(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const double K = fh[19 + j] - mh[j] * Fh[4 * N + n] / rh;
+      const R K = fh[19 + j] - mh[j] * Fh[4 * N + n] / rh;
       numP += D2 * fh[22 + j] * dT[j] - Dh2 * rh * Shm * dTh[j] * dT[j];
       denP += K * dT[j];
     }
-    acc[0] += wgt * numC;
-    acc[1] += wgt * denC;
-    acc[2] += wgt * Lkk;
-    acc[3] += wgt * denI;
-    acc[4] += wgt * numP;
-    acc[5] += wgt * denP;
+    acc[0] += wgt * (double)numC;
+    acc[1] += wgt * (double)denC;
+    acc[2] += wgt * (double)Lkk;
+    acc[3] += wgt * (double)denI;
+    acc[4] += wgt * (double)numP;
+    acc[5] += wgt * (double)denP;
     acc[6] += wgt;
   }
   __shared__ double red[kDynSums][32];
@@ -247,19 +256,36 @@ __global__ void k_dyn_final(const double* __restrict__ partials, double pr_defau
 
 }  // namespace
 
+template <typename R, typename TQ, typename TM>
+static void dynamic_t(const Grid& g, const les_params& p, const TQ* Q, const TM* M, const R* node,
+                      R* scratch, double* partials, DevScalars* sc, const Launch& L) {
+  const int th = 256, nb = blocks_for(g.N, th);
+  R* D = scratch;                                 // products, then the eta pass
+  R* T = scratch + (long long)kDynFields * g.N;  // zeta pass, then the filtered fields
+  k_dyn_products<R, TQ, TM><<<nb, th, 0, L.s>>>(g, Q, M, node, D);
+  k_dyn_filter1<2, R><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
+  k_dyn_filter1<1, R><<<nb, th, 0, L.s>>>(g, T, kDynFields, D);
+  k_dyn_filter1<0, R><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
+  k_dyn_favre<R><<<nb, th, 0, L.s>>>(g.N, T, D);  // D is free again: u^, v^, w^, T^
+  k_dyn_sums<R, TM><<<kRedBlocks, kRedThreads, 0, L.s>>>(g, M, node, T, D, partials);
+  k_dyn_final<<<1, 32 * kDynSums, 0, L.s>>>(partials, p.Pr_sgs, sc);
+  *L.counter += 7;
+}
+
 void launch_dynamic64(const Grid& g, const les_params& p, const StageIO64& io, double* scratch,
                       const Launch& L) {
+  dynamic_t<double, double, double>(g, p, io.Qin, io.M, io.node, scratch, io.partials, io.sc, L);
+}
+
+void launch_dynamic32(const Grid& g, const les_params& p, const float* Q, const float* M,
+                      float* node, float* scratch, double* partials, DevScalars* sc,
+                      const Launch& L) {
+  // the FP32 node fields (u v w p T; the radii are not used) of the float state
   const int th = 256, nb = blocks_for(g.N, th);
-  double* D = scratch;                                 // products, then the eta pass
-  double* T = scratch + (long long)kDynFields * g.N;  // zeta pass, then the filtered fields
-  k_dyn_products<<<nb, th, 0, L.s>>>(g, io.Qin, io.M, io.node, D);
-  k_dyn_filter1<2><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
-  k_dyn_filter1<1><<<nb, th, 0, L.s>>>(g, T, kDynFields, D);
-  k_dyn_filter1<0><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
-  k_dyn_favre<<<nb, th, 0, L.s>>>(g.N, T, D);  // D is free again: u^, v^, w^, T^
-  k_dyn_sums<<<kRedBlocks, kRedThreads, 0, L.s>>>(g, io.M, io.node, T, D, io.partials);
-  k_dyn_final<<<1, 32 * kDynSums, 0, L.s>>>(io.partials, p.Pr_sgs, io.sc);
-  *L.counter += 7;
+  k_node<float, float, float, false><<<nb, th, 0, L.s>>>(g, make_consts<float>(p), Q, M, node,
+                                                        partials, sc);
+  ++*L.counter;
+  dynamic_t<float, float, float>(g, p, Q, M, node, scratch, partials, sc, L);
 }
 
 }  // namespace lesjet

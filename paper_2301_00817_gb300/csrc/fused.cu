@@ -58,13 +58,13 @@ __device__ __forceinline__ void cp_async_wait() {
 // q_mod with Fourier's sign) from compact interface gradients.
 // m*[0..8] = xi_x .. zeta_z, m*[9] = J^-1; W* = (rho, rho u, rho v, rho w,
 // e + p); dphi[q][t] = computational derivative of u, v, w, T along t.
-template <int D, typename R, bool AXIS>
+template <int D, typename R, bool AXIS, bool DYN>
 __device__ __forceinline__ void iface_flux(const Consts<R>& K, const R* Wm, const R* Wa,
                                            const R* Wb, const R* Wp, bool has_m, bool has_p,
                                            R nua, R nub, R lba, R lbb, const R* ma, const R* mb,
                                            R pa, R pb, R ua, R va, R wa, R ub, R vb, R wb,
                                            const R (&dphi)[4][3], R mua, R mub, R kaa, R kab,
-                                           R F[5]) {
+                                           R sga, R sgb, R F[5]) {
   const R tha = ma[3 * D] * ua + ma[3 * D + 1] * va + ma[3 * D + 2] * wa;
   const R thb = mb[3 * D] * ub + mb[3 * D + 1] * vb + mb[3 * D + 2] * wb;
   const R Ja = ma[9], Jb = mb[9];
@@ -131,6 +131,16 @@ __device__ __forceinline__ void iface_flux(const Consts<R>& K, const R* Wm, cons
   F[3] -= cf * sv[2];
   const R us = (ua + ub) * sv[0] + (va + vb) * sv[1] + (wa + wb) * sv[2];  // 8 u_f . m.tau / mu
   F[4] -= sJ * (smu * us * R(1.0 / 32.0) + skap * aT * R(1.0 / 16.0));
+  if (DYN) {
+    // the modelled isotropic SGS stress sigma_ll/3 (Eq. yoshizawa) at the
+    // interface mean, subtracted from the normal stresses: m.tau_i gains
+    // -m_i sigma/3 and u_f.(m.tau) gains -(u_f . m) sigma/3
+    const R e1 = sJ * (sga + sgb) * R(1.0 / 24.0);
+    F[1] += e1 * mx;
+    F[2] += e1 * my;
+    F[3] += e1 * mz;
+    F[4] += e1 * R(0.5) * ((ua + ub) * mx + (va + vb) * my + (wa + wb) * mz);
+  }
 }
 
 // Pressure sensor from the three pressures around a (possibly shifted) node.
@@ -183,7 +193,8 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
                                                  const TM* __restrict__ M, R* __restrict__ mk,
                                                  double* __restrict__ partials,
                                                  DevScalars* __restrict__ sc,
-                                                 R* __restrict__ dtl, R cfl) {
+                                                 R* __restrict__ dtl, R cfl,
+                                                 const double* __restrict__ dyn = nullptr) {
   const long long N = g.N;
   R local_min = R(1e30);
   int bad = 0;
@@ -228,7 +239,8 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
     if (dtl) dtl[n] = cfl * inv;  // local step of Eq. localdt
 
     const R mu_l = K.mu_scale * T * dev_sqrt(T) * (R(1) + K.S_suth) / (T + K.S_suth);
-    R mu_s = R(0);
+    R mu_s = R(0), kap_s = R(0);
+    bool kap_set = false;
     if (K.sgs != LES_SGS_NONE) {
       int c[3];
       decompose(g, n, c);
@@ -278,7 +290,7 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
 #pragma unroll
         for (int x = 0; x < 3; ++x) gr[q][x] = m[x] * dd[q][0] + m[3 + x] * dd[q][1] + m[6 + x] * dd[q][2];
       const R delta = cbrt(m[9]);
-      if (K.sgs == LES_SGS_SMAGORINSKY) {
+      if (K.sgs == LES_SGS_SMAGORINSKY || K.sgs == LES_SGS_DYNAMIC) {
         R ss = R(0);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -287,7 +299,19 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
             const R sij = R(0.5) * (gr[i][j] + gr[j][i]);
             ss += sij * sij;
           }
-        mu_s = rho * (delta * delta) * K.cs2 * dev_sqrt(R(2) * ss);
+        const R smag = dev_sqrt(R(2) * ss);
+        if (K.sgs == LES_SGS_SMAGORINSKY) {
+          mu_s = rho * (delta * delta) * K.cs2 * smag;
+        } else {
+          // dynamic model (coefficients dyn[6..8] from the procedure):
+          // mu_sgs = C_ds rho Delta^2 |S|, kappa_sgs with the dynamic Pr_sgs,
+          // and the Yoshizawa sigma_ll = 2 C_I rho Delta^2 |S|^2
+          const R d2 = delta * delta;
+          mu_s = (R)dyn[6] * rho * d2 * smag;
+          kap_s = mu_s / (K.gm1 * (R)dyn[8]);
+          kap_set = true;
+          mk[2 * N + n] = R(2) * (R)dyn[7] * rho * d2 * smag * smag;
+        }
       } else {
         R aa = R(0);
 #pragma unroll
@@ -307,7 +331,7 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
       }
     }
     mk[n] = mu_l + mu_s;
-    mk[N + n] = mu_l * K.inv_gm1_pr + mu_s * K.inv_gm1_prs;
+    mk[N + n] = mu_l * K.inv_gm1_pr + (kap_set ? kap_s : mu_s * K.inv_gm1_prs);
   }
   __shared__ R smin[32];
   __shared__ int sbad[32];
@@ -368,6 +392,17 @@ constexpr int OFF_PR = 3 * 5 * PL2, OFF_PW = OFF_PR + 3 * 4 * PL2,
               OFF_M = OFF_PW + 3 * 2 * PL2, OFF_K = OFF_M + 3 * 10 * PL1,
               OFF_L = OFF_K + 3 * 2 * PL1, OFF_FE = OFF_L + 2 * 3 * PL1,
               OFF_FZ = OFF_FE + 5 * (FTJ + 1) * FTK, SMEM_FLOATS = OFF_FZ + 5 * FTJ;
+// With the dynamic SGS model the viscosity slots hold a third field, the
+// Yoshizawa sigma_ll (sK[3][3][PL1]); the regions after sK move up.
+template <bool DYN>
+struct FLayout {
+  static constexpr int NKF = DYN ? 3 : 2;  // fields per viscosity slot
+  static constexpr int L = OFF_K + 3 * NKF * PL1;
+  static constexpr int FE = L + 2 * 3 * PL1;
+  static constexpr int FZ = FE + 5 * (FTJ + 1) * FTK;
+  static constexpr int FLOATS = FZ + 5 * FTJ;
+};
+static_assert(FLayout<true>::FLOATS * 4 <= 227 * 1024, "shared memory plan exceeds 227 KB");
 
 // Computational derivatives of (u, v, w, T) at an interface from node
 // records (float4 u, v, w, T): along the interface normal, phi_b - phi_a;
@@ -401,7 +436,7 @@ struct FusedPtrs {
   float* lo[5];         // Q^(0) lo part (last stage)
   float* hiw[5];        // Q^(0) hi part, written in the last stage
   const float* m[10];   // metrics
-  const float* mk[2];   // mu_eff, kappa_eff
+  const float* mk[3];   // mu_eff, kappa_eff (and sigma_ll with the dynamic model)
   float* out[5];        // stage output
   double* outd[5];      // residual output (RHS mode)
   const float* dtl;     // local steps (dt_mode LOCAL) or nullptr: global dt
@@ -432,7 +467,7 @@ __device__ __forceinline__ int wrap_fast(int v, int n, int per) {
 // LOCAL: node n advances with its own step P.dtl[n] (dt_mode LOCAL) in
 // place of the global one; a separate instantiation keeps the global-step
 // kernel free of the per-node load and its branch.
-template <int MODE, bool LOCAL, bool AXIS>
+template <int MODE, bool LOCAL, bool AXIS, bool DYN>
 __global__ void __launch_bounds__(FNT, 1)
     k_stage_fused(const FusedGeom G, const Consts<float> K, const FusedPtrs P,
                   const DevScalars* __restrict__ sc, double alpha) {
@@ -442,9 +477,10 @@ __global__ void __launch_bounds__(FNT, 1)
   float2* sPw = reinterpret_cast<float2*>(smem + OFF_PW);
   float* sM = smem + OFF_M;
   float* sK = smem + OFF_K;
-  float* sL = smem + OFF_L;
-  float* sFe = smem + OFF_FE;
-  float* sFz = smem + OFF_FZ;
+  constexpr int NKF = FLayout<DYN>::NKF;
+  float* sL = smem + FLayout<DYN>::L;
+  float* sFe = smem + FLayout<DYN>::FE;
+  float* sFz = smem + FLayout<DYN>::FZ;
   const int ni = G.ni, nj = G.nj, nk = G.nk;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   // kt: first column of the unshifted tile; k0: global column of tile
@@ -465,7 +501,7 @@ __global__ void __launch_bounds__(FNT, 1)
   // ---- stage plane x (state: 2-node halo; metrics, mu/kappa: 1-node halo)
   auto stage_plane = [&](int slot, int x) {
     const int ig = wrap_fast(x, ni, G.per[0]);
-    constexpr int JQ = 5 * R2, JM = 10 * R1, JK = 2 * R1;
+    constexpr int JQ = 5 * R2, JM = 10 * R1, JK = NKF * R1;
     // one row per thread, taken by the highest-numbered threads: the lowest
     // ones derive a second node record in the same phase
     const int tid = threadIdx.x - (FNT - (JQ + JM + JK));
@@ -492,7 +528,7 @@ __global__ void __launch_bounds__(FNT, 1)
       const int u = tid - JQ - JM, f = u / R1;
       jj = u - f * R1 - 1;
       src = P.mk[f];
-      dst = sK + (slot * 2 + f) * PL1 + (jj + 1) * SK;
+      dst = sK + (slot * NKF + f) * PL1 + (jj + 1) * SK;
       halo = 1;
       benign = 0.f;
     }
@@ -645,13 +681,14 @@ __global__ void __launch_bounds__(FNT, 1)
       ma[t] = mown ? mown[t] : sM[(m0 * 10 + t) * PL1 + o1];
       mb[t] = sM[(m1 * 10 + t) * PL1 + o1];
     }
-    const float* Ka = sK + m0 * 2 * PL1;
-    const float* Kb = sK + m1 * 2 * PL1;
-    iface_flux<0, float, AXIS>(K, Wq[0], Wq[1], Wq[2], Wq[3], vq[0], vq[3], nua, nub,
+    const float* Ka = sK + m0 * NKF * PL1;
+    const float* Kb = sK + m1 * NKF * PL1;
+    iface_flux<0, float, AXIS, DYN>(K, Wq[0], Wq[1], Wq[2], Wq[3], vq[0], vq[3], nua, nub,
                          sL[l0 * 3 * PL1 + o1], sL[l1 * 3 * PL1 + o1], ma, mb,
                          wown ? wown->x : sPw[p0 * PL2 + o2].x,
                          sPw[p1 * PL2 + o2].x, a0.x, a0.y, a0.z, b0.x, b0.y, b0.z, dphi, Ka[o1],
-                         Kb[o1], Ka[PL1 + o1], Kb[PL1 + o1], F);
+                         Kb[o1], Ka[PL1 + o1], Kb[PL1 + o1], DYN ? Ka[2 * PL1 + o1] : 0.f,
+                         DYN ? Kb[2 * PL1 + o1] : 0.f, F);
   };
 
   // eta interface between tile rows ra and ra+1 (ra in [-1, FTJ-1]), own
@@ -702,11 +739,12 @@ __global__ void __launch_bounds__(FNT, 1)
       ma[t] = mown ? mown[t] : sM[(ms * 10 + t) * PL1 + a1];
       mb[t] = sM[(ms * 10 + t) * PL1 + b1];
     }
-    const float* Kc = sK + ms * 2 * PL1;
+    const float* Kc = sK + ms * NKF * PL1;
     const float* L = sL + ls * 3 * PL1 + PL1;
-    iface_flux<1, float, AXIS>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
+    iface_flux<1, float, AXIS, DYN>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
                          wb.x, ca.x, ca.y, ca.z, cb.x, cb.y, cb.z, dphi, Kc[a1], Kc[b1],
-                         Kc[PL1 + a1], Kc[PL1 + b1], F);
+                         Kc[PL1 + a1], Kc[PL1 + b1], DYN ? Kc[2 * PL1 + a1] : 0.f,
+                         DYN ? Kc[2 * PL1 + b1] : 0.f, F);
   };
 
   // zeta interface between tile columns ca and ca+1 (ca in [-1, FTK-1]) in
@@ -759,11 +797,12 @@ __global__ void __launch_bounds__(FNT, 1)
       ma[t] = mown ? mown[t] : sM[(ms * 10 + t) * PL1 + a1];
       mb[t] = sM[(ms * 10 + t) * PL1 + b1];
     }
-    const float* Kc = sK + ms * 2 * PL1;
+    const float* Kc = sK + ms * NKF * PL1;
     const float* L = sL + ls * 3 * PL1 + 2 * PL1;
-    iface_flux<2, float, AXIS>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
+    iface_flux<2, float, AXIS, DYN>(K, Wm, Wa, Wb, Wp, has_m, has_p, nua, nub, L[a1], L[b1], ma, mb, wa.x,
                          wb.x, pa.x, pa.y, pa.z, pb.x, pb.y, pb.z, dphi, Kc[a1], Kc[b1],
-                         Kc[PL1 + a1], Kc[PL1 + b1], F);
+                         Kc[PL1 + a1], Kc[PL1 + b1], DYN ? Kc[2 * PL1 + a1] : 0.f,
+                         DYN ? Kc[2 * PL1 + b1] : 0.f, F);
   };
 
   auto m3 = [](int x) { return ((x % 3) + 3) % 3; };
@@ -1018,10 +1057,11 @@ static Consts<R> fused_consts(const les_params& p) {
 }
 
 void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
-                    float* mk, double* partials, DevScalars* sc, float* dtl, const Launch& L) {
+                    float* mk, double* partials, DevScalars* sc, float* dtl, const double* dyn,
+                    const Launch& L) {
   const Consts<float> K = fused_consts<float>(p);
   k_prestep<float, float, float><<<kRedBlocks, kRedThreads, 0, L.s>>>(
-      g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl);
+      g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl, dyn);
   ++*L.counter;
   if (p.axis) {
     k_mu_axis<float, TempFromState<float, float>><<<g.n[0], 128, g.n[2] * sizeof(float), L.s>>>(
@@ -1071,11 +1111,11 @@ static int choose_nch(int ni, int tiles, int slots) {
   return best;
 }
 
-template <int MODE, bool LOCAL, bool AXIS>
+template <int MODE, bool LOCAL, bool AXIS, bool DYN>
 static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const FusedPtrs& P,
                            const DevScalars* sc, double alpha, const Launch& L) {
   FusedGeom G = G0;
-  const size_t smem = (size_t)SMEM_FLOATS * sizeof(float);
+  const size_t smem = (size_t)FLayout<DYN>::FLOATS * sizeof(float);
   // the shared-memory opt-in is a per-device function attribute: set it once
   // for each device this process launches on
   static std::atomic<unsigned long long> attr_set{0};
@@ -1083,31 +1123,31 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-    cudaFuncSetAttribute(k_stage_fused<MODE, LOCAL, AXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_stage_fused<MODE, LOCAL, AXIS, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
   G.nch = choose_nch(G.ni, tk * tj, sm_count());  // one CTA per SM
   dim3 grid(tk, tj, G.nch);
-  k_stage_fused<MODE, LOCAL, AXIS><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
+  k_stage_fused<MODE, LOCAL, AXIS, DYN><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
   ++*L.counter;
 }
 
-template <bool AXIS>
+template <bool AXIS, bool DYN>
 static void launch_stage_dispatch(int mode, bool local, const FusedGeom& G, const Consts<float>& K,
                                   const FusedPtrs& P, const DevScalars* sc, double alpha,
                                   const Launch& L) {
   if (mode == FMODE_RHS)
-    launch_stage_t<FMODE_RHS, false, AXIS>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_RHS, false, AXIS, DYN>(G, K, P, sc, alpha, L);
   else if (mode == FMODE_STAGE && !local)
-    launch_stage_t<FMODE_STAGE, false, AXIS>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_STAGE, false, AXIS, DYN>(G, K, P, sc, alpha, L);
   else if (mode == FMODE_STAGE)
-    launch_stage_t<FMODE_STAGE, true, AXIS>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_STAGE, true, AXIS, DYN>(G, K, P, sc, alpha, L);
   else if (!local)
-    launch_stage_t<FMODE_LAST, false, AXIS>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_LAST, false, AXIS, DYN>(G, K, P, sc, alpha, L);
   else
-    launch_stage_t<FMODE_LAST, true, AXIS>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_LAST, true, AXIS, DYN>(G, K, P, sc, alpha, L);
 }
 
 void launch_stage_fused(int mode, const Grid& g, const les_params& p, const FusedIO& io,
@@ -1133,14 +1173,17 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
     P.outd[c] = (mode == FMODE_RHS) ? (double*)io.out + c * N : nullptr;
   }
   for (int t = 0; t < 10; ++t) P.m[t] = (const float*)io.M + t * N;
-  for (int t = 0; t < 2; ++t) P.mk[t] = (const float*)io.mk + t * N;
+  const bool dyn = p.sgs_model == LES_SGS_DYNAMIC;
+  for (int t = 0; t < 3; ++t) P.mk[t] = (t < 2 || dyn) ? (const float*)io.mk + t * N : nullptr;
   P.dtl = io.dtl;
   const Consts<float> K = fused_consts<float>(p);
   const bool local = P.dtl != nullptr;
-  if (p.axis)
-    launch_stage_dispatch<true>(mode, local, G, K, P, io.sc, alpha, L);
+  if (dyn)  // (not with an axis: rejected at creation)
+    launch_stage_dispatch<false, true>(mode, local, G, K, P, io.sc, alpha, L);
+  else if (p.axis)
+    launch_stage_dispatch<true, false>(mode, local, G, K, P, io.sc, alpha, L);
   else
-    launch_stage_dispatch<false>(mode, local, G, K, P, io.sc, alpha, L);
+    launch_stage_dispatch<false, false>(mode, local, G, K, P, io.sc, alpha, L);
 }
 
 void launch_split(long long count, const double* q, float* hi, float* lo, const Launch& L) {

@@ -53,6 +53,12 @@ void launch_mu64(const Grid& g, const les_params& p, const StageIO64& io, const 
 // into io.sc->dyn; io.partials holds 7 x kRedBlocks block sums
 void launch_dynamic64(const Grid& g, const les_params& p, const StageIO64& io, double* scratch,
                       const Launch& L);
+// the mixed forms' procedure on the float state: FP32 node fields into node
+// [8][N], the procedure's fields in FP32 (scratch [50][N]), its sums in
+// FP64; coefficients into sc->dyn
+void launch_dynamic32(const Grid& g, const les_params& p, const float* Q, const float* M,
+                      float* node, float* scratch, double* partials, DevScalars* sc,
+                      const Launch& L);
 void launch_flux64(const Grid& g, const les_params& p, const StageIO64& io, int dir,
                    const Launch& L);
 // the three pressure sensors of every node into io.nu (after launch_node64)
@@ -73,8 +79,11 @@ struct FusedIO {
   void* out;            // RHS mode: double [5][N]; stage mode: stage type [5][N]
 };
 // mixed form: mu_eff/kappa_eff and CFL block minima of the float state
+// dyn: the dynamic procedure's coefficients (device) with LES_SGS_DYNAMIC,
+// else nullptr
 void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
-                    float* mk, double* partials, DevScalars* sc, float* dtl, const Launch& L);
+                    float* mk, double* partials, DevScalars* sc, float* dtl, const double* dyn,
+                    const Launch& L);
 // mode 0: residual into io.out (double); 1: stage update into io.out;
 // 2: last stage, Q^(0) (hi, lo) updated in place with compensated sums
 void launch_stage_fused(int mode, const Grid& g, const les_params& p, const FusedIO& io,

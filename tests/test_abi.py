@@ -173,13 +173,23 @@ def test_local_time_steps_are_chosen_at_creation(lib):
     assert base > 0
 
 
-def test_dynamic_model_is_chosen_at_creation_in_fp64(lib):
-    """The dynamic SGS model needs its scratch in the workspace: FP64 only,
-    chosen at creation (about 408 more bytes per point)."""
+def test_dynamic_model_is_chosen_at_creation(lib):
+    """The dynamic SGS model needs its scratch in the workspace, chosen at
+    creation: about 408 more bytes per point in FP64; in the mixed forms 236
+    (50 FP32 procedure fields, 8 FP32 node fields, the third viscosity
+    field)."""
     import paper_2301_00817_gb300 as lj
-    h = C.c_void_p()
-    p = lj.make_params(sgs_model=lj.SGS_DYNAMIC, precision=lj.PREC_MIXED)
-    assert lib.les_create(C.byref(p), 16, 12, 8, C.byref(h)) == lj.LES_ERR_UNSUPPORTED
+    for prec in (lj.PREC_MIXED, lj.PREC_MIXED_COMPACT):
+        h0, h1 = C.c_void_p(), C.c_void_p()
+        a = lj.make_params(sgs_model=lj.SGS_SMAGORINSKY, precision=prec)
+        b = lj.make_params(sgs_model=lj.SGS_DYNAMIC, precision=prec)
+        assert lib.les_create(C.byref(a), 16, 12, 8, C.byref(h0)) == lj.LES_OK
+        assert lib.les_create(C.byref(b), 16, 12, 8, C.byref(h1)) == lj.LES_OK
+        N = 16 * 12 * 8
+        grow = lib.les_workspace_bytes(h1) - lib.les_workspace_bytes(h0)
+        assert 236 * N <= grow <= 236 * N + 1024, grow / N
+        lib.les_destroy(h0)
+        lib.les_destroy(h1)
     h0, h1 = C.c_void_p(), C.c_void_p()
     a, b = lj.make_params(sgs_model=lj.SGS_SMAGORINSKY), lj.make_params(sgs_model=lj.SGS_DYNAMIC)
     assert lib.les_create(C.byref(a), 16, 12, 8, C.byref(h0)) == lj.LES_OK

@@ -261,6 +261,39 @@ def test_dynamic_model_steps(orc, lj, torch):
     assert np.abs(np.array(d.totals) - tot0).max() / scale <= 1e-13
 
 
+@pytest.mark.parametrize("prec", ["mixed", "compact"])
+def test_dynamic_model_mixed_forms(orc, lj, torch, prec):
+    """The dynamic model in the FP32-mixed forms: the procedure's products,
+    filter and per-node terms in FP32 with FP64 fixed-order sums, the
+    Yoshizawa term in the fused stage kernel.  The coefficients within 1e-4
+    (relative) of the oracle's, the residual within 2e-5 of the flux scale,
+    and 20 steps within 1e-5 (relative L2) of the FP64 oracle's run."""
+    pc = lj.PREC_MIXED if prec == "mixed" else lj.PREC_MIXED_COMPACT
+    shape, xyz, shift, kw, Q0 = _dyn_case(orc, lj, "jet_c1")
+    ctx, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=lj.SGS_DYNAMIC, precision=pc, **kw)
+    P = oracle_params(orc, sgs_model=3, **kw)
+    M = orc.metrics(xyz, kw["periodic"], shift)
+    Qd = torch.from_numpy(Q0).cuda()
+    got = ctx.les_dynamic_coefficients(Qd)
+    want = orc.dynamic_coefficients(P, Q0, M)
+    assert want["CI"] > 0
+    for k in ("Cd", "CI", "Prt"):
+        assert abs(got[k] - want[k]) <= 1e-4 * abs(want[k]) + 1e-12, (k, got[k], want[k])
+    R = torch.empty_like(Qd)
+    ctx.les_rhs(Qd, R)
+    Ro = orc.rhs(P, Q0, M)
+    Rg = R.cpu().numpy()
+    fscale = (np.abs(M[9]) * np.sqrt(M[0] ** 2 + M[1] ** 2 + M[2] ** 2)).max()
+    for c in range(5):
+        qs = np.abs(Q0[c]).max() + (np.abs(Q0[4]).max() if c in (1, 2, 3, 4) else 0.0)
+        assert np.abs(Rg[c] - Ro[c]).max() <= 2e-5 * fscale * qs, c
+    d = ctx.les_run_n_steps(20, Qd)
+    Qo, to = orc.run(P, Q0, M, xyz, 20)
+    assert d.status == 0
+    assert rel_l2(Qd.cpu().numpy(), Qo) <= 1e-5
+    assert abs(d.t - to) <= 1e-5 * to
+
+
 def test_init_jet(orc, lj, torch):
     shape = C1
     xyz = lj.synth.jet_grid(*shape)
