@@ -475,15 +475,16 @@ def large_leg(lj, torch, local, hbm_peak, warmup):
 
 def extensions_leg(lj, torch, local, xyz, shape, base_ms, steps=10, warmup=2):
     """Cost of the options beyond the configured workload, on the same grid:
-    the dynamic SGS model (FP64), local time steps and the characteristic
-    entrance (mixed), and the conservative metric setup."""
+    the dynamic SGS model (FP64 and mixed), local time steps and the
+    characteristic entrance (mixed), and the conservative metric setup."""
     stream = torch.cuda.current_stream()
     out = {"steps": steps}
     cases = (("fp64_dynamic", dict(precision=lj.PREC_FP64, sgs_model=lj.SGS_DYNAMIC)),
              ("mixed_local_dt", dict(precision=lj.PREC_MIXED, sgs_model=lj.SGS_SMAGORINSKY,
                                      dt_mode=lj.DT_LOCAL)),
              ("mixed_char_bc", dict(precision=lj.PREC_MIXED, sgs_model=lj.SGS_SMAGORINSKY,
-                                    bc=lj.BC_JET_CHAR)))
+                                    bc=lj.BC_JET_CHAR)),
+             ("mixed_dynamic", dict(precision=lj.PREC_MIXED, sgs_model=lj.SGS_DYNAMIC)))
     for name, kw in cases:
         ctx = lj.Context(lj.make_params(**kw), shape, f"cuda:{local}")
         ctx.les_set_grid(xyz)
@@ -498,7 +499,7 @@ def extensions_leg(lj, torch, local, xyz, shape, base_ms, steps=10, warmup=2):
                "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]}}
         ref = base_ms["fp64" if kw["precision"] == lj.PREC_FP64 else "mixed"]
         rec["vs_configured_step"] = rec["ms_per_step"] / ref
-        if name == "fp64_dynamic":
+        if name in ("fp64_dynamic", "mixed_dynamic"):
             co = ctx.les_dynamic_coefficients(Q)
             rec["coefficients"] = {k: co[k] for k in ("Cd", "CI", "Prt")}
         out[name] = rec
