@@ -316,10 +316,12 @@ const char *les_profile_name(int kind);
  * sgs_model LES_SGS_NONE, freeze_visc 1; LES_ERR_UNSUPPORTED otherwise.
  * Scratch lives in a caller-owned adjoint workspace of
  * les_adjoint_workspace_bytes(ctx, nsteps, ckpt_every) bytes: about
- * (165 + 5 ceil(nsteps/ckpt_every) + 72 ckpt_every) N doubles for a window
+ * (300 + 5 ceil(nsteps/ckpt_every) + 72 ckpt_every) N doubles for a window
  * (checkpoints, plus every stage state and stage-input node quantity of one
- * segment), 165 N for
- * nsteps = 0 (residual and single-step calls only).  At non-smooth
+ * segment), 300 N for nsteps = 0 (residual and single-step calls only); 135
+ * N of it hold each interface's cotangent record, which a per-node gather
+ * sums in a fixed order, so every adjoint result is bitwise reproducible
+ * (no atomics).  At non-smooth
  * points the derivative follows the forward branch: |x| has slope -1 for
  * x < 0 and +1 otherwise; a max passes to the operand it selected.
  * ------------------------------------------------------------------------ */

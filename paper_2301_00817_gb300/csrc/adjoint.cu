@@ -7,10 +7,13 @@
 // k_adj_iface<D> recomputes the forward intermediates of the interface flux
 // (centred inviscid flux, Turkel-Vatsa dissipation, compact viscous flux) and
 // runs them in reverse, accumulating cotangents of the node quantities it
-// read (conserved state, p, u, v, w, T, sensors, lbar, mu, kappa) into
-// per-node accumulators.  k_adj_sensor moves sensor cotangents to the
-// pressures they were computed from, and k_adj_node reverses the node
-// quantities (radii, primitive recovery) into cotangents of Q.
+// read (conserved state, p, u, v, w, T, sensors, lbar, mu, kappa) into a
+// record of that interface (what it owes each node it read); k_adj_gather
+// then sums, per node and in a fixed order, the records of the interfaces
+// that read it, so the accumulation is bitwise reproducible (no atomics).
+// k_adj_sensor_terms / k_adj_sensor_gather move sensor cotangents to the
+// pressures they were computed from the same way, and k_adj_node reverses
+// the node quantities (radii, primitive recovery) into cotangents of Q.
 //
 // Non-differentiable points follow the forward kernels' branch choices:
 // |x| has derivative -1 for x < 0 and +1 otherwise, max(a, b) passes the
@@ -44,9 +47,25 @@ enum {
   NACC = 18
 };
 
-__device__ __forceinline__ void acc_add(double* A, long long N, int slot, long long n, double v) {
-  if (v != 0.0) atomicAdd(A + (long long)slot * N + n, v);
-}
+// Per-interface record (each [N] doubles, indexed by the interface's node a,
+// one record array per direction): the cotangents it owes each node it read.
+enum {
+  RQA = 0,    // conserved state at a (5), then at b, a-1, b+1 (5 each)
+  RQB = 5,
+  RQM = 10,
+  RQP = 15,
+  RPA = 20,   // pressure at a, b, a-1, b+1
+  RUA = 24,   // u, v, w, T at a (4), then at b
+  RUB = 28,
+  RG1 = 32,   // tangential derivative cotangents g1 (T1) and g2 (T2): +g at
+  RG2 = 36,   //   a+t and b+t, -g at a-t and b-t, per component (4 each)
+  RNUA = 40,  // sensor of direction D at a, at b
+  RNUB = 41,
+  RLB = 42,   // half the lbar cotangent (a and b each)
+  RMU = 43,   // half the mu_eff and kappa_eff cotangents (a and b each)
+  RKA = 44,
+  NREC = 45
+};
 
 // face-shifted centre triple of the pressure sensor of node x along D
 template <int D>
@@ -79,7 +98,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_iface(Grid g, Consts<double> K,
                                                    const double* __restrict__ node,
                                                    const double* __restrict__ mk,
                                                    const double* __restrict__ lamR,
-                                                   double* __restrict__ A) {
+                                                   double* __restrict__ Rec) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const long long N = g.N;
   const double* U = node;
@@ -92,9 +111,17 @@ __global__ void __launch_bounds__(256, 2) k_adj_iface(Grid g, Consts<double> K,
        n += (long long)gridDim.x * blockDim.x) {
     int c[3];
     decompose(g, n, c);
-    if (!g.per[D] && c[D] == g.n[D] - 1) continue;
-    if (!g.per[T1] && (c[T1] == 0 || c[T1] == g.n[T1] - 1)) continue;
-    if (!g.per[T2] && (c[T2] == 0 || c[T2] == g.n[T2] - 1)) continue;
+    // no interface here, or no cotangent on it: an empty record
+    auto empty = [&]() {
+#pragma unroll 1
+      for (int r = 0; r < NREC; ++r) Rec[(long long)r * N + n] = 0.0;
+    };
+    if ((!g.per[D] && c[D] == g.n[D] - 1) ||
+        (!g.per[T1] && (c[T1] == 0 || c[T1] == g.n[T1] - 1)) ||
+        (!g.per[T2] && (c[T2] == 0 || c[T2] == g.n[T2] - 1))) {
+      empty();
+      continue;
+    }
     const long long a = n;
     const long long b = step(g, n, c, D, 1);
     int cb[3] = {c[0], c[1], c[2]};
@@ -109,7 +136,10 @@ __global__ void __launch_bounds__(256, 2) k_adj_iface(Grid g, Consts<double> K,
       lF[q] = (a_in ? lamR[q * N + a] : 0.0) - (b_in ? lamR[q * N + b] : 0.0);
       any = any || lF[q] != 0.0;
     }
-    if (!any) continue;
+    if (!any) {
+      empty();
+      continue;
+    }
     const long long am = step(g, n, c, D, -1);
     const long long bp = step(g, n, c, D, 2);
 
@@ -280,53 +310,123 @@ __global__ void __launch_bounds__(256, 2) k_adj_iface(Grid g, Consts<double> K,
     const double lthb = Jb * (Qb[0] * hFa[0] + Qb[1] * hFa[1] + Qb[2] * hFa[2] + Qb[3] * hFa[3] +
                               (Qb[4] + pb) * hFa[4]);
 
-    // ---- scatter: conserved state and pressure (W4 = Q4 + p)
+    // ---- the record: conserved state and pressure (W4 = Q4 + p)
+    auto put = [&](int r, double v) { Rec[(long long)r * N + n] = v; };
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      acc_add(A, N, AQ0 + q, a, lQa[q] + lWa[q]);
-      acc_add(A, N, AQ0 + q, b, lQb[q] + lWb[q]);
-      if (am >= 0) acc_add(A, N, AQ0 + q, am, lWm[q]);
-      if (bp >= 0) acc_add(A, N, AQ0 + q, bp, lWp[q]);
+      put(RQA + q, lQa[q] + lWa[q]);
+      put(RQB + q, lQb[q] + lWb[q]);
+      put(RQM + q, am >= 0 ? lWm[q] : 0.0);
+      put(RQP + q, bp >= 0 ? lWp[q] : 0.0);
     }
-    acc_add(A, N, AP, a, lpa_f + lWa[4]);
-    acc_add(A, N, AP, b, lpb_f + lWb[4]);
-    if (am >= 0) acc_add(A, N, AP, am, lWm[4]);
-    if (bp >= 0) acc_add(A, N, AP, bp, lWp[4]);
+    put(RPA, lpa_f + lWa[4]);
+    put(RPA + 1, lpb_f + lWb[4]);
+    put(RPA + 2, am >= 0 ? lWm[4] : 0.0);
+    put(RPA + 3, bp >= 0 ? lWp[4] : 0.0);
     // velocities: contravariant velocity and interface mean
-    acc_add(A, N, AU + 0, a, ma0 * ltha + 0.5 * luf - ldphi[0][D]);
-    acc_add(A, N, AU + 1, a, ma1 * ltha + 0.5 * lvf - ldphi[1][D]);
-    acc_add(A, N, AU + 2, a, ma2 * ltha + 0.5 * lwf - ldphi[2][D]);
-    acc_add(A, N, AU + 3, a, -ldphi[3][D]);
-    acc_add(A, N, AU + 0, b, mb0 * lthb + 0.5 * luf + ldphi[0][D]);
-    acc_add(A, N, AU + 1, b, mb1 * lthb + 0.5 * lvf + ldphi[1][D]);
-    acc_add(A, N, AU + 2, b, mb2 * lthb + 0.5 * lwf + ldphi[2][D]);
-    acc_add(A, N, AU + 3, b, ldphi[3][D]);
+    put(RUA + 0, ma0 * ltha + 0.5 * luf - ldphi[0][D]);
+    put(RUA + 1, ma1 * ltha + 0.5 * lvf - ldphi[1][D]);
+    put(RUA + 2, ma2 * ltha + 0.5 * lwf - ldphi[2][D]);
+    put(RUA + 3, -ldphi[3][D]);
+    put(RUB + 0, mb0 * lthb + 0.5 * luf + ldphi[0][D]);
+    put(RUB + 1, mb1 * lthb + 0.5 * lvf + ldphi[1][D]);
+    put(RUB + 2, mb2 * lthb + 0.5 * lwf + ldphi[2][D]);
+    put(RUB + 3, ldphi[3][D]);
     // tangential derivatives: 1/4 (phi(a+t) - phi(a-t) + phi(b+t) - phi(b-t))
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const double g1 = 0.25 * ldphi[q][T1], g2 = 0.25 * ldphi[q][T2];
-      acc_add(A, N, AU + q, tn[0][0], g1);
-      acc_add(A, N, AU + q, tn[0][1], -g1);
-      acc_add(A, N, AU + q, tn[0][2], g1);
-      acc_add(A, N, AU + q, tn[0][3], -g1);
-      acc_add(A, N, AU + q, tn[1][0], g2);
-      acc_add(A, N, AU + q, tn[1][1], -g2);
-      acc_add(A, N, AU + q, tn[1][2], g2);
-      acc_add(A, N, AU + q, tn[1][3], -g2);
+      put(RG1 + q, 0.25 * ldphi[q][T1]);
+      put(RG2 + q, 0.25 * ldphi[q][T2]);
     }
     // sensor, spectral radius, viscosity
-    acc_add(A, N, ANU + D, pick_b ? b : a, lnu);
-    acc_add(A, N, ALB + D, a, 0.5 * llam);
-    acc_add(A, N, ALB + D, b, 0.5 * llam);
-    acc_add(A, N, AMU, a, 0.5 * lmu);
-    acc_add(A, N, AMU, b, 0.5 * lmu);
-    acc_add(A, N, AMU + 1, a, 0.5 * lkap);
-    acc_add(A, N, AMU + 1, b, 0.5 * lkap);
+    put(RNUA, pick_b ? 0.0 : lnu);
+    put(RNUB, pick_b ? lnu : 0.0);
+    put(RLB, 0.5 * llam);
+    put(RMU, 0.5 * lmu);
+    put(RKA, 0.5 * lkap);
   }
 }
 
-// Sensor cotangents to the pressures of the (face-shifted) centre triple.
-__global__ void k_adj_sensor(Grid g, const double* __restrict__ node, double* __restrict__ A) {
+// Per node, in a fixed order (direction 0, 1, 2; then the roles), the sum of
+// what the interface records owe it: as node a of the interface at n, as b
+// of the one at n - e_D, as a - 1 of the one at n + e_D, as b + 1 of the one
+// at n - 2 e_D, and as a tangential neighbour (a + t, a - t, b + t, b - t)
+// of the interfaces at n - e_t, n + e_t, n - e_t - e_D, n + e_t - e_D.
+// Writes every accumulator slot of every node (the sensor pass adds to the
+// pressure slot afterwards).
+__global__ void __launch_bounds__(256) k_adj_gather(Grid g, const double* __restrict__ R0,
+                                                   const double* __restrict__ R1,
+                                                   const double* __restrict__ R2,
+                                                   double* __restrict__ A) {
+  const long long N = g.N;
+  const double* Rd[3] = {R0, R1, R2};
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    double q[5] = {0, 0, 0, 0, 0}, pr = 0.0, uv[4] = {0, 0, 0, 0}, mu = 0.0, ka = 0.0;
+    double nu[3], lb[3];
+#pragma unroll
+    for (int D = 0; D < 3; ++D) {
+      const double* R = Rd[D];
+      auto rec = [&](int r, long long m) { return m >= 0 ? R[(long long)r * N + m] : 0.0; };
+      const long long mB = step(g, n, c, D, -1);   // interface whose b is n
+      const long long mM = step(g, n, c, D, 1);    // interface whose a - 1 is n
+      const long long mP = step(g, n, c, D, -2);   // interface whose b + 1 is n
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        q[k] += ((rec(RQA + k, n) + rec(RQB + k, mB)) + rec(RQM + k, mM)) + rec(RQP + k, mP);
+      pr += ((rec(RPA, n) + rec(RPA + 1, mB)) + rec(RPA + 2, mM)) + rec(RPA + 3, mP);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) uv[k] += rec(RUA + k, n) + rec(RUB + k, mB);
+      nu[D] = rec(RNUA, n) + rec(RNUB, mB);
+      lb[D] = rec(RLB, n) + rec(RLB, mB);
+      mu += rec(RMU, n) + rec(RMU, mB);
+      ka += rec(RKA, n) + rec(RKA, mB);
+      // tangential: for t = T1 (g1) and T2 (g2)
+#pragma unroll
+      for (int s = 1; s <= 2; ++s) {
+        const int t = (D + s) % 3;
+        const int G = (s == 1) ? RG1 : RG2;
+        const long long tm = step(g, n, c, t, -1), tp = step(g, n, c, t, 1);
+        long long tmb = -1, tpb = -1;  // n - e_t - e_D, n + e_t - e_D
+        if (tm >= 0) {
+          int ct[3] = {c[0], c[1], c[2]};
+          ct[t] = (int)((tm / g.stride[t]) % g.n[t]);
+          tmb = step(g, tm, ct, D, -1);
+        }
+        if (tp >= 0) {
+          int ct[3] = {c[0], c[1], c[2]};
+          ct[t] = (int)((tp / g.stride[t]) % g.n[t]);
+          tpb = step(g, tp, ct, D, -1);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          uv[k] += ((rec(G + k, tm) - rec(G + k, tp)) + rec(G + k, tmb)) - rec(G + k, tpb);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) A[(AQ0 + k) * N + n] = q[k];
+    A[AP * N + n] = pr;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) A[(AU + k) * N + n] = uv[k];
+#pragma unroll
+    for (int D = 0; D < 3; ++D) {
+      A[(ANU + D) * N + n] = nu[D];
+      A[(ALB + D) * N + n] = lb[D];
+    }
+    A[AMU * N + n] = mu;
+    A[(AMU + 1) * N + n] = ka;
+  }
+}
+
+// Sensor cotangents to the pressures of the (face-shifted) centre triple:
+// per node x and direction d the two terms it owes (ls + lden to its outer
+// pair, -2 ls + 2 lden to its centre) into ST[2 d], ST[2 d + 1]; then each
+// node gathers, in a fixed order, the terms of the nodes whose triple holds
+// it (x within two nodes along d).
+__global__ void k_adj_sensor_terms(Grid g, const double* __restrict__ node,
+                                   const double* __restrict__ A, double* __restrict__ ST) {
   const long long N = g.N;
   const double* P = node + 3 * N;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
@@ -336,21 +436,53 @@ __global__ void k_adj_sensor(Grid g, const double* __restrict__ node, double* __
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double ln = A[(ANU + d) * N + n];
-      if (ln == 0.0) continue;
-      long long xm, xc, xp;
-      if (d == 0) sensor_triple<0>(g, n, c[0], xm, xc, xp);
-      else if (d == 1) sensor_triple<1>(g, n, c[1], xm, xc, xp);
-      else sensor_triple<2>(g, n, c[2], xm, xc, xp);
-      const double s = P[xp] - 2.0 * P[xc] + P[xm];
-      const double den = P[xp] + 2.0 * P[xc] + P[xm];
-      // nu = |s| / den
-      const double iden = 1.0 / den;
-      const double ls = ln * sgn_abs(s) * iden;
-      const double lden = -ln * fabs(s) * iden * iden;
-      atomicAdd(A + AP * N + xp, ls + lden);
-      atomicAdd(A + AP * N + xc, -2.0 * ls + 2.0 * lden);
-      atomicAdd(A + AP * N + xm, ls + lden);
+      double outer = 0.0, centre = 0.0;
+      if (ln != 0.0) {
+        long long xm, xc, xp;
+        if (d == 0) sensor_triple<0>(g, n, c[0], xm, xc, xp);
+        else if (d == 1) sensor_triple<1>(g, n, c[1], xm, xc, xp);
+        else sensor_triple<2>(g, n, c[2], xm, xc, xp);
+        const double s = P[xp] - 2.0 * P[xc] + P[xm];
+        const double den = P[xp] + 2.0 * P[xc] + P[xm];
+        // nu = |s| / den
+        const double iden = 1.0 / den;
+        const double ls = ln * sgn_abs(s) * iden;
+        const double lden = -ln * fabs(s) * iden * iden;
+        outer = ls + lden;
+        centre = -2.0 * ls + 2.0 * lden;
+      }
+      ST[(2 * d) * N + n] = outer;
+      ST[(2 * d + 1) * N + n] = centre;
     }
+  }
+}
+
+__global__ void k_adj_sensor_gather(Grid g, const double* __restrict__ ST, double* __restrict__ A) {
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    double add = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int nd = g.n[d];
+#pragma unroll
+      for (int off = -2; off <= 2; ++off) {
+        const long long x = step(g, n, c, d, off);
+        if (x < 0) continue;
+        int cx[3] = {c[0], c[1], c[2]};
+        cx[d] = (int)((x / g.stride[d]) % nd);
+        long long xm, xc, xp;
+        if (d == 0) sensor_triple<0>(g, x, cx[0], xm, xc, xp);
+        else if (d == 1) sensor_triple<1>(g, x, cx[1], xm, xc, xp);
+        else sensor_triple<2>(g, x, cx[2], xm, xc, xp);
+        if (xp == n) add += ST[(2 * d) * N + x];
+        if (xc == n) add += ST[(2 * d + 1) * N + x];
+        if (xm == n) add += ST[(2 * d) * N + x];
+      }
+    }
+    A[AP * N + n] += add;
   }
 }
 
@@ -787,14 +919,19 @@ void launch_rhs_vjp(const Grid& g, const les_params& p, const double* Q, const d
                     const double* node, const double* mk, const double* lamR, double* acc,
                     double* lamQ, double* lamMK, const Launch& L) {
   const Consts<double> K = make_consts<double>(p);
-  cudaMemsetAsync(acc, 0, (size_t)NACC * g.N * sizeof(double), L.s);
   const int nb = nb_for(g.N);
-  k_adj_iface<0><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, acc);
-  k_adj_iface<1><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, acc);
-  k_adj_iface<2><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, acc);
-  k_adj_sensor<<<nb, 256, 0, L.s>>>(g, node, acc);
+  // acc holds the NACC accumulator slots, then the three directions' records
+  double* rec = acc + (size_t)NACC * g.N;
+  const size_t rs = (size_t)NREC * g.N;
+  k_adj_iface<0><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec);
+  k_adj_iface<1><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec + rs);
+  k_adj_iface<2><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec + 2 * rs);
+  k_adj_gather<<<nb, 256, 0, L.s>>>(g, rec, rec + rs, rec + 2 * rs, acc);
+  // the records are consumed: their space holds the sensor terms
+  k_adj_sensor_terms<<<nb, 256, 0, L.s>>>(g, node, acc, rec);
+  k_adj_sensor_gather<<<nb, 256, 0, L.s>>>(g, rec, acc);
   k_adj_node<<<nb, 256, 0, L.s>>>(g, K, Q, M, node, acc, lamQ, lamMK);
-  *L.counter += 5;
+  *L.counter += 7;
 }
 
 void launch_rhs_jvp(const Grid& g, const les_params& p, const Dual* Q, const double* M,

@@ -979,7 +979,7 @@ AdjLayout adj_layout(const les_ctx* c, int nsteps, int K) {
     o = align256(o + bytes);
     return at_;
   };
-  L.acc = take(18 * N * d);
+  L.acc = take((18 + 3 * 45) * N * d);  // accumulators, then the interface records
   L.node = take(8 * N * d);
   L.mk = take(2 * N * d);
   L.lamMK = take(2 * N * d);

@@ -389,9 +389,7 @@ __host__ __device__ constexpr int colk(int kk) { return kk + 2; }
 //   sFz[5][FTJ]         the tile's left-edge zeta interface fluxes (the
 //                       others pass between neighbouring lanes by shuffle)
 constexpr int OFF_PR = 3 * 5 * PL2, OFF_PW = OFF_PR + 3 * 4 * PL2,
-              OFF_M = OFF_PW + 3 * 2 * PL2, OFF_K = OFF_M + 3 * 10 * PL1,
-              OFF_L = OFF_K + 3 * 2 * PL1, OFF_FE = OFF_L + 2 * 3 * PL1,
-              OFF_FZ = OFF_FE + 5 * (FTJ + 1) * FTK, SMEM_FLOATS = OFF_FZ + 5 * FTJ;
+              OFF_M = OFF_PW + 3 * 2 * PL2, OFF_K = OFF_M + 3 * 10 * PL1;
 // With the dynamic SGS model the viscosity slots hold a third field, the
 // Yoshizawa sigma_ll (sK[3][3][PL1]); the regions after sK move up.
 template <bool DYN>
