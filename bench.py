@@ -63,17 +63,17 @@ NCU_SOURCES = {"stage_fused": ("paper_2301_00817_gb300/csrc/fused.cu",
                           "paper_2301_00817_gb300/csrc/lesjet_dev.cuh")}
 NCU_COUNTS = {
     ("stage_fused", "bytes_per_point"):
-        (109.2, "3af0f2209e26129185d7d85e6228c68326a6f25e91c54ba3e5404c826f1e85c4"),
+        (109.4, "1097cb795854c2db84e0a19c4d204b06c568fc3036af3a4b8e010a100997c922"),
     ("stage_fused", "fp32_flop_per_point"):
-        (1045, "3af0f2209e26129185d7d85e6228c68326a6f25e91c54ba3e5404c826f1e85c4"),
+        (1045, "1097cb795854c2db84e0a19c4d204b06c568fc3036af3a4b8e010a100997c922"),
     # smsp__inst_executed.sum x 32 per point, mean of the five stages
     ("stage_fused", "inst_per_point"):
-        (1730, "3af0f2209e26129185d7d85e6228c68326a6f25e91c54ba3e5404c826f1e85c4"),
+        (1727, "1097cb795854c2db84e0a19c4d204b06c568fc3036af3a4b8e010a100997c922"),
     # FP64 flop (dadd + 2 x dfma + dmul) per grid point of one residual's
     # flux group on the 96 x 160 x 128 jet: k_sensor 64 + k_flux 260 + 259
     # + 257
     ("flux64", "fp64_flop_per_point"):
-        (840, "9208cea02a08fca14ed1f8f8d27216ce3063a3a0d59ff641acd20a69f3b3bf7b"),
+        (840, "685d4337d68481aa1c5e7581e9fdbacdd8053ef0b35a8a676108b94a5e31f2bb"),
 }
 NCU_CAPTURE = {"stage_fused": "profiles/stage_fused_jet96x160x128.md",
                "flux64": "profiles/flux64_jet96x160x128.md"}

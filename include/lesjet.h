@@ -189,9 +189,9 @@ const char *les_last_error(const les_ctx *ctx);
 int les_set_params(les_ctx *ctx, const les_params *p);
 
 /* Bytes of the caller-owned device workspace this context needs: about
- * 384 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
+ * 408 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
  * per point with LES_DT_LOCAL and, with LES_SGS_DYNAMIC, 408 B per point
- * (FP64) or 236 B per point (mixed). */
+ * more (FP64) or 236 B per point more (mixed). */
 size_t les_workspace_bytes(const les_ctx *ctx);
 
 /* Bind the workspace and compute the Jacobian and the nine metric terms on

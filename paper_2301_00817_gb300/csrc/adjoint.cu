@@ -488,9 +488,11 @@ __global__ void k_adj_sensor_gather(Grid g, const double* __restrict__ ST, doubl
 
 // Node quantities back to Q: radii lbar(lambda_d), lambda_d = |m_d.u| +
 // sqrt(T)|grad d|, then u = Q1/rho, p = (g-1)(Q4 - rho|u|^2/2), T = g p/rho.
-// lamQ = direct + chained; mu/kappa cotangents are added to lamMK.
+// lamQ = direct + chained; mu/kappa cotangents are added to lamMK.  |grad d|
+// comes from gn ([3][N], set-up) when given, else from M.
 __global__ void __launch_bounds__(256, 2) k_adj_node(Grid g, Consts<double> K, const double* __restrict__ Q,
-                           const double* __restrict__ M, const double* __restrict__ node,
+                           const double* __restrict__ M, const double* __restrict__ gn,
+                           const double* __restrict__ node,
                            const double* __restrict__ A, double* __restrict__ lamQ,
                            double* __restrict__ lamMK) {
   const long long N = g.N;
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_node(Grid g, Consts<double> K, c
       for (int d = 0; d < 3; ++d) {
         const double mx = M[(3 * d) * N + n], my = M[(3 * d + 1) * N + n], mz = M[(3 * d + 2) * N + n];
         th[d] = mx * u + my * v + mz * w;
-        gm[d] = sqrt(mx * mx + my * my + mz * mz);
+        gm[d] = gn ? gn[d * N + n] : sqrt(mx * mx + my * my + mz * mz);
         l[d] = fabs(th[d]) + a * gm[d];
       }
       const double s01 = sqrt(l[0] * l[1]), s02 = sqrt(l[0] * l[2]), s12 = sqrt(l[1] * l[2]);
@@ -916,7 +918,7 @@ static int nb_for(long long count) {
 }
 
 void launch_rhs_vjp(const Grid& g, const les_params& p, const double* Q, const double* M,
-                    const double* node, const double* mk, const double* lamR, double* acc,
+                    const double* gn, const double* node, const double* mk, const double* lamR, double* acc,
                     double* lamQ, double* lamMK, const Launch& L) {
   const Consts<double> K = make_consts<double>(p);
   const int nb = nb_for(g.N);
@@ -930,7 +932,7 @@ void launch_rhs_vjp(const Grid& g, const les_params& p, const double* Q, const d
   // the records are consumed: their space holds the sensor terms
   k_adj_sensor_terms<<<nb, 256, 0, L.s>>>(g, node, acc, rec);
   k_adj_sensor_gather<<<nb, 256, 0, L.s>>>(g, rec, acc);
-  k_adj_node<<<nb, 256, 0, L.s>>>(g, K, Q, M, node, acc, lamQ, lamMK);
+  k_adj_node<<<nb, 256, 0, L.s>>>(g, K, Q, M, gn, node, acc, lamQ, lamMK);
   *L.counter += 7;
 }
 
@@ -938,7 +940,7 @@ void launch_rhs_jvp(const Grid& g, const les_params& p, const Dual* Q, const dou
                     const Dual* mk, Dual* node, Dual* flux, Dual* R, const Launch& L) {
   const Consts<Dual> K = make_consts<Dual>(p);
   const int nb = nb_for(g.N);
-  k_node<Dual, Dual, double, false><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, nullptr, nullptr);
+  k_node<Dual, Dual, double, false><<<nb, 256, 0, L.s>>>(g, K, Q, M, nullptr, node, nullptr, nullptr);
   k_flux<0, Dual, Dual, double><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, flux);
   k_flux<1, Dual, Dual, double><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, flux + 5 * g.N);
   k_flux<2, Dual, Dual, double><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, flux + 10 * g.N);

@@ -39,7 +39,7 @@ struct les_ctx {
   les_params p;
   Grid g;
   // workspace layout (byte offsets, 256-byte aligned)
-  size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_hi, off_lo, off_node, off_flux, off_nu, off_rth,
+  size_t off_m64, off_m32, off_mk, off_sa, off_sb, off_hi, off_lo, off_node, off_flux, off_nu, off_gn, off_rth,
       off_sc, off_part, off_dtl, off_dyn;
   size_t total;
   bool local_dt;  // the workspace holds per-node steps (dt_mode LOCAL at creation)
@@ -196,6 +196,7 @@ void layout(les_ctx* c) {
   c->off_node = o; o = align256(o + (mixed ? (c->dyn_ws ? 8 * N * sizeof(float) : 0) : 8 * N * sizeof(double)));
   c->off_flux = o; o = align256(o + (mixed ? 0 : 15 * N * sizeof(double)));
   c->off_nu = o; o = align256(o + (mixed ? 0 : 3 * N * sizeof(double)));
+  c->off_gn = o; o = align256(o + (mixed ? 0 : 3 * N * sizeof(double)));
   c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
   c->off_sc = o; o = align256(o + sizeof(DevScalars));
   c->off_part = o; o = align256(o + 8 * (size_t)lesjet::kMaxPartials * sizeof(double));
@@ -227,6 +228,7 @@ lesjet::StageIO64 io64(les_ctx* c, const double* Qin) {
   lesjet::StageIO64 io;
   io.Qin = Qin;
   io.M = at<double>(c, c->off_m64);
+  io.gn = is_mixed(c) ? nullptr : at<double>(c, c->off_gn);
   io.node = at<double>(c, c->off_node);
   io.mk = at<double>(c, c->off_mk);
   io.flux = at<double>(c, c->off_flux);
@@ -457,6 +459,7 @@ int les_set_grid(les_ctx* c, const double* xyz, const double shift[9], void* wor
     double* M64 = at<double>(c, c->off_m64);
     lesjet::launch_metrics(c->g, xyz, shift, c->p.metric_form, M64, L);
     if (is_mixed(c)) lesjet::launch_to_float(10 * c->g.N, M64, at<float>(c, c->off_m32), L);
+    else lesjet::launch_grad_norms(c->g, M64, at<double>(c, c->off_gn), L);
   } else {
     lesjet::launch_metrics(c->g, xyz, shift, c->p.metric_form, at<float>(c, c->off_m32), L);
   }
@@ -1040,6 +1043,7 @@ lesjet::StageIO64 adj_io(les_ctx* c, void* aw, const AdjLayout& Ly, const double
   lesjet::StageIO64 io;
   io.Qin = Qin;
   io.M = at<double>(c, c->off_m64);
+  io.gn = at<double>(c, c->off_gn);
   io.node = aw_at<double>(aw, Ly.node);
   io.mk = aw_at<double>(aw, Ly.mk);
   io.flux = at<double>(c, c->off_flux);
@@ -1110,7 +1114,7 @@ void adj_reverse(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], 
       io.node = const_cast<double*>(nodes) + (size_t)(l - 1) * 8 * g.N;  // kept by adj_forward
     else
       lesjet::launch_node64(g, c->p, io, false, L);
-    lesjet::launch_rhs_vjp(g, c->p, S[l - 1], M, io.node, io.mk, lamR, aw_at<double>(aw, Ly.acc),
+    lesjet::launch_rhs_vjp(g, c->p, S[l - 1], M, io.gn, io.node, io.mk, lamR, aw_at<double>(aw, Ly.acc),
                            lamS, lamMK, L);
   }
   lesjet::launch_axpy(5 * g.N, 1.0, lamS, lamQ0, L);
@@ -1167,7 +1171,7 @@ int les_rhs_vjp(les_ctx* c, const double* Q, const double* lamR, double* lamQ, d
   lesjet::launch_node64(c->g, c->p, io, false, L);
   lesjet::launch_mu64(c->g, c->p, io, L);
   cudaMemsetAsync(lamMK, 0, 2 * (size_t)c->g.N * sizeof(double), s);
-  lesjet::launch_rhs_vjp(c->g, c->p, Q, io.M, io.node, io.mk, lamR, aw_at<double>(aw, Ly.acc), lamQ,
+  lesjet::launch_rhs_vjp(c->g, c->p, Q, io.M, io.gn, io.node, io.mk, lamR, aw_at<double>(aw, Ly.acc), lamQ,
                          lamMK, L);
   return cuda_check(c, "les_rhs_vjp");
 }

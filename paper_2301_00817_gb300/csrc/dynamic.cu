@@ -282,7 +282,7 @@ void launch_dynamic32(const Grid& g, const les_params& p, const float* Q, const 
                       const Launch& L) {
   // the FP32 node fields (u v w p T; the radii are not used) of the float state
   const int th = 256, nb = blocks_for(g.N, th);
-  k_node<float, float, float, false><<<nb, th, 0, L.s>>>(g, make_consts<float>(p), Q, M, node,
+  k_node<float, float, float, false><<<nb, th, 0, L.s>>>(g, make_consts<float>(p), Q, M, nullptr, node,
                                                         partials, sc);
   ++*L.counter;
   dynamic_t<float, float, float>(g, p, Q, M, node, scratch, partials, sc, L);

@@ -188,7 +188,9 @@ __device__ __forceinline__ void prim_uvw(const TQ* __restrict__ Q, long long N, 
   w = (R)Q[3 * N + n] * ir;
 }
 
-template <typename R, typename TQ, typename TM>
+// DYN: the dynamic SGS model's branch (coefficients from dyn); a separate
+// instantiation keeps the other models' kernel at about half the registers.
+template <typename R, typename TQ, typename TM, bool DYN>
 __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* __restrict__ Q,
                                                  const TM* __restrict__ M, R* __restrict__ mk,
                                                  double* __restrict__ partials,
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
 #pragma unroll
         for (int x = 0; x < 3; ++x) gr[q][x] = m[x] * dd[q][0] + m[3 + x] * dd[q][1] + m[6 + x] * dd[q][2];
       const R delta = cbrt(m[9]);
-      if (K.sgs == LES_SGS_SMAGORINSKY || K.sgs == LES_SGS_DYNAMIC) {
+      if (DYN || K.sgs == LES_SGS_SMAGORINSKY) {
         R ss = R(0);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
             ss += sij * sij;
           }
         const R smag = dev_sqrt(R(2) * ss);
-        if (K.sgs == LES_SGS_SMAGORINSKY) {
+        if (!DYN) {
           mu_s = rho * (delta * delta) * K.cs2 * smag;
         } else {
           // dynamic model (coefficients dyn[6..8] from the procedure):
@@ -937,11 +939,8 @@ __global__ void __launch_bounds__(FNT, 1)
         for (int c = 0; c < 5; ++c) sFz[c * FTJ + rr] = F[c];
       }
     }
-    // plane i+2, staged at the top of this iteration, must have landed before
-    // the next iteration derives it: wait here, and let this barrier (which
-    // also publishes the eta/zeta fluxes) make it visible
-    cp_async_wait<0>();
-    __syncthreads();
+    // this plane's Q^(0) moves to hc/lc/dc and the next plane's global loads
+    // are issued before the barrier, so their latency overlaps the wait
     float hc[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) hc[c] = h0[c];
@@ -950,6 +949,11 @@ __global__ void __launch_bounds__(FNT, 1)
     for (int c = 0; c < 5; ++c) lc[c] = l0[c];
     const float dc = d0;
     fetch_h(i + 1);
+    // plane i+2, staged at the top of this iteration, must have landed before
+    // the next iteration derives it: wait here, and let this barrier (which
+    // also publishes the eta/zeta fluxes) make it visible
+    cp_async_wait<0>();
+    __syncthreads();
     if (own && ig >= 0) {
       const int n = (ig * nj + jown) * nk + kown;
       if (iint && jint && kint) {
@@ -1058,8 +1062,12 @@ void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const f
                     float* mk, double* partials, DevScalars* sc, float* dtl, const double* dyn,
                     const Launch& L) {
   const Consts<float> K = fused_consts<float>(p);
-  k_prestep<float, float, float><<<kRedBlocks, kRedThreads, 0, L.s>>>(
-      g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl, dyn);
+  if (p.sgs_model == LES_SGS_DYNAMIC)
+    k_prestep<float, float, float, true><<<kRedBlocks, kRedThreads, 0, L.s>>>(
+        g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl, dyn);
+  else
+    k_prestep<float, float, float, false><<<kRedBlocks, kRedThreads, 0, L.s>>>(
+        g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl, dyn);
   ++*L.counter;
   if (p.axis) {
     k_mu_axis<float, TempFromState<float, float>><<<g.n[0], 128, g.n[2] * sizeof(float), L.s>>>(

@@ -152,6 +152,20 @@ __global__ void k_to_float(long long count, const double* __restrict__ a, float*
     b[n] = (float)a[n];
 }
 
+// |grad d| = |(d_x, d_y, d_z)| of the three computational coordinates (the
+// metric norms of the spectral radii lambda_d = |U_d| + a |grad d|): grid
+// constants, so the FP64 form takes them once here instead of per residual.
+__global__ void k_grad_norms(long long N, const double* __restrict__ M, double* __restrict__ gn) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double mx = M[(3 * d) * N + n], my = M[(3 * d + 1) * N + n], mz = M[(3 * d + 2) * N + n];
+      gn[d * N + n] = dev_sqrt(mx * mx + my * my + mz * mz);
+    }
+  }
+}
+
 // Synthetic annular jet grid (Table tab:mesh stand-in): node (i, j, k) at
 // x_i = L (q^i - 1)/(q^(ni-1) - 1) (L i/(ni-1) for q = 1), radius
 // r_j = r0 + (r1 - r0) g(s_j)/g(1) with s_j = j/(nj-1) and the clustering map
@@ -276,6 +290,11 @@ void launch_metrics(const Grid& g, const double* xyz, const double shift[9], int
 
 void launch_to_float(long long count, const double* a, float* b, const Launch& L) {
   k_to_float<<<grid_blocks(count, 256), 256, 0, L.s>>>(count, a, b);
+  ++*L.counter;
+}
+
+void launch_grad_norms(const Grid& g, const double* M, double* gn, const Launch& L) {
+  k_grad_norms<<<grid_blocks(g.N, 256), 256, 0, L.s>>>(g.N, M, gn);
   ++*L.counter;
 }
 

@@ -31,10 +31,10 @@ void launch_node64(const Grid& g, const les_params& p, const StageIO64& io, bool
   const int nb = with_dt ? kRedBlocks : blocks_for(g.N, th);
   auto K = make_consts<double>(p);
   if (with_dt)
-    k_node<double, double, double, true><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node,
+    k_node<double, double, double, true><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.gn, io.node,
                                                              io.partials, io.sc, io.dtl, p.cfl);
   else
-    k_node<double, double, double, false><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.node,
+    k_node<double, double, double, false><<<nb, th, 0, L.s>>>(g, K, io.Qin, io.M, io.gn, io.node,
                                                               io.partials, io.sc);
   ++*L.counter;
 }

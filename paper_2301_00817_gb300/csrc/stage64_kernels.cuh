@@ -38,10 +38,12 @@ inline int blocks_for(long long count, int threads, long long cap = 0) {
 // Primitive recovery (System I energy), spectral radii lambda_d = |U_d| +
 // a |grad d| and lbar_xi = lambda_xi + sqrt(lambda_xi lambda_eta) +
 // sqrt(lambda_xi lambda_zeta) (= lambda_xi [1 + (lambda_eta/lambda_xi)^0.5 +
-// (lambda_zeta/lambda_xi)^0.5]), cyclic for eta and zeta.
+// (lambda_zeta/lambda_xi)^0.5]), cyclic for eta and zeta.  |grad d| is read
+// from gn ([3][N], taken once at set-up) when given, else evaluated from M.
 template <typename R, typename TQ, typename TM, bool WITH_DT>
 __global__ void __launch_bounds__(256) k_node(Grid g, Consts<R> K, const TQ* __restrict__ Q,
-                                              const TM* __restrict__ M, R* __restrict__ node,
+                                              const TM* __restrict__ M,
+                                              const double* __restrict__ gn, R* __restrict__ node,
                                               double* __restrict__ partials,
                                               DevScalars* __restrict__ sc,
                                               double* __restrict__ dtl = nullptr,
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(256) k_node(Grid g, Consts<R> K, const TQ* __r
     for (int d = 0; d < 3; ++d) {
       const R mx = (R)M[(3 * d) * N + nr], my = (R)M[(3 * d + 1) * N + nr],
               mz = (R)M[(3 * d + 2) * N + nr];
-      lam[d] = dev_abs(mx * ur + my * vr + mz * wr) + ar * dev_sqrt(mx * mx + my * my + mz * mz);
+      const R gd = gn ? (R)gn[d * N + nr] : dev_sqrt(mx * mx + my * my + mz * mz);
+      lam[d] = dev_abs(mx * ur + my * vr + mz * wr) + ar * gd;
     }
     const R s01 = dev_sqrt(lam[0] * lam[1]);
     const R s02 = dev_sqrt(lam[0] * lam[2]);
