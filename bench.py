@@ -63,17 +63,17 @@ NCU_SOURCES = {"stage_fused": ("paper_2301_00817_gb300/csrc/fused.cu",
                           "paper_2301_00817_gb300/csrc/lesjet_dev.cuh")}
 NCU_COUNTS = {
     ("stage_fused", "bytes_per_point"):
-        (109.4, "1097cb795854c2db84e0a19c4d204b06c568fc3036af3a4b8e010a100997c922"),
+        (109.1, "9d0cfa1b6f0083f68adc2bbcf6384189a2e5dd6a98d3bb2ff4ba395afb0f42a1"),
     ("stage_fused", "fp32_flop_per_point"):
-        (1045, "1097cb795854c2db84e0a19c4d204b06c568fc3036af3a4b8e010a100997c922"),
+        (1045, "9d0cfa1b6f0083f68adc2bbcf6384189a2e5dd6a98d3bb2ff4ba395afb0f42a1"),
     # smsp__inst_executed.sum x 32 per point, mean of the five stages
     ("stage_fused", "inst_per_point"):
-        (1727, "1097cb795854c2db84e0a19c4d204b06c568fc3036af3a4b8e010a100997c922"),
+        (1727, "9d0cfa1b6f0083f68adc2bbcf6384189a2e5dd6a98d3bb2ff4ba395afb0f42a1"),
     # FP64 flop (dadd + 2 x dfma + dmul) per grid point of one residual's
     # flux group on the 96 x 160 x 128 jet: k_sensor 64 + k_flux 260 + 259
     # + 257
     ("flux64", "fp64_flop_per_point"):
-        (840, "685d4337d68481aa1c5e7581e9fdbacdd8053ef0b35a8a676108b94a5e31f2bb"),
+        (840, "65e036c8b9cc09be8479dba5958162653523c86ee1a101ff181a149cdf3cce16"),
 }
 NCU_CAPTURE = {"stage_fused": "profiles/stage_fused_jet96x160x128.md",
                "flux64": "profiles/flux64_jet96x160x128.md"}

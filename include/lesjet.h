@@ -189,7 +189,7 @@ const char *les_last_error(const les_ctx *ctx);
 int les_set_params(les_ctx *ctx, const les_params *p);
 
 /* Bytes of the caller-owned device workspace this context needs: about
- * 408 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
+ * 416 B per point in FP64, 208 B mixed, 128 B compact mixed; plus one value
  * per point with LES_DT_LOCAL and, with LES_SGS_DYNAMIC, 408 B per point
  * more (FP64) or 236 B per point more (mixed). */
 size_t les_workspace_bytes(const les_ctx *ctx);

@@ -353,7 +353,9 @@ __global__ void __launch_bounds__(256, 2) k_adj_iface(Grid g, Consts<double> K,
 // at n - 2 e_D, and as a tangential neighbour (a + t, a - t, b + t, b - t)
 // of the interfaces at n - e_t, n + e_t, n - e_t - e_D, n + e_t - e_D.
 // Writes every accumulator slot of every node (the sensor pass adds to the
-// pressure slot afterwards).
+// pressure slot afterwards).  One output slot at a time (its own fixed
+// order of terms), so few accumulators are live and the kernel keeps
+// enough warps resident to cover its memory latency.
 __global__ void __launch_bounds__(256) k_adj_gather(Grid g, const double* __restrict__ R0,
                                                    const double* __restrict__ R1,
                                                    const double* __restrict__ R2,
@@ -364,56 +366,64 @@ __global__ void __launch_bounds__(256) k_adj_gather(Grid g, const double* __rest
        n += (long long)gridDim.x * blockDim.x) {
     int c[3];
     decompose(g, n, c);
-    double q[5] = {0, 0, 0, 0, 0}, pr = 0.0, uv[4] = {0, 0, 0, 0}, mu = 0.0, ka = 0.0;
-    double nu[3], lb[3];
+    long long mB[3], mM[3], mP[3];  // interfaces whose b, a - 1, b + 1 is n
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
-      const double* R = Rd[D];
-      auto rec = [&](int r, long long m) { return m >= 0 ? R[(long long)r * N + m] : 0.0; };
-      const long long mB = step(g, n, c, D, -1);   // interface whose b is n
-      const long long mM = step(g, n, c, D, 1);    // interface whose a - 1 is n
-      const long long mP = step(g, n, c, D, -2);   // interface whose b + 1 is n
-#pragma unroll
-      for (int k = 0; k < 5; ++k)
-        q[k] += ((rec(RQA + k, n) + rec(RQB + k, mB)) + rec(RQM + k, mM)) + rec(RQP + k, mP);
-      pr += ((rec(RPA, n) + rec(RPA + 1, mB)) + rec(RPA + 2, mM)) + rec(RPA + 3, mP);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) uv[k] += rec(RUA + k, n) + rec(RUB + k, mB);
-      nu[D] = rec(RNUA, n) + rec(RNUB, mB);
-      lb[D] = rec(RLB, n) + rec(RLB, mB);
-      mu += rec(RMU, n) + rec(RMU, mB);
-      ka += rec(RKA, n) + rec(RKA, mB);
-      // tangential: for t = T1 (g1) and T2 (g2)
-#pragma unroll
-      for (int s = 1; s <= 2; ++s) {
-        const int t = (D + s) % 3;
-        const int G = (s == 1) ? RG1 : RG2;
-        const long long tm = step(g, n, c, t, -1), tp = step(g, n, c, t, 1);
-        long long tmb = -1, tpb = -1;  // n - e_t - e_D, n + e_t - e_D
-        if (tm >= 0) {
-          int ct[3] = {c[0], c[1], c[2]};
-          ct[t] = (int)((tm / g.stride[t]) % g.n[t]);
-          tmb = step(g, tm, ct, D, -1);
-        }
-        if (tp >= 0) {
-          int ct[3] = {c[0], c[1], c[2]};
-          ct[t] = (int)((tp / g.stride[t]) % g.n[t]);
-          tpb = step(g, tp, ct, D, -1);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          uv[k] += ((rec(G + k, tm) - rec(G + k, tp)) + rec(G + k, tmb)) - rec(G + k, tpb);
-      }
+      mB[D] = step(g, n, c, D, -1);
+      mM[D] = step(g, n, c, D, 1);
+      mP[D] = step(g, n, c, D, -2);
     }
+    auto rec = [&](int D, int r, long long m) { return m >= 0 ? Rd[D][(long long)r * N + m] : 0.0; };
+    // conserved state (k < 5) and pressure (k = 5): four roles per direction
+#pragma unroll 1
+    for (int k = 0; k < 6; ++k) {
+      const int ra = k < 5 ? RQA + k : RPA, rb = k < 5 ? RQB + k : RPA + 1;
+      const int rm = k < 5 ? RQM + k : RPA + 2, rp = k < 5 ? RQP + k : RPA + 3;
+      double acc = 0.0;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) A[(AQ0 + k) * N + n] = q[k];
-    A[AP * N + n] = pr;
+      for (int D = 0; D < 3; ++D)
+        acc += ((rec(D, ra, n) + rec(D, rb, mB[D])) + rec(D, rm, mM[D])) + rec(D, rp, mP[D]);
+      A[(k < 5 ? AQ0 + k : AP) * N + n] = acc;
+    }
+    // u, v, w, T: as a and b, then as a tangential neighbour along T1, T2
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      double acc = 0.0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) A[(AU + k) * N + n] = uv[k];
+      for (int D = 0; D < 3; ++D) {
+        acc += rec(D, RUA + k, n) + rec(D, RUB + k, mB[D]);
+#pragma unroll
+        for (int s = 1; s <= 2; ++s) {
+          const int t = (D + s) % 3;
+          const int G = (s == 1) ? RG1 : RG2;
+          const long long tm = step(g, n, c, t, -1), tp = step(g, n, c, t, 1);
+          long long tmb = -1, tpb = -1;  // n - e_t - e_D, n + e_t - e_D
+          if (tm >= 0) {
+            int ct[3] = {c[0], c[1], c[2]};
+            ct[t] = coord_step(g, c, t, -1);
+            tmb = step(g, tm, ct, D, -1);
+          }
+          if (tp >= 0) {
+            int ct[3] = {c[0], c[1], c[2]};
+            ct[t] = coord_step(g, c, t, 1);
+            tpb = step(g, tp, ct, D, -1);
+          }
+          acc += ((rec(D, G + k, tm) - rec(D, G + k, tp)) + rec(D, G + k, tmb)) - rec(D, G + k, tpb);
+        }
+      }
+      A[(AU + k) * N + n] = acc;
+    }
+    // sensor and lbar of each direction; mu_eff and kappa_eff over the three
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
-      A[(ANU + D) * N + n] = nu[D];
-      A[(ALB + D) * N + n] = lb[D];
+      A[(ANU + D) * N + n] = rec(D, RNUA, n) + rec(D, RNUB, mB[D]);
+      A[(ALB + D) * N + n] = rec(D, RLB, n) + rec(D, RLB, mB[D]);
+    }
+    double mu = 0.0, ka = 0.0;
+#pragma unroll
+    for (int D = 0; D < 3; ++D) {
+      mu += rec(D, RMU, n) + rec(D, RMU, mB[D]);
+      ka += rec(D, RKA, n) + rec(D, RKA, mB[D]);
     }
     A[AMU * N + n] = mu;
     A[(AMU + 1) * N + n] = ka;
@@ -466,13 +476,12 @@ __global__ void k_adj_sensor_gather(Grid g, const double* __restrict__ ST, doubl
     double add = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const int nd = g.n[d];
 #pragma unroll
       for (int off = -2; off <= 2; ++off) {
         const long long x = step(g, n, c, d, off);
         if (x < 0) continue;
         int cx[3] = {c[0], c[1], c[2]};
-        cx[d] = (int)((x / g.stride[d]) % nd);
+        cx[d] = coord_step(g, c, d, off);
         long long xm, xc, xp;
         if (d == 0) sensor_triple<0>(g, x, cx[0], xm, xc, xp);
         else if (d == 1) sensor_triple<1>(g, x, cx[1], xm, xc, xp);

@@ -196,7 +196,7 @@ void layout(les_ctx* c) {
   c->off_node = o; o = align256(o + (mixed ? (c->dyn_ws ? 8 * N * sizeof(float) : 0) : 8 * N * sizeof(double)));
   c->off_flux = o; o = align256(o + (mixed ? 0 : 15 * N * sizeof(double)));
   c->off_nu = o; o = align256(o + (mixed ? 0 : 3 * N * sizeof(double)));
-  c->off_gn = o; o = align256(o + (mixed ? 0 : 3 * N * sizeof(double)));
+  c->off_gn = o; o = align256(o + (mixed ? 0 : 4 * N * sizeof(double)));
   c->off_rth = o; o = align256(o + 2 * (size_t)c->g.n[1] * c->g.n[2] * sizeof(double));
   c->off_sc = o; o = align256(o + sizeof(DevScalars));
   c->off_part = o; o = align256(o + 8 * (size_t)lesjet::kMaxPartials * sizeof(double));
@@ -1044,6 +1044,7 @@ lesjet::StageIO64 adj_io(les_ctx* c, void* aw, const AdjLayout& Ly, const double
   io.Qin = Qin;
   io.M = at<double>(c, c->off_m64);
   io.gn = at<double>(c, c->off_gn);
+  io.nu = at<double>(c, c->off_nu);
   io.node = aw_at<double>(aw, Ly.node);
   io.mk = aw_at<double>(aw, Ly.mk);
   io.flux = at<double>(c, c->off_flux);
@@ -1071,6 +1072,7 @@ void adj_forward(les_ctx* c, void* aw, const AdjLayout& Ly, double* const S[6], 
     io.Qin = S[l - 1];
     io.node = node_of(l);
     if (l > 1) lesjet::launch_node64(g, c->p, io, false, L);
+    lesjet::launch_sensor64(g, io, L);
     for (int d = 0; d < 3; ++d) lesjet::launch_flux64(g, c->p, io, d, L);
     lesjet::launch_update64(g, io, S[0], kAlpha[l - 1], 1, S[l], L);
   }

@@ -78,6 +78,14 @@ __host__ __device__ inline long long idx3(const Grid& g, int i, int j, int k) {
 }
 
 __device__ __forceinline__ void decompose(const Grid& g, long long n, int c[3]) {
+  if (g.N <= 0x7fffffffLL) {  // every index fits 32 bits: the cheaper division
+    const unsigned u = (unsigned)n, nk = (unsigned)g.n[2], nj = (unsigned)g.n[1];
+    const unsigned r = u / nk;
+    c[2] = (int)(u - r * nk);
+    c[0] = (int)(r / nj);
+    c[1] = (int)(r - (unsigned)c[0] * nj);
+    return;
+  }
   long long r = n / g.n[2];
   c[2] = (int)(n - r * g.n[2]);
   c[0] = (int)(r / g.n[1]);
@@ -97,6 +105,15 @@ __device__ __forceinline__ long long step(const Grid& g, long long n, const int 
     return -1;
   }
   return n + (long long)(v - c[d]) * g.stride[d];
+}
+
+// Coordinate along d of the node step(g, n, c, d, off) returned (valid only
+// when that node exists): c[d] + off, wrapped like step().
+__device__ __forceinline__ int coord_step(const Grid& g, const int c[3], int d, int off) {
+  int v = c[d] + off;
+  if (v >= g.n[d]) v -= g.n[d];
+  else if (v < 0) v += g.n[d];
+  return v;
 }
 
 // A node the stages update: inside every non-periodic face, and along xi

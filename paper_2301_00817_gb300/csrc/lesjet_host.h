@@ -16,7 +16,7 @@ void launch_metrics(const Grid& g, const double* xyz, const double shift[9], int
 void launch_metrics(const Grid& g, const double* xyz, const double shift[9], int form, float* M,
                     const Launch& L);
 void launch_to_float(long long count, const double* a, float* b, const Launch& L);
-// the metric norms |grad xi_d| of M ([10][N]) into gn ([3][N])
+// the metric norms |grad xi_d| and J/2 of M ([10][N]) into gn ([4][N])
 void launch_grad_norms(const Grid& g, const double* M, double* gn, const Launch& L);
 void launch_inflow_geometry(const Grid& g, const double* xyz, double* rth, const Launch& L);
 // synthetic jet grid coordinates [3][N] (s_c: the clustering centre in s)
@@ -38,8 +38,8 @@ void launch_mk_to_double(int precision, const Grid& g, const void* mk, int field
 struct StageIO64 {
   const double* Qin;   // [5][N] stage input state
   const double* M;     // [10][N] metrics
-  const double* gn = nullptr;  // [3][N] metric norms |grad xi_d| (set-up), or
-                               // nullptr: k_node evaluates them
+  const double* gn = nullptr;  // [4][N] metric norms |grad xi_d| and J/2
+                               // (set-up), or nullptr: the kernels evaluate them
   double* node;        // [8][N] u v w p T lbar_xi lbar_eta lbar_zeta
   double* mk;          // [2][N] mu_eff kappa_eff
   double* flux;        // [3][5][N] interface fluxes

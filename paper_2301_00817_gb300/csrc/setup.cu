@@ -152,9 +152,11 @@ __global__ void k_to_float(long long count, const double* __restrict__ a, float*
     b[n] = (float)a[n];
 }
 
+// Grid constants the FP64 form takes once here instead of per residual:
 // |grad d| = |(d_x, d_y, d_z)| of the three computational coordinates (the
-// metric norms of the spectral radii lambda_d = |U_d| + a |grad d|): grid
-// constants, so the FP64 form takes them once here instead of per residual.
+// metric norms of the spectral radii lambda_d = |U_d| + a |grad d|), and
+// J/2 = 0.5 / J^-1 of the stage update (0 where J^-1 = 0: an axis node,
+// which the stages do not update).
 __global__ void k_grad_norms(long long N, const double* __restrict__ M, double* __restrict__ gn) {
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
@@ -163,6 +165,8 @@ __global__ void k_grad_norms(long long N, const double* __restrict__ M, double* 
       const double mx = M[(3 * d) * N + n], my = M[(3 * d + 1) * N + n], mz = M[(3 * d + 2) * N + n];
       gn[d * N + n] = dev_sqrt(mx * mx + my * my + mz * mz);
     }
+    const double Ji = M[9 * N + n];
+    gn[3 * N + n] = Ji == 0.0 ? 0.0 : 0.5 / Ji;
   }
 }
 

@@ -87,9 +87,11 @@ void launch_update64(const Grid& g, const StageIO64& io, const double* Q0, doubl
   if (mode == 0)
     k_update<double, double, double, 0><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out, io.dtl);
   else if (mode == 1)
-    k_update<double, double, double, 1><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out, io.dtl);
+    k_update<double, double, double, 1><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out, io.dtl,
+                                                            io.gn ? io.gn + 3 * g.N : nullptr);
   else
-    k_update<double, double, double, 2><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out, io.dtl);
+    k_update<double, double, double, 2><<<nb, th, 0, L.s>>>(g, io.flux, Q0, io.M, io.sc, alpha, out, io.dtl,
+                                                            io.gn ? io.gn + 3 * g.N : nullptr);
   ++*L.counter;
 }
 

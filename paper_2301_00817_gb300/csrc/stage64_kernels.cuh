@@ -461,7 +461,8 @@ __global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
                                                 const TM* __restrict__ M,
                                                 const DevScalars* __restrict__ sc, double alpha,
                                                 TO* __restrict__ out,
-                                                const double* __restrict__ dtl = nullptr) {
+                                                const double* __restrict__ dtl = nullptr,
+                                                const double* __restrict__ jh = nullptr) {
   const long long N = g.N;
   const R* F0 = F;
   const R* F1 = F + 5 * N;
@@ -484,8 +485,9 @@ __global__ void __launch_bounds__(256) k_update(Grid g, const R* __restrict__ F,
     const long long m0 = step(g, n, c, 0, -1);
     const long long m1 = step(g, n, c, 1, -1);
     const long long m2 = step(g, n, c, 2, -1);
-    // J once per node, halved: k_flux writes 2x the interface fluxes
-    const double Jn = (MODE == 0) ? 0.0 : 0.5 / (double)M[9 * N + n];
+    // J once per node, halved: k_flux writes 2x the interface fluxes (jh
+    // holds the same quotient, taken at set-up)
+    const double Jn = (MODE == 0) ? 0.0 : (jh ? jh[n] : 0.5 / (double)M[9 * N + n]);
     const double a = (MODE == 0) ? 0.0 : (dtl ? alpha * dtl[n] : adt);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
