@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256, 2) k_adj_iface(Grid g, Consts<double> K,
                                                    const double* __restrict__ node,
                                                    const double* __restrict__ mk,
                                                    const double* __restrict__ lamR,
-                                                   double* __restrict__ Rec) {
+                                                   double* __restrict__ Rec,
+                                                   const double* __restrict__ NU) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   const long long N = g.N;
   const double* U = node;
@@ -156,11 +157,9 @@ __global__ void __launch_bounds__(256, 2) k_adj_iface(Grid g, Consts<double> K,
       Qa[q] = Q[q * N + a];
       Qb[q] = Q[q * N + b];
     }
-    long long sm, sc_, sp;
-    sensor_triple<D>(g, a, c[D], sm, sc_, sp);
-    const double nua = fabs(P[sp] - 2.0 * P[sc_] + P[sm]) / (P[sp] + 2.0 * P[sc_] + P[sm]);
-    sensor_triple<D>(g, b, cb[D], sm, sc_, sp);
-    const double nub = fabs(P[sp] - 2.0 * P[sc_] + P[sm]) / (P[sp] + 2.0 * P[sc_] + P[sm]);
+    // the two nodes' sensors, as the forward read them (k_sensor of this
+    // stage input)
+    const double nua = NU[D * N + a], nub = NU[D * N + b];
     // forward: dev_max(nua, nub) = nua > nub ? nua : nub; max(0, x) keeps x for x >= 0
     const bool pick_b = !(nua > nub);
     const double eps2 = K.k2 * (pick_b ? nub : nua);
@@ -928,15 +927,16 @@ static int nb_for(long long count) {
 
 void launch_rhs_vjp(const Grid& g, const les_params& p, const double* Q, const double* M,
                     const double* gn, const double* node, const double* mk, const double* lamR, double* acc,
-                    double* lamQ, double* lamMK, const Launch& L) {
+                    double* lamQ, double* lamMK, const Launch& L, const double* nu) {
+  // nu: the three sensors of the stage input (launch_sensor64 on node)
   const Consts<double> K = make_consts<double>(p);
   const int nb = nb_for(g.N);
   // acc holds the NACC accumulator slots, then the three directions' records
   double* rec = acc + (size_t)NACC * g.N;
   const size_t rs = (size_t)NREC * g.N;
-  k_adj_iface<0><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec);
-  k_adj_iface<1><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec + rs);
-  k_adj_iface<2><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec + 2 * rs);
+  k_adj_iface<0><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec, nu);
+  k_adj_iface<1><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec + rs, nu);
+  k_adj_iface<2><<<nb, 256, 0, L.s>>>(g, K, Q, M, node, mk, lamR, rec + 2 * rs, nu);
   k_adj_gather<<<nb, 256, 0, L.s>>>(g, rec, rec + rs, rec + 2 * rs, acc);
   // the records are consumed: their space holds the sensor terms
   k_adj_sensor_terms<<<nb, 256, 0, L.s>>>(g, node, acc, rec);

@@ -100,7 +100,7 @@ void launch_join(long long count, const float* hi, const float* lo, double* q, c
 struct Dual;
 void launch_rhs_vjp(const Grid& g, const les_params& p, const double* Q, const double* M,
                     const double* gn, const double* node, const double* mk, const double* lamR, double* acc,
-                    double* lamQ, double* lamMK, const Launch& L);
+                    double* lamQ, double* lamMK, const Launch& L, const double* nu);
 void launch_rhs_jvp(const Grid& g, const les_params& p, const Dual* Q, const double* M,
                     const Dual* mk, Dual* node, Dual* flux, Dual* R, const Launch& L);
 void launch_mu_vjp(const Grid& g, const les_params& p, const double* Q, const double* lamMK,
