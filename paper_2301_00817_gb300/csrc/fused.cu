@@ -449,6 +449,7 @@ struct FusedGeom {
   int vec16;  // zeta periodic, nk % 4 == 0 and nk >= FTK: tiles shifted by
               // two columns, rows staged as 16-byte copies
   int ilo, ihi;  // planes the stage updates along a non-periodic xi: [ilo, ihi)
+  int N;         // points per field (the fields of qin, m and mk are N apart)
 };
 
 __device__ __forceinline__ int wrap_fast(int v, int n, int per) {
@@ -466,8 +467,11 @@ __device__ __forceinline__ int wrap_fast(int v, int n, int per) {
 
 // LOCAL: node n advances with its own step P.dtl[n] (dt_mode LOCAL) in
 // place of the global one; a separate instantiation keeps the global-step
-// kernel free of the per-node load and its branch.
-template <int MODE, bool LOCAL, bool AXIS, bool DYN>
+// kernel free of the per-node load and its branch.  PM >= 0: the grid's
+// periodicity as a compile-time mask (bit d: direction d periodic), so the
+// face, wrap and one-sided-difference tests fold away; PM = -1 reads it from
+// the grid.
+template <int MODE, bool LOCAL, bool AXIS, bool DYN, int PM>
 __global__ void __launch_bounds__(FNT, 1)
     k_stage_fused(const FusedGeom G, const Consts<float> K, const FusedPtrs P,
                   const DevScalars* __restrict__ sc, double alpha) {
@@ -482,6 +486,11 @@ __global__ void __launch_bounds__(FNT, 1)
   float* sFe = smem + FLayout<DYN>::FE;
   float* sFz = smem + FLayout<DYN>::FZ;
   const int ni = G.ni, nj = G.nj, nk = G.nk;
+  // periodicity of xi, eta, zeta: fixed at compile time for PM >= 0 (bit d:
+  // direction d periodic), else the grid's flags
+  const int per0 = PM >= 0 ? (PM & 1) : G.per[0];
+  const int per1 = PM >= 0 ? ((PM >> 1) & 1) : G.per[1];
+  const int per2 = PM >= 0 ? ((PM >> 2) & 1) : G.per[2];
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   // kt: first column of the unshifted tile; k0: global column of tile
   // column 0 (kt + 2 with the shifted tiling; may exceed nk - 1, wrapped)
@@ -492,15 +501,15 @@ __global__ void __launch_bounds__(FNT, 1)
   const int jown = j0 + ty;
   const int kown = (k0 + tx < nk) ? k0 + tx : k0 + tx - nk;  // wraps in the shifted case only
   const bool own = jown < nj && kt + tx < nk;
-  const bool jint = G.per[1] || (jown > 0 && jown < nj - 1);
-  const bool kint = G.per[2] || (kown > 0 && kown < nk - 1);
-  const bool per_i = G.per[0] != 0;
+  const bool jint = per1 || (jown > 0 && jown < nj - 1);
+  const bool kint = per2 || (kown > 0 && kown < nk - 1);
+  const bool per_i = per0 != 0;
   const int o2 = (ty + 2) * SK + tx + 2;  // own node, 2-node-halo planes
   const int o1 = (ty + 1) * SK + tx + 2;  // own node, 1-node-halo planes
 
   // ---- stage plane x (state: 2-node halo; metrics, mu/kappa: 1-node halo)
   auto stage_plane = [&](int slot, int x) {
-    const int ig = wrap_fast(x, ni, G.per[0]);
+    const int ig = wrap_fast(x, ni, per0);
     constexpr int JQ = 5 * R2, JM = 10 * R1, JK = NKF * R1;
     // one row per thread, taken by the highest-numbered threads: the lowest
     // ones derive a second node record in the same phase
@@ -513,35 +522,40 @@ __global__ void __launch_bounds__(FNT, 1)
     if (tid < JQ) {
       const int f = tid / R2;
       jj = tid - f * R2 - 2;
-      src = P.qin[f];
+      src = P.qin[0] + (long long)f * G.N;
       dst = sQ + (slot * 5 + f) * PL2 + (jj + 2) * SK;
       halo = 2;
       benign = (f == 0 || f == 4) ? 1.f : 0.f;
     } else if (tid < JQ + JM) {
       const int u = tid - JQ, f = u / R1;
       jj = u - f * R1 - 1;
-      src = P.m[f];
+      src = P.m[0] + (long long)f * G.N;
       dst = sM + (slot * 10 + f) * PL1 + (jj + 1) * SK;
       halo = 1;
       benign = 1.f;
     } else {
       const int u = tid - JQ - JM, f = u / R1;
       jj = u - f * R1 - 1;
-      src = P.mk[f];
+      src = P.mk[0] + (long long)f * G.N;
       dst = sK + (slot * NKF + f) * PL1 + (jj + 1) * SK;
       halo = 1;
       benign = 0.f;
     }
-    const int jg = wrap_fast(j0 + jj, nj, G.per[1]);
+    const int jg = wrap_fast(j0 + jj, nj, per1);
     if (ig < 0 || jg < 0) {
       for (int c = 0; c < SK; ++c) dst[c] = benign;
       return;
     }
     const float* row = src + (ig * nj + jg) * nk;
-    if (vec_ok) {
-      // the row's global columns kt .. kt + SK - 1, wrapped at nk (a
-      // multiple of 4, so no 16-byte piece straddles the wrap; kt + SK <
-      // 2 nk because nk >= FTK)
+    if (vec_ok && kt + SK <= nk) {
+      // the row's global columns kt .. kt + SK - 1, inside the row
+      const float* rk = row + kt;
+#pragma unroll
+      for (int v = 0; v < SK / 4; ++v) cp_async16(dst + 4 * v, rk + 4 * v);
+    } else if (vec_ok) {
+      // the last tile: columns kt .. kt + SK - 1 wrapped at nk (a multiple
+      // of 4, so no 16-byte piece straddles the wrap; kt + SK < 2 nk because
+      // nk >= FTK)
 #pragma unroll
       for (int v = 0; v < SK / 4; ++v) {
         const int kg = (kt + 4 * v < nk) ? kt + 4 * v : kt + 4 * v - nk;
@@ -549,7 +563,7 @@ __global__ void __launch_bounds__(FNT, 1)
       }
     } else {
       for (int kk = -halo; kk < FTK + halo; ++kk) {
-        const int kg = wrap_fast(k0 + kk, nk, G.per[2]);
+        const int kg = wrap_fast(k0 + kk, nk, per2);
         if (kg >= 0)
           cp_async4(dst + colk(kk), row + kg);
         else
@@ -611,7 +625,7 @@ __global__ void __launch_bounds__(FNT, 1)
   float qn[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   bool vn = false;
   auto fetch_q = [&](int x) {
-    const int ig = wrap_fast(x, ni, G.per[0]);
+    const int ig = wrap_fast(x, ni, per0);
     vn = own && ig >= 0;
     if (vn) {
       const int n = (ig * nj + jown) * nk + kown;
@@ -626,7 +640,7 @@ __global__ void __launch_bounds__(FNT, 1)
   float l0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // lo part, last stage only
   float d0 = 0.f;                            // local step (LOCAL only)
   auto fetch_h = [&](int x) {
-    const int ig = wrap_fast(x, ni, G.per[0]);
+    const int ig = wrap_fast(x, ni, per0);
     if (MODE != FMODE_RHS && own && ig >= 0) {
       const int n = (ig * nj + jown) * nk + kown;
 #pragma unroll
@@ -703,8 +717,8 @@ __global__ void __launch_bounds__(FNT, 1)
     const int a2 = (ra + 2) * SK + colk(tx), b2 = a2 + SK;
     const int a1 = (ra + 1) * SK + colk(tx), b1 = a1 + SK;
     const int jga = j0 + ra;
-    const bool has_m = G.per[1] || jga - 1 >= 0;
-    const bool has_p = G.per[1] || jga + 2 <= nj - 1;
+    const bool has_m = per1 || jga - 1 >= 0;
+    const bool has_p = per1 || jga + 2 <= nj - 1;
     const float2 wm = Pw[a2 - SK], wa = wown ? *wown : Pw[a2], wb = Pw[b2], wp = Pw[b2 + SK];
     float Wm[5], Wa[5], Wb[5], Wp[5];
 #pragma unroll
@@ -719,11 +733,11 @@ __global__ void __launch_bounds__(FNT, 1)
     Wm[4] = wm.y;
     Wp[4] = wp.y;
     float nua, nub;
-    if (!G.per[1] && jga == 0)
+    if (!per1 && jga == 0)
       nua = sensor3(wa.x, wb.x, wp.x);
     else
       nua = sensor3(wm.x, wa.x, wb.x);
-    if (!G.per[1] && jga + 1 == nj - 1)
+    if (!per1 && jga + 1 == nj - 1)
       nub = sensor3(wm.x, wa.x, wb.x);
     else
       nub = sensor3(wa.x, wb.x, wp.x);
@@ -762,8 +776,8 @@ __global__ void __launch_bounds__(FNT, 1)
     const int a2 = rb2 + ca_c, b2 = rb2 + cb_c, m2 = rb2 + cm_c, q2 = rb2 + cp_c;
     const int a1 = rb1 + ca_c, b1 = rb1 + cb_c;
     const int kga = k0 + ca;
-    const bool has_m = G.per[2] || kga - 1 >= 0;
-    const bool has_p = G.per[2] || kga + 2 <= nk - 1;
+    const bool has_m = per2 || kga - 1 >= 0;
+    const bool has_p = per2 || kga + 2 <= nk - 1;
     const float2 wm = Pw[m2], wa = wown ? *wown : Pw[a2], wb = Pw[b2], wp = Pw[q2];
     float Wm[5], Wa[5], Wb[5], Wp[5];
 #pragma unroll
@@ -778,11 +792,11 @@ __global__ void __launch_bounds__(FNT, 1)
     Wm[4] = wm.y;
     Wp[4] = wp.y;
     float nua, nub;
-    if (!G.per[2] && kga == 0)
+    if (!per2 && kga == 0)
       nua = sensor3(wa.x, wb.x, wp.x);
     else
       nua = sensor3(wm.x, wa.x, wb.x);
-    if (!G.per[2] && kga + 1 == nk - 1)
+    if (!per2 && kga + 1 == nk - 1)
       nub = sensor3(wm.x, wa.x, wb.x);
     else
       nub = sensor3(wa.x, wb.x, wp.x);
@@ -822,7 +836,7 @@ __global__ void __launch_bounds__(FNT, 1)
   // the own column's planes ib-2 .. ib+1: all loads issued before any is used
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int igq = wrap_fast(ib - 2 + q, ni, G.per[0]);
+    const int igq = wrap_fast(ib - 2 + q, ni, per0);
     vq[q] = own && igq >= 0;
     if (vq[q]) {
       const int n = (igq * nj + jown) * nk + kown;
@@ -879,7 +893,7 @@ __global__ void __launch_bounds__(FNT, 1)
     derive_plane(s_p, s_p, s_p, l_p);
     __syncthreads();
 
-    const int ig = wrap_fast(i, ni, G.per[0]);
+    const int ig = wrap_fast(i, ni, per0);
     const bool iint = per_i || (i >= G.ilo && i < G.ihi);
     float Fx[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     // the own node's metrics, read once for its three interfaces
@@ -903,12 +917,12 @@ __global__ void __launch_bounds__(FNT, 1)
       xi_flux(i, s_c, s_p, s_c, s_p, l_c, l_p, mo, &ro, rpm, &wo, Fx);
     if (own && iint && kint) {
       float F[5];
-      if (G.per[1] || jown + 1 <= nj - 1) {
+      if (per1 || jown + 1 <= nj - 1) {
         eta_flux(ty, s_c, s_m, s_c, s_p, s_c, l_c, mo, &ro, rpm, &wo, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1) + ty + 1) * FTK + tx] = F[c];
       }
-      if (ty == 0 && (G.per[1] || j0 - 1 >= 0)) {
+      if (ty == 0 && (per1 || j0 - 1 >= 0)) {
         eta_flux(-1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, nullptr, nullptr, nullptr, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) sFe[(c * (FTJ + 1)) * FTK + tx] = F[c];
@@ -920,7 +934,7 @@ __global__ void __launch_bounds__(FNT, 1)
     float dz[5];
     {
       float Fz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      if (own && iint && jint && (G.per[2] || kown + 1 <= nk - 1))
+      if (own && iint && jint && (per2 || kown + 1 <= nk - 1))
         zeta_flux(ty, tx, s_c, s_m, s_c, s_p, s_c, l_c, mo, &ro, rpm, &wo, Fz);
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
@@ -929,9 +943,9 @@ __global__ void __launch_bounds__(FNT, 1)
       }
     }
     // left-edge zeta interfaces (k0-1, k0) of the FTJ rows: lanes of warp 1
-    if (ty == 1 && tx < FTJ && iint && (G.per[2] || k0 - 1 >= 0)) {
+    if (ty == 1 && tx < FTJ && iint && (per2 || k0 - 1 >= 0)) {
       const int rr = tx, jr = j0 + rr;
-      const bool rint = G.per[1] || (jr > 0 && jr < nj - 1);
+      const bool rint = per1 || (jr > 0 && jr < nj - 1);
       if (jr < nj && rint) {
         float F[5];
         zeta_flux(rr, -1, s_c, s_m, s_c, s_p, s_c, l_c, nullptr, nullptr, nullptr, nullptr, F);
@@ -1117,7 +1131,7 @@ static int choose_nch(int ni, int tiles, int slots) {
   return best;
 }
 
-template <int MODE, bool LOCAL, bool AXIS, bool DYN>
+template <int MODE, bool LOCAL, bool AXIS, bool DYN, int PM>
 static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const FusedPtrs& P,
                            const DevScalars* sc, double alpha, const Launch& L) {
   FusedGeom G = G0;
@@ -1129,31 +1143,31 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-    cudaFuncSetAttribute(k_stage_fused<MODE, LOCAL, AXIS, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_stage_fused<MODE, LOCAL, AXIS, DYN, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
   G.nch = choose_nch(G.ni, tk * tj, sm_count());  // one CTA per SM
   dim3 grid(tk, tj, G.nch);
-  k_stage_fused<MODE, LOCAL, AXIS, DYN><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
+  k_stage_fused<MODE, LOCAL, AXIS, DYN, PM><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
   ++*L.counter;
 }
 
-template <bool AXIS, bool DYN>
+template <bool AXIS, bool DYN, int PM>
 static void launch_stage_dispatch(int mode, bool local, const FusedGeom& G, const Consts<float>& K,
                                   const FusedPtrs& P, const DevScalars* sc, double alpha,
                                   const Launch& L) {
   if (mode == FMODE_RHS)
-    launch_stage_t<FMODE_RHS, false, AXIS, DYN>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_RHS, false, AXIS, DYN, PM>(G, K, P, sc, alpha, L);
   else if (mode == FMODE_STAGE && !local)
-    launch_stage_t<FMODE_STAGE, false, AXIS, DYN>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_STAGE, false, AXIS, DYN, PM>(G, K, P, sc, alpha, L);
   else if (mode == FMODE_STAGE)
-    launch_stage_t<FMODE_STAGE, true, AXIS, DYN>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_STAGE, true, AXIS, DYN, PM>(G, K, P, sc, alpha, L);
   else if (!local)
-    launch_stage_t<FMODE_LAST, false, AXIS, DYN>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_LAST, false, AXIS, DYN, PM>(G, K, P, sc, alpha, L);
   else
-    launch_stage_t<FMODE_LAST, true, AXIS, DYN>(G, K, P, sc, alpha, L);
+    launch_stage_t<FMODE_LAST, true, AXIS, DYN, PM>(G, K, P, sc, alpha, L);
 }
 
 void launch_stage_fused(int mode, const Grid& g, const les_params& p, const FusedIO& io,
@@ -1169,6 +1183,7 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   G.ilo = g.glo > 0 ? g.glo : 1;
   G.ihi = g.n[0] - (g.ghi > 0 ? g.ghi : 1);
   const long long N = g.N;
+  G.N = (int)N;  // the mixed forms hold N < 2^31 (checked at creation)
   FusedPtrs P;
   for (int c = 0; c < 5; ++c) {
     P.qin[c] = (const float*)io.Qin + c * N;
@@ -1184,12 +1199,20 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   P.dtl = io.dtl;
   const Consts<float> K = fused_consts<float>(p);
   const bool local = P.dtl != nullptr;
-  if (dyn)  // (not with an axis: rejected at creation)
-    launch_stage_dispatch<false, true>(mode, local, G, K, P, io.sc, alpha, L);
-  else if (p.axis)
-    launch_stage_dispatch<true, false>(mode, local, G, K, P, io.sc, alpha, L);
-  else
-    launch_stage_dispatch<false, false>(mode, local, G, K, P, io.sc, alpha, L);
+  // xi and eta bounded, zeta periodic (every jet grid): an instantiation with
+  // the periodicity fixed at compile time (PM = 4), which folds the face and
+  // wrap tests; other grids read the flags at run time (PM = -1)
+  const bool jet_per = !g.per[0] && !g.per[1] && g.per[2];
+  if (dyn) {  // (not with an axis: rejected at creation)
+    if (jet_per) launch_stage_dispatch<false, true, 4>(mode, local, G, K, P, io.sc, alpha, L);
+    else launch_stage_dispatch<false, true, -1>(mode, local, G, K, P, io.sc, alpha, L);
+  } else if (p.axis) {
+    if (jet_per) launch_stage_dispatch<true, false, 4>(mode, local, G, K, P, io.sc, alpha, L);
+    else launch_stage_dispatch<true, false, -1>(mode, local, G, K, P, io.sc, alpha, L);
+  } else {
+    if (jet_per) launch_stage_dispatch<false, false, 4>(mode, local, G, K, P, io.sc, alpha, L);
+    else launch_stage_dispatch<false, false, -1>(mode, local, G, K, P, io.sc, alpha, L);
+  }
 }
 
 void launch_split(long long count, const double* q, float* hi, float* lo, const Launch& L) {
