@@ -22,7 +22,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas"
               "--expt-relaxed-constexpr"]
 # Per-file flags: the FP32-mixed kernels use approximate FP32 division and
 # square root (FP64 code is unaffected by these flags).
-FILE_FLAGS = {"fused.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
+_FAST_FP32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+FILE_FLAGS = {"fused.cu": _FAST_FP32, "fused_jet12.cu": _FAST_FP32, "fused_jet28.cu": _FAST_FP32}
 
 
 def _nvcc() -> str:
