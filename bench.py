@@ -752,8 +752,8 @@ def run_ours(args, world, rank, local):
 def run_profile_case(which: str):
     """Small case for ncu captures: 96 x 160 x 128 jet (1.97M points, state
     and metrics above the 129 MB L2), two full steps, one precision (the
-    dynamic case: FP64 with the dynamic SGS model); or the adjoint window on
-    96 x 96 x 128 (10 steps, checkpoint every 5)."""
+    dynamic cases: FP64 or FP32-mixed with the dynamic SGS model); or the
+    adjoint window on 96 x 96 x 128 (10 steps, checkpoint every 5)."""
     import numpy as np
     import torch
 
@@ -813,8 +813,8 @@ def run_profile_case(which: str):
         out["oracle_one_step"] = {"seconds": sec, "cores": cores, "gpt_steps_per_s": val}
         print(json.dumps(out))
         return 0
-    prec = lj.PREC_MIXED if which == "mixed" else lj.PREC_FP64
-    sgs = lj.SGS_DYNAMIC if which == "dynamic" else lj.SGS_SMAGORINSKY
+    prec = lj.PREC_MIXED if which in ("mixed", "dynamic_mixed") else lj.PREC_FP64
+    sgs = lj.SGS_DYNAMIC if which in ("dynamic", "dynamic_mixed") else lj.SGS_SMAGORINSKY
     shape = (96, 160, 128)
     ctx = lj.Context(lj.make_params(sgs_model=sgs, precision=prec), shape)
     xyz = torch.from_numpy(lj.synth.jet_grid(*shape)).cuda()
@@ -840,7 +840,8 @@ def main():
                     help="skip the dynamic-SGS / local-step / entrance / metric-form timings")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 1.02e9-point compact mixed leg")
-    ap.add_argument("--profile-case", choices=("fp64", "mixed", "adjoint", "dynamic", "c3"),
+    ap.add_argument("--profile-case", choices=("fp64", "mixed", "adjoint", "dynamic", "dynamic_mixed",
+                                               "c3"),
                     default=None,
                     help="run the small ncu case (two steps) and exit")
     args = ap.parse_args()

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) k_dyn_filter1(Grid g, const R* __restrict
     }
     const long long np = (c[D] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
     const long long nm = (c[D] == 0) ? n + (long long)(nd - 1) * s : n - s;
+#pragma unroll 5
     for (int q = 0; q < count; ++q)
       dst[q * N + n] = R(0.25) * src[q * N + nm] + R(0.5) * src[q * N + n] + R(0.25) * src[q * N + np];
   }
