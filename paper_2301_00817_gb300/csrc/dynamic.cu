@@ -62,8 +62,11 @@ __device__ __forceinline__ R strain(const R gr[3][3], R S[3][3]) {
 __constant__ int kI6[6] = {0, 1, 2, 0, 0, 1};
 __constant__ int kJ6[6] = {0, 1, 2, 1, 2, 2};
 
+// Register bounds (here and on k_dyn_sums): left free, the compiler gave
+// these kernels 230-254 registers, one 256-thread block per SM for a
+// latency-bound pass; the FP32 forms fit 64 (80 for the sums) registers.
 template <typename R, typename TQ, typename TM>
-__global__ void __launch_bounds__(256) k_dyn_products(Grid g, const TQ* __restrict__ Q,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_dyn_products(Grid g, const TQ* __restrict__ Q,
                                                       const TM* __restrict__ M,
                                                       const R* __restrict__ node,
                                                       R* __restrict__ D) {
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(256) k_dyn_favre(long long N, const R* __restr
 // Per interior node the six terms (numerators and denominators of the
 // three coefficients), in R; their J^-1-weighted sums in FP64.
 template <typename R, typename TM>
-__global__ void __launch_bounds__(256) k_dyn_sums(Grid g, const TM* __restrict__ M,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_dyn_sums(Grid g, const TM* __restrict__ M,
                                                   const R* __restrict__ node,
                                                   const R* __restrict__ Fh,
                                                   const R* __restrict__ H,
