@@ -7,9 +7,9 @@
 //   k_dyn_products  per node: the 25 fields the test filter acts on (rho,
 //                   rho u_i, rho T, rho u_i u_j, rho|S| S_ij, rho|S| S_mm,
 //                   rho|S|^2, rho u_j T, rho|S| dT/dx_j);
-//   k_dyn_filter1   the test filter, one direction per pass (zeta, eta, xi:
-//                   the filter is a tensor product, so three 3-point passes
-//                   replace the 27-point sum);
+//   k_dyn_filter3   the test filter (a tensor product of 3-point filters:
+//                   zeta, eta, xi, applied in that order in one pass over
+//                   the fields instead of the 27-point sum);
 //   k_dyn_favre     the Favre-filtered velocity and temperature per node;
 //   k_dyn_sums      per interior node: the strain of the Favre-filtered
 //                   velocity, the Leonard-type terms, and the six
@@ -103,29 +103,90 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_dyn_products(Gr
   }
 }
 
-// One pass of the test filter along direction D for `count` fields:
-// dst = (src_{-1} + 2 src_0 + src_{+1})/4 along D (periodic wrap), the
-// identity at the faces of a non-periodic D.
-template <int D, typename R>
-__global__ void __launch_bounds__(256) k_dyn_filter1(Grid g, const R* __restrict__ src,
-                                                     int count, R* __restrict__ dst) {
+// The test filter's three directions in one kernel.  A CTA owns a tile of
+// kF3J x kF3K (eta, zeta) columns and a range of planes [i0, i1), and takes
+// the fields NB at a time.  For each group it marches along xi over planes
+// i0 - 1 .. i1: it stages the plane's tile with a one-node halo in shared
+// memory, filters along zeta over the halo rows, then along eta, and keeps
+// the last three of its column's 2-D-filtered values in registers to
+// filter along xi.  Each output takes the same operations in the same order
+// as three one-direction passes would (zeta, eta, xi; identity at the faces
+// of a non-periodic direction).  Traffic: each field read once (with the
+// tile and chunk halos) and written once, against three reads and three
+// writes for separate passes; the NB fields of a group share the barriers
+// and keep several loads in flight per thread (one field at a time was
+// latency-bound: 40% slower than three passes).
+constexpr int kF3J = 8, kF3K = 32;  // tile rows (eta) x columns (zeta); 256 threads
+
+template <typename R, int NB>
+__global__ void __launch_bounds__(kF3J * kF3K) k_dyn_filter3(Grid g, const R* __restrict__ src,
+                                                             int count, int nch,
+                                                             R* __restrict__ dst) {
+  __shared__ R S[NB][kF3J + 2][kF3K + 2];  // the plane's tile with a one-node halo
+  __shared__ R Z[NB][kF3J + 2][kF3K];      // filtered along zeta, rows -1 .. kF3J
   const long long N = g.N;
-  const long long s = g.stride[D];
-  const int nd = g.n[D];
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    decompose(g, n, c);
-    const bool face = !g.per[D] && (c[D] == 0 || c[D] == nd - 1);
-    if (face) {
-      for (int q = 0; q < count; ++q) dst[q * N + n] = src[q * N + n];
-      continue;
+  const int ni = g.n[0], nj = g.n[1], nk = g.n[2];
+  const int tx = threadIdx.x % kF3K, ty = threadIdx.x / kF3K;
+  const int k0 = blockIdx.x * kF3K, j0 = blockIdx.y * kF3J;
+  const int i0 = (int)((long long)blockIdx.z * ni / nch);
+  const int i1 = (int)((long long)(blockIdx.z + 1) * ni / nch);
+  const int j = j0 + ty, k = k0 + tx;
+  const bool own = j < nj && k < nk;
+  auto wrap = [](int v, int n, int per) {  // -1 outside a non-periodic range
+    if (per) return ((v % n) + n) % n;     // (a tile may span several periods)
+    return (v >= 0 && v < n) ? v : -1;
+  };
+  const bool jface = !g.per[1] && (j == 0 || j == nj - 1);
+  for (int f0 = 0; f0 < count; f0 += NB) {  // NB fields at a time (count % NB == 0)
+    R em[NB], ec[NB];  // 2-D-filtered values of planes x - 2, x - 1
+#pragma unroll
+    for (int b = 0; b < NB; ++b) em[b] = ec[b] = R(0);
+    for (int x = i0 - 1; x <= i1; ++x) {
+      const int ig = wrap(x, ni, g.per[0]);
+      R e[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) e[b] = R(0);
+      if (ig >= 0) {  // (uniform over the CTA)
+        const long long pbase = (long long)ig * nj * nk;
+        for (int q = threadIdx.x; q < (kF3J + 2) * (kF3K + 2); q += blockDim.x) {
+          const int r = q / (kF3K + 2), c = q - r * (kF3K + 2);
+          const int jg = wrap(j0 - 1 + r, nj, g.per[1]), kg = wrap(k0 - 1 + c, nk, g.per[2]);
+          const bool in = jg >= 0 && kg >= 0;
+          const long long off = pbase + (long long)jg * nk + kg;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) S[b][r][c] = in ? src[(long long)(f0 + b) * N + off] : R(0);
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < (kF3J + 2) * kF3K; q += blockDim.x) {
+          const int r = q / kF3K, c = q - r * kF3K;
+          const int kk = k0 + c;
+          const bool face = !g.per[2] && (kk == 0 || kk == nk - 1);
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            Z[b][r][c] = face ? S[b][r][c + 1]
+                              : R(0.25) * S[b][r][c] + R(0.5) * S[b][r][c + 1] + R(0.25) * S[b][r][c + 2];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          e[b] = jface ? Z[b][ty + 1][tx]
+                       : R(0.25) * Z[b][ty][tx] + R(0.5) * Z[b][ty + 1][tx] + R(0.25) * Z[b][ty + 2][tx];
+      }
+      // plane x - 1 has both xi neighbours now
+      const int xo = x - 1;
+      if (xo >= i0 && xo < i1 && own) {
+        const bool face = !g.per[0] && (xo == 0 || xo == ni - 1);
+        const long long o = (long long)xo * nj * nk + (long long)j * nk + k;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          dst[(long long)(f0 + b) * N + o] = face ? ec[b] : R(0.25) * em[b] + R(0.5) * ec[b] + R(0.25) * e[b];
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        em[b] = ec[b];
+        ec[b] = e[b];
+      }
     }
-    const long long np = (c[D] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
-    const long long nm = (c[D] == 0) ? n + (long long)(nd - 1) * s : n - s;
-#pragma unroll 5
-    for (int q = 0; q < count; ++q)
-      dst[q * N + n] = R(0.25) * src[q * N + nm] + R(0.5) * src[q * N + n] + R(0.25) * src[q * N + np];
   }
 }
 
@@ -267,13 +328,20 @@ static void dynamic_t(const Grid& g, const les_params& p, const TQ* Q, const TM*
   R* D = scratch;                                 // products, then the eta pass
   R* T = scratch + (long long)kDynFields * g.N;  // zeta pass, then the filtered fields
   k_dyn_products<R, TQ, TM><<<nb, th, 0, L.s>>>(g, Q, M, node, D);
-  k_dyn_filter1<2, R><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
-  k_dyn_filter1<1, R><<<nb, th, 0, L.s>>>(g, T, kDynFields, D);
-  k_dyn_filter1<0, R><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
+  {
+    // the test filter in one pass (k_dyn_filter3): enough axial chunks for
+    // about eight CTAs per SM
+    const int tk = (g.n[2] + kF3K - 1) / kF3K, tj = (g.n[1] + kF3J - 1) / kF3J;
+    const long long want = 8LL * sm_count();
+    int nch = (int)((want + (long long)tk * tj - 1) / ((long long)tk * tj));
+    nch = nch < 1 ? 1 : (nch > g.n[0] ? g.n[0] : nch);
+    static_assert(kDynFields % 5 == 0, "the filter takes the fields five at a time");
+    k_dyn_filter3<R, 5><<<dim3(tk, tj, nch), kF3J * kF3K, 0, L.s>>>(g, D, kDynFields, nch, T);
+  }
   k_dyn_favre<R><<<nb, th, 0, L.s>>>(g.N, T, D);  // D is free again: u^, v^, w^, T^
   k_dyn_sums<R, TM><<<kRedBlocks, kRedThreads, 0, L.s>>>(g, M, node, T, D, partials);
   k_dyn_final<<<1, 32 * kDynSums, 0, L.s>>>(partials, p.Pr_sgs, sc);
-  *L.counter += 7;
+  *L.counter += 5;
 }
 
 void launch_dynamic64(const Grid& g, const les_params& p, const StageIO64& io, double* scratch,
