@@ -54,10 +54,6 @@ struct les_ctx {
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[PK_COUNT];
   unsigned long long prof_n[PK_COUNT];
-  // a second stream (created on first use) on which the end of a host-buffer
-  // run computes the totals while the main stream writes the state back
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -424,9 +420,6 @@ int les_destroy(les_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
-  if (c->side) cudaStreamDestroy(c->side);
   delete c;
   return LES_OK;
 }
@@ -874,33 +867,6 @@ const void* mapped_host(const void* host, size_t bytes) {
   return a.devicePointer;
 }
 
-// Fork work after everything queued on s onto the context's side stream
-// (created on first use); s itself when the stream or its events cannot be
-// made.  side_join makes s wait for what was queued on ts.
-static cudaStream_t side_fork(les_ctx* c, cudaStream_t s) {
-  if (!c->side) {
-    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-      if (c->side) cudaStreamDestroy(c->side);
-      c->side = nullptr;
-      c->ev_fork = c->ev_join = nullptr;
-      return s;
-    }
-  }
-  cudaEventRecord(c->ev_fork, s);
-  cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-  return c->side;
-}
-
-static void side_join(les_ctx* c, cudaStream_t ts, cudaStream_t s) {
-  if (ts == s) return;
-  cudaEventRecord(c->ev_join, ts);
-  cudaStreamWaitEvent(s, c->ev_join, 0);
-}
-
 int les_run_host(les_ctx* c, int n, double* Q_host, double* Q_dev, les_diag* diag,
                  les_stream_t stream) {
   int rc = ready(c);
@@ -918,23 +884,19 @@ int les_run_host(les_ctx* c, int n, double* Q_host, double* Q_dev, les_diag* dia
       lesjet::Launch L{s, &c->launches};
       split_state(c, Qm, L);
       for (int i = 0; i < n; ++i) rk_step(c, Qm, s);
-      // the totals (FP64-pipe bound, reading the float pair) run on the side
-      // stream while the join writes the state back over the host link
-      cudaStream_t ts = side_fork(c, s);
       {
-        lesjet::Launch Lt{ts, &c->launches};
-        ProfScope ps(c, PK_TOTALS, ts);
+        // one pass joins the state into the host buffer and sums the totals:
+        // their FP64 arithmetic hides under the write-back over the host link
+        ProfScope ps(c, PK_CONVERT, s);
         if (has_m64(c))
-          lesjet::launch_totals_hl(c->g, at<float>(c, c->off_hi), at<float>(c, c->off_lo),
-                                   at<double>(c, c->off_m64), at<double>(c, c->off_part),
-                                   at<DevScalars>(c, c->off_sc), Lt);
+          lesjet::launch_join_totals_hl(c->g, at<float>(c, c->off_hi), at<float>(c, c->off_lo),
+                                        at<double>(c, c->off_m64), Qm, at<double>(c, c->off_part),
+                                        at<DevScalars>(c, c->off_sc), L);
         else
-          lesjet::launch_totals_hl(c->g, at<float>(c, c->off_hi), at<float>(c, c->off_lo),
-                                   at<float>(c, c->off_m32), at<double>(c, c->off_part),
-                                   at<DevScalars>(c, c->off_sc), Lt);
+          lesjet::launch_join_totals_hl(c->g, at<float>(c, c->off_hi), at<float>(c, c->off_lo),
+                                        at<float>(c, c->off_m32), Qm, at<double>(c, c->off_part),
+                                        at<DevScalars>(c, c->off_sc), L);
       }
-      join_state(c, Qm, L);
-      side_join(c, ts, s);
       return finish_run(c, n, diag, s);
     }
   }

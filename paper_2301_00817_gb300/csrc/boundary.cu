@@ -275,17 +275,26 @@ struct ViewHL {
 };
 
 // Block partials of sum_n J^-1 Q_c (grid-stride order fixed by the launch).
-template <class View, typename TM>
+// JOIN: every node's state as read (for the float pair, the FP64 value hi +
+// lo) is also written to qout, so one pass both joins the state and sums it.
+template <class View, typename TM, bool JOIN = false>
 __global__ void k_totals_partial(Grid g, View Q, const TM* __restrict__ M,
-                                 double* __restrict__ partials) {
+                                 double* __restrict__ partials, double* __restrict__ qout = nullptr) {
   const long long N = g.N;
   double s[5] = {0, 0, 0, 0, 0};
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
+    double v[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) v[q] = Q.ld(q * N + n);
+    if (JOIN) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) qout[q * N + n] = v[q];
+    }
     if ((g.glo | g.ghi) != 0 && !owned_plane(g, (int)(n / g.stride[0]))) continue;  // a slab sums its own planes
     const double jv = (double)M[9 * N + n];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) s[q] += jv * Q.ld(q * N + n);
+    for (int q = 0; q < 5; ++q) s[q] += jv * v[q];
   }
   __shared__ double red[5][32];
 #pragma unroll
@@ -410,6 +419,25 @@ void launch_totals_hl(const Grid& g, const float* hi, const float* lo, const dou
 void launch_totals_hl(const Grid& g, const float* hi, const float* lo, const float* M32,
                       double* partials, DevScalars* sc, const Launch& L) {
   totals_t(g, ViewHL{hi, lo}, M32, partials, sc, L);
+}
+
+template <typename TM>
+static void join_totals_t(const Grid& g, const float* hi, const float* lo, const TM* M, double* q,
+                          double* partials, DevScalars* sc, const Launch& L) {
+  k_totals_partial<ViewHL, TM, true><<<kRedBlocks, kRedThreads, 0, L.s>>>(g, ViewHL{hi, lo}, M,
+                                                                        partials, q);
+  k_totals_final<<<1, 160, 0, L.s>>>(partials, sc);
+  *L.counter += 2;
+}
+
+void launch_join_totals_hl(const Grid& g, const float* hi, const float* lo, const double* M64,
+                           double* q, double* partials, DevScalars* sc, const Launch& L) {
+  join_totals_t(g, hi, lo, M64, q, partials, sc, L);
+}
+
+void launch_join_totals_hl(const Grid& g, const float* hi, const float* lo, const float* M32,
+                           double* q, double* partials, DevScalars* sc, const Launch& L) {
+  join_totals_t(g, hi, lo, M32, q, partials, sc, L);
 }
 
 void launch_set_time(DevScalars* sc, double t, const Launch& L) {

@@ -7,9 +7,10 @@
 //   k_dyn_products  per node: the 25 fields the test filter acts on (rho,
 //                   rho u_i, rho T, rho u_i u_j, rho|S| S_ij, rho|S| S_mm,
 //                   rho|S|^2, rho u_j T, rho|S| dT/dx_j);
-//   k_dyn_filter3   the test filter (a tensor product of 3-point filters:
-//                   zeta, eta, xi, applied in that order in one pass over
-//                   the fields instead of the 27-point sum);
+//   k_dyn_filter3   the test filter (a tensor product of 3-point filters,
+//                   applied along zeta, eta, xi in that order) in one pass
+//                   over the FP32 fields; k_dyn_filter1, one direction per
+//                   pass, for the FP64 fields;
 //   k_dyn_favre     the Favre-filtered velocity and temperature per node;
 //   k_dyn_sums      per interior node: the strain of the Favre-filtered
 //                   velocity, the Leonard-type terms, and the six
@@ -100,6 +101,32 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_dyn_products(Gr
       D[(19 + j) * N + n] = rho * vel[j] * T;
       D[(22 + j) * N + n] = rho * Sm * dT[j];
     }
+  }
+}
+
+// One pass of the test filter along direction D for `count` fields:
+// dst = (src_{-1} + 2 src_0 + src_{+1})/4 along D (periodic wrap), the
+// identity at the faces of a non-periodic D.
+template <int D, typename R>
+__global__ void __launch_bounds__(256) k_dyn_filter1(Grid g, const R* __restrict__ src,
+                                                     int count, R* __restrict__ dst) {
+  const long long N = g.N;
+  const long long s = g.stride[D];
+  const int nd = g.n[D];
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    decompose(g, n, c);
+    const bool face = !g.per[D] && (c[D] == 0 || c[D] == nd - 1);
+    if (face) {
+      for (int q = 0; q < count; ++q) dst[q * N + n] = src[q * N + n];
+      continue;
+    }
+    const long long np = (c[D] == nd - 1) ? n - (long long)(nd - 1) * s : n + s;
+    const long long nm = (c[D] == 0) ? n + (long long)(nd - 1) * s : n - s;
+#pragma unroll 5
+    for (int q = 0; q < count; ++q)
+      dst[q * N + n] = R(0.25) * src[q * N + nm] + R(0.5) * src[q * N + n] + R(0.25) * src[q * N + np];
   }
 }
 
@@ -328,20 +355,28 @@ static void dynamic_t(const Grid& g, const les_params& p, const TQ* Q, const TM*
   R* D = scratch;                                 // products, then the eta pass
   R* T = scratch + (long long)kDynFields * g.N;  // zeta pass, then the filtered fields
   k_dyn_products<R, TQ, TM><<<nb, th, 0, L.s>>>(g, Q, M, node, D);
-  {
-    // the test filter in one pass (k_dyn_filter3): enough axial chunks for
-    // about eight CTAs per SM
+  if constexpr (sizeof(R) == 4) {
+    // FP32 fields: the test filter in one pass (k_dyn_filter3), with enough
+    // axial chunks for about eight CTAs per SM
     const int tk = (g.n[2] + kF3K - 1) / kF3K, tj = (g.n[1] + kF3J - 1) / kF3J;
     const long long want = 8LL * sm_count();
     int nch = (int)((want + (long long)tk * tj - 1) / ((long long)tk * tj));
     nch = nch < 1 ? 1 : (nch > g.n[0] ? g.n[0] : nch);
     static_assert(kDynFields % 5 == 0, "the filter takes the fields five at a time");
     k_dyn_filter3<R, 5><<<dim3(tk, tj, nch), kF3J * kF3K, 0, L.s>>>(g, D, kDynFields, nch, T);
+    *L.counter += 1;
+  } else {
+    // FP64 fields: three one-direction passes (the one-pass kernel is bound
+    // by its FP64 work and latency there: 1.24 against 0.86 ms on 1.97M points)
+    k_dyn_filter1<2, R><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
+    k_dyn_filter1<1, R><<<nb, th, 0, L.s>>>(g, T, kDynFields, D);
+    k_dyn_filter1<0, R><<<nb, th, 0, L.s>>>(g, D, kDynFields, T);
+    *L.counter += 3;
   }
   k_dyn_favre<R><<<nb, th, 0, L.s>>>(g.N, T, D);  // D is free again: u^, v^, w^, T^
   k_dyn_sums<R, TM><<<kRedBlocks, kRedThreads, 0, L.s>>>(g, M, node, T, D, partials);
   k_dyn_final<<<1, 32 * kDynSums, 0, L.s>>>(partials, p.Pr_sgs, sc);
-  *L.counter += 5;
+  *L.counter += 4;
 }
 
 void launch_dynamic64(const Grid& g, const les_params& p, const StageIO64& io, double* scratch,

@@ -138,6 +138,12 @@ void launch_totals(const Grid& g, const double* Q, const float* M32, double* par
 // totals of the mixed form's float pair state (hi + lo)
 void launch_totals_hl(const Grid& g, const float* hi, const float* lo, const double* M64,
                       double* partials, DevScalars* sc, const Launch& L);
+// the float pair joined into q ([5][N] FP64, e.g. mapped host memory) and
+// summed in the same pass (totals_hl's sums, bit for bit)
+void launch_join_totals_hl(const Grid& g, const float* hi, const float* lo, const double* M64,
+                           double* q, double* partials, DevScalars* sc, const Launch& L);
+void launch_join_totals_hl(const Grid& g, const float* hi, const float* lo, const float* M32,
+                           double* q, double* partials, DevScalars* sc, const Launch& L);
 void launch_totals_hl(const Grid& g, const float* hi, const float* lo, const float* M32,
                       double* partials, DevScalars* sc, const Launch& L);
 void launch_set_time(DevScalars* sc, double t, const Launch& L);
