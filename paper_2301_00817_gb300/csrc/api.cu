@@ -271,7 +271,9 @@ void join_state(les_ctx* c, double* Q, const lesjet::Launch& L) {
 
 // mu_eff/kappa_eff of the float state (frozen for the step) and the block
 // minima of the CFL step; sc == nullptr leaves the status word alone.
-void prestep32(les_ctx* c, const float* Qs, DevScalars* sc, const lesjet::Launch& L) {
+// finalize >= 0: the prestep kernel also sets dt (advance = finalize).
+void prestep32(les_ctx* c, const float* Qs, DevScalars* sc, const lesjet::Launch& L,
+               int finalize = -1) {
   const double* dyn = nullptr;
   if (c->dyn_ws) {
     // the dynamic procedure on the float state: coefficients into dyn[6..8]
@@ -287,7 +289,7 @@ void prestep32(les_ctx* c, const float* Qs, DevScalars* sc, const lesjet::Launch
   // prestep (the one that also takes the CFL minima, sc != nullptr)
   float* dtl = (sc && c->p.dt_mode == LES_DT_LOCAL) ? at<float>(c, c->off_dtl) : nullptr;
   lesjet::launch_prestep(c->g, c->p, Qs, at<float>(c, c->off_m32), at<float>(c, c->off_mk),
-                         at<double>(c, c->off_part), sc, dtl, dyn, L);
+                         at<double>(c, c->off_part), sc, dtl, dyn, L, finalize);
 }
 
 lesjet::FusedIO fused_io(les_ctx* c, const void* Qin, void* out) {
@@ -330,11 +332,7 @@ void rk_step(les_ctx* c, double* Q, cudaStream_t s) {
   float* hi = at<float>(c, c->off_hi);
   float* SA = at<float>(c, c->off_sa);
   float* SB = at<float>(c, c->off_sb);
-  prestep32(c, hi, sc, L);
-  {
-    ProfScope ps(c, PK_DT, s);
-    lesjet::launch_dt_finalize(c->p, at<double>(c, c->off_part), sc, 1, L);
-  }
+  prestep32(c, hi, sc, L, 1);  // its last block takes the step and advances t
   for (int l = 1; l <= 5; ++l) {
     const float* in = (l == 1) ? hi : ((l % 2 == 0) ? SA : SB);
     float* out = (l == 5) ? nullptr : ((l % 2 == 1) ? SA : SB);

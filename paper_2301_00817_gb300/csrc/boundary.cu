@@ -328,6 +328,7 @@ __global__ void k_set_time(DevScalars* sc, double t) {
   sc->dt = 0.0;
   sc->status = 0;
   sc->steps = 0;
+  sc->ticket = 0;
 }
 
 static int nblocks(long long count) {

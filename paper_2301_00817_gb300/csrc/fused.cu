@@ -29,14 +29,16 @@ __global__ void k_join(long long count, const float* __restrict__ hi, const floa
 
 void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
                     float* mk, double* partials, DevScalars* sc, float* dtl, const double* dyn,
-                    const Launch& L) {
+                    const Launch& L, int finalize) {
+  // finalize >= 0: the kernel's last block also takes the step (advance = finalize)
+  const int fm = finalize >= 0 ? p.dt_mode : -1;
   const Consts<float> K = fused_consts<float>(p);
   if (p.sgs_model == LES_SGS_DYNAMIC)
     k_prestep<float, float, float, true><<<kRedBlocks, kRedThreads, 0, L.s>>>(
-        g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl, dyn);
+        g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl, dyn, fm, p.cfl, p.dt_fixed, finalize);
   else
     k_prestep<float, float, float, false><<<kRedBlocks, kRedThreads, 0, L.s>>>(
-        g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl, dyn);
+        g, K, Q0, M, mk, partials, sc, dtl, (float)p.cfl, dyn, fm, p.cfl, p.dt_fixed, finalize);
   ++*L.counter;
   if (p.axis) {
     k_mu_axis<float, TempFromState<float, float>><<<g.n[0], 128, g.n[2] * sizeof(float), L.s>>>(

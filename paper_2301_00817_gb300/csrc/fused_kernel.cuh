@@ -190,7 +190,9 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
                                                  double* __restrict__ partials,
                                                  DevScalars* __restrict__ sc,
                                                  R* __restrict__ dtl, R cfl,
-                                                 const double* __restrict__ dyn = nullptr) {
+                                                 const double* __restrict__ dyn = nullptr,
+                                                 int fin_mode = -1, double fin_cfl = 0.0,
+                                                 double fin_dt = 0.0, int fin_advance = 0) {
   const long long N = g.N;
   R local_min = R(1e30);
   int bad = 0;
@@ -365,6 +367,47 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
     if (threadIdx.x == 0) {
       partials[blockIdx.x] = (double)mm;
       if (bb && sc) atomicOr(&sc->status, 1);
+    }
+  }
+  // fin_mode >= 0 (and sc): the last block to finish takes the step, as
+  // k_dt_finalize would in a launch of its own: the minimum over every
+  // block's partial (exact in any order), dt = cfl x that (or the fixed
+  // step), the status, and t^{n+1} when fin_advance
+  if (fin_mode >= 0 && sc) {
+    __shared__ int last;
+    __shared__ double dmin[32];
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      double m = 1.0e300;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmin(m, __ldcg(partials + b));
+      for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if ((threadIdx.x & 31) == 0) dmin[threadIdx.x >> 5] = m;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? dmin[threadIdx.x] : 1.0e300;
+        for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (threadIdx.x == 0) {
+          double dt = (fin_mode == LES_DT_FIXED) ? fin_dt : fin_cfl * m;
+          const int status = atomicOr(&sc->status, 0);
+          if (!(dt > 0.0) || !(dt < 1.0e300)) {
+            sc->status = LES_ERR_NONFINITE;
+            dt = 0.0;
+          } else if (status != 0) {
+            sc->status = LES_ERR_NONFINITE;
+          }
+          sc->dt = dt;
+          if (fin_advance) {
+            sc->t += dt;
+            sc->steps += 1;
+          }
+          sc->ticket = 0;
+        }
+      }
     }
   }
 }

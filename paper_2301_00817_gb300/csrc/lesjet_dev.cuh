@@ -48,6 +48,9 @@ struct DevScalars {
   double dt;         // current step
   int status;        // LES_OK or LES_ERR_NONFINITE (sticky)
   int steps;
+  unsigned int ticket;  // blocks of a reduction that have finished (its last
+                        // block finalises and resets it to 0)
+  int pad_;
   double totals[5];
   double dyn[9];     // dynamic SGS procedure: 6 averaged terms, C_ds, C_I, Pr_sgs
 };

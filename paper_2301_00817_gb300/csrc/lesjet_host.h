@@ -85,9 +85,11 @@ struct FusedIO {
 // mixed form: mu_eff/kappa_eff and CFL block minima of the float state
 // dyn: the dynamic procedure's coefficients (device) with LES_SGS_DYNAMIC,
 // else nullptr
+// finalize >= 0 (with sc): the kernel's last block also sets dt from the
+// block minima, as launch_dt_finalize(p, partials, sc, finalize) would
 void launch_prestep(const Grid& g, const les_params& p, const float* Q0, const float* M,
                     float* mk, double* partials, DevScalars* sc, float* dtl, const double* dyn,
-                    const Launch& L);
+                    const Launch& L, int finalize = -1);
 // mode 0: residual into io.out (double); 1: stage update into io.out;
 // 2: last stage, Q^(0) (hi, lo) updated in place with compensated sums
 void launch_stage_fused(int mode, const Grid& g, const les_params& p, const FusedIO& io,
