@@ -55,6 +55,8 @@ void launch_stage_fused(int mode, const Grid& g, const les_params& p, const Fuse
   G.nk = g.n[2];
   for (int d = 0; d < 3; ++d) G.per[d] = g.per[d];
   G.nch = 1;
+  G.n1 = 0;
+  G.a1 = 0;
   G.vec16 = (g.per[2] && g.n[2] % 4 == 0 && g.n[2] >= FTK) ? 1 : 0;
   // inside the physical faces and, for an axial slab, its own planes
   G.ilo = g.glo > 0 ? g.glo : 1;

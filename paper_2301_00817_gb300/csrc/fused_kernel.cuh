@@ -493,7 +493,9 @@ struct FusedPtrs {
 struct FusedGeom {
   int ni, nj, nk;
   int per[3];
-  int nch;  // axial chunks; chunk z holds planes [z ni / nch, (z + 1) ni / nch)
+  // axial chunks: the first n1 hold a1 planes each, the other nch - n1
+  // split the remaining planes evenly (n1 = 0: nch chunks of equal length)
+  int nch, n1, a1;
   int vec16;  // zeta periodic, nk % 4 == 0 and nk >= FTK: tiles shifted by
               // two columns, rows staged as 16-byte copies
   int ilo, ihi;  // planes the stage updates along a non-periodic xi: [ilo, ihi)
@@ -545,8 +547,18 @@ __global__ void __launch_bounds__(FNT, 1)
   // column 0 (kt + 2 with the shifted tiling; may exceed nk - 1, wrapped)
   const bool vec_ok = PM >= 0 ? ((PM >> 3) & 1) != 0 : G.vec16 != 0;
   const int kt = blockIdx.x * FTK, k0 = kt + (vec_ok ? 2 : 0), j0 = blockIdx.y * FTJ;
-  const int ib = (int)((long long)blockIdx.z * ni / G.nch);
-  const int ie = (int)((long long)(blockIdx.z + 1) * ni / G.nch);
+  int ib, ie;
+  {
+    const int z = blockIdx.z, b = G.n1 * G.a1;
+    if (z < G.n1) {
+      ib = z * G.a1;
+      ie = ib + G.a1;
+    } else {
+      const int n2 = G.nch - G.n1, z2 = z - G.n1;
+      ib = b + (int)((long long)z2 * (ni - b) / n2);
+      ie = b + (int)((long long)(z2 + 1) * (ni - b) / n2);
+    }
+  }
   const int jown = j0 + ty;
   const int kown = (k0 + tx < nk) ? k0 + tx : k0 + tx - nk;  // wraps in the shifted case only
   const bool own = (PM >= 0 && ((PM >> 4) & 1)) ? true : (jown < nj && kt + tx < nk);
@@ -1101,40 +1113,90 @@ static Consts<R> fused_consts(const les_params& p) {
   return K;
 }
 
-// Number of axial chunks.  CTAs are dispatched chunk-major (all tiles of a
-// chunk together, which keeps neighbouring tiles' halo rows in L2) and take
-// (chunk planes + one plane of prologue) each; the count minimises the
-// finishing time of a greedy list schedule of the CTAs on the SMs, simulated
-// once per grid shape and cached.
-static int choose_nch(int ni, int tiles, int slots) {
+// Axial chunks.  CTAs are dispatched chunk-major (all tiles of a chunk
+// together, which keeps neighbouring tiles' halo rows in L2); a CTA takes its
+// chunk's planes plus a prologue worth about 1.5 planes (three planes staged,
+// two derived, one xi flux: the cost per plane that makes the measured launch
+// times of the 288 x 160 x 128 and 576 x 320 x 256 jets agree).  Chunk
+// lengths come from a two-level family: n1 chunks of a1 planes first, then
+// the other planes split evenly over n2 chunks (n1 = 0: equal chunks).  Long
+// chunks first leave the short ones to fill the last wave.  The choice
+// minimises the finishing time of a greedy list schedule of the CTAs on the
+// SMs, simulated once per grid shape and cached.
+struct Chunks {
+  int nch, n1, a1;
+};
+
+static double chunk_schedule(int ni, int n1, int a1, int n2, int tiles, int slots, double pro) {
+  // SM free time -> number of SMs free at that time (times are multiples of
+  // 0.5, exact in double); each CTA goes to the earliest free SM
+  std::map<double, long long> fr;
+  fr[0.0] = slots;
+  double t_end = 0.0;
+  const long long b = (long long)n1 * a1, rest = ni - b;
+  for (int z = 0; z < n1 + n2; ++z) {
+    const long long len =
+        z < n1 ? a1 : (z - n1 + 1) * rest / n2 - (long long)(z - n1) * rest / n2;
+    const double d = (double)len + pro;
+    long long need = tiles;
+    while (need > 0) {
+      auto it = fr.begin();
+      const double t = it->first;
+      const long long take = need < it->second ? need : it->second;
+      if (take == it->second)
+        fr.erase(it);
+      else
+        it->second -= take;
+      fr[t + d] += take;
+      need -= take;
+      if (t + d > t_end) t_end = t + d;
+    }
+  }
+  return t_end;
+}
+
+static Chunks choose_chunks(int ni, int tiles, int slots) {
   static std::mutex mu;
-  static std::map<std::pair<int, int>, int> cache;
+  static std::map<std::pair<int, int>, Chunks> cache;
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find({ni, tiles});
     if (it != cache.end()) return it->second;
   }
-  int best = 1;
+  const double pro = 1.5;
+  const long long cap = 24LL * slots;  // at most 24 waves of CTAs
+  Chunks best{1, 0, 0};
   double best_t = 1e300;
-  const int max_nch = ni < 64 ? ni : 64;
-  std::vector<double> busy;
-  for (int nch = 1; nch <= max_nch; ++nch) {
-    if ((long long)tiles * nch > 24LL * slots) break;  // beyond 24 waves
-    std::priority_queue<double, std::vector<double>, std::greater<double>> q;
-    for (int s = 0; s < slots; ++s) q.push(0.0);
-    double t_end = 0.0;
-    for (int z = 0; z < nch; ++z) {
-      const double d = (double)((long long)(z + 1) * ni / nch - (long long)z * ni / nch) + 1.0;
-      for (int tile = 0; tile < tiles; ++tile) {
-        const double t = q.top() + d;
-        q.pop();
-        q.push(t);
-        if (t > t_end) t_end = t;
-      }
+  auto consider = [&](int n1, int a1, int n2) {
+    const double t = chunk_schedule(ni, n1, a1, n2, tiles, slots, pro);
+    if (t < best_t - 1e-9) {
+      best_t = t;
+      best = Chunks{n1 + n2, n1, a1};
     }
-    if (t_end < best_t - 1e-9) {
-      best_t = t_end;
-      best = nch;
+  };
+  const int max_nch = ni < 64 ? ni : 64;
+  for (int n2 = 1; n2 <= max_nch; ++n2) {
+    if (n2 > 1 && (long long)tiles * n2 > cap) break;
+    consider(0, 0, n2);
+  }
+  // long chunks about as long as the whole schedule over w waves of them
+  const double ideal = (double)ni * tiles / slots + pro;
+  for (int n1 = 1; n1 <= 16 && n1 <= max_nch; ++n1) {
+    if ((long long)tiles * n1 > cap) break;
+    for (int w = 1; w <= 8; ++w) {
+      const int a0 = (int)(ideal / w - pro);
+      for (int a1 = a0 - 3; a1 <= a0 + 3; ++a1) {
+        if (a1 < 1 || (long long)n1 * a1 > ni) continue;
+        const int rest = ni - n1 * a1;
+        if (rest == 0) {
+          consider(n1, a1, 0);
+          continue;
+        }
+        for (int n2 = 1; n2 <= rest && n1 + n2 <= max_nch; ++n2) {
+          if ((long long)tiles * (n1 + n2) > cap) break;
+          consider(n1, a1, n2);
+        }
+      }
     }
   }
   std::lock_guard<std::mutex> lk(mu);
@@ -1159,7 +1221,10 @@ static void launch_stage_t(const FusedGeom& G0, const Consts<float>& K, const Fu
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   const int tk = (G.nk + FTK - 1) / FTK, tj = (G.nj + FTJ - 1) / FTJ;
-  G.nch = choose_nch(G.ni, tk * tj, sm_count());  // one CTA per SM
+  const Chunks ch = choose_chunks(G.ni, tk * tj, sm_count());  // one CTA per SM
+  G.nch = ch.nch;
+  G.n1 = ch.n1;
+  G.a1 = ch.a1;
   dim3 grid(tk, tj, G.nch);
   k_stage_fused<MODE, LOCAL, AXIS, DYN, PM><<<grid, FNT, smem, L.s>>>(G, K, P, sc, alpha);
   ++*L.counter;
