@@ -59,6 +59,21 @@ __device__ __forceinline__ void load_prim(const Acc& Q, long long N, long long n
 // branches by q_n,e/a_e.  Returns true for the supersonic exit (the caller
 // copies the neighbour's conserved values); otherwise the primitives of the
 // boundary state are in f = (rho, u, v, w, p).
+// x^(2/(gamma-1)).  When 2/(gamma-1) is an integer up to 8 (gamma = 1.4: 5;
+// gamma = 5/3: 3) the power is taken by repeated multiplication: it differs
+// from pow(x, 2/(gamma-1)) only by the rounding of the computed exponent
+// (about 1e-16 relative for x near 1), at a small fraction of FP64 pow's
+// cost on a GPU whose FP64 rate is 1/64 of its FP32 rate.
+__device__ __forceinline__ double pow_entropy(double x, double e) {
+  const double n = rint(e);
+  if (fabs(e - n) < 1e-12 && n >= 1.0 && n <= 8.0) {
+    double r = x;
+    for (int i = 1; i < (int)n; ++i) r *= x;
+    return r;
+  }
+  return pow(x, e);
+}
+
 __device__ __forceinline__ bool far_field_state(double gamma, double rho, double u, double v,
                                                 double w, double p, double nx, double ny,
                                                 double nz, double f[5]) {
@@ -75,7 +90,7 @@ __device__ __forceinline__ bool far_field_state(double gamma, double rho, double
     // entropy of the interior node: rho_f = (rho_e^gamma a_f^2/(gamma p_e))^(1/(gamma-1))
     // = rho_e (a_f/a_e)^(2/(gamma-1)), one power instead of two
     const double dq = qnf - qne;
-    const double rf = rho * pow(af / ae, 2.0 / gm1);
+    const double rf = rho * pow_entropy(af / ae, 2.0 / gm1);
     f[0] = rf;
     f[1] = u + dq * nx;
     f[2] = v + dq * ny;
@@ -83,7 +98,7 @@ __device__ __forceinline__ bool far_field_state(double gamma, double rho, double
     f[4] = rf * af * af / gamma;
   } else if (Mn > -1.0) {
     // free-stream entropy (rho = 1, p = 1/gamma): rho_f = a_f^(2/(gamma-1))
-    const double rf = pow(af, 2.0 / gm1);
+    const double rf = pow_entropy(af, 2.0 / gm1);
     f[0] = rf;
     f[1] = qnf * nx;
     f[2] = qnf * ny;
@@ -106,16 +121,19 @@ __device__ __forceinline__ bool far_field_state(double gamma, double rho, double
 // relations (u = target, v and w from (1, j, k), T = T_t/(1 + (gamma-1)
 // |u|^2/2) with the jet's T_t = 1 + (gamma-1) Mj^2/2, p = T^(gamma/(gamma-1))
 // /gamma).  The plane i = 1 is read before any other boundary kernel runs.
+// (blk, nblk: this block's index among the nblk blocks given to the part)
 template <class Acc, typename TM>
-__global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
-                            const TM* __restrict__ M, const DevScalars* __restrict__ sc,
-                            int use_host_t, double t_host, Acc Q) {
+__device__ __forceinline__ void bc_inflow_part(const Grid& g, const JetBC& b,
+                                               const double* __restrict__ rth,
+                                               const TM* __restrict__ M,
+                                               const DevScalars* __restrict__ sc, int use_host_t,
+                                               double t_host, const Acc& Q, int blk, int nblk) {
   const long long plane = (long long)g.n[1] * g.n[2];
   const long long N = g.N;
   const double t = use_host_t ? t_host : sc->t;
   const double two_pi = 6.283185307179586476925286766559;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < plane;
-       n += (long long)gridDim.x * blockDim.x) {
+  for (long long n = blk * (long long)blockDim.x + threadIdx.x; n < plane;
+       n += (long long)nblk * blockDim.x) {
     const double r = rth[n], th = rth[plane + n];
     double u = 0.5 * b.Mj * (1.0 + tanh((b.r_jet - r) / (2.0 * b.theta_m)));
     if (b.forced) {
@@ -167,16 +185,25 @@ __global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
   }
 }
 
+template <class Acc, typename TM>
+__global__ void k_bc_inflow(Grid g, JetBC b, const double* __restrict__ rth,
+                            const TM* __restrict__ M, const DevScalars* __restrict__ sc,
+                            int use_host_t, double t_host, Acc Q) {
+  bc_inflow_part(g, b, rth, M, sc, use_host_t, t_host, Q, blockIdx.x, gridDim.x);
+}
+
 // Far field j = nj-1 (0 < i < ni-1): Riemann invariants along the unit
 // eta-normal with R+ from the adjacent interior node and R- from the free
 // stream at rest (rho = 1, p = 1/gamma, a = 1); four branches by q_n/a.
 template <class Acc, typename TM>
-__global__ void k_bc_farfield(Grid g, double gamma, const TM* __restrict__ M, Acc Q) {
+__device__ __forceinline__ void bc_farfield_part(const Grid& g, double gamma,
+                                                 const TM* __restrict__ M, const Acc& Q, int blk,
+                                                 int nblk) {
   const int ni = g.n[0], nj = g.n[1], nk = g.n[2];
   const long long count = (long long)(ni - 2) * nk;
   const long long N = g.N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
-       e += (long long)gridDim.x * blockDim.x) {
+  for (long long e = blk * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)nblk * blockDim.x) {
     const int i = 1 + (int)(e / nk), k = (int)(e % nk);
     const long long nf = idx3(g, i, nj - 1, k), ne = idx3(g, i, nj - 2, k);
     const double ex = (double)M[3 * N + nf], ey = (double)M[4 * N + nf], ez = (double)M[5 * N + nf];
@@ -192,11 +219,16 @@ __global__ void k_bc_farfield(Grid g, double gamma, const TM* __restrict__ M, Ac
   }
 }
 
+template <class Acc, typename TM>
+__global__ void k_bc_farfield(Grid g, double gamma, const TM* __restrict__ M, Acc Q) {
+  bc_farfield_part(g, gamma, M, Q, blockIdx.x, gridDim.x);
+}
+
 // Inner ring j = 0 (0 < i < ni-1): azimuthal mean of the first interior
 // ring, one block per axial station, fixed-order tree (deterministic).
 template <class Acc>
-__global__ void k_bc_ring(Grid g, Acc Q) {
-  const int i = 1 + blockIdx.x;
+__device__ __forceinline__ void bc_ring_part(const Grid& g, const Acc& Q, int blk) {
+  const int i = 1 + blk;
   const int nk = g.n[2];
   const long long N = g.N;
   __shared__ double red[5][32];
@@ -224,6 +256,30 @@ __global__ void k_bc_ring(Grid g, Acc Q) {
   for (int k = threadIdx.x; k < nk; k += blockDim.x)
 #pragma unroll
     for (int q = 0; q < 5; ++q) Q.st(q * N + base0 + k, red[q][0]);
+}
+
+template <class Acc>
+__global__ void k_bc_ring(Grid g, Acc Q) {
+  bc_ring_part(g, Q, blockIdx.x);
+}
+
+// The Dirichlet entrance, the far field and the inner ring in one launch
+// (blocks [0, nb_ff) the far field, then nb_in for the entrance, then one per
+// axial station for the ring).  They write disjoint surfaces (i = 0; j = nj-1
+// and j = 0 for 0 < i < ni-1) and read nothing another writes: the far field
+// reads j = nj-2 and the ring j = 1 (distinct for nj >= 3), and the
+// Dirichlet entrance reads no state.
+template <class Acc, typename TM>
+__global__ void k_bc_sides(Grid g, JetBC b, const double* __restrict__ rth,
+                           const TM* __restrict__ M, const DevScalars* __restrict__ sc,
+                           int use_host_t, double t_host, Acc Q, int nb_ff, int nb_in) {
+  const int blk = blockIdx.x;
+  if (blk < nb_ff)
+    bc_farfield_part(g, b.gamma, M, Q, blk, nb_ff);
+  else if (blk < nb_ff + nb_in)
+    bc_inflow_part(g, b, rth, M, sc, use_host_t, t_host, Q, blk - nb_ff, nb_in);
+  else
+    bc_ring_part(g, Q, blk - nb_ff - nb_in);
 }
 
 // Exit i = ni-1 from the updated column i = ni-2: supersonic (q/a >= 1 along
@@ -359,13 +415,24 @@ static void bc_jet(const Grid& g, const les_params& p, Acc Q, const TM* M,
   // an axial slab has the entrance only if it starts at the physical face
   // and the exit only if it ends there (its far field and inner ring cover
   // its ghost planes too, which the next exchange overwrites)
-  if (g.glo == 0) {
-    k_bc_inflow<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, M, sc, use_host_t, t_host, Q);
+  const int nb_ff = nblocks((long long)(g.n[0] - 2) * g.n[2]);
+  if (p.bc != LES_BC_JET_CHAR && g.n[1] >= 3) {
+    const int nb_in = g.glo == 0 ? nblocks(plane) : 0;
+    k_bc_sides<Acc, TM><<<nb_ff + nb_in + (g.n[0] - 2), 256, 0, L.s>>>(
+        g, b, rth, M, sc, use_host_t, t_host, Q, nb_ff, nb_in);
     ++*L.counter;
+  } else {
+    // the characteristic entrance reads the plane i = 1 before the far field
+    // and the ring write its edges
+    if (g.glo == 0) {
+      k_bc_inflow<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, b, rth, M, sc, use_host_t, t_host,
+                                                             Q);
+      ++*L.counter;
+    }
+    k_bc_farfield<Acc, TM><<<nb_ff, 256, 0, L.s>>>(g, p.gamma, M, Q);
+    k_bc_ring<Acc><<<g.n[0] - 2, 256, 0, L.s>>>(g, Q);
+    *L.counter += 2;
   }
-  k_bc_farfield<Acc, TM><<<nblocks((long long)(g.n[0] - 2) * g.n[2]), 256, 0, L.s>>>(g, p.gamma, M, Q);
-  k_bc_ring<Acc><<<g.n[0] - 2, 256, 0, L.s>>>(g, Q);
-  *L.counter += 2;
   if (g.ghi == 0) {
     k_bc_exit<Acc, TM><<<nblocks(plane), 256, 0, L.s>>>(g, p.gamma, M, Q);
     ++*L.counter;
