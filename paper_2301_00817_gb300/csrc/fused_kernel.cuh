@@ -177,6 +177,82 @@ __device__ __forceinline__ void load_metrics(const TM* __restrict__ M, long long
 }
 
 // --------------------------------------------------------------- prestep
+// End of a prestep block: the block's minimum of 1/(sum of radii) into
+// partials[blockIdx.x] and its non-finite flag into the status word.  With
+// fin_mode >= 0 (and sc) the last block to finish also takes the step, as
+// k_dt_finalize would in a launch of its own: the minimum over every block's
+// partial (exact in any order), dt = cfl x that (or the fixed step), the
+// status, and t^{n+1} when fin_advance.
+template <typename R>
+__device__ __forceinline__ void prestep_finish(R local_min, int bad, double* __restrict__ partials,
+                                               DevScalars* __restrict__ sc, int fin_mode,
+                                               double fin_cfl, double fin_dt, int fin_advance) {
+  __shared__ R smin[32];
+  __shared__ int sbad[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    // every lane executes each shuffle unconditionally (full mask)
+    const R o = __shfl_xor_sync(0xffffffffu, local_min, off);
+    local_min = local_min < o ? local_min : o;
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    smin[threadIdx.x >> 5] = local_min;
+    sbad[threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool live = threadIdx.x < (blockDim.x >> 5);
+    R mm = live ? smin[threadIdx.x] : R(1e30);
+    int bb = live ? sbad[threadIdx.x] : 0;
+    for (int off = 16; off > 0; off >>= 1) {
+      const R o = __shfl_xor_sync(0xffffffffu, mm, off);
+      mm = mm < o ? mm : o;
+      bb |= __shfl_xor_sync(0xffffffffu, bb, off);
+    }
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = (double)mm;
+      if (bb && sc) atomicOr(&sc->status, 1);
+    }
+  }
+  if (fin_mode >= 0 && sc) {
+    __shared__ int last;
+    __shared__ double dmin[32];
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      double m = 1.0e300;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmin(m, __ldcg(partials + b));
+      for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if ((threadIdx.x & 31) == 0) dmin[threadIdx.x >> 5] = m;
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? dmin[threadIdx.x] : 1.0e300;
+        for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (threadIdx.x == 0) {
+          double dt = (fin_mode == LES_DT_FIXED) ? fin_dt : fin_cfl * m;
+          const int status = atomicOr(&sc->status, 0);
+          if (!(dt > 0.0) || !(dt < 1.0e300)) {
+            sc->status = LES_ERR_NONFINITE;
+            dt = 0.0;
+          } else if (status != 0) {
+            sc->status = LES_ERR_NONFINITE;
+          }
+          sc->dt = dt;
+          if (fin_advance) {
+            sc->t += dt;
+            sc->steps += 1;
+          }
+          sc->ticket = 0;
+        }
+      }
+    }
+  }
+}
+
 // Once per time step, from Q^n: block minima of 1/(sum of radii) for the CFL
 // step, the non-finite flag, and mu_eff / kappa_eff (frozen over the five
 // stages).  Q^n is read as TQ (double, or the float hi part of the mixed
@@ -342,74 +418,7 @@ __global__ void __launch_bounds__(256) k_prestep(Grid g, Consts<R> K, const TQ* 
     mk[n] = mu_l + mu_s;
     mk[N + n] = mu_l * K.inv_gm1_pr + (kap_set ? kap_s : mu_s * K.inv_gm1_prs);
   }
-  __shared__ R smin[32];
-  __shared__ int sbad[32];
-  for (int off = 16; off > 0; off >>= 1) {
-    // every lane executes each shuffle unconditionally (full mask)
-    const R o = __shfl_xor_sync(0xffffffffu, local_min, off);
-    local_min = local_min < o ? local_min : o;
-    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    smin[threadIdx.x >> 5] = local_min;
-    sbad[threadIdx.x >> 5] = bad;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const bool live = threadIdx.x < (blockDim.x >> 5);
-    R mm = live ? smin[threadIdx.x] : R(1e30);
-    int bb = live ? sbad[threadIdx.x] : 0;
-    for (int off = 16; off > 0; off >>= 1) {
-      const R o = __shfl_xor_sync(0xffffffffu, mm, off);
-      mm = mm < o ? mm : o;
-      bb |= __shfl_xor_sync(0xffffffffu, bb, off);
-    }
-    if (threadIdx.x == 0) {
-      partials[blockIdx.x] = (double)mm;
-      if (bb && sc) atomicOr(&sc->status, 1);
-    }
-  }
-  // fin_mode >= 0 (and sc): the last block to finish takes the step, as
-  // k_dt_finalize would in a launch of its own: the minimum over every
-  // block's partial (exact in any order), dt = cfl x that (or the fixed
-  // step), the status, and t^{n+1} when fin_advance
-  if (fin_mode >= 0 && sc) {
-    __shared__ int last;
-    __shared__ double dmin[32];
-    if (threadIdx.x == 0) {
-      __threadfence();
-      last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      double m = 1.0e300;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmin(m, __ldcg(partials + b));
-      for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
-      if ((threadIdx.x & 31) == 0) dmin[threadIdx.x >> 5] = m;
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        m = threadIdx.x < (blockDim.x >> 5) ? dmin[threadIdx.x] : 1.0e300;
-        for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
-        if (threadIdx.x == 0) {
-          double dt = (fin_mode == LES_DT_FIXED) ? fin_dt : fin_cfl * m;
-          const int status = atomicOr(&sc->status, 0);
-          if (!(dt > 0.0) || !(dt < 1.0e300)) {
-            sc->status = LES_ERR_NONFINITE;
-            dt = 0.0;
-          } else if (status != 0) {
-            sc->status = LES_ERR_NONFINITE;
-          }
-          sc->dt = dt;
-          if (fin_advance) {
-            sc->t += dt;
-            sc->steps += 1;
-          }
-          sc->ticket = 0;
-        }
-      }
-    }
-  }
+  prestep_finish(local_min, bad, partials, sc, fin_mode, fin_cfl, fin_dt, fin_advance);
 }
 
 // ------------------------------------------------------------ fused stage

@@ -49,6 +49,17 @@ def _grid(lj, case):
         s = (17, 11, 9)
         xyz, shift = lj.synth.box_grid(s, (1.0, 1.3, 0.8), wave=0.25)
         return s, xyz, shift, dict(periodic=(1, 1, 1), bc=0)
+    # rows of a multiple of four nodes (the mixed forms' four-node viscosity
+    # pass): periodic in every direction, and open in every direction (the
+    # one-sided gradients at all six faces)
+    if case == "wavy_box4":
+        s = (17, 11, 12)
+        xyz, shift = lj.synth.box_grid(s, (1.0, 1.3, 0.8), wave=0.25)
+        return s, xyz, shift, dict(periodic=(1, 1, 1), bc=0)
+    if case == "wavy_open4":
+        s = (11, 10, 12)
+        xyz, _ = lj.synth.box_grid(s, (1.0, 1.3, 0.8), wave=0.3)
+        return s, xyz, None, dict(periodic=(0, 0, 0), bc=0)
     raise ValueError(case)
 
 
@@ -343,13 +354,16 @@ def test_rhs(orc, lj, torch, case, sgs):
 
 
 @pytest.mark.parametrize("sgs", [0, 1, 2])
-@pytest.mark.parametrize("case", ["jet_c1", "wavy_box", "jet_ragged", "jet_min"])
+@pytest.mark.parametrize("case", ["jet_c1", "wavy_box", "jet_ragged", "jet_min", "wavy_box4",
+                                  "wavy_open4"])
 @pytest.mark.parametrize("prec", ["mixed", "compact"])
 def test_rhs_mixed_forms(orc, lj, torch, case, sgs, prec):
     """The fused kernel's residual mode against the oracle on the same cases
     as the FP64 residual: periodic xi (wavy box), ragged tiles and rows whose
-    length is not a multiple of four (13 x 9 x 7), the smallest grid (5^3).
-    FP32 arithmetic: within 2e-5 of each component's flux scale."""
+    length is not a multiple of four (13 x 9 x 7), the smallest grid (5^3);
+    and two grids whose rows are a multiple of four nodes, periodic and open
+    in every direction.  FP32 arithmetic: within 2e-5 of each component's flux
+    scale."""
     shape, xyz, shift, kw = _grid(lj, case)
     pc = lj.PREC_MIXED if prec == "mixed" else lj.PREC_MIXED_COMPACT
     ctx, _ = device_ctx(lj, torch, shape, xyz, shift, sgs_model=sgs, Re=2000.0, precision=pc, **kw)
