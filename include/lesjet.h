@@ -268,7 +268,12 @@ int les_set_time(les_ctx *ctx, double t, les_stream_t stream);
 int les_rk_step(les_ctx *ctx, double *Q, les_stream_t stream);
 
 /* n time steps on Q in place, then SYNCHRONISES and fills *diag (may be
- * NULL).  Returns LES_ERR_NONFINITE if any step saw a non-finite state. */
+ * NULL).  Returns LES_ERR_NONFINITE if any step saw a non-finite state.
+ * In the mixed forms the context's first step runs as plain kernel launches
+ * and is then captured as a CUDA graph (on a stream the context creates and
+ * les_destroy releases); later steps replay the graph on `stream`, unless
+ * the event profiler is on.  les_set_params, les_set_grid and les_profile
+ * drop the graph.  The same holds for les_run_host. */
 int les_run_n_steps(les_ctx *ctx, int n, double *Q, les_diag *diag,
                     les_stream_t stream);
 

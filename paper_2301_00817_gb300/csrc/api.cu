@@ -54,6 +54,12 @@ struct les_ctx {
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[PK_COUNT];
   unsigned long long prof_n[PK_COUNT];
+  // the FP32-mixed step as a CUDA graph (mixed_steps): its executable, the
+  // stream it is captured on, and the kernel launches one replay stands for
+  cudaGraphExec_t step_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  unsigned long long step_launches = 0;
+  bool graph_failed = false;
 };
 
 namespace {
@@ -65,6 +71,12 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 int fail(les_ctx* c, int code, const char* msg) {
   if (c) c->err = msg;
   return code;
+}
+
+void drop_step_graph(les_ctx* c) {
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  c->step_exec = nullptr;
+  c->graph_failed = false;
 }
 
 int cuda_check(les_ctx* c, const char* where) {
@@ -418,6 +430,8 @@ int les_destroy(les_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
+  drop_step_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return LES_OK;
 }
@@ -440,6 +454,7 @@ int les_set_params(les_ctx* c, const les_params* p) {
   if (p->slab_ghost[0] != c->g.glo || p->slab_ghost[1] != c->g.ghi)
     return fail(c, LES_ERR_INVALID_ARG, "the slab's ghost planes are fixed at creation");
   c->p = *p;
+  drop_step_graph(c);
   return LES_OK;
 }
 
@@ -452,6 +467,7 @@ int les_set_grid(les_ctx* c, const double* xyz, const double shift[9], void* wor
     return fail(c, LES_ERR_ALIGN, "device pointers must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   lesjet::Launch L{s, &c->launches};
+  drop_step_graph(c);
   c->ws = (char*)workspace;
   if (has_m64(c)) {
     double* M64 = at<double>(c, c->off_m64);
@@ -591,6 +607,61 @@ int les_set_time(les_ctx* c, double t, les_stream_t stream) {
   lesjet::Launch L{(cudaStream_t)stream, &c->launches};
   lesjet::launch_set_time(at<DevScalars>(c, c->off_sc), t, L);
   return cuda_check(c, "les_set_time");
+}
+
+// ------------------------------------------------ the mixed step as a graph
+// One FP32-mixed RK step reads and writes only the workspace (the caller's
+// state enters through the split and leaves through the join) and takes dt
+// and t from the device scalars, so its launches are the same every step.
+// The step is captured once on the context's own stream, and the graph is
+// replayed for every later step: one graph launch in place of eight or more
+// kernel launches, with shorter gaps between the kernels.  A new parameter
+// set, grid (workspace) or profiler state drops the graph; a capture that
+// fails leaves the context on plain launches.
+static void capture_step_graph(les_ctx* c) {
+  if (!c->cap_stream &&
+      cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->graph_failed = true;
+    return;
+  }
+  const unsigned long long before = c->launches;
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    rk_step(c, nullptr, c->cap_stream);  // the mixed step does not touch Q
+    ok = cudaStreamEndCapture(c->cap_stream, &graph) == cudaSuccess && graph != nullptr;
+  }
+  c->step_launches = c->launches - before;
+  c->launches = before;  // captured, not run
+  if (ok) ok = cudaGraphInstantiate(&c->step_exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    c->step_exec = nullptr;
+    c->graph_failed = true;
+    cudaGetLastError();
+  }
+}
+
+// n FP32-mixed steps on stream s.  A context's first step runs as plain
+// launches (its first launches set the fused kernel's shared-memory
+// attribute and choose the axial chunks), then the step is captured and
+// every later step replays the graph; with the event profiler on, every
+// step runs as plain launches (the profiler records events around them).
+static void mixed_steps(les_ctx* c, int n, cudaStream_t s) {
+  int i = 0;
+  if (!c->prof_on && !c->step_exec && !c->graph_failed && n > 0) {
+    rk_step(c, nullptr, s);
+    ++i;
+    capture_step_graph(c);
+  }
+  if (!c->prof_on && c->step_exec) {
+    for (; i < n; ++i) {
+      if (cudaGraphLaunch(c->step_exec, s) != cudaSuccess) break;
+      c->launches += c->step_launches;
+    }
+  }
+  for (; i < n; ++i) rk_step(c, nullptr, s);
 }
 
 int les_rk_step(les_ctx* c, double* Q, les_stream_t stream) {
@@ -809,9 +880,13 @@ int les_run_n_steps(les_ctx* c, int n, double* Q, les_diag* diag, les_stream_t s
   if (!aligned16(Q)) return fail(c, LES_ERR_ALIGN, "unaligned device pointer");
   cudaStream_t s = (cudaStream_t)stream;
   lesjet::Launch L{s, &c->launches};
-  if (is_mixed(c)) split_state(c, Q, L);
-  for (int i = 0; i < n; ++i) rk_step(c, Q, s);
-  if (is_mixed(c)) join_state(c, Q, L);
+  if (is_mixed(c)) {
+    split_state(c, Q, L);
+    mixed_steps(c, n, s);
+    join_state(c, Q, L);
+  } else {
+    for (int i = 0; i < n; ++i) rk_step(c, Q, s);
+  }
   {
     ProfScope ps(c, PK_TOTALS, s);
     totals(c, Q, L);
@@ -881,7 +956,7 @@ int les_run_host(les_ctx* c, int n, double* Q_host, double* Q_dev, les_diag* dia
     if (Qm && aligned16(Qm)) {
       lesjet::Launch L{s, &c->launches};
       split_state(c, Qm, L);
-      for (int i = 0; i < n; ++i) rk_step(c, Qm, s);
+      mixed_steps(c, n, s);
       {
         // one pass joins the state into the host buffer and sums the totals:
         // their FP64 arithmetic hides under the write-back over the host link
@@ -927,6 +1002,7 @@ uint64_t les_launch_count(const les_ctx* c) { return c ? c->launches : 0; }
 int les_profile(les_ctx* c, int enable) {
   if (!c) return LES_ERR_INVALID_ARG;
   c->prof_on = enable != 0;
+  drop_step_graph(c);
   if (enable) {
     for (int k = 0; k < PK_COUNT; ++k) {
       c->prof_ms[k] = 0.0;
