@@ -76,7 +76,7 @@ NCU_COUNTS = {
     # flux group on the 96 x 160 x 128 jet: k_sensor 64 + k_flux 260 + 259
     # + 257
     ("flux64", "fp64_flop_per_point"):
-        (840, "65e036c8b9cc09be8479dba5958162653523c86ee1a101ff181a149cdf3cce16"),
+        (840, "e63f4edca7b4abbcc9117f9e6a9c50273f8fd20840063d4a79cfc30f512a18f5"),
 }
 NCU_CAPTURE = {"stage_fused": "profiles/stage_fused_jet96x160x128.md",
                "flux64": "profiles/flux64_jet96x160x128.md"}
